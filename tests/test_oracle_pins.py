@@ -1,0 +1,401 @@
+"""Pins of the FP64 oracle against things other than itself.
+
+Each test ties an oracle function to a definition, a closed form, an invariant, a
+library routine or a brute-force result, chosen so that a dropped term, a wrong
+sign, a factor 2 or a transposed operand fails at least one of them.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+from paper_2412_09285_b300 import instances as I
+
+
+def _rng(seed):
+    return np.random.Generator(np.random.PCG64(seed))
+
+
+# ---------------------------------------------------------------- schedules
+
+def test_beta_schedules_endpoints_and_shape():
+    n = 1000
+    b = O.beta_schedule("exponential", 0.05, 5.0, n)
+    assert b[0] == pytest.approx(0.05, rel=1e-15) and b[-1] == pytest.approx(5.0, rel=1e-14)
+    r = b[1:] / b[:-1]                                      # geometric: constant ratio
+    assert np.allclose(r, (5.0 / 0.05) ** (1.0 / (n - 1)), rtol=1e-12)
+    b2 = O.beta_schedule("inverse_proportional", 1 / 1.16, 1 / 6e-5, 1100)
+    T = 1.0 / b2                                            # linear cooling in T
+    assert T[0] == pytest.approx(1.16) and T[-1] == pytest.approx(6e-5)
+    assert np.allclose(np.diff(T), (6e-5 - 1.16) / 1099, rtol=1e-9)
+    lam = O.lambda_ramp(2.0, 11)
+    assert lam[0] == 0.0 and lam[-1] == 2.0 and np.allclose(np.diff(lam), 0.2)
+    assert O.beta_schedule("exponential", 0.05, 5.0, 1)[0] == 0.05
+
+
+# ---------------------------------------------------- free energies by Eq. FP
+
+def _small_graph(n, p, seed, weights):
+    g = I.er_gnp(n, p, seed, weights)
+    return g, O.coupling_matrix(g.n, g.ei, g.ej, g.w)
+
+
+def test_maxcut_free_energy_matches_enumeration():
+    g, W = _small_graph(7, 0.6, 1, "real")
+    h = _rng(2).normal(size=(7, 2))
+    beta = 0.7
+    F = O.maxcut_free_energy(W, h, beta)
+    for r in range(2):
+        P = O.sigmoid(h[:, r])
+        marg = np.stack([P, 1 - P], axis=1)                 # state 0 = sigma +1
+        # ordered-pair energy: each edge counted twice, E2 = -2 sum_E W [x_i != x_j]
+        E = lambda X: -2.0 * (g.w[None, :] * (X[:, g.ei] != X[:, g.ej])).sum(axis=1)
+        ref = O.mf_free_energy_by_enumeration(marg, E, beta)
+        assert F[r] == pytest.approx(ref, rel=1e-12, abs=1e-12)
+
+
+def test_bmincut_free_energy_matches_enumeration():
+    g, W = _small_graph(5, 0.7, 3, "real")
+    q, beta, lam = 3, 1.3, 0.4
+    h = _rng(4).normal(size=(5, 2, q))
+    F = O.bmincut_free_energy(W, h, beta, lam)
+    for r in range(2):
+        z = np.exp(h[:, r] - h[:, r].max(axis=1, keepdims=True))
+        marg = z / z.sum(axis=1, keepdims=True)
+
+        def E(X):
+            cut = (g.w[None, :] * (X[:, g.ei] != X[:, g.ej])).sum(axis=1)
+            sizes = np.stack([(X == s).sum(axis=1) for s in range(q)], axis=1)
+            return 2.0 * cut + lam * (sizes * (sizes - 1)).sum(axis=1)
+
+        ref = O.mf_free_energy_by_enumeration(marg, E, beta)
+        assert F[r] == pytest.approx(ref, rel=1e-12, abs=1e-12)
+
+
+def test_sat_free_energy_matches_enumeration():
+    cl = I.random_ksat(6, 11, 3, seed=5)
+    groups = O.sat_arrays(cl.ptr, cl.lits)
+    h = _rng(6).normal(size=(6, 2))
+    beta = 0.9
+    F = O.sat_free_energy(groups, h, beta)
+    for r in range(2):
+        p = O.sigmoid(h[:, r])
+        marg = np.stack([1 - p, p], axis=1)                 # state index = sigma value
+
+        def E(X):
+            out = np.zeros(X.shape[0])
+            for m in range(cl.n_clauses):
+                sat = np.zeros(X.shape[0], bool)
+                for l in cl.lits[cl.ptr[m]:cl.ptr[m + 1]]:
+                    sat |= (X[:, abs(l) - 1] == (1 if l > 0 else 0))
+                out += ~sat
+            return out
+
+        ref = O.mf_free_energy_by_enumeration(marg, E, beta)
+        assert F[r] == pytest.approx(ref, rel=1e-12, abs=1e-12)
+
+
+# ------------------------------------------- exact gradients = FD of the energy
+
+def _fd(Ffun, h, eps=1e-6):
+    g = np.zeros_like(h)
+    flat = h.reshape(h.shape[0], h.shape[1], -1)
+    gflat = g.reshape(flat.shape)
+    for i in range(flat.shape[0]):
+        for s in range(flat.shape[2]):
+            hp = flat.copy(); hp[i, :, s] += eps
+            hm = flat.copy(); hm[i, :, s] -= eps
+            gflat[i, :, s] = (Ffun(hp.reshape(h.shape)) - Ffun(hm.reshape(h.shape))) / (2 * eps)
+    return g
+
+
+@pytest.mark.parametrize("weights", ["unit", "pm1", "real"])
+def test_maxcut_exact_gradient_is_fd_of_F(weights):
+    g, W = _small_graph(12, 0.4, 7, weights)
+    h = _rng(8).normal(size=(12, 3)) * 1.5
+    beta = 0.8
+    ana = O.maxcut_grad(W, h, beta, mode="exact")
+    fd = _fd(lambda x: O.maxcut_free_energy(W, x, beta), h)
+    assert np.max(np.abs(ana - fd)) <= 1e-7 * max(1.0, np.max(np.abs(fd)))
+
+
+def test_bmincut_exact_gradient_is_fd_of_F():
+    g, W = _small_graph(8, 0.5, 9, "real")
+    h = _rng(10).normal(size=(8, 2, 4))
+    beta, lam = 0.6, 0.3
+    ana = O.bmincut_grad(W, h, beta, lam, mode="exact")
+    fd = _fd(lambda x: O.bmincut_free_energy(W, x, beta, lam), h)
+    assert np.max(np.abs(ana - fd)) <= 1e-7 * max(1.0, np.max(np.abs(fd)))
+    # softmax invariance: the field gradient sums to zero over the states
+    assert np.allclose(ana.sum(axis=2), 0.0, atol=1e-13)
+
+
+def test_sat_gradient_is_fd_of_F():
+    cl = I.random_ksat(10, 30, 3, seed=11)
+    groups = O.sat_arrays(cl.ptr, cl.lits)
+    h = _rng(12).normal(size=(10, 2))
+    beta = 1.1
+    ana = O.sat_grad(groups, h, beta)
+    fd = _fd(lambda x: O.sat_free_energy(groups, x, beta), h)
+    assert np.max(np.abs(ana - fd)) <= 1e-7 * max(1.0, np.max(np.abs(fd)))
+
+
+def test_sat_gradient_mixed_widths_is_fd_of_F():
+    ptr = np.array([0, 2, 5, 9, 10])
+    lits = np.array([1, -2, 2, 3, -4, -1, 4, 5, -3, 5])
+    groups = O.sat_arrays(ptr, lits)
+    h = _rng(13).normal(size=(5, 2))
+    ana = O.sat_grad(groups, h, 0.5)
+    fd = _fd(lambda x: O.sat_free_energy(groups, x, 0.5), h)
+    assert np.max(np.abs(ana - fd)) <= 1e-7 * max(1.0, np.max(np.abs(fd)))
+
+
+# ------------------------------------------------- paper-mode reduction identities
+
+def test_maxcut_paper_mode_reduces_to_exact():
+    g, W = _small_graph(20, 0.3, 14, "pm1")
+    h = _rng(15).normal(size=(20, 4))
+    exact = O.maxcut_grad(W, h, 0.7, mode="exact")
+    red = O.maxcut_grad(W, h, 0.7, mode="paper", c=np.full(20, 2.0), discretise=False)
+    assert np.allclose(red, exact, rtol=1e-13, atol=1e-15)
+
+
+def test_maxcut_paper_mode_formula_and_ties():
+    # a 3-node path 0-1-2 with weights 1 and -2; h_1 = 0 must count as sgn = +1
+    W = O.coupling_matrix(3, [0, 1], [1, 2], [1.0, -2.0])
+    h = np.array([[0.3], [0.0], [-0.2]])
+    g = O.maxcut_grad(W, h, 2.0, gamma=1.0, mode="paper")
+    m = np.tanh(h[:, 0] / 2)
+    # node 0: c = 1, neighbour 1 has sgn +1;  node 1: c = 1/3, sum = 1*(+1) - 2*(-1) = 3
+    # node 2: c = 1/2, neighbour 1 sgn +1, weight -2
+    s = np.array([1.0, 3.0 / 3.0, -2.0 / 2.0])
+    expect = 0.25 * (s + h[:, 0] / 2.0) * (1 - m * m)
+    assert np.allclose(g[:, 0], expect, rtol=1e-14)
+    assert O.maxcut_states(np.array([[0.0], [-0.0], [-1e-300]]))[:, 0].tolist() == [1, 1, -1]
+
+
+def test_bmincut_paper_mode_reduces_to_exact():
+    g, W = _small_graph(10, 0.5, 16, "real")
+    h = _rng(17).normal(size=(10, 3, 4))
+    exact = O.bmincut_grad(W, h, 0.9, 0.25, mode="exact")
+    red = O.bmincut_grad(W, h, 0.9, 0.25, mode="paper", cf=np.full(10, 2.0),
+                         ca=np.full(10, 2.0), discretise=False)
+    assert np.allclose(red, exact, rtol=1e-12, atol=1e-14)
+
+
+def test_bmincut_argmax_ties_lowest_index():
+    h = np.array([[[0.5, 0.5, 0.1, 0.5]]])
+    assert O.bmincut_states(h)[0, 0] == 0
+
+
+# --------------------------------------------------- mean-field fixed point
+
+def test_exact_mode_fixed_point_is_mean_field_equation():
+    """At a fixed beta, the exact-gradient stationary point satisfies the
+    mean-field equation m = tanh(-beta W m) (SM, 'mean field equations for the
+    Ising problem', with W -> -W for the antiferromagnetic MaxCut coupling)."""
+    g, W = _small_graph(24, 0.3, 18, "pm1")
+    h0 = _rng(19).normal(size=(24, 3))
+    beta = 0.35
+    h, _ = O.anneal(("maxcut", W), h0, 6000, schedule="exponential", beta_min=beta,
+                    beta_max=beta, optimizer="sgd", opt_kw=dict(lr=1.0), mode="exact")
+    m = np.tanh(h / 2)
+    resid = np.abs(m - np.tanh(-beta * (W @ m)))
+    assert resid.max() < 1e-9
+    # and the fixed point is not the trivial one for this beta (the test has teeth)
+    assert np.abs(m).max() > 0.1
+
+
+# -------------------------------------------------------------- optimizers
+
+def _torch_run(opt_cls, kw, gs, h0):
+    p = torch.tensor(h0, dtype=torch.float64, requires_grad=True)
+    opt = opt_cls([p], **kw)
+    for g in gs:
+        p.grad = torch.tensor(g, dtype=torch.float64)
+        opt.step()
+    return p.detach().numpy()
+
+
+@pytest.mark.parametrize("name,kw", [
+    ("adam", dict(lr=0.1, betas=(0.9, 0.999), eps=1e-8, weight_decay=0.0)),
+    ("adam", dict(lr=0.03, betas=(0.8, 0.99), eps=1e-6, weight_decay=0.01)),
+    ("rmsprop", dict(lr=0.03, alpha=0.56, eps=1e-8, weight_decay=0.013, momentum=0.63)),
+    ("rmsprop", dict(lr=0.01, alpha=0.99, eps=1e-8, weight_decay=0.0, momentum=0.0)),
+    ("sgd", dict(lr=1.27, momentum=0.71, dampening=0.11, weight_decay=0.018)),
+    ("sgd", dict(lr=0.2, momentum=0.0, dampening=0.0, weight_decay=0.0)),
+])
+def test_optimizers_match_torch(name, kw):
+    rng = _rng(20)
+    h0 = rng.normal(size=(5, 3))
+    gs = [rng.normal(size=(5, 3)) for _ in range(25)]
+    cls = {"adam": torch.optim.Adam, "rmsprop": torch.optim.RMSprop, "sgd": torch.optim.SGD}[name]
+    ref = _torch_run(cls, kw, gs, h0)
+    okw = dict(kw)
+    if "betas" in okw:
+        okw["beta1"], okw["beta2"] = okw.pop("betas")
+    opt = O.make_optimizer(name, h0.shape, **okw)
+    h = h0.copy()
+    for t, g in enumerate(gs, start=1):
+        opt.step(h, g, t)
+    assert np.allclose(h, ref, rtol=1e-12, atol=1e-14)
+
+
+def test_adam_first_step_closed_form():
+    g = np.array([[3.0, -1e-3, 0.0]])
+    h = np.zeros_like(g)
+    O.Adam(g.shape, lr=0.1).step(h, g, 1)
+    assert np.allclose(h, -0.1 * g / (np.abs(g) + 1e-8), rtol=1e-15)
+
+
+# ------------------------------- full exact-mode trajectories vs autograd + torch.optim
+
+def _torch_maxcut_F(Wt, h, beta):
+    P = torch.sigmoid(h)
+    cut = 0
+    for Ps in (P, 1 - P):
+        cut = cut + ((Wt @ Ps) * (1 - Ps)).sum(0)
+    S = -(P * P.log() + (1 - P) * (1 - P).log()).sum(0)
+    return -cut - S / beta
+
+
+def test_maxcut_exact_trajectory_matches_autograd_adam():
+    g, W = _small_graph(15, 0.4, 21, "pm1")
+    h0 = I.initial_fields(15, 4, seed=22).astype(np.float64)
+    n_step = 40
+    h, _ = O.anneal(("maxcut", W), h0, n_step, mode="exact", optimizer="adam",
+                    opt_kw=dict(lr=0.1))
+    Wt = torch.tensor(W.toarray())
+    ht = torch.tensor(h0, requires_grad=True)
+    opt = torch.optim.Adam([ht], lr=0.1)
+    for beta in O.beta_schedule("exponential", 0.05, 5.0, n_step):
+        F = _torch_maxcut_F(Wt, ht, float(beta))
+        opt.zero_grad()
+        F.backward(gradient=torch.ones_like(F))
+        opt.step()
+    assert np.allclose(h, ht.detach().numpy(), rtol=1e-9, atol=1e-11)
+
+
+def test_bmincut_exact_trajectory_matches_autograd_adam():
+    g, W = _small_graph(12, 0.4, 23, "unit")
+    q, n_step, lam_max = 3, 30, 0.5
+    h0 = I.initial_fields(12, 3, seed=24, q=q).astype(np.float64)
+    h, _ = O.anneal(("bmincut", W), h0, n_step, mode="exact", optimizer="adam",
+                    opt_kw=dict(lr=0.05), lambda_max=lam_max)
+    Wt = torch.tensor(W.toarray())
+    ht = torch.tensor(h0.transpose(1, 0, 2).copy(), requires_grad=True)   # [R, N, q] like the listing
+    opt = torch.optim.Adam([ht], lr=0.05)
+    betas = O.beta_schedule("exponential", 0.05, 5.0, n_step)
+    lams = O.lambda_ramp(lam_max, n_step)
+    for beta, lam in zip(betas, lams):
+        p = torch.softmax(ht, dim=2)
+        cut = ((Wt @ p) * (1 - p)).sum((1, 2))
+        bal = (p.sum(1) ** 2).sum(1) - (p ** 2).sum(2).sum(1)
+        S = -(p * p.log()).sum(2).sum(1)
+        F = cut + float(lam) * bal - S / float(beta)
+        opt.zero_grad()
+        F.backward(gradient=torch.ones_like(F))
+        opt.step()
+    assert np.allclose(h, ht.detach().numpy().transpose(1, 0, 2), rtol=1e-9, atol=1e-11)
+
+
+def test_sat_trajectory_matches_autograd_adam():
+    cl = I.random_ksat(12, 50, 3, seed=25)
+    groups = O.sat_arrays(cl.ptr, cl.lits)
+    h0 = I.initial_fields(12, 3, seed=26).astype(np.float64)
+    n_step = 30
+    h, _ = O.anneal(("sat", groups), h0, n_step, optimizer="adam", opt_kw=dict(lr=0.1))
+    var = torch.tensor(np.abs(cl.lits.reshape(-1, 3)) - 1)
+    pos = torch.tensor(cl.lits.reshape(-1, 3) > 0)
+    ht = torch.tensor(h0, requires_grad=True)
+    opt = torch.optim.Adam([ht], lr=0.1)
+    for beta in O.beta_schedule("exponential", 0.05, 5.0, n_step):
+        p = torch.sigmoid(ht)
+        pv = p[var]                                          # [M, 3, R]
+        u = torch.where(pos[..., None], 1 - pv, pv)
+        S = -(p * p.log() + (1 - p) * (1 - p).log()).sum(0)
+        F = u.prod(1).sum(0) - S / float(beta)
+        opt.zero_grad()
+        F.backward(gradient=torch.ones_like(F))
+        opt.step()
+    assert np.allclose(h, ht.detach().numpy(), rtol=1e-9, atol=1e-11)
+
+
+# ------------------------------------------------------------- objectives
+
+@pytest.mark.parametrize("weights", ["unit", "pm1", "real"])
+def test_cut_three_recomputations_agree(weights):
+    g, W = _small_graph(60, 0.1, 27, weights)
+    sigma = np.where(_rng(28).random((60, 8)) < 0.5, 1, -1).astype(np.int8)
+    a = O.maxcut_cut_edges(g.ei, g.ej, g.w, sigma)
+    b = O.maxcut_cut_spin(g.ei, g.ej, g.w, sigma)
+    c = O.maxcut_cut_matrix(W, sigma)
+    if weights == "real":
+        assert np.allclose(a, b, rtol=1e-12) and np.allclose(a, c, rtol=1e-12)
+    else:
+        assert a.dtype == np.int64 and np.array_equal(a, b) and np.array_equal(a, np.rint(c))
+    # brute force on a single replica by a plain loop
+    for r in range(2):
+        ref = sum(w for i, j, w in zip(g.ei, g.ej, g.w) if sigma[i, r] != sigma[j, r])
+        assert a[r] == pytest.approx(ref)
+
+
+def test_sat_unsat_direct_scan():
+    cl = I.random_ksat(20, 80, 3, seed=29)
+    st = (_rng(30).random((20, 5)) < 0.5).astype(np.int8)
+    got = O.sat_unsat(cl.ptr, cl.lits, st)
+    for r in range(5):
+        cnt = 0
+        for m in range(cl.n_clauses):
+            lits = cl.lits[cl.ptr[m]:cl.ptr[m + 1]]
+            if not any((st[abs(l) - 1, r] == 1) == (l > 0) for l in lits):
+                cnt += 1
+        assert got[r] == cnt
+
+
+def test_bmincut_objective_sizes_and_energy():
+    g = I.rgg(200, 8, seed=31)
+    st = _rng(32).integers(0, 4, size=(200, 3)).astype(np.int32)
+    E, cut, sizes = O.bmincut_objective(g.ei, g.ej, g.w, st, 4, 1.0)
+    assert np.all(sizes.sum(axis=1) == 200)
+    for r in range(3):
+        c = sum(1 for i, j in zip(g.ei, g.ej) if st[i, r] != st[j, r])
+        n = np.bincount(st[:, r], minlength=4)
+        assert cut[r] == c and E[r] == c + int((n * (n - 1)).sum())
+
+
+# ------------------------------------------- end to end: FEM reaches brute-force optima
+
+@pytest.mark.parametrize("seed,weights", [(40, "unit"), (41, "pm1"), (42, "pm1")])
+def test_oracle_maxcut_reaches_bruteforce_optimum(seed, weights):
+    g, W = _small_graph(16, 0.3, seed, weights)
+    best = O.maxcut_bruteforce(g.n, g.ei, g.ej, g.w)
+    h0 = I.initial_fields(16, 32, seed=seed + 100).astype(np.float64)
+    h, _ = O.anneal(("maxcut", W), h0, 1000, mode="paper", optimizer="adam",
+                    opt_kw=dict(lr=0.1))
+    cuts = O.maxcut_cut_edges(g.ei, g.ej, g.w, O.maxcut_states(h))
+    assert cuts.max() == best
+
+
+@pytest.mark.parametrize("seed", [43, 44])
+def test_oracle_sat_reaches_bruteforce_optimum(seed):
+    cl = I.random_ksat(16, 67, 3, seed=seed)
+    best = O.sat_bruteforce(cl.n, cl.ptr, cl.lits)
+    groups = O.sat_arrays(cl.ptr, cl.lits)
+    h0 = I.initial_fields(16, 32, seed=seed + 100).astype(np.float64)
+    h, _ = O.anneal(("sat", groups), h0, 1000, optimizer="adam", opt_kw=dict(lr=0.1))
+    unsat = O.sat_unsat(cl.ptr, cl.lits, O.sat_states(h))
+    assert unsat.min() == best
+
+
+@pytest.mark.parametrize("seed", [45, 46])
+def test_oracle_bmincut_reaches_bruteforce_optimum(seed):
+    g = I.rgg(9, 4.0, seed=seed)
+    W = O.coupling_matrix(g.n, g.ei, g.ej, g.w)
+    q, lam = 3, 1.0
+    best = O.bmincut_bruteforce(g.n, g.ei, g.ej, g.w, q, lam)
+    h0 = I.initial_fields(9, 32, seed=seed + 100, q=q).astype(np.float64)
+    h, _ = O.anneal(("bmincut", W), h0, 1000, mode="paper", optimizer="adam",
+                    opt_kw=dict(lr=0.1), lambda_max=lam)
+    E, _, _ = O.bmincut_objective(g.ei, g.ej, g.w, O.bmincut_states(h), q, lam)
+    assert E.min() == best

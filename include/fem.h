@@ -1,0 +1,224 @@
+/*
+ * fem.h - C ABI of the B300 Free-Energy Machine library (libfem.so).
+ *
+ * The Free-Energy Machine (FEM) minimises R replicas of the variational
+ * mean-field free energy F = U - S/beta over marginals P_i(s) = softmax(h_i)(s)
+ * while beta is annealed upwards, then reads every replica out by argmax and
+ * keeps the replica of lowest energy (Results, "Free-Energy Machine", and its
+ * argmax / argmin equations).  This library runs that per-step replica update on
+ * one GPU: the coupling contraction, the hand-written gradient of F, the
+ * optimizer step and the schedule, then the argmax and an exact objective.
+ *
+ * Problems (Results, Eqs. maxcut1, bmincut, maxksat_E):
+ *   FEM_MAXCUT   E = -sum_{(i,j) in E} W_ij [s_i != s_j]                 (q = 2)
+ *   FEM_BMINCUT  E =  sum_{(i,j) in E} W_ij [s_i != s_j]
+ *                    + lambda_max * sum_s n_s (n_s - 1)                    (q >= 2)
+ *   FEM_MAXKSAT  E = number of unsatisfied clauses                         (q = 2)
+ *
+ * Conventions shared by every call:
+ *   - Every call returns a fem_status; nothing aborts, traps or prints.
+ *     fem_last_error() gives a one-line reason for the last failure on the
+ *     calling thread.
+ *   - Host input buffers are copied before the call returns; the caller keeps
+ *     ownership of everything it passes in.  Outputs go to caller buffers.
+ *   - `stream` is a cudaStream_t (NULL = the legacy default stream) on the
+ *     device that was current when the problem was created.  fem_anneal is
+ *     asynchronous on that stream; fem_read_* synchronise it.
+ *   - Device kernels never trap.  A device-side check (index bounds, a bounded
+ *     wait that ran out) sets a sticky error flag in the problem; the next
+ *     fem_read_* or fem_sync call reports it as FEM_ERR_DEVICE / FEM_ERR_TIMEOUT.
+ *   - A handle is not thread-safe; concurrent calls on one handle are undefined.
+ *
+ * Layouts of per-replica state (fp32, replica-contiguous per variable):
+ *   single-field problems (MaxCut, Max-k-SAT): h[n][R]      (element i*R + r)
+ *   q-state problems (bMinCut):                h[n][R][q]   (element (i*R + r)*q + s)
+ */
+#ifndef FEM_H
+#define FEM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  FEM_OK = 0,
+  FEM_ERR_INVALID_ARG = 1, /* a pointer, size, index, weight or flag is out of range   */
+  FEM_ERR_UNSUPPORTED = 2, /* valid input this build does not handle (e.g. R % 32 != 0) */
+  FEM_ERR_OOM = 3,         /* a device allocation failed                               */
+  FEM_ERR_CUDA = 4,        /* a CUDA runtime call failed                               */
+  FEM_ERR_TIMEOUT = 5,     /* a bounded device-side wait gave up                       */
+  FEM_ERR_STATE = 6,       /* call out of order (e.g. resume before initialisation)    */
+  FEM_ERR_DEVICE = 7       /* a device-side bounds check failed                        */
+} fem_status;
+
+typedef enum { FEM_MAXCUT = 0, FEM_BMINCUT = 1, FEM_MAXKSAT = 2 } fem_kind;
+
+/* Methods, "Different annealing schedules for the inverse temperature":
+ *   exponential          beta(t) = exp(ln b_min + t (ln b_max - ln b_min)/(N_step - 1))
+ *   inverse-proportional 1/beta(t) = 1/b_min + t (1/b_max - 1/b_min)/(N_step - 1)
+ * t = 0 .. N_step-1; N_step = 1 gives beta(0) = b_min. */
+typedef enum { FEM_SCHED_EXPONENTIAL = 0, FEM_SCHED_INVERSE_PROPORTIONAL = 1 } fem_schedule;
+
+/* Methods, "Hyperparameter tunning": the PyTorch Adam, RMSprop and SGD updates. */
+typedef enum { FEM_OPT_ADAM = 0, FEM_OPT_RMSPROP = 1, FEM_OPT_SGD = 2 } fem_optimizer;
+
+/* FEM_GRAD_EXACT: the true gradient dF/dh (SM Eqs. S-maxcut_gradient, the bMinCut
+ *   gradient, the MaxSAT gradient, through the chain rule Eq. gradients_wrt_h).
+ * FEM_GRAD_PAPER: the manipulated gradients the paper benchmarks - one-hot
+ *   discretisation e_j of the neighbours and per-node normalisers c_i
+ *   (SM Eq. maxcut_modified_gradient and the bMinCut manipulated gradient).
+ *   Max-k-SAT is never manipulated, so both modes are the same there. */
+typedef enum { FEM_GRAD_EXACT = 0, FEM_GRAD_PAPER = 1 } fem_grad_mode;
+
+/* Arithmetic of the dense J.M contraction (dense_J problems only):
+ *   FP32     CUDA-core fp32 products and sums (the plain FP32 FEM).
+ *   BF16     tensor cores, bf16 operands, fp32 accumulation.
+ *   BF16X2   tensor cores, M split as m_hi + m_lo in bf16 (two products), fp32 accumulation.
+ *   FP8      tensor cores, e4m3 operands, fp32 accumulation (FEM_GRAD_PAPER only:
+ *            the discretised +-1 marginals and integer couplings |J| <= 16 are exact). */
+typedef enum { FEM_PREC_FP32 = 0, FEM_PREC_BF16 = 1, FEM_PREC_BF16X2 = 2, FEM_PREC_FP8 = 3 } fem_precision;
+
+typedef struct fem_problem* fem_problem_t; /* opaque; owned by the library until fem_destroy */
+
+/* Problem description.  All pointers are HOST pointers; they are read during
+ * fem_create_problem only.
+ *   kind       fem_kind.
+ *   n          number of variables, 1 <= n < 2^31.
+ *   q          states per variable: 2 for MaxCut and Max-k-SAT, 2..8 for bMinCut.
+ *   Graph (MaxCut, bMinCut), undirected, each edge listed once:
+ *     n_edges, ei[n_edges], ej[n_edges], w[n_edges]
+ *       0 <= ei, ej < n, ei != ej, no pair repeated; w finite and nonzero
+ *       (bMinCut: w > 0, SM "The bMinCut problem" uses W_ij > 0).  w may be NULL
+ *       for unit weights.  Integer weights with |w| <= 2^24 give exact int64
+ *       objectives; other weights give fp64 objectives summed in a fixed order.
+ *     dense_J    optional n*n row-major couplings (MaxCut only).  When non-NULL the
+ *       dense tensor-core path is used and ei/ej/w are ignored.  Must be symmetric
+ *       with a zero diagonal and integer entries, |J_ij| <= 2^8 (BF16 exact).
+ *   Clauses (Max-k-SAT), DIMACS style:
+ *     n_clauses, clause_ptr[n_clauses + 1] (clause_ptr[0] = 0, non-decreasing),
+ *     lits[clause_ptr[n_clauses]]: signed 1-based variable indices, +v for the
+ *     literal v and -v for its negation; a clause must not repeat a variable.
+ */
+typedef struct {
+  int32_t kind;
+  int32_t n;
+  int32_t q;
+  int64_t n_edges;
+  const int32_t* ei;
+  const int32_t* ej;
+  const double* w;
+  const float* dense_J;
+  int64_t n_clauses;
+  const int64_t* clause_ptr;
+  const int32_t* lits;
+} fem_problem_desc;
+
+/* Anneal parameters.
+ *   replicas     R >= 1; MaxCut sparse: R % 32 == 0; bMinCut: R % 16 == 0 and R*bits(q) % 32 == 0;
+ *                Max-k-SAT: R % 16 == 0; dense: R % 128 == 0.  Fixed by the call with t_begin == 0.
+ *   n_steps      N_step of the schedules (>= 1).
+ *   t_begin, t_end  run steps t_begin .. t_end-1 (0 <= t_begin <= t_end <= n_steps).
+ *                t_begin == 0 (re)initialises the fields from h_init and zeroes the
+ *                optimizer state; t_begin > 0 resumes and must equal the number of
+ *                steps already run (else FEM_ERR_STATE).  Splitting [0, T) into
+ *                [0, a) + [a, T) gives bit-identical fields.
+ *   schedule, beta_min, beta_max   see fem_schedule (0 < beta_min, 0 < beta_max).
+ *   optimizer, lr, beta1, beta2, eps, weight_decay, momentum, alpha, dampening
+ *                PyTorch semantics; unused fields are ignored.
+ *   gamma_grad   the gradient scale gamma_grad of Eq. gradients_wrt_h.
+ *   lambda_max   bMinCut: lambda(t) = lambda_max * t/(N_step - 1) (SM, bMinCut demonstration),
+ *                and the weight of the balance term in the read-out energy.
+ *   grad_mode    fem_grad_mode.
+ *   precision    fem_precision (dense_J problems only).
+ *   h_init       required when t_begin == 0: initial fields in the layout of the
+ *                file header, fp32, host pointer (or device pointer when
+ *                h_init_is_device != 0). */
+typedef struct {
+  int32_t replicas;
+  int32_t n_steps;
+  int32_t t_begin;
+  int32_t t_end;
+  int32_t schedule;
+  double beta_min;
+  double beta_max;
+  int32_t optimizer;
+  double lr;
+  double beta1;
+  double beta2;
+  double eps;
+  double weight_decay;
+  double momentum;
+  double alpha;
+  double dampening;
+  double gamma_grad;
+  double lambda_max;
+  int32_t grad_mode;
+  int32_t precision;
+  const float* h_init;
+  int32_t h_init_is_device;
+} fem_anneal_params;
+
+/* Validate `desc`, build the device-side problem (CSR with the +-1 weight packed
+ * into the column index when |w| == 1, normalisers c_i, c^f_i, c^a_i; the clause
+ * list and its variable-occurrence transpose; or the dense couplings) and copy it
+ * to the current device on `stream`.  Returns FEM_ERR_INVALID_ARG on malformed
+ * input (self-loop, duplicate edge, index out of range, repeated variable in a
+ * clause, non-symmetric dense_J ...).  On success *out owns device memory until
+ * fem_destroy. */
+fem_status fem_create_problem(const fem_problem_desc* desc, void* stream, fem_problem_t* out);
+
+/* Run anneal steps [t_begin, t_end) of FEM (Results "Free-Energy Machine"): per step,
+ * beta(t) (and lambda(t)), the coupling contraction, the gradient of F with respect
+ * to the fields, and one optimizer step on all R replicas.  Asynchronous. */
+fem_status fem_anneal(fem_problem_t p, const fem_anneal_params* prm, void* stream);
+
+/* Read out (Results, argmax and argmin equations): each replica's state is the
+ * argmax of its marginals (single field: h >= 0 selects the state of P = sigmoid(h);
+ * q states: the lowest index among maximal fields), its energy E is computed
+ * exactly (int64 for integer weights, fp64 in a fixed order otherwise), and the
+ * replica of minimum E wins (lowest index on ties).  Synchronises `stream`.
+ *   best_replica  out, may be NULL.
+ *   states        out, may be NULL: the winning replica's states, n int32
+ *                 (MaxCut +1/-1; bMinCut 0..q-1; Max-k-SAT 0/1).
+ *   energy_i64    out, may be NULL: R energies (integer-weighted problems).
+ *   energy_f64    out, may be NULL: R energies as fp64 (all problems).
+ * MaxCut energies are minus the cut.  Returns FEM_ERR_STATE before any anneal. */
+fem_status fem_read_best(fem_problem_t p, int32_t* best_replica, int32_t* states,
+                         int64_t* energy_i64, double* energy_f64, void* stream);
+
+/* Copy the current fields to host memory `h_host` (layout of the file header;
+ * n*R (single field) or n*R*q floats).  Synchronises `stream`. */
+fem_status fem_read_fields(fem_problem_t p, float* h_host, void* stream);
+
+/* Copy every replica's argmax states to `states_host`, n*R int32, layout [n][R]. */
+fem_status fem_read_states(fem_problem_t p, int32_t* states_host, void* stream);
+
+/* Number of steps run so far, and the problem's sizes (any pointer may be NULL):
+ * n, q, R (0 before the first anneal), and the number of units one step processes
+ * per replica (|E| undirected edges for graphs, n(n-1)/2 for dense_J, the
+ * literal-occurrence count for clause lists). */
+fem_status fem_problem_info(fem_problem_t p, int32_t* steps_done, int32_t* n, int32_t* q,
+                            int32_t* replicas, int64_t* units_per_replica);
+
+/* Synchronise `stream` and report any sticky device-side error. */
+fem_status fem_sync(fem_problem_t p, void* stream);
+
+/* Release every resource owned by p (NULL is ignored). */
+void fem_destroy(fem_problem_t p);
+
+/* Static English name of a status code. */
+const char* fem_status_string(fem_status s);
+
+/* One-line description of the last failure on the calling thread ("" if none). */
+const char* fem_last_error(void);
+
+/* Number of CUDA kernels this library has launched in the process so far (all
+ * handles, all threads).  Lets a caller count the device work behind a call. */
+int64_t fem_kernel_launches(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FEM_H */

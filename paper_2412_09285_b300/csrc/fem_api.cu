@@ -1,0 +1,468 @@
+// The C ABI of libfem: argument validation, host-side problem builders, state
+// management and dispatch to the kernels.  Nothing here prints or aborts.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <atomic>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "fem_internal.h"
+
+namespace fem {
+
+static thread_local std::string g_last_error;
+static std::atomic<int64_t> g_launches{0};
+
+void count_launches(int64_t k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
+
+fem_status fail(fem_status s, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_last_error = buf;
+  return s;
+}
+
+fem_status cuda_fail(cudaError_t e, const char* what) {
+  cudaGetLastError();  // clear a non-sticky error so the context stays usable
+  if (e == cudaErrorMemoryAllocation) return fail(FEM_ERR_OOM, "%s: out of device memory", what);
+  return fail(FEM_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+fem_status dev_alloc(Problem* p, void** ptr, size_t bytes) {
+  *ptr = nullptr;
+  if (bytes == 0) bytes = 16;
+  const cudaError_t e = cudaMalloc(ptr, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    *ptr = nullptr;
+    return fail(FEM_ERR_OOM, "cudaMalloc of %zu bytes failed: %s", bytes, cudaGetErrorString(e));
+  }
+  p->allocs.push_back(*ptr);
+  return FEM_OK;
+}
+
+template <typename T>
+static fem_status upload(Problem* p, T** dst, const std::vector<T>& src, cudaStream_t s) {
+  fem_status st = dev_alloc_t(p, dst, src.size());
+  if (st != FEM_OK) return st;
+  if (!src.empty()) FEM_CUDA(cudaMemcpyAsync(*dst, src.data(), src.size() * sizeof(T),
+                                             cudaMemcpyHostToDevice, s));
+  return FEM_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Per-step scalars: the beta schedule (Methods, "Different annealing schedules"),
+// the lambda ramp (SM bMinCut demonstration) and the optimizer constants.
+// ---------------------------------------------------------------------------
+static double beta_at(const fem_anneal_params& a, int t) {
+  if (a.n_steps == 1) return a.beta_min;
+  const double x = (double)t / (double)(a.n_steps - 1);
+  if (a.schedule == FEM_SCHED_EXPONENTIAL)
+    return std::exp((std::log(a.beta_max) - std::log(a.beta_min)) / (a.n_steps - 1) * t +
+                    std::log(a.beta_min));
+  (void)x;
+  return 1.0 / ((1.0 / a.beta_max - 1.0 / a.beta_min) / (a.n_steps - 1) * t + 1.0 / a.beta_min);
+}
+
+std::vector<StepScalars> make_step_scalars(const fem_anneal_params& a, int32_t single_field) {
+  std::vector<StepScalars> out;
+  out.reserve(a.t_end - a.t_begin);
+  for (int t = a.t_begin; t < a.t_end; ++t) {
+    StepScalars s;
+    std::memset(&s, 0, sizeof(s));
+    const double beta = beta_at(a, t);
+    const double lam = a.n_steps == 1 ? 0.0 : a.lambda_max * (double)t / (double)(a.n_steps - 1);
+    s.inv_beta = (float)(1.0 / beta);
+    s.lambda = (float)lam;
+    s.gq = (float)(single_field ? a.gamma_grad / 4.0 : a.gamma_grad);
+    const int tt = t + 1;
+    switch (a.optimizer) {
+      case FEM_OPT_ADAM:
+        s.lr = (float)(a.lr / (1.0 - std::pow(a.beta1, tt)));
+        s.b1 = (float)a.beta1;
+        s.omb1 = (float)(1.0 - a.beta1);
+        s.b2 = (float)a.beta2;
+        s.omb2 = (float)(1.0 - a.beta2);
+        s.inv_sqrt_bc2 = (float)(1.0 / std::sqrt(1.0 - std::pow(a.beta2, tt)));
+        s.eps = (float)a.eps;
+        break;
+      case FEM_OPT_RMSPROP:
+        s.lr = (float)a.lr;
+        s.b1 = (float)a.alpha;
+        s.omb1 = (float)(1.0 - a.alpha);
+        s.eps = (float)a.eps;
+        s.momentum = (float)a.momentum;
+        break;
+      default:
+        s.lr = (float)a.lr;
+        s.b1 = (float)a.momentum;
+        s.omb1 = (float)(1.0 - a.dampening);
+        s.first = tt == 1;
+        break;
+    }
+    s.wd = (float)a.weight_decay;
+    out.push_back(s);
+  }
+  return out;
+}
+
+// Declared in the kernel files.
+fem_status maxcut_pack_words(Problem* p, int hbuf, int wbuf, cudaStream_t s);
+const float* maxcut_current_fields(const Problem* p);
+fem_status maxcut_states_all(Problem* p, int32_t* out_dev, cudaStream_t s);
+
+// ---------------------------------------------------------------------------
+// Graph builder: validated undirected edge list -> CSR of directed entries.
+// Host-only (no CUDA call), so malformed input is rejected before any device work.
+// ---------------------------------------------------------------------------
+struct HostGraph {
+  int64_t n_edges = 0;
+  bool unit = true, integer = true;
+  std::vector<int32_t> row_ptr;
+  std::vector<uint32_t> col;
+  std::vector<float> wf, cnorm, cnorm2;
+  std::vector<double> w64;
+};
+
+static fem_status host_graph(int32_t kind, int32_t q, const fem_problem_desc* d, HostGraph& g) {
+  const int32_t n = d->n;
+  const int64_t E = d->n_edges;
+  if (E < 0) return fail(FEM_ERR_INVALID_ARG, "n_edges < 0");
+  if (E > 0 && (!d->ei || !d->ej)) return fail(FEM_ERR_INVALID_ARG, "ei/ej must be non-NULL");
+  if (2 * E >= (int64_t)INT32_MAX) return fail(FEM_ERR_UNSUPPORTED, "2|E| must be < 2^31");
+  bool unit = true, integer = true;
+  std::vector<int32_t> deg(n + 1, 0);
+  for (int64_t e = 0; e < E; ++e) {
+    const int32_t i = d->ei[e], j = d->ej[e];
+    if (i < 0 || i >= n || j < 0 || j >= n)
+      return fail(FEM_ERR_INVALID_ARG, "edge %lld: endpoint out of range [0, %d)", (long long)e, n);
+    if (i == j) return fail(FEM_ERR_INVALID_ARG, "edge %lld: self-loop at %d", (long long)e, i);
+    const double w = d->w ? d->w[e] : 1.0;
+    if (!std::isfinite(w) || w == 0.0)
+      return fail(FEM_ERR_INVALID_ARG, "edge %lld: weight must be finite and nonzero", (long long)e);
+    if (kind == FEM_BMINCUT && w < 0.0)
+      return fail(FEM_ERR_INVALID_ARG, "edge %lld: bMinCut weights must be positive", (long long)e);
+    if (std::fabs(w) != 1.0) unit = false;
+    if (w != std::rint(w) || std::fabs(w) > 16777216.0) integer = false;
+    deg[i]++;
+    deg[j]++;
+  }
+  std::vector<int32_t>& row_ptr = g.row_ptr;
+  row_ptr.assign(n + 1, 0);
+  for (int32_t i = 0; i < n; ++i) row_ptr[i + 1] = row_ptr[i] + deg[i];
+  const int64_t nnz = row_ptr[n];
+  std::vector<std::pair<int32_t, double>> ent(nnz);
+  std::vector<int32_t> fillp(row_ptr.begin(), row_ptr.end() - 1);
+  for (int64_t e = 0; e < E; ++e) {
+    const int32_t i = d->ei[e], j = d->ej[e];
+    const double w = d->w ? d->w[e] : 1.0;
+    ent[fillp[i]++] = {j, w};
+    ent[fillp[j]++] = {i, w};
+  }
+  g.col.assign(nnz, 0);
+  g.wf.assign(unit ? 0 : nnz, 0.f);
+  g.w64.assign(integer ? 0 : nnz, 0.0);
+  std::vector<double> rsum(n, 0.0), rabs(n, 0.0);
+  for (int32_t i = 0; i < n; ++i) {
+    auto b = ent.begin() + row_ptr[i], en = ent.begin() + row_ptr[i + 1];
+    std::sort(b, en, [](const std::pair<int32_t, double>& x, const std::pair<int32_t, double>& y) {
+      return x.first < y.first;
+    });
+    for (auto it = b; it != en; ++it) {
+      if (it != b && (it - 1)->first == it->first)
+        return fail(FEM_ERR_INVALID_ARG, "duplicate edge (%d, %d)", i, it->first);
+      const int64_t k = it - ent.begin();
+      g.col[k] = (uint32_t)it->first | ((unit && it->second < 0) ? 0x80000000u : 0u);
+      if (!unit) g.wf[k] = (float)it->second;
+      if (!integer) g.w64[k] = it->second;
+      rsum[i] += it->second;
+      rabs[i] += std::fabs(it->second);
+    }
+  }
+  g.n_edges = E;
+  g.unit = unit;
+  g.integer = integer;
+  if (kind == FEM_MAXCUT) {
+    // c_i = 1 / sum_j |W_ij| (SM, after Eq. maxcut_modified_gradient); unit weights
+    // derive it from the degree inside the kernel.
+    if (!unit) {
+      g.cnorm.resize(n);
+      for (int32_t i = 0; i < n; ++i) g.cnorm[i] = rabs[i] > 0 ? (float)(1.0 / rabs[i]) : 0.f;
+    }
+  } else {
+    // c^f_i = q / sum_j W_ij, c^a_i = q / sqrt(sum_j W_ij) (SM "The bMinCut problem").
+    g.cnorm.resize(n);
+    g.cnorm2.resize(n);
+    for (int32_t i = 0; i < n; ++i) {
+      g.cnorm[i] = rsum[i] > 0 ? (float)(q / rsum[i]) : 0.f;
+      g.cnorm2[i] = rsum[i] > 0 ? (float)(q / std::sqrt(rsum[i])) : 0.f;
+    }
+  }
+  return FEM_OK;
+}
+
+static fem_status upload_graph(Problem* p, const HostGraph& g, cudaStream_t s) {
+  p->n_edges = g.n_edges;
+  p->nnz = (int64_t)g.col.size();
+  p->unit_w = g.unit;
+  p->int_w = g.integer;
+  fem_status st;
+  if ((st = upload(p, &p->row_ptr, g.row_ptr, s)) != FEM_OK) return st;
+  if ((st = upload(p, &p->col, g.col, s)) != FEM_OK) return st;
+  if (!g.unit && (st = upload(p, &p->w, g.wf, s)) != FEM_OK) return st;
+  if (!g.integer && (st = upload(p, &p->w64, g.w64, s)) != FEM_OK) return st;
+  if (!g.cnorm.empty() && (st = upload(p, &p->cnorm, g.cnorm, s)) != FEM_OK) return st;
+  if (!g.cnorm2.empty() && (st = upload(p, &p->cnorm2, g.cnorm2, s)) != FEM_OK) return st;
+  return FEM_OK;
+}
+
+static fem_status ensure_state(Problem* p, int32_t R, cudaStream_t s) {
+  const size_t per = (size_t)p->n * R * (p->kind == FEM_BMINCUT ? p->q : 1);
+  if (p->R == R && p->h[0]) return FEM_OK;
+  fem_status st;
+  for (int b = 0; b < 2; ++b)
+    if ((st = dev_alloc_t(p, &p->h[b], per)) != FEM_OK) return st;
+  if ((st = dev_alloc_t(p, &p->m, per)) != FEM_OK) return st;
+  if ((st = dev_alloc_t(p, &p->v, per)) != FEM_OK) return st;
+  p->words_per_node = (p->kind == FEM_MAXCUT) ? R / 32 : 0;
+  if (p->words_per_node)
+    for (int b = 0; b < 2; ++b)
+      if ((st = dev_alloc_t(p, &p->words[b], (size_t)p->n * p->words_per_node)) != FEM_OK) return st;
+  p->part_blocks = std::max(1, std::min((p->n + 7) / 8, p->sm_count * 4));
+  const size_t part = (size_t)p->part_blocks * R * (p->kind == FEM_BMINCUT ? (p->q + 1) : 1);
+  if ((st = dev_alloc_t(p, &p->part_i, part)) != FEM_OK) return st;
+  if ((st = dev_alloc_t(p, &p->part_f, part)) != FEM_OK) return st;
+  if ((st = dev_alloc_t(p, &p->energy_i, (size_t)R)) != FEM_OK) return st;
+  if ((st = dev_alloc_t(p, &p->energy_f, (size_t)R)) != FEM_OK) return st;
+  if ((st = dev_alloc_t(p, &p->best, 1)) != FEM_OK) return st;
+  if ((st = dev_alloc_t(p, &p->states_dev, (size_t)p->n)) != FEM_OK) return st;
+  p->R = R;
+  (void)s;
+  return FEM_OK;
+}
+
+static fem_status check_sticky(Problem* p, cudaStream_t s) {
+  int32_t e = 0;
+  FEM_CUDA(cudaMemcpyAsync(&e, p->err, sizeof(e), cudaMemcpyDeviceToHost, s));
+  FEM_CUDA(cudaStreamSynchronize(s));
+  if (e & ERR_TIMEOUT) return fail(FEM_ERR_TIMEOUT, "a bounded device-side wait gave up");
+  if (e & ERR_BOUNDS) return fail(FEM_ERR_DEVICE, "a device-side bounds check failed");
+  return FEM_OK;
+}
+
+}  // namespace fem
+
+using namespace fem;
+
+extern "C" {
+
+const char* fem_status_string(fem_status s) {
+  switch (s) {
+    case FEM_OK: return "FEM_OK";
+    case FEM_ERR_INVALID_ARG: return "FEM_ERR_INVALID_ARG";
+    case FEM_ERR_UNSUPPORTED: return "FEM_ERR_UNSUPPORTED";
+    case FEM_ERR_OOM: return "FEM_ERR_OOM";
+    case FEM_ERR_CUDA: return "FEM_ERR_CUDA";
+    case FEM_ERR_TIMEOUT: return "FEM_ERR_TIMEOUT";
+    case FEM_ERR_STATE: return "FEM_ERR_STATE";
+    case FEM_ERR_DEVICE: return "FEM_ERR_DEVICE";
+  }
+  return "FEM_ERR_UNKNOWN";
+}
+
+const char* fem_last_error(void) { return g_last_error.c_str(); }
+
+int64_t fem_kernel_launches(void) { return g_launches.load(std::memory_order_relaxed); }
+
+void fem_destroy(fem_problem_t p) {
+  if (!p) return;
+  int cur = 0;
+  cudaGetDevice(&cur);
+  if (cur != p->device) cudaSetDevice(p->device);
+  for (void* a : p->allocs) cudaFree(a);
+  if (cur != p->device) cudaSetDevice(cur);
+  delete p;
+}
+
+fem_status fem_create_problem(const fem_problem_desc* d, void* stream, fem_problem_t* out) {
+  g_last_error.clear();
+  if (!d || !out) return fail(FEM_ERR_INVALID_ARG, "desc and out must be non-NULL");
+  *out = nullptr;
+  if (d->kind < FEM_MAXCUT || d->kind > FEM_MAXKSAT) return fail(FEM_ERR_INVALID_ARG, "unknown kind %d", d->kind);
+  if (d->n < 1) return fail(FEM_ERR_INVALID_ARG, "n must be >= 1");
+  if ((d->kind == FEM_MAXCUT || d->kind == FEM_MAXKSAT) && d->q != 2)
+    return fail(FEM_ERR_INVALID_ARG, "q must be 2 for MaxCut and Max-k-SAT");
+  if (d->kind == FEM_BMINCUT && (d->q < 2 || d->q > 8))
+    return fail(FEM_ERR_UNSUPPORTED, "bMinCut supports 2 <= q <= 8");
+  cudaStream_t s = (cudaStream_t)stream;
+  // 1. host-side validation and construction (no CUDA call yet)
+  HostGraph hg;
+  fem_status st = FEM_OK;
+  if (d->kind == FEM_MAXCUT && d->dense_J) {
+    return fail(FEM_ERR_UNSUPPORTED, "dense couplings are not built in this library version");
+  } else if (d->kind == FEM_MAXKSAT) {
+    return fail(FEM_ERR_UNSUPPORTED, "Max-k-SAT is not built in this library version");
+  } else {
+    if ((st = host_graph(d->kind, d->q, d, hg)) != FEM_OK) return st;
+  }
+  // 2. device side
+  std::unique_ptr<fem_problem> p(new fem_problem());
+  p->kind = d->kind;
+  p->n = d->n;
+  p->q = d->q;
+  FEM_CUDA(cudaGetDevice(&p->device));
+  FEM_CUDA(cudaDeviceGetAttribute(&p->sm_count, cudaDevAttrMultiProcessorCount, p->device));
+  st = upload_graph(p.get(), hg, s);
+  if (st == FEM_OK) st = dev_alloc_t(p.get(), &p->err, 1);
+  if (st == FEM_OK) {
+    const cudaError_t e1 = cudaMemsetAsync(p->err, 0, sizeof(int32_t), s);
+    const cudaError_t e2 = e1 == cudaSuccess ? cudaStreamSynchronize(s) : e1;
+    if (e2 != cudaSuccess) st = cuda_fail(e2, "fem_create_problem upload");
+  }
+  if (st != FEM_OK) {
+    fem_destroy(p.release());
+    return st;
+  }
+  *out = p.release();
+  return FEM_OK;
+}
+
+fem_status fem_anneal(fem_problem_t p, const fem_anneal_params* a, void* stream) {
+  g_last_error.clear();
+  if (!p || !a) return fail(FEM_ERR_INVALID_ARG, "problem and params must be non-NULL");
+  cudaStream_t s = (cudaStream_t)stream;
+  if (a->n_steps < 1) return fail(FEM_ERR_INVALID_ARG, "n_steps must be >= 1");
+  if (a->t_begin < 0 || a->t_end < a->t_begin || a->t_end > a->n_steps)
+    return fail(FEM_ERR_INVALID_ARG, "need 0 <= t_begin <= t_end <= n_steps");
+  if (!(a->beta_min > 0) || !(a->beta_max > 0) || !std::isfinite(a->beta_min) || !std::isfinite(a->beta_max))
+    return fail(FEM_ERR_INVALID_ARG, "beta_min and beta_max must be finite and > 0");
+  if (a->schedule != FEM_SCHED_EXPONENTIAL && a->schedule != FEM_SCHED_INVERSE_PROPORTIONAL)
+    return fail(FEM_ERR_INVALID_ARG, "unknown schedule %d", a->schedule);
+  if (a->optimizer < FEM_OPT_ADAM || a->optimizer > FEM_OPT_SGD)
+    return fail(FEM_ERR_INVALID_ARG, "unknown optimizer %d", a->optimizer);
+  if (a->grad_mode != FEM_GRAD_EXACT && a->grad_mode != FEM_GRAD_PAPER)
+    return fail(FEM_ERR_INVALID_ARG, "unknown grad_mode %d", a->grad_mode);
+  const int32_t R = a->replicas;
+  if (R < 1) return fail(FEM_ERR_INVALID_ARG, "replicas must be >= 1");
+  if (p->kind == FEM_MAXCUT && R % 32 != 0)
+    return fail(FEM_ERR_UNSUPPORTED, "sparse MaxCut needs replicas %% 32 == 0");
+  int cur_dev = 0;
+  FEM_CUDA(cudaGetDevice(&cur_dev));
+  if (cur_dev != p->device) return fail(FEM_ERR_STATE, "the current device is not the problem's device");
+
+  if (a->t_begin == 0) {
+    if (!a->h_init) return fail(FEM_ERR_INVALID_ARG, "h_init is required when t_begin == 0");
+    fem_status st = ensure_state(p, R, s);
+    if (st != FEM_OK) return st;
+    const size_t per = (size_t)p->n * R * (p->kind == FEM_BMINCUT ? p->q : 1);
+    FEM_CUDA(cudaMemcpyAsync(p->h[0], a->h_init, per * sizeof(float),
+                             a->h_init_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
+    FEM_CUDA(cudaMemsetAsync(p->m, 0, per * sizeof(float), s));
+    FEM_CUDA(cudaMemsetAsync(p->v, 0, per * sizeof(float), s));
+    p->cur = 0;
+    p->steps_done = 0;
+    p->n_steps = a->n_steps;
+    p->grad_mode = a->grad_mode;
+    p->optimizer = a->optimizer;
+    p->precision = a->precision;
+    if (p->kind == FEM_MAXCUT) {
+      if ((st = maxcut_pack_words(p, 0, 0, s)) != FEM_OK) return st;
+    }
+    if (!a->h_init_is_device) FEM_CUDA(cudaStreamSynchronize(s));  // h_init may be pageable
+    p->initialised = true;
+  } else {
+    if (!p->initialised) return fail(FEM_ERR_STATE, "resume before the first anneal call");
+    if (a->t_begin != p->steps_done)
+      return fail(FEM_ERR_STATE, "t_begin (%d) must equal the steps already run (%d)", a->t_begin, p->steps_done);
+    if (R != p->R || a->n_steps != p->n_steps || a->grad_mode != p->grad_mode || a->optimizer != p->optimizer)
+      return fail(FEM_ERR_STATE, "a resumed call must keep replicas, n_steps, grad_mode and optimizer");
+  }
+  if (a->t_end == a->t_begin) return FEM_OK;
+  const std::vector<StepScalars> sc = make_step_scalars(*a, p->kind != FEM_BMINCUT);
+  fem_status st = FEM_OK;
+  if (p->kind == FEM_MAXCUT) st = maxcut_sparse_steps(p, *a, sc, s);
+  else st = fail(FEM_ERR_UNSUPPORTED, "problem kind not built in this library version");
+  if (st != FEM_OK) return st;
+  p->steps_done = a->t_end;
+  return FEM_OK;
+}
+
+fem_status fem_read_best(fem_problem_t p, int32_t* best_replica, int32_t* states,
+                         int64_t* energy_i64, double* energy_f64, void* stream) {
+  g_last_error.clear();
+  if (!p) return fail(FEM_ERR_INVALID_ARG, "problem must be non-NULL");
+  if (!p->initialised) return fail(FEM_ERR_STATE, "read-out before the first anneal call");
+  cudaStream_t s = (cudaStream_t)stream;
+  fem_status st = FEM_OK;
+  if (p->kind == FEM_MAXCUT) st = maxcut_readout(p, s);
+  else st = fail(FEM_ERR_UNSUPPORTED, "problem kind not built");
+  if (st != FEM_OK) return st;
+  if (best_replica) FEM_CUDA(cudaMemcpyAsync(best_replica, p->best, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+  if (states) FEM_CUDA(cudaMemcpyAsync(states, p->states_dev, (size_t)p->n * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+  if (energy_i64) FEM_CUDA(cudaMemcpyAsync(energy_i64, p->energy_i, (size_t)p->R * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+  if (energy_f64) FEM_CUDA(cudaMemcpyAsync(energy_f64, p->energy_f, (size_t)p->R * sizeof(double), cudaMemcpyDeviceToHost, s));
+  return check_sticky(p, s);
+}
+
+fem_status fem_read_fields(fem_problem_t p, float* h_host, void* stream) {
+  g_last_error.clear();
+  if (!p || !h_host) return fail(FEM_ERR_INVALID_ARG, "problem and h_host must be non-NULL");
+  if (!p->initialised) return fail(FEM_ERR_STATE, "no fields before the first anneal call");
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t per = (size_t)p->n * p->R * (p->kind == FEM_BMINCUT ? p->q : 1);
+  const float* src = p->kind == FEM_MAXCUT ? maxcut_current_fields(p) : p->h[p->cur];
+  FEM_CUDA(cudaMemcpyAsync(h_host, src, per * sizeof(float), cudaMemcpyDeviceToHost, s));
+  return check_sticky(p, s);
+}
+
+fem_status fem_read_states(fem_problem_t p, int32_t* states_host, void* stream) {
+  g_last_error.clear();
+  if (!p || !states_host) return fail(FEM_ERR_INVALID_ARG, "problem and states_host must be non-NULL");
+  if (!p->initialised) return fail(FEM_ERR_STATE, "no states before the first anneal call");
+  cudaStream_t s = (cudaStream_t)stream;
+  int32_t* tmp = nullptr;
+  const size_t total = (size_t)p->n * p->R;
+  FEM_CUDA(cudaMallocAsync((void**)&tmp, total * sizeof(int32_t), s));
+  fem_status st = FEM_OK;
+  if (p->kind == FEM_MAXCUT) st = maxcut_states_all(p, tmp, s);
+  else st = fail(FEM_ERR_UNSUPPORTED, "problem kind not built");
+  if (st == FEM_OK) {
+    const cudaError_t e = cudaMemcpyAsync(states_host, tmp, total * sizeof(int32_t), cudaMemcpyDeviceToHost, s);
+    if (e != cudaSuccess) st = cuda_fail(e, "fem_read_states copy");
+  }
+  cudaFreeAsync(tmp, s);
+  if (st != FEM_OK) return st;
+  return check_sticky(p, s);
+}
+
+fem_status fem_problem_info(fem_problem_t p, int32_t* steps_done, int32_t* n, int32_t* q,
+                            int32_t* replicas, int64_t* units_per_replica) {
+  if (!p) return fail(FEM_ERR_INVALID_ARG, "problem must be non-NULL");
+  if (steps_done) *steps_done = p->steps_done;
+  if (n) *n = p->n;
+  if (q) *q = p->q;
+  if (replicas) *replicas = p->R;
+  if (units_per_replica) {
+    if (p->dense) *units_per_replica = (int64_t)p->n * (p->n - 1) / 2;
+    else if (p->kind == FEM_MAXKSAT) *units_per_replica = p->n_occ;
+    else *units_per_replica = p->n_edges;
+  }
+  return FEM_OK;
+}
+
+fem_status fem_sync(fem_problem_t p, void* stream) {
+  g_last_error.clear();
+  if (!p) return fail(FEM_ERR_INVALID_ARG, "problem must be non-NULL");
+  return check_sticky(p, (cudaStream_t)stream);
+}
+
+}  // extern "C"

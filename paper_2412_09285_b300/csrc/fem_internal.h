@@ -1,0 +1,126 @@
+// Internal declarations of libfem (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "fem.h"
+
+namespace fem {
+
+// Bits of the sticky device error word.
+enum : int32_t { ERR_BOUNDS = 1, ERR_TIMEOUT = 2 };
+
+// Per-step scalars, computed on the host in double and rounded to float once.
+// The optimizer fields hold the PyTorch update constants of the step's count t+1.
+struct StepScalars {
+  float inv_beta;      // 1 / beta(t)
+  float lambda;        // lambda(t) (bMinCut)
+  float gq;            // gamma_grad / 4 (single field) or gamma_grad (q states)
+  float lr;            // Adam: lr / (1 - beta1^(t+1)); RMSprop, SGD: lr
+  float b1, omb1;      // Adam: beta1, 1-beta1 | RMSprop: alpha, 1-alpha | SGD: momentum, 1-dampening
+  float b2, omb2;      // Adam: beta2, 1-beta2
+  float inv_sqrt_bc2;  // Adam: 1 / sqrt(1 - beta2^(t+1))
+  float eps;
+  float wd;            // L2 weight decay
+  float momentum;      // RMSprop momentum
+  int32_t first;       // SGD: 1 at the first step (momentum buffer starts as g)
+  int32_t pad[3];
+};
+static_assert(sizeof(StepScalars) == 64, "StepScalars must stay 64 bytes");
+
+struct Problem {
+  int32_t kind = 0, n = 0, q = 2;
+  int device = 0, sm_count = 148;
+
+  // ---- graph, CSR over directed entries (each undirected edge twice)
+  int64_t n_edges = 0, nnz = 0;
+  bool unit_w = true;        // every |w| == 1: the sign lives in bit 31 of col
+  bool int_w = true;         // every w integer with |w| <= 2^24: exact int64 objectives
+  int32_t* row_ptr = nullptr;  // [n+1]
+  uint32_t* col = nullptr;     // [nnz], bit 31 = weight sign when unit_w
+  float* w = nullptr;          // [nnz] when !unit_w
+  double* w64 = nullptr;       // [nnz] fp64 weights when !int_w (objectives)
+  float* cnorm = nullptr;      // MaxCut c_i = 1/sum|W_ij| (when !unit_w); bMinCut c^f
+  float* cnorm2 = nullptr;     // bMinCut c^a
+
+  // ---- clauses (Max-k-SAT)
+  int64_t n_clauses = 0, n_occ = 0;
+  int32_t* cl_ptr = nullptr;   // [M+1]
+  int32_t* cl_lit = nullptr;   // [n_occ]: (var << 1) | negated
+  int32_t* occ_ptr = nullptr;  // [n+1]: variable -> occurrences
+  int32_t* occ = nullptr;      // [n_occ]: (clause << 2) | position   (k <= 4) or clause index
+  int32_t max_width = 0;
+
+  // ---- dense couplings (MaxCut, dense_J)
+  bool dense = false;
+  int32_t n_pad = 0;           // n rounded up to the tensor tile
+  float* J32 = nullptr;        // [n][n]
+  void* J16 = nullptr;         // bf16 [n_pad][n_pad]
+  void* J8 = nullptr;          // e4m3 [n_pad][n_pad]
+  float* rowabs = nullptr;     // sum_j |J_ij|
+
+  // ---- replica state
+  int32_t R = 0, steps_done = 0, n_steps = 0;
+  bool initialised = false;
+  int32_t grad_mode = 1, optimizer = 0, precision = 0;
+  int32_t cur = 0;             // which h / words buffer is current
+  float* h[2] = {nullptr, nullptr};
+  float* m = nullptr;
+  float* v = nullptr;
+  uint32_t* words[2] = {nullptr, nullptr};
+  int32_t words_per_node = 0;
+  void* mt[2] = {nullptr, nullptr};    // dense: discretised marginals for the tensor cores
+  int32_t* cnt[2] = {nullptr, nullptr};  // bMinCut per-replica group counts [R][q]
+
+  // ---- readout scratch
+  int32_t part_blocks = 0;
+  int64_t* part_i = nullptr;   // [part_blocks][R] (or [part_blocks][R][q+1])
+  double* part_f = nullptr;
+  int64_t* energy_i = nullptr; // [R]
+  double* energy_f = nullptr;  // [R]
+  int32_t* best = nullptr;     // [1]
+  int32_t* states_dev = nullptr;  // [n]
+  StepScalars* d_steps = nullptr;  // per-step scalars table
+  int32_t d_steps_cap = 0;
+
+  int32_t* err = nullptr;      // sticky device error word
+  std::vector<void*> allocs;   // every cudaMalloc, freed by fem_destroy
+};
+
+// ---- error reporting (thread-local last error)
+fem_status fail(fem_status s, const char* fmt, ...);
+fem_status cuda_fail(cudaError_t e, const char* what);
+#define FEM_CUDA(call)                                       \
+  do {                                                       \
+    cudaError_t e_ = (call);                                 \
+    if (e_ != cudaSuccess) return ::fem::cuda_fail(e_, #call); \
+  } while (0)
+
+fem_status dev_alloc(Problem* p, void** ptr, size_t bytes);
+template <typename T>
+fem_status dev_alloc_t(Problem* p, T** ptr, size_t count) {
+  return dev_alloc(p, reinterpret_cast<void**>(ptr), count * sizeof(T));
+}
+
+// ---- kernel launch accounting (fem_kernel_launches)
+void count_launches(int64_t k);
+
+// ---- step scalars
+std::vector<StepScalars> make_step_scalars(const fem_anneal_params& a, int32_t q_single_field_scale);
+
+// ---- MaxCut sparse (maxcut_sparse.cu)
+fem_status maxcut_sparse_steps(Problem* p, const fem_anneal_params& a,
+                               const std::vector<StepScalars>& sc, cudaStream_t s);
+fem_status maxcut_readout(Problem* p, cudaStream_t s);
+
+// ---- readout common (readout.cu)
+fem_status finish_argmin(Problem* p, cudaStream_t s);
+
+}  // namespace fem
+
+// The opaque handle of the C ABI is the internal problem record.
+struct fem_problem : public fem::Problem {};

@@ -1,0 +1,367 @@
+// MaxCut on sparse graphs: the fused per-step kernel (neighbour contraction +
+// single-field gradient + optimizer) and the read-out of cuts.
+//
+// Single-field form (SM "Simplification of FEM for solving the MaxCut problem",
+// Eq. grad_m_h): P_i = sigmoid(h_i), m_i = tanh(h_i/2),
+//   paper mode: g_i = (gamma/4) [c_i sum_j W_ij sgn(m_j) + h_i/beta] (1 - m_i^2)
+//   exact mode: g_i = (gamma/4) [2 sum_j W_ij m_j      + h_i/beta] (1 - m_i^2)
+// with c_i = 1/sum_j |W_ij| (SM, after Eq. maxcut_modified_gradient; 0 when isolated).
+//
+// Layout: h, m, v are [n][R] fp32 with the R replicas of a node contiguous, so a
+// warp (lane = replica) reads and writes 128 B per array per node.  The
+// discretised state sgn(m_j) of 32 replicas is one uint32 per node ("sign word";
+// bit r set <=> h_jr < 0 <=> state -1), ping-ponged between steps, so a
+// neighbour gather moves 4 bytes per edge instead of 128.
+#include "fem_internal.h"
+#include "step_common.cuh"
+
+namespace fem {
+namespace {
+
+struct MaxcutArgs {
+  const int32_t* row_ptr;
+  const uint32_t* col;
+  const float* w;
+  const float* cnorm;
+  int32_t n, R, wpn;
+  const float* h_in;
+  float* h_out;
+  float* m;
+  float* v;
+  const uint32_t* words_in;
+  uint32_t* words_out;
+};
+
+// One warp per (node, block of 32 replicas); lane = replica.  Neighbour column
+// indices are loaded 32 at a time (one coalesced load), each lane gathers the
+// sign word of "its" neighbour, and the words are then broadcast by shuffles.
+template <int MODE, int OPT, bool UNIT>
+__global__ void __launch_bounds__(256) k_maxcut_step(MaxcutArgs a, StepScalars s) {
+  const int lane = threadIdx.x & 31;
+  const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+  const long long items = (long long)a.n * a.wpn;
+  for (long long it = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; it < items;
+       it += nwarps) {
+    const int i = (int)(it / a.wpn);
+    const int wb = (int)(it - (long long)i * a.wpn);
+    const size_t idx = (size_t)i * a.R + (size_t)wb * 32 + lane;
+    float hi = a.h_in[idx];
+    float mi = a.m[idx];
+    float vi = (OPT == FEM_OPT_SGD) ? 0.f : a.v[idx];
+    const int beg = a.row_ptr[i], end = a.row_ptr[i + 1];
+    float field;
+    if (MODE == FEM_GRAD_PAPER) {
+      int iacc = 0;
+      float facc = 0.f;
+      for (int k0 = beg; k0 < end; k0 += 32) {
+        const int k = k0 + lane;
+        uint32_t c = 0, word = 0;
+        float wk = 0.f;
+        if (k < end) {
+          c = a.col[k];
+          word = a.words_in[(size_t)(c & 0x7fffffffu) * a.wpn + wb];
+          if (!UNIT) wk = a.w[k];
+        }
+        const int cnt = min(32, end - k0);
+        for (int e = 0; e < cnt; ++e) {
+          const uint32_t bit = (__shfl_sync(kFullMask, word, e) >> lane) & 1u;
+          if (UNIT) {
+            const uint32_t ce = __shfl_sync(kFullMask, c, e);
+            iacc += ((ce >> 31) ^ bit) ? -1 : 1;
+          } else {
+            const float wv = __shfl_sync(kFullMask, wk, e);
+            facc += bit ? -wv : wv;
+          }
+        }
+      }
+      const float cn = UNIT ? (end > beg ? 1.f / (float)(end - beg) : 0.f) : a.cnorm[i];
+      field = cn * (UNIT ? (float)iacc : facc);
+    } else {
+      float facc = 0.f;
+      for (int k0 = beg; k0 < end; k0 += 32) {
+        const int k = k0 + lane;
+        uint32_t c = 0;
+        float wk = 0.f;
+        if (k < end) {
+          c = a.col[k];
+          if (!UNIT) wk = a.w[k];
+        }
+        const int cnt = min(32, end - k0);
+        for (int e = 0; e < cnt; ++e) {
+          const uint32_t ce = __shfl_sync(kFullMask, c, e);
+          const float hj = a.h_in[(size_t)(ce & 0x7fffffffu) * a.R + (size_t)wb * 32 + lane];
+          const float mj = tanhf(0.5f * hj);
+          if (UNIT) {
+            facc += (ce >> 31) ? -mj : mj;
+          } else {
+            facc = fmaf(__shfl_sync(kFullMask, wk, e), mj, facc);
+          }
+        }
+      }
+      field = 2.f * facc;
+    }
+    const float g = s.gq * (field + hi * s.inv_beta) * one_minus_m2(hi);
+    opt_update<OPT>(hi, mi, vi, g, s);
+    a.h_out[idx] = hi;
+    a.m[idx] = mi;
+    if (OPT != FEM_OPT_SGD) a.v[idx] = vi;
+    const uint32_t ball = __ballot_sync(kFullMask, hi < 0.f);
+    if (lane == 0) a.words_out[(size_t)i * a.wpn + wb] = ball;
+  }
+}
+
+// Sign words of the fields: bit r of word (i, b) is set when h[i][32b + r] < 0.
+__global__ void k_pack_sign_words(const float* __restrict__ h, int32_t n, int32_t R,
+                                  int32_t wpn, uint32_t* __restrict__ words) {
+  const int lane = threadIdx.x & 31;
+  const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+  for (long long it = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+       it < (long long)n * wpn; it += nwarps) {
+    const float x = h[it * 32 + lane];  // [n][R] with R = 32 wpn: item it covers elements it*32..
+    const uint32_t b = __ballot_sync(kFullMask, x < 0.f);
+    if (lane == 0) words[it] = b;
+  }
+}
+
+// Per-block partial cuts: cut_r = sum over undirected edges (j > i in the CSR)
+// of W_ij [bit_ir != bit_jr].  blockIdx.y selects the block of 32 replicas;
+// the lane is the replica.  Integer weights accumulate in int64, others in fp64
+// in CSR order, then the 8 warps of the block are added in warp order.
+template <bool UNIT, bool INTW>
+__global__ void __launch_bounds__(256) k_maxcut_cut_partial(
+    const int32_t* __restrict__ row_ptr, const uint32_t* __restrict__ col,
+    const float* __restrict__ w, const double* __restrict__ w64,
+    const uint32_t* __restrict__ words, int32_t n, int32_t R, int32_t wpn,
+    int64_t* __restrict__ part_i, double* __restrict__ part_f) {
+  __shared__ int64_t si[8][32];
+  __shared__ double sf[8][32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int wb = blockIdx.y;
+  int64_t acc_i = 0;
+  double acc_f = 0.0;
+  for (int i = blockIdx.x * 8 + warp; i < n; i += gridDim.x * 8) {
+    const uint32_t bi = (words[(size_t)i * wpn + wb] >> lane) & 1u;
+    const int beg = row_ptr[i], end = row_ptr[i + 1];
+    for (int k0 = beg; k0 < end; k0 += 32) {
+      const int k = k0 + lane;
+      uint32_t c = 0, word = 0;
+      if (k < end) {
+        c = col[k];
+        word = words[(size_t)(c & 0x7fffffffu) * wpn + wb];
+      }
+      const int cnt = min(32, end - k0);
+      for (int e = 0; e < cnt; ++e) {
+        const uint32_t ce = __shfl_sync(kFullMask, c, e);
+        const uint32_t bj = (__shfl_sync(kFullMask, word, e) >> lane) & 1u;
+        const uint32_t j = ce & 0x7fffffffu;
+        if ((int)j <= i || bj == bi) continue;
+        if (INTW) {
+          acc_i += UNIT ? ((ce >> 31) ? -1 : 1) : (int64_t)w[k0 + e];
+        } else {
+          acc_f += w64[k0 + e];
+        }
+      }
+    }
+  }
+  si[warp][lane] = acc_i;
+  sf[warp][lane] = acc_f;
+  __syncthreads();
+  if (warp == 0) {
+    int64_t ti = 0;
+    double tf = 0.0;
+    for (int k = 0; k < 8; ++k) {
+      ti += si[k][lane];
+      tf += sf[k][lane];
+    }
+    const size_t o = (size_t)blockIdx.x * R + (size_t)wb * 32 + lane;
+    if (INTW) part_i[o] = ti;
+    else part_f[o] = tf;
+  }
+}
+
+// Sum the partials of every replica in block order, set E_r = -cut_r, then the
+// argmin over replicas with the lowest index winning ties.  One block.
+template <bool INTW>
+__global__ void __launch_bounds__(1024) k_maxcut_finish(const int64_t* __restrict__ part_i,
+                                                        const double* __restrict__ part_f,
+                                                        int32_t nblk, int32_t R,
+                                                        int64_t* __restrict__ e_i,
+                                                        double* __restrict__ e_f,
+                                                        int32_t* __restrict__ best) {
+  __shared__ double sval[1024];
+  __shared__ int sidx[1024];
+  double bv = 0.0;
+  int bidx = 0x7fffffff;
+  for (int r = threadIdx.x; r < R; r += blockDim.x) {
+    double ef;
+    if (INTW) {
+      int64_t t = 0;
+      for (int b = 0; b < nblk; ++b) t += part_i[(size_t)b * R + r];
+      e_i[r] = -t;
+      ef = (double)(-t);
+    } else {
+      double t = 0.0;
+      for (int b = 0; b < nblk; ++b) t += part_f[(size_t)b * R + r];
+      ef = -t;
+      e_i[r] = 0;
+    }
+    e_f[r] = ef;
+    if (bidx == 0x7fffffff || ef < bv) {
+      bv = ef;
+      bidx = r;
+    }
+  }
+  sval[threadIdx.x] = bv;
+  sidx[threadIdx.x] = bidx;
+  __syncthreads();
+  for (int off = blockDim.x / 2; off > 0; off >>= 1) {
+    if (threadIdx.x < off) {
+      const double ov = sval[threadIdx.x + off];
+      const int oi = sidx[threadIdx.x + off];
+      const int mi = sidx[threadIdx.x];
+      if (oi != 0x7fffffff && (mi == 0x7fffffff || ov < sval[threadIdx.x] ||
+                               (ov == sval[threadIdx.x] && oi < mi))) {
+        sval[threadIdx.x] = ov;
+        sidx[threadIdx.x] = oi;
+      }
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) best[0] = sidx[0];
+}
+
+// states[i] = +1 / -1 of replica r (from the sign words).
+__global__ void k_maxcut_states_one(const uint32_t* __restrict__ words, int32_t n, int32_t wpn,
+                                    const int32_t* __restrict__ best, int32_t* __restrict__ out) {
+  const int r = best[0];
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    out[i] = ((words[(size_t)i * wpn + (r >> 5)] >> (r & 31)) & 1u) ? -1 : 1;
+  }
+}
+
+__global__ void k_maxcut_states_all(const uint32_t* __restrict__ words, int32_t n, int32_t R,
+                                    int32_t wpn, int32_t* __restrict__ out) {
+  const size_t total = (size_t)n * R;
+  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (size_t)gridDim.x * blockDim.x) {
+    const size_t i = e / R;
+    const int r = (int)(e - i * R);
+    out[e] = ((words[i * wpn + (r >> 5)] >> (r & 31)) & 1u) ? -1 : 1;
+  }
+}
+
+template <int MODE, int OPT, bool UNIT>
+void launch_step(const MaxcutArgs& a, const StepScalars& s, int grid, cudaStream_t st) {
+  k_maxcut_step<MODE, OPT, UNIT><<<grid, 256, 0, st>>>(a, s);
+}
+
+using StepFn = void (*)(const MaxcutArgs&, const StepScalars&, int, cudaStream_t);
+
+template <int MODE, bool UNIT>
+StepFn pick_opt(int opt) {
+  switch (opt) {
+    case FEM_OPT_ADAM: return launch_step<MODE, FEM_OPT_ADAM, UNIT>;
+    case FEM_OPT_RMSPROP: return launch_step<MODE, FEM_OPT_RMSPROP, UNIT>;
+    default: return launch_step<MODE, FEM_OPT_SGD, UNIT>;
+  }
+}
+
+StepFn pick_step(int mode, int opt, bool unit) {
+  if (mode == FEM_GRAD_PAPER) return unit ? pick_opt<FEM_GRAD_PAPER, true>(opt) : pick_opt<FEM_GRAD_PAPER, false>(opt);
+  return unit ? pick_opt<FEM_GRAD_EXACT, true>(opt) : pick_opt<FEM_GRAD_EXACT, false>(opt);
+}
+
+int grid_for_warps(const Problem* p, long long warps) {
+  long long blocks = (warps + 7) / 8;
+  const long long cap = (long long)p->sm_count * 8;
+  if (blocks > cap) blocks = cap;
+  return (int)(blocks < 1 ? 1 : blocks);
+}
+
+}  // namespace
+
+fem_status maxcut_pack_words(Problem* p, int hbuf, int wbuf, cudaStream_t s) {
+  const long long items = (long long)p->n * p->words_per_node;
+  k_pack_sign_words<<<grid_for_warps(p, items), 256, 0, s>>>(p->h[hbuf], p->n, p->R,
+                                                              p->words_per_node, p->words[wbuf]);
+  count_launches(1);
+  FEM_CUDA(cudaGetLastError());
+  return FEM_OK;
+}
+
+fem_status maxcut_sparse_steps(Problem* p, const fem_anneal_params& a,
+                               const std::vector<StepScalars>& sc, cudaStream_t s) {
+  const StepFn fn = pick_step(p->grad_mode, p->optimizer, p->unit_w);
+  const long long items = (long long)p->n * p->words_per_node;
+  const int grid = grid_for_warps(p, items);
+  MaxcutArgs args{};
+  args.row_ptr = p->row_ptr;
+  args.col = p->col;
+  args.w = p->w;
+  args.cnorm = p->cnorm;
+  args.n = p->n;
+  args.R = p->R;
+  args.wpn = p->words_per_node;
+  args.m = p->m;
+  args.v = p->v;
+  for (size_t k = 0; k < sc.size(); ++k) {
+    if (p->grad_mode == FEM_GRAD_PAPER) {
+      args.h_in = p->h[0];
+      args.h_out = p->h[0];
+    } else {
+      args.h_in = p->h[p->cur];
+      args.h_out = p->h[p->cur ^ 1];
+    }
+    args.words_in = p->words[p->cur];
+    args.words_out = p->words[p->cur ^ 1];
+    fn(args, sc[k], grid, s);
+    p->cur ^= 1;
+  }
+  count_launches((int64_t)sc.size());
+  FEM_CUDA(cudaGetLastError());
+  (void)a;
+  return FEM_OK;
+}
+
+const float* maxcut_current_fields(const Problem* p) {
+  return p->grad_mode == FEM_GRAD_PAPER ? p->h[0] : p->h[p->cur];
+}
+
+fem_status maxcut_readout(Problem* p, cudaStream_t s) {
+  const int wpn = p->words_per_node;
+  const dim3 grid(p->part_blocks, wpn);
+  const uint32_t* words = p->words[p->cur];
+  if (p->int_w) {
+    if (p->unit_w)
+      k_maxcut_cut_partial<true, true><<<grid, 256, 0, s>>>(p->row_ptr, p->col, p->w, p->w64, words,
+                                                            p->n, p->R, wpn, p->part_i, p->part_f);
+    else
+      k_maxcut_cut_partial<false, true><<<grid, 256, 0, s>>>(p->row_ptr, p->col, p->w, p->w64, words,
+                                                             p->n, p->R, wpn, p->part_i, p->part_f);
+    k_maxcut_finish<true><<<1, 1024, 0, s>>>(p->part_i, p->part_f, p->part_blocks, p->R,
+                                             p->energy_i, p->energy_f, p->best);
+  } else {
+    k_maxcut_cut_partial<false, false><<<grid, 256, 0, s>>>(p->row_ptr, p->col, p->w, p->w64, words,
+                                                            p->n, p->R, wpn, p->part_i, p->part_f);
+    k_maxcut_finish<false><<<1, 1024, 0, s>>>(p->part_i, p->part_f, p->part_blocks, p->R,
+                                              p->energy_i, p->energy_f, p->best);
+  }
+  k_maxcut_states_one<<<(p->n + 255) / 256 < 1024 ? (p->n + 255) / 256 : 1024, 256, 0, s>>>(
+      words, p->n, wpn, p->best, p->states_dev);
+  count_launches(3);
+  FEM_CUDA(cudaGetLastError());
+  return FEM_OK;
+}
+
+fem_status maxcut_states_all(Problem* p, int32_t* out_dev, cudaStream_t s) {
+  const size_t total = (size_t)p->n * p->R;
+  size_t blocks = (total + 255) / 256;
+  if (blocks > (size_t)p->sm_count * 16) blocks = (size_t)p->sm_count * 16;
+  k_maxcut_states_all<<<(int)blocks, 256, 0, s>>>(p->words[p->cur], p->n, p->R, p->words_per_node,
+                                                  out_dev);
+  count_launches(1);
+  FEM_CUDA(cudaGetLastError());
+  return FEM_OK;
+}
+
+}  // namespace fem

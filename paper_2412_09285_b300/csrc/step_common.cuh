@@ -1,0 +1,58 @@
+// Device helpers shared by the step kernels: the optimizer updates and the
+// single-field marginal algebra.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "fem_internal.h"
+
+namespace fem {
+
+constexpr unsigned kFullMask = 0xffffffffu;
+
+// One optimizer update of one field with PyTorch's semantics (Methods,
+// "Hyperparameter tunning": the paper uses torch.optim's Adam, RMSprop and SGD).
+//   Adam:    m = b1 m + (1-b1) g;  v = b2 v + (1-b2) g^2;
+//            h -= lr/(1-b1^t) * m / (sqrt(v)/sqrt(1-b2^t) + eps)
+//   RMSprop: v = a v + (1-a) g^2;  avg = sqrt(v) + eps;
+//            momentum mu > 0: buf = mu buf + g/avg, h -= lr buf;  else h -= lr g/avg
+//   SGD:     momentum mu != 0: buf = g (first step) or mu buf + (1-d) g;  h -= lr buf
+// The L2 weight decay adds wd*h to g first.  `m` doubles as the momentum buffer
+// of RMSprop and SGD.
+template <int OPT>
+__device__ __forceinline__ void opt_update(float& h, float& m, float& v, float g,
+                                           const StepScalars& s) {
+  if (s.wd != 0.f) g = fmaf(s.wd, h, g);
+  if (OPT == FEM_OPT_ADAM) {
+    m = fmaf(s.b1, m, s.omb1 * g);
+    v = fmaf(s.b2, v, s.omb2 * g * g);
+    const float denom = fmaf(sqrtf(v), s.inv_sqrt_bc2, s.eps);
+    h = h - s.lr * (m / denom);
+  } else if (OPT == FEM_OPT_RMSPROP) {
+    v = fmaf(s.b1, v, s.omb1 * g * g);
+    const float avg = sqrtf(v) + s.eps;
+    if (s.momentum > 0.f) {
+      m = fmaf(s.momentum, m, g / avg);
+      h = h - s.lr * m;
+    } else {
+      h = h - s.lr * (g / avg);
+    }
+  } else {
+    if (s.b1 != 0.f) {
+      m = s.first ? g : fmaf(s.b1, m, s.omb1 * g);
+      g = m;
+    }
+    h = h - s.lr * g;
+  }
+}
+
+// 1 - m^2 for m = tanh(h/2) = 2 sigmoid(h) - 1, evaluated as 4e/(1+e)^2 with
+// e = exp(-|h|) so that it keeps full relative accuracy when |m| -> 1.
+__device__ __forceinline__ float one_minus_m2(float h) {
+  const float e = expf(-fabsf(h));
+  const float d = 1.f + e;
+  return 4.f * e / (d * d);
+}
+
+}  // namespace fem

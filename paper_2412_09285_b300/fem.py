@@ -1,0 +1,269 @@
+"""Thin ctypes binding of libfem's C ABI (``include/fem.h``).
+
+Argument marshalling only: every step of the method runs in the library's CUDA
+kernels.  The functions keep the C names (``fem_create_problem``, ``fem_anneal``,
+``fem_read_best`` ...); ``Problem`` is a small convenience wrapper over them that
+takes numpy arrays or torch tensors.  Importing this module loads the in-tree
+``libfem.so``; if it is missing, the import fails loudly - there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libfem.so")
+
+FEM_OK, FEM_ERR_INVALID_ARG, FEM_ERR_UNSUPPORTED, FEM_ERR_OOM = 0, 1, 2, 3
+FEM_ERR_CUDA, FEM_ERR_TIMEOUT, FEM_ERR_STATE, FEM_ERR_DEVICE = 4, 5, 6, 7
+FEM_MAXCUT, FEM_BMINCUT, FEM_MAXKSAT = 0, 1, 2
+FEM_SCHED_EXPONENTIAL, FEM_SCHED_INVERSE_PROPORTIONAL = 0, 1
+FEM_OPT_ADAM, FEM_OPT_RMSPROP, FEM_OPT_SGD = 0, 1, 2
+FEM_GRAD_EXACT, FEM_GRAD_PAPER = 0, 1
+FEM_PREC_FP32, FEM_PREC_BF16, FEM_PREC_BF16X2, FEM_PREC_FP8 = 0, 1, 2, 3
+
+KINDS = {"maxcut": FEM_MAXCUT, "bmincut": FEM_BMINCUT, "sat": FEM_MAXKSAT}
+SCHEDULES = {"exponential": FEM_SCHED_EXPONENTIAL, "inverse_proportional": FEM_SCHED_INVERSE_PROPORTIONAL}
+OPTIMIZERS = {"adam": FEM_OPT_ADAM, "rmsprop": FEM_OPT_RMSPROP, "sgd": FEM_OPT_SGD}
+GRAD_MODES = {"exact": FEM_GRAD_EXACT, "paper": FEM_GRAD_PAPER}
+PRECISIONS = {"fp32": FEM_PREC_FP32, "bf16": FEM_PREC_BF16, "bf16x2": FEM_PREC_BF16X2, "fp8": FEM_PREC_FP8}
+
+
+class fem_problem_desc(C.Structure):
+    _fields_ = [
+        ("kind", C.c_int32), ("n", C.c_int32), ("q", C.c_int32),
+        ("n_edges", C.c_int64), ("ei", C.c_void_p), ("ej", C.c_void_p), ("w", C.c_void_p),
+        ("dense_J", C.c_void_p),
+        ("n_clauses", C.c_int64), ("clause_ptr", C.c_void_p), ("lits", C.c_void_p),
+    ]
+
+
+class fem_anneal_params(C.Structure):
+    _fields_ = [
+        ("replicas", C.c_int32), ("n_steps", C.c_int32), ("t_begin", C.c_int32), ("t_end", C.c_int32),
+        ("schedule", C.c_int32), ("beta_min", C.c_double), ("beta_max", C.c_double),
+        ("optimizer", C.c_int32), ("lr", C.c_double), ("beta1", C.c_double), ("beta2", C.c_double),
+        ("eps", C.c_double), ("weight_decay", C.c_double), ("momentum", C.c_double),
+        ("alpha", C.c_double), ("dampening", C.c_double), ("gamma_grad", C.c_double),
+        ("lambda_max", C.c_double), ("grad_mode", C.c_int32), ("precision", C.c_int32),
+        ("h_init", C.c_void_p), ("h_init_is_device", C.c_int32),
+    ]
+
+
+class FemError(RuntimeError):
+    def __init__(self, status, where, msg):
+        super().__init__(f"{where}: {status_string(status)}: {msg}")
+        self.status = status
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"libfem.so not built at {LIB_PATH}; run python -m paper_2412_09285_b300.build")
+    lib = C.CDLL(LIB_PATH)
+    P, S = C.c_void_p, C.c_int
+    sig = {
+        "fem_create_problem": (S, [C.POINTER(fem_problem_desc), P, C.POINTER(P)]),
+        "fem_anneal": (S, [P, C.POINTER(fem_anneal_params), P]),
+        "fem_read_best": (S, [P, P, P, P, P, P]),
+        "fem_read_fields": (S, [P, P, P]),
+        "fem_read_states": (S, [P, P, P]),
+        "fem_problem_info": (S, [P, P, P, P, P, P]),
+        "fem_sync": (S, [P, P]),
+        "fem_destroy": (None, [P]),
+        "fem_status_string": (C.c_char_p, [S]),
+        "fem_last_error": (C.c_char_p, []),
+        "fem_kernel_launches": (C.c_int64, []),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype, f.argtypes = res, args
+    return lib
+
+
+_lib = _load()
+
+
+def status_string(s: int) -> str:
+    return _lib.fem_status_string(int(s)).decode()
+
+
+def _check(status, where):
+    if status != FEM_OK:
+        raise FemError(status, where, _lib.fem_last_error().decode())
+
+
+def _ptr(a):
+    """Address of a numpy array's or torch tensor's data (None -> NULL)."""
+    if a is None:
+        return None
+    if hasattr(a, "data_ptr"):
+        return a.data_ptr()
+    return a.ctypes.data
+
+
+def _stream(stream):
+    if stream is None:
+        try:
+            import torch
+            if torch.cuda.is_available():
+                return torch.cuda.current_stream().cuda_stream
+        except Exception:
+            pass
+        return None
+    if hasattr(stream, "cuda_stream"):
+        return stream.cuda_stream
+    return int(stream)
+
+
+# ----------------------------------------------------------------- C-named calls
+
+def fem_create_problem(desc: fem_problem_desc, stream=None) -> int:
+    h = C.c_void_p()
+    _check(_lib.fem_create_problem(C.byref(desc), _stream(stream), C.byref(h)), "fem_create_problem")
+    return h.value
+
+
+def fem_anneal(handle: int, params: fem_anneal_params, stream=None) -> None:
+    _check(_lib.fem_anneal(handle, C.byref(params), _stream(stream)), "fem_anneal")
+
+
+def fem_read_best(handle, best_replica=None, states=None, energy_i64=None, energy_f64=None, stream=None):
+    _check(_lib.fem_read_best(handle, _ptr(best_replica), _ptr(states), _ptr(energy_i64),
+                              _ptr(energy_f64), _stream(stream)), "fem_read_best")
+
+
+def fem_read_fields(handle, h_host, stream=None):
+    _check(_lib.fem_read_fields(handle, _ptr(h_host), _stream(stream)), "fem_read_fields")
+
+
+def fem_read_states(handle, states_host, stream=None):
+    _check(_lib.fem_read_states(handle, _ptr(states_host), _stream(stream)), "fem_read_states")
+
+
+def fem_problem_info(handle):
+    vals = [C.c_int32(), C.c_int32(), C.c_int32(), C.c_int32(), C.c_int64()]
+    _check(_lib.fem_problem_info(handle, *[C.byref(v) for v in vals]), "fem_problem_info")
+    return dict(steps_done=vals[0].value, n=vals[1].value, q=vals[2].value,
+                replicas=vals[3].value, units_per_replica=vals[4].value)
+
+
+def fem_sync(handle, stream=None):
+    _check(_lib.fem_sync(handle, _stream(stream)), "fem_sync")
+
+
+def fem_destroy(handle):
+    _lib.fem_destroy(handle)
+
+
+def fem_kernel_launches() -> int:
+    return int(_lib.fem_kernel_launches())
+
+
+# ----------------------------------------------------------------- convenience
+
+DEFAULTS = dict(schedule="exponential", beta_min=0.05, beta_max=5.0, optimizer="adam", lr=0.1,
+                beta1=0.9, beta2=0.999, eps=1e-8, weight_decay=0.0, momentum=0.0, alpha=0.99,
+                dampening=0.0, gamma_grad=1.0, lambda_max=1.0, grad_mode="paper", precision="bf16")
+
+
+def make_params(replicas, n_steps, t_begin=0, t_end=None, h_init=None, **kw) -> fem_anneal_params:
+    o = dict(DEFAULTS)
+    o.update(kw)
+    p = fem_anneal_params()
+    p.replicas, p.n_steps = int(replicas), int(n_steps)
+    p.t_begin = int(t_begin)
+    p.t_end = int(n_steps if t_end is None else t_end)
+    p.schedule = SCHEDULES[o["schedule"]]
+    p.beta_min, p.beta_max = float(o["beta_min"]), float(o["beta_max"])
+    p.optimizer = OPTIMIZERS[o["optimizer"]]
+    for k in ("lr", "beta1", "beta2", "eps", "weight_decay", "momentum", "alpha", "dampening",
+              "gamma_grad", "lambda_max"):
+        setattr(p, k, float(o[k]))
+    p.grad_mode = GRAD_MODES[o["grad_mode"]]
+    p.precision = PRECISIONS[o["precision"]]
+    p.h_init = _ptr(h_init)
+    p.h_init_is_device = int(bool(h_init is not None and hasattr(h_init, "is_cuda") and h_init.is_cuda))
+    return p
+
+
+class Problem:
+    """Owns one libfem problem handle.  Inputs are host numpy arrays (or objects
+    from ``instances``); h_init may also be a CUDA torch tensor."""
+
+    def __init__(self, kind="maxcut", graph=None, clauses=None, dense=None, q=2, stream=None):
+        self.kind = kind
+        self.stream = stream
+        d = fem_problem_desc()
+        d.kind = KINDS[kind]
+        d.q = int(q)
+        self._keep = []
+        if graph is not None:
+            d.n = graph.n
+            ei = np.ascontiguousarray(graph.ei, np.int32)
+            ej = np.ascontiguousarray(graph.ej, np.int32)
+            w = np.ascontiguousarray(graph.w, np.float64)
+            self._keep += [ei, ej, w]
+            d.n_edges, d.ei, d.ej, d.w = ei.shape[0], _ptr(ei), _ptr(ej), _ptr(w)
+        if dense is not None:
+            J = np.ascontiguousarray(dense, np.float32)
+            self._keep.append(J)
+            d.n = J.shape[0]
+            d.dense_J = _ptr(J)
+        if clauses is not None:
+            d.n = clauses.n
+            ptr = np.ascontiguousarray(clauses.ptr, np.int64)
+            lits = np.ascontiguousarray(clauses.lits, np.int32)
+            self._keep += [ptr, lits]
+            d.n_clauses, d.clause_ptr, d.lits = ptr.shape[0] - 1, _ptr(ptr), _ptr(lits)
+        self.n, self.q = d.n, d.q
+        self.handle = fem_create_problem(d, stream)
+        self._keep = []
+        self.replicas = 0
+
+    def anneal(self, h_init=None, replicas=None, n_steps=1000, t_begin=0, t_end=None, **kw):
+        if h_init is not None and not hasattr(h_init, "data_ptr"):
+            h_init = np.ascontiguousarray(h_init, np.float32)
+        if replicas is None:
+            replicas = h_init.shape[1] if h_init is not None else self.replicas
+        self.replicas = int(replicas)
+        p = make_params(replicas, n_steps, t_begin, t_end, h_init, **kw)
+        fem_anneal(self.handle, p, self.stream)
+        return self
+
+    def fields(self):
+        shape = (self.n, self.replicas) if self.kind != "bmincut" else (self.n, self.replicas, self.q)
+        out = np.empty(shape, np.float32)
+        fem_read_fields(self.handle, out, self.stream)
+        return out
+
+    def states(self):
+        out = np.empty((self.n, self.replicas), np.int32)
+        fem_read_states(self.handle, out, self.stream)
+        return out
+
+    def best(self):
+        br = np.zeros(1, np.int32)
+        st = np.empty(self.n, np.int32)
+        ei = np.empty(self.replicas, np.int64)
+        ef = np.empty(self.replicas, np.float64)
+        fem_read_best(self.handle, br, st, ei, ef, self.stream)
+        return dict(best_replica=int(br[0]), states=st, energy_i64=ei, energy_f64=ef)
+
+    def info(self):
+        return fem_problem_info(self.handle)
+
+    def sync(self):
+        fem_sync(self.handle, self.stream)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            fem_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

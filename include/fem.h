@@ -195,6 +195,23 @@ fem_status fem_read_fields(fem_problem_t p, float* h_host, void* stream);
 /* Copy every replica's argmax states to `states_host`, n*R int32, layout [n][R]. */
 fem_status fem_read_states(fem_problem_t p, int32_t* states_host, void* stream);
 
+/* Checkpoint: copy the fields h and the optimizer state to host buffers in the
+ * layout of the fields (any pointer may be NULL).  m holds Adam's first moment or
+ * the momentum buffer of RMSprop/SGD; v holds Adam's second moment or RMSprop's
+ * running square average.  Together with fem_problem_info's steps_done this is
+ * the complete state of an anneal.  Synchronises `stream`. */
+fem_status fem_read_state(fem_problem_t p, float* h, float* m, float* v, void* stream);
+
+/* Restore a checkpoint: overwrite h, m and v from host buffers (m or v NULL =
+ * zeros) and set the number of steps already run to `steps_done`
+ * (0 <= steps_done <= n_steps), so that the next fem_anneal resumes with
+ * t_begin = steps_done.  The problem must already be initialised by a
+ * fem_anneal call with t_begin == 0, which fixes R, N_step, the gradient mode and
+ * the optimizer (FEM_ERR_STATE otherwise).  Derived per-step data (discretised
+ * states, group counts) are recomputed from h.  Synchronises `stream`. */
+fem_status fem_write_state(fem_problem_t p, const float* h, const float* m, const float* v,
+                           int32_t steps_done, void* stream);
+
 /* Number of steps run so far, and the problem's sizes (any pointer may be NULL):
  * n, q, R (0 before the first anneal), and the number of units one step processes
  * per replica (|E| undirected edges for graphs, n(n-1)/2 for dense_J, the

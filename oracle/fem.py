@@ -314,6 +314,9 @@ class Adam:
         vhat = self.v / (1.0 - self.b2 ** t)
         h -= self.lr * mhat / (np.sqrt(vhat) + self.eps)
 
+    def denominator(self, t):
+        return np.sqrt(self.v / (1.0 - self.b2 ** t)) + self.eps
+
 
 class RMSprop:
     """PyTorch RMSprop (not centred): g += wd h; v = a v + (1-a) g^2;
@@ -335,6 +338,9 @@ class RMSprop:
         else:
             h -= self.lr * g / avg
 
+    def denominator(self, t):
+        return np.sqrt(self.v) + self.eps
+
 
 class SGD:
     """PyTorch SGD (no Nesterov): g += wd h; with momentum mu != 0:
@@ -355,6 +361,9 @@ class SGD:
             g = self.buf
         h -= self.lr * g
 
+    def denominator(self, t):
+        return np.full(self.buf.shape, np.inf)
+
 
 def make_optimizer(name, shape, **kw):
     return {"adam": Adam, "rmsprop": RMSprop, "sgd": SGD}[name](shape, **kw)
@@ -368,12 +377,16 @@ def make_optimizer(name, shape, **kw):
 
 def anneal(problem, h0, n_step, *, t_begin=0, t_end=None, schedule="exponential",
            beta_min=0.05, beta_max=5.0, optimizer="adam", opt_kw=None, mode="paper",
-           gamma=1.0, lambda_max=1.0, opt=None, trace=None):
+           gamma=1.0, lambda_max=1.0, opt=None, trace=None, cond=None):
     """Run anneal steps t_begin .. t_end-1 from fields h0 (copied, float64).
 
     problem: ("maxcut", W) | ("bmincut", W) | ("sat", groups)
     Returns (h, opt); pass ``opt`` back in to resume.  ``trace``, if a dict
-    {t: None}, is filled with copies of h after step t (1-based count of steps done)."""
+    {t: None}, is filled with copies of h after step t (1-based count of steps done).
+    ``cond``, if a dict {t: None}, is filled with the elementwise minimum over the
+    steps up to t of the optimizer's denominator (a conditioning record for
+    comparisons in fp32: the update divides by it, so gradient rounding is
+    amplified where it is small)."""
     kind, data = problem
     t_end = n_step if t_end is None else t_end
     h = np.array(h0, dtype=np.float64, copy=True)
@@ -381,6 +394,7 @@ def anneal(problem, h0, n_step, *, t_begin=0, t_end=None, schedule="exponential"
     lams = lambda_ramp(lambda_max, n_step)
     if opt is None:
         opt = make_optimizer(optimizer, h.shape, **(opt_kw or {}))
+    gm = np.full(h.shape, np.inf) if cond is not None else None
     for t in range(t_begin, t_end):
         beta = betas[t]
         if kind == "maxcut":
@@ -392,6 +406,10 @@ def anneal(problem, h0, n_step, *, t_begin=0, t_end=None, schedule="exponential"
         else:
             raise ValueError(kind)
         opt.step(h, g, t + 1)
+        if gm is not None:
+            np.minimum(gm, opt.denominator(t + 1), out=gm)
+            if (t + 1) in cond:
+                cond[t + 1] = gm.copy()
         if trace is not None and (t + 1) in trace:
             trace[t + 1] = h.copy()
     return h, opt

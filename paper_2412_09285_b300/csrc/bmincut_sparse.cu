@@ -1,0 +1,576 @@
+// Balanced q-way MinCut on sparse graphs: the fused per-step kernel (softmax
+// marginals, neighbour contraction, balance term, chain rule, optimizer) and the
+// read-out of cut, group sizes and energy.
+//
+// Gradient (SM "The bMinCut problem" and Eq. gradients_wrt_h):
+//   g_i(s) = gamma [ghat_i(s) - sum_s' P_i(s') ghat_i(s')] P_i(s),  P_i = softmax(h_i)
+//   paper: ghat = -c^f_i sum_j W_ij e_j(s) + lambda c^a_i [n(s) - e_i(s)] + ln P_i(s)/beta
+//   exact: ghat = -2 sum_j W_ij P_j(s) + 2 lambda [sum_j P_j(s) - P_i(s)] + ln P_i(s)/beta
+// c^f = q/sum_j W_ij, c^a = q/sqrt(sum_j W_ij) (0 for isolated nodes).  The "+1" of
+// (ln P + 1)/beta and every other s-independent term cancel in the centred form
+// and are not evaluated.
+//
+// Layout: h, m, v are [n][R][q] fp32 (the q fields of one replica contiguous).
+// The argmax state of each (node, replica) is packed B bits wide (B = 1, 2, 4 for
+// q = 2, <= 4, <= 8) into uint32 words, R*B/32 words per node, ping-ponged between
+// steps.  The per-replica group counts n(s) = sum_j e_j(s) (paper mode) and the
+// fixed-point column sums sum_j P_j(s) * 2^32 (exact mode, integer atomics, so the
+// result does not depend on the order of the additions) are produced by step t for
+// step t+1 in a rotation of three buffers: step t reads buffer t%3, writes
+// (t+1)%3 and zeroes (t+2)%3 for the step after.
+#include <cmath>
+
+#include "fem_internal.h"
+#include "step_common.cuh"
+
+namespace fem {
+namespace {
+
+template <int Q>
+struct QBits {
+  static constexpr int B = Q <= 2 ? 1 : (Q <= 4 ? 2 : 4);
+  static constexpr int RPW = 32 / B;  // replicas per word
+  static constexpr uint32_t MASK = (1u << B) - 1u;
+};
+
+constexpr float kPsumScale = 4294967296.0f;         // 2^32
+constexpr float kPsumInv = 2.3283064365386963e-10f;  // 2^-32
+
+struct BmcArgs {
+  const int32_t* row_ptr;
+  const uint32_t* col;
+  const float* w;  // NULL for unit weights
+  const float* cf;
+  const float* ca;
+  int32_t n, R, wpn, opt;
+  const float* h_in;
+  float* h_out;
+  float* m;
+  float* v;
+  const uint32_t* words_in;
+  uint32_t* words_out;
+  const int32_t* cnt_in;
+  int32_t* cnt_out;
+  int32_t* cnt_zero;
+  const unsigned long long* ps_in;
+  unsigned long long* ps_out;
+  unsigned long long* ps_zero;
+};
+
+template <int Q>
+__device__ __forceinline__ void softmax_q(const float (&h)[Q], float (&P)[Q], float (&lnP)[Q]) {
+  float mx = h[0];
+#pragma unroll
+  for (int s = 1; s < Q; ++s) mx = fmaxf(mx, h[s]);
+  float ex[Q], Z = 0.f;
+#pragma unroll
+  for (int s = 0; s < Q; ++s) {
+    ex[s] = expf(h[s] - mx);
+    Z += ex[s];
+  }
+  const float invZ = 1.f / Z, lz = logf(Z);
+#pragma unroll
+  for (int s = 0; s < Q; ++s) {
+    P[s] = ex[s] * invZ;
+    lnP[s] = h[s] - mx - lz;
+  }
+}
+
+template <int Q>
+__device__ __forceinline__ int argmax_q(const float (&h)[Q]) {
+  int best = 0;
+  float bv = h[0];
+#pragma unroll
+  for (int s = 1; s < Q; ++s)
+    if (h[s] > bv) {
+      bv = h[s];
+      best = s;
+    }
+  return best;
+}
+
+template <int Q>
+__device__ __forceinline__ void load_q(const float* p, float (&x)[Q]) {
+  if (Q == 4) {
+    const float4 t = *reinterpret_cast<const float4*>(p);
+    x[0] = t.x; x[1] = t.y; x[2] = t.z; x[3] = t.w;
+  } else if (Q == 2) {
+    const float2 t = *reinterpret_cast<const float2*>(p);
+    x[0] = t.x; x[1] = t.y;
+  } else {
+#pragma unroll
+    for (int s = 0; s < Q; ++s) x[s] = p[s];
+  }
+}
+
+template <int Q>
+__device__ __forceinline__ void store_q(float* p, const float (&x)[Q]) {
+  if (Q == 4) {
+    *reinterpret_cast<float4*>(p) = make_float4(x[0], x[1], x[2], x[3]);
+  } else if (Q == 2) {
+    *reinterpret_cast<float2*>(p) = make_float2(x[0], x[1]);
+  } else {
+#pragma unroll
+    for (int s = 0; s < Q; ++s) p[s] = x[s];
+  }
+}
+
+// One thread per (node, replica); a warp covers 32 consecutive (node, replica)
+// pairs, so R % RPW == 0 keeps every packed word inside one group of lanes.
+template <int Q, int MODE>
+__global__ void __launch_bounds__(256) k_bmincut_step(BmcArgs a, StepScalars s) {
+  constexpr int B = QBits<Q>::B, RPW = QBits<Q>::RPW;
+  constexpr uint32_t SM = QBits<Q>::MASK;
+  extern __shared__ unsigned long long smem_u64[];
+  const int RQ = a.R * Q;
+  unsigned long long* sps = smem_u64;                                // [R*Q] exact mode
+  int32_t* scnt = reinterpret_cast<int32_t*>(smem_u64 + (MODE == FEM_GRAD_EXACT ? RQ : 0));
+  for (int x = threadIdx.x; x < RQ; x += blockDim.x) {
+    scnt[x] = 0;
+    if (MODE == FEM_GRAD_EXACT) sps[x] = 0ull;
+  }
+  if (blockIdx.x == 0) {
+    for (int x = threadIdx.x; x < RQ; x += blockDim.x) {
+      a.cnt_zero[x] = 0;
+      if (MODE == FEM_GRAD_EXACT) a.ps_zero[x] = 0ull;
+    }
+  }
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  const long long total = (long long)a.n * a.R;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long base = (long long)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < total;
+       base += stride) {
+    const long long e = base + lane;
+    const bool act = e < total;
+    const int i = act ? (int)(e / a.R) : 0;
+    const int r = act ? (int)(e - (long long)i * a.R) : 0;
+    const int wsel = r / RPW, sh = (r % RPW) * B;
+    float h[Q], mm[Q], vv[Q];
+#pragma unroll
+    for (int q = 0; q < Q; ++q) h[q] = mm[q] = vv[q] = 0.f;
+    const size_t idx = ((size_t)i * a.R + r) * Q;
+    float acc[Q];
+#pragma unroll
+    for (int q = 0; q < Q; ++q) acc[q] = 0.f;
+    int own = 0;
+    float cf = 0.f, ca = 0.f;
+    if (act) {
+      load_q<Q>(a.h_in + idx, h);
+      load_q<Q>(a.m + idx, mm);
+      if (a.opt != FEM_OPT_SGD) load_q<Q>(a.v + idx, vv);
+      const int beg = a.row_ptr[i], end = a.row_ptr[i + 1];
+      if (MODE == FEM_GRAD_PAPER) {
+        own = (int)((a.words_in[(size_t)i * a.wpn + wsel] >> sh) & SM);
+        cf = a.cf[i];
+        ca = a.ca[i];
+        for (int k = beg; k < end; ++k) {
+          const uint32_t j = a.col[k] & 0x7fffffffu;
+          const float wk = a.w ? a.w[k] : 1.f;
+          const int sj = (int)((a.words_in[(size_t)j * a.wpn + wsel] >> sh) & SM);
+#pragma unroll
+          for (int q = 0; q < Q; ++q) acc[q] += (sj == q) ? wk : 0.f;
+        }
+      } else {
+        // accumulate sum_j W_ij (P_j(s) - 1/q): the constant drops out of every
+        // difference below, and the small deviations keep fp32 sums precise
+        for (int k = beg; k < end; ++k) {
+          const uint32_t j = a.col[k] & 0x7fffffffu;
+          const float wk = a.w ? a.w[k] : 1.f;
+          float hj[Q], Pj[Q], lj[Q];
+          load_q<Q>(a.h_in + ((size_t)j * a.R + r) * Q, hj);
+          softmax_q<Q>(hj, Pj, lj);
+#pragma unroll
+          for (int q = 0; q < Q; ++q) acc[q] = fmaf(wk, Pj[q] - 1.f / Q, acc[q]);
+        }
+      }
+    }
+    // Centred gradient ghat(s) - sum_s' P(s') ghat(s') = sum_s' P(s') [ghat(s) - ghat(s')],
+    // with every difference formed before it is scaled: integer count differences
+    // (paper), exact fixed-point column-sum differences (exact), ln P(s) - ln P(s') =
+    // h(s) - h(s').  Algebraically the formula above; in fp32 it avoids cancelling the
+    // large s-independent parts (deg/q, lambda N/q) of ghat.
+    float P[Q], lnP[Q];
+    softmax_q<Q>(h, P, lnP);
+    int32_t nc[Q];
+    unsigned long long ps[Q];
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+      if (MODE == FEM_GRAD_PAPER) nc[q] = act ? a.cnt_in[r * Q + q] - (own == q ? 1 : 0) : 0;
+      else ps[q] = act ? a.ps_in[r * Q + q] : 0ull;
+    }
+    float cen[Q];
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+      float c = 0.f;
+#pragma unroll
+      for (int q2 = 0; q2 < Q; ++q2) {
+        float d;
+        if (MODE == FEM_GRAD_PAPER) {
+          d = -cf * (acc[q] - acc[q2]) + s.lambda * ca * (float)(nc[q] - nc[q2]);
+        } else {
+          const float dcol = (float)(long long)(ps[q] - ps[q2]) * kPsumInv;
+          d = -2.f * (acc[q] - acc[q2]) + 2.f * s.lambda * (dcol - (P[q] - P[q2]));
+        }
+        d = fmaf(h[q] - h[q2], s.inv_beta, d);
+        c = fmaf(P[q2], d, c);
+      }
+      cen[q] = c;
+    }
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+      const float g = s.gq * cen[q] * P[q];
+      opt_update_rt(a.opt, h[q], mm[q], vv[q], g, s);
+    }
+    const int sn = argmax_q<Q>(h);
+    if (act) {
+      store_q<Q>(a.h_out + idx, h);
+      store_q<Q>(a.m + idx, mm);
+      if (a.opt != FEM_OPT_SGD) store_q<Q>(a.v + idx, vv);
+      atomicAdd(&scnt[r * Q + sn], 1);
+      if (MODE == FEM_GRAD_EXACT) {
+        float Pn[Q], ln[Q];
+        softmax_q<Q>(h, Pn, ln);
+#pragma unroll
+        for (int q = 0; q < Q; ++q) atomicAdd(&sps[r * Q + q], __float2ull_rn(Pn[q] * kPsumScale));
+      }
+    }
+    uint32_t word = act ? ((uint32_t)sn << sh) : 0u;
+#pragma unroll
+    for (int off = 1; off < RPW; off <<= 1) word |= __shfl_xor_sync(kFullMask, word, off);
+    if (act && (r % RPW) == 0) a.words_out[(size_t)i * a.wpn + wsel] = word;
+  }
+  __syncthreads();
+  for (int x = threadIdx.x; x < RQ; x += blockDim.x) {
+    if (scnt[x]) atomicAdd(&a.cnt_out[x], scnt[x]);
+    if (MODE == FEM_GRAD_EXACT && sps[x]) atomicAdd(&a.ps_out[x], sps[x]);
+  }
+}
+
+// From fields h: packed argmax words, group counts and fixed-point column sums.
+template <int Q>
+__global__ void __launch_bounds__(256) k_bmincut_derive(const float* __restrict__ h, int32_t n, int32_t R,
+                                                        int32_t wpn, uint32_t* __restrict__ words,
+                                                        int32_t* __restrict__ cnt,
+                                                        unsigned long long* __restrict__ ps) {
+  constexpr int B = QBits<Q>::B, RPW = QBits<Q>::RPW;
+  const int lane = threadIdx.x & 31;
+  const long long total = (long long)n * R;
+  for (long long base = (long long)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < total;
+       base += (long long)gridDim.x * blockDim.x) {
+    const long long e = base + lane;
+    const bool act = e < total;
+    const int i = act ? (int)(e / R) : 0;
+    const int r = act ? (int)(e - (long long)i * R) : 0;
+    float x[Q];
+#pragma unroll
+    for (int q = 0; q < Q; ++q) x[q] = 0.f;
+    if (act) load_q<Q>(h + ((size_t)i * R + r) * Q, x);
+    const int sn = argmax_q<Q>(x);
+    if (act) {
+      atomicAdd(&cnt[r * Q + sn], 1);
+      float P[Q], ln[Q];
+      softmax_q<Q>(x, P, ln);
+#pragma unroll
+      for (int q = 0; q < Q; ++q) atomicAdd(&ps[r * Q + q], __float2ull_rn(P[q] * kPsumScale));
+    }
+    uint32_t word = act ? ((uint32_t)sn << ((r % RPW) * B)) : 0u;
+#pragma unroll
+    for (int off = 1; off < RPW; off <<= 1) word |= __shfl_xor_sync(kFullMask, word, off);
+    if (act && (r % RPW) == 0) words[(size_t)i * wpn + r / RPW] = word;
+  }
+}
+
+// Per-block partial cut (undirected edges, j > i) and group sizes per replica.
+// Block = 16 nodes x 16 replicas; blockIdx.y selects the block of 16 replicas.
+// Each thread keeps its own (fixed) replica, so every sum runs in a fixed order.
+template <int Q, bool INTW>
+__global__ void __launch_bounds__(256) k_bmincut_cut_partial(
+    const int32_t* __restrict__ row_ptr, const uint32_t* __restrict__ col,
+    const float* __restrict__ w, const double* __restrict__ w64, const uint32_t* __restrict__ words,
+    int32_t n, int32_t R, int32_t wpn, int64_t* __restrict__ part_i, double* __restrict__ part_f,
+    int64_t* __restrict__ part_cnt) {
+  constexpr int B = QBits<Q>::B, RPW = QBits<Q>::RPW;
+  constexpr uint32_t SM = QBits<Q>::MASK;
+  __shared__ int64_t si[256];
+  __shared__ double sf[256];
+  __shared__ int32_t sc[256 * Q];
+  const int nl = threadIdx.x >> 4, rl = threadIdx.x & 15;
+  const int r = blockIdx.y * 16 + rl;
+  const int wsel = r / RPW, sh = (r % RPW) * B;
+  int64_t acc_i = 0;
+  double acc_f = 0.0;
+  int32_t cnt[Q];
+#pragma unroll
+  for (int q = 0; q < Q; ++q) cnt[q] = 0;
+  for (int i = blockIdx.x * 16 + nl; i < n; i += gridDim.x * 16) {
+    const int si_ = (int)((words[(size_t)i * wpn + wsel] >> sh) & SM);
+#pragma unroll
+    for (int q = 0; q < Q; ++q) cnt[q] += (si_ == q);
+    const int beg = row_ptr[i], end = row_ptr[i + 1];
+    for (int k = beg; k < end; ++k) {
+      const int j = (int)(col[k] & 0x7fffffffu);
+      if (j <= i) continue;
+      const int sj = (int)((words[(size_t)j * wpn + wsel] >> sh) & SM);
+      if (sj == si_) continue;
+      if (INTW) acc_i += w ? (int64_t)w[k] : 1;
+      else acc_f += w64[k];
+    }
+  }
+  si[threadIdx.x] = acc_i;
+  sf[threadIdx.x] = acc_f;
+#pragma unroll
+  for (int q = 0; q < Q; ++q) sc[threadIdx.x * Q + q] = cnt[q];
+  __syncthreads();
+  if (nl == 0) {
+    int64_t ti = 0;
+    double tf = 0.0;
+    int64_t tc[Q];
+#pragma unroll
+    for (int q = 0; q < Q; ++q) tc[q] = 0;
+    for (int k = 0; k < 16; ++k) {
+      ti += si[k * 16 + rl];
+      tf += sf[k * 16 + rl];
+#pragma unroll
+      for (int q = 0; q < Q; ++q) tc[q] += sc[(k * 16 + rl) * Q + q];
+    }
+    const size_t o = (size_t)blockIdx.x * R + r;
+    part_i[o] = ti;
+    part_f[o] = tf;
+#pragma unroll
+    for (int q = 0; q < Q; ++q) part_cnt[o * Q + q] = tc[q];
+  }
+}
+
+// E_r = cut_r + lambda_max * sum_s n_s (n_s - 1), then argmin (lowest index on ties).
+template <int Q>
+__global__ void __launch_bounds__(1024) k_bmincut_finish(
+    const int64_t* __restrict__ part_i, const double* __restrict__ part_f,
+    const int64_t* __restrict__ part_cnt, int32_t nblk, int32_t R, int32_t intw, int32_t lam_is_int,
+    double lam, int64_t* __restrict__ e_i, double* __restrict__ e_f, int32_t* __restrict__ best) {
+  __shared__ double sval[1024];
+  __shared__ int sidx[1024];
+  double bv = 0.0;
+  int bidx = 0x7fffffff;
+  for (int r = threadIdx.x; r < R; r += blockDim.x) {
+    int64_t ci = 0;
+    double cfv = 0.0;
+    int64_t sz[Q];
+#pragma unroll
+    for (int q = 0; q < Q; ++q) sz[q] = 0;
+    for (int b = 0; b < nblk; ++b) {
+      const size_t o = (size_t)b * R + r;
+      ci += part_i[o];
+      cfv += part_f[o];
+#pragma unroll
+      for (int q = 0; q < Q; ++q) sz[q] += part_cnt[o * Q + q];
+    }
+    int64_t bal = 0;
+#pragma unroll
+    for (int q = 0; q < Q; ++q) bal += sz[q] * (sz[q] - 1);
+    double ef;
+    if (intw && lam_is_int) {
+      const int64_t ei = ci + (int64_t)lam * bal;
+      e_i[r] = ei;
+      ef = (double)ei;
+    } else {
+      e_i[r] = 0;
+      ef = (intw ? (double)ci : cfv) + lam * (double)bal;
+    }
+    e_f[r] = ef;
+    if (bidx == 0x7fffffff || ef < bv) {
+      bv = ef;
+      bidx = r;
+    }
+  }
+  sval[threadIdx.x] = bv;
+  sidx[threadIdx.x] = bidx;
+  __syncthreads();
+  for (int off = blockDim.x / 2; off > 0; off >>= 1) {
+    if (threadIdx.x < off) {
+      const double ov = sval[threadIdx.x + off];
+      const int oi = sidx[threadIdx.x + off];
+      const int mi = sidx[threadIdx.x];
+      if (oi != 0x7fffffff &&
+          (mi == 0x7fffffff || ov < sval[threadIdx.x] || (ov == sval[threadIdx.x] && oi < mi))) {
+        sval[threadIdx.x] = ov;
+        sidx[threadIdx.x] = oi;
+      }
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) best[0] = sidx[0];
+}
+
+template <int Q>
+__global__ void k_bmincut_states(const uint32_t* __restrict__ words, int32_t n, int32_t R,
+                                 int32_t wpn, const int32_t* __restrict__ best, int32_t* __restrict__ out,
+                                 int32_t all) {
+  constexpr int B = QBits<Q>::B, RPW = QBits<Q>::RPW;
+  constexpr uint32_t SM = QBits<Q>::MASK;
+  const size_t total = all ? (size_t)n * R : (size_t)n;
+  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (size_t)gridDim.x * blockDim.x) {
+    const size_t i = all ? e / R : e;
+    const int r = all ? (int)(e - i * R) : best[0];
+    out[e] = (int32_t)((words[i * wpn + r / RPW] >> ((r % RPW) * B)) & SM);
+  }
+}
+
+template <typename K>
+int resident_grid(K kernel, int sm_count, long long threads, size_t smem) {
+  int per_sm = 1;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, 256, smem) != cudaSuccess ||
+      per_sm < 1)
+    per_sm = 1;
+  long long blocks = (threads + 255) / 256;
+  const long long cap = (long long)per_sm * sm_count;
+  if (blocks > cap) blocks = cap;
+  return (int)(blocks < 1 ? 1 : blocks);
+}
+
+template <int Q>
+fem_status steps_q(Problem* p, const std::vector<StepScalars>& sc, int t_begin, cudaStream_t st) {
+  BmcArgs a{};
+  a.row_ptr = p->row_ptr;
+  a.col = p->col;
+  a.w = p->unit_w ? nullptr : p->w;
+  a.cf = p->cnorm;
+  a.ca = p->cnorm2;
+  a.n = p->n;
+  a.R = p->R;
+  a.wpn = p->words_per_node;
+  a.opt = p->optimizer;
+  a.m = p->m;
+  a.v = p->v;
+  const bool exact = p->grad_mode == FEM_GRAD_EXACT;
+  const size_t smem = (size_t)p->R * Q * (exact ? 12 : 4);
+  auto kern = exact ? k_bmincut_step<Q, FEM_GRAD_EXACT> : k_bmincut_step<Q, FEM_GRAD_PAPER>;
+  if (smem > 48 * 1024) FEM_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  const int grid = resident_grid(kern, p->sm_count, (long long)p->n * p->R, smem);
+  for (size_t k = 0; k < sc.size(); ++k) {
+    const int t = t_begin + (int)k;
+    a.h_in = exact ? p->h[t & 1] : p->h[0];
+    a.h_out = exact ? p->h[(t + 1) & 1] : p->h[0];
+    a.words_in = p->words[t & 1];
+    a.words_out = p->words[(t + 1) & 1];
+    a.cnt_in = p->cnt[t % 3];
+    a.cnt_out = p->cnt[(t + 1) % 3];
+    a.cnt_zero = p->cnt[(t + 2) % 3];
+    a.ps_in = p->psum[t % 3];
+    a.ps_out = p->psum[(t + 1) % 3];
+    a.ps_zero = p->psum[(t + 2) % 3];
+    kern<<<grid, 256, smem, st>>>(a, sc[k]);
+  }
+  count_launches((int64_t)sc.size());
+  FEM_CUDA(cudaGetLastError());
+  return FEM_OK;
+}
+
+// Derived data for step t from the fields step t reads: words[t%2], counts and
+// column sums in buffer t%3; buffer (t+1)%3, which step t accumulates into, is zeroed.
+template <int Q>
+fem_status derive_q(Problem* p, int t, cudaStream_t st) {
+  const size_t rq = (size_t)p->R * Q;
+  const float* h = p->grad_mode == FEM_GRAD_PAPER ? p->h[0] : p->h[t & 1];
+  for (int b : {t % 3, (t + 1) % 3}) {
+    FEM_CUDA(cudaMemsetAsync(p->cnt[b], 0, rq * sizeof(int32_t), st));
+    FEM_CUDA(cudaMemsetAsync(p->psum[b], 0, rq * sizeof(unsigned long long), st));
+  }
+  const int grid = resident_grid(k_bmincut_derive<Q>, p->sm_count, (long long)p->n * p->R, 0);
+  k_bmincut_derive<Q><<<grid, 256, 0, st>>>(h, p->n, p->R, p->words_per_node, p->words[t & 1],
+                                           p->cnt[t % 3], p->psum[t % 3]);
+  count_launches(1);
+  FEM_CUDA(cudaGetLastError());
+  return FEM_OK;
+}
+
+template <int Q>
+fem_status readout_q(Problem* p, cudaStream_t st) {
+  const dim3 grid(p->part_blocks, p->R / 16);
+  const uint32_t* words = p->words[p->steps_done & 1];
+  if (p->int_w)
+    k_bmincut_cut_partial<Q, true><<<grid, 256, 0, st>>>(p->row_ptr, p->col, p->unit_w ? nullptr : p->w,
+                                                         p->w64, words, p->n, p->R, p->words_per_node,
+                                                         p->part_i, p->part_f, p->part_cnt);
+  else
+    k_bmincut_cut_partial<Q, false><<<grid, 256, 0, st>>>(p->row_ptr, p->col, p->unit_w ? nullptr : p->w,
+                                                          p->w64, words, p->n, p->R, p->words_per_node,
+                                                          p->part_i, p->part_f, p->part_cnt);
+  const double lam = p->lambda_max;
+  k_bmincut_finish<Q><<<1, 1024, 0, st>>>(p->part_i, p->part_f, p->part_cnt, p->part_blocks, p->R,
+                                          p->int_w ? 1 : 0, lam == std::floor(lam) ? 1 : 0, lam,
+                                          p->energy_i, p->energy_f, p->best);
+  k_bmincut_states<Q><<<(p->n + 255) / 256 < 1024 ? (p->n + 255) / 256 : 1024, 256, 0, st>>>(
+      words, p->n, p->R, p->words_per_node, p->best, p->states_dev, 0);
+  count_launches(3);
+  FEM_CUDA(cudaGetLastError());
+  return FEM_OK;
+}
+
+template <int Q>
+fem_status states_q(Problem* p, int32_t* out, cudaStream_t st) {
+  const size_t total = (size_t)p->n * p->R;
+  size_t blocks = (total + 255) / 256;
+  if (blocks > (size_t)p->sm_count * 16) blocks = (size_t)p->sm_count * 16;
+  k_bmincut_states<Q><<<(int)blocks, 256, 0, st>>>(p->words[p->steps_done & 1], p->n, p->R,
+                                                   p->words_per_node, p->best, out, 1);
+  count_launches(1);
+  FEM_CUDA(cudaGetLastError());
+  return FEM_OK;
+}
+
+}  // namespace
+
+int bmincut_bits(int q) { return q <= 2 ? 1 : (q <= 4 ? 2 : 4); }
+
+fem_status bmincut_sparse_steps(Problem* p, const std::vector<StepScalars>& sc, int t_begin,
+                                cudaStream_t s) {
+  switch (p->q) {
+    case 2: return steps_q<2>(p, sc, t_begin, s);
+    case 3: return steps_q<3>(p, sc, t_begin, s);
+    case 4: return steps_q<4>(p, sc, t_begin, s);
+    case 5: return steps_q<5>(p, sc, t_begin, s);
+    case 6: return steps_q<6>(p, sc, t_begin, s);
+    case 7: return steps_q<7>(p, sc, t_begin, s);
+    default: return steps_q<8>(p, sc, t_begin, s);
+  }
+}
+
+fem_status bmincut_derive(Problem* p, int t, cudaStream_t s) {
+  switch (p->q) {
+    case 2: return derive_q<2>(p, t, s);
+    case 3: return derive_q<3>(p, t, s);
+    case 4: return derive_q<4>(p, t, s);
+    case 5: return derive_q<5>(p, t, s);
+    case 6: return derive_q<6>(p, t, s);
+    case 7: return derive_q<7>(p, t, s);
+    default: return derive_q<8>(p, t, s);
+  }
+}
+
+fem_status bmincut_readout(Problem* p, cudaStream_t s) {
+  switch (p->q) {
+    case 2: return readout_q<2>(p, s);
+    case 3: return readout_q<3>(p, s);
+    case 4: return readout_q<4>(p, s);
+    case 5: return readout_q<5>(p, s);
+    case 6: return readout_q<6>(p, s);
+    case 7: return readout_q<7>(p, s);
+    default: return readout_q<8>(p, s);
+  }
+}
+
+fem_status bmincut_states_all(Problem* p, int32_t* out, cudaStream_t s) {
+  switch (p->q) {
+    case 2: return states_q<2>(p, out, s);
+    case 3: return states_q<3>(p, out, s);
+    case 4: return states_q<4>(p, out, s);
+    case 5: return states_q<5>(p, out, s);
+    case 6: return states_q<6>(p, out, s);
+    case 7: return states_q<7>(p, out, s);
+    default: return states_q<8>(p, out, s);
+  }
+}
+
+}  // namespace fem

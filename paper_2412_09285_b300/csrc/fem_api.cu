@@ -120,6 +120,14 @@ fem_status maxcut_pack_words(Problem* p, int hbuf, int wbuf, cudaStream_t s);
 const float* maxcut_current_fields(const Problem* p);
 fem_status maxcut_states_all(Problem* p, int32_t* out_dev, cudaStream_t s);
 
+// The field buffer step `steps_done` reads.  Paper-mode graph problems and
+// Max-k-SAT update h in place; exact-mode graph problems ping-pong it.
+static float* fields_for_step(Problem* p, int t) {
+  if (p->kind == FEM_MAXKSAT || p->grad_mode == FEM_GRAD_PAPER) return p->h[0];
+  return p->h[t & 1];
+}
+static const float* current_fields(Problem* p) { return fields_for_step(p, p->steps_done); }
+
 // ---------------------------------------------------------------------------
 // Graph builder: validated undirected edge list -> CSR of directed entries.
 // Host-only (no CUDA call), so malformed input is rejected before any device work.
@@ -225,6 +233,69 @@ static fem_status upload_graph(Problem* p, const HostGraph& g, cudaStream_t s) {
   return FEM_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Clause builder: DIMACS-style clause list -> packed literals and the
+// variable -> occurrence transpose (occurrences in clause order).  Host-only.
+// ---------------------------------------------------------------------------
+struct HostSat {
+  int64_t n_clauses = 0;
+  int32_t max_width = 0;
+  std::vector<int32_t> cl_ptr, cl_lit, occ_ptr, occ;
+};
+
+static fem_status host_sat(const fem_problem_desc* d, HostSat& g) {
+  const int32_t n = d->n;
+  const int64_t M = d->n_clauses;
+  if (M < 0) return fail(FEM_ERR_INVALID_ARG, "n_clauses < 0");
+  if (M > 0 && (!d->clause_ptr || !d->lits)) return fail(FEM_ERR_INVALID_ARG, "clause_ptr/lits must be non-NULL");
+  if (M >= (1ll << 28)) return fail(FEM_ERR_UNSUPPORTED, "at most 2^28 - 1 clauses");
+  const int64_t L = M > 0 ? d->clause_ptr[M] : 0;
+  if (M > 0 && d->clause_ptr[0] != 0) return fail(FEM_ERR_INVALID_ARG, "clause_ptr[0] must be 0");
+  if (L < 0 || L >= (int64_t)INT32_MAX) return fail(FEM_ERR_UNSUPPORTED, "literal count must be < 2^31");
+  g.cl_ptr.assign(M + 1, 0);
+  g.cl_lit.assign(L, 0);
+  std::vector<int32_t> cnt(n + 1, 0);
+  for (int64_t c = 0; c < M; ++c) {
+    const int64_t b = d->clause_ptr[c], e = d->clause_ptr[c + 1];
+    if (e < b || e > L) return fail(FEM_ERR_INVALID_ARG, "clause_ptr must be non-decreasing and end at the literal count");
+    if (e - b > 8) return fail(FEM_ERR_UNSUPPORTED, "clause %lld has more than 8 literals", (long long)c);
+    g.max_width = std::max<int32_t>(g.max_width, (int32_t)(e - b));
+    g.cl_ptr[c + 1] = (int32_t)e;
+    for (int64_t k = b; k < e; ++k) {
+      const int32_t lit = d->lits[k];
+      if (lit == 0 || lit > n || lit < -n)
+        return fail(FEM_ERR_INVALID_ARG, "clause %lld: literal %d out of range", (long long)c, lit);
+      const int32_t v = std::abs(lit) - 1;
+      for (int64_t k2 = b; k2 < k; ++k2)
+        if (std::abs(d->lits[k2]) - 1 == v)
+          return fail(FEM_ERR_INVALID_ARG, "clause %lld repeats variable %d", (long long)c, v + 1);
+      g.cl_lit[k] = (v << 1) | (lit < 0 ? 1 : 0);
+      cnt[v]++;
+    }
+  }
+  g.occ_ptr.assign(n + 1, 0);
+  for (int32_t i = 0; i < n; ++i) g.occ_ptr[i + 1] = g.occ_ptr[i] + cnt[i];
+  g.occ.assign(L, 0);
+  std::vector<int32_t> fill(g.occ_ptr.begin(), g.occ_ptr.end() - 1);
+  for (int64_t c = 0; c < M; ++c)
+    for (int32_t k = g.cl_ptr[c]; k < g.cl_ptr[c + 1]; ++k)
+      g.occ[fill[g.cl_lit[k] >> 1]++] = (int32_t)((c << 3) | (k - g.cl_ptr[c]));
+  g.n_clauses = M;
+  return FEM_OK;
+}
+
+static fem_status upload_sat(Problem* p, const HostSat& g, cudaStream_t s) {
+  p->n_clauses = g.n_clauses;
+  p->n_occ = (int64_t)g.cl_lit.size();
+  p->max_width = g.max_width;
+  fem_status st;
+  if ((st = upload(p, &p->cl_ptr, g.cl_ptr, s)) != FEM_OK) return st;
+  if ((st = upload(p, &p->cl_lit, g.cl_lit, s)) != FEM_OK) return st;
+  if ((st = upload(p, &p->occ_ptr, g.occ_ptr, s)) != FEM_OK) return st;
+  if ((st = upload(p, &p->occ, g.occ, s)) != FEM_OK) return st;
+  return FEM_OK;
+}
+
 static fem_status ensure_state(Problem* p, int32_t R, cudaStream_t s) {
   const size_t per = (size_t)p->n * R * (p->kind == FEM_BMINCUT ? p->q : 1);
   if (p->R == R && p->h[0]) return FEM_OK;
@@ -233,14 +304,24 @@ static fem_status ensure_state(Problem* p, int32_t R, cudaStream_t s) {
     if ((st = dev_alloc_t(p, &p->h[b], per)) != FEM_OK) return st;
   if ((st = dev_alloc_t(p, &p->m, per)) != FEM_OK) return st;
   if ((st = dev_alloc_t(p, &p->v, per)) != FEM_OK) return st;
-  p->words_per_node = (p->kind == FEM_MAXCUT) ? R / 32 : 0;
-  if (p->words_per_node)
+  p->words_per_node = (p->kind == FEM_MAXCUT) ? R / 32
+                      : (p->kind == FEM_BMINCUT) ? R * bmincut_bits(p->q) / 32 : (R + 31) / 32;
+  for (int b = 0; b < 2; ++b)
+    if ((st = dev_alloc_t(p, &p->words[b], (size_t)p->n * p->words_per_node)) != FEM_OK) return st;
+  if (p->kind == FEM_BMINCUT) {
+    for (int b = 0; b < 3; ++b) {
+      if ((st = dev_alloc_t(p, &p->cnt[b], (size_t)R * p->q)) != FEM_OK) return st;
+      if ((st = dev_alloc_t(p, &p->psum[b], (size_t)R * p->q)) != FEM_OK) return st;
+    }
+  }
+  if (p->kind == FEM_MAXKSAT)
     for (int b = 0; b < 2; ++b)
-      if ((st = dev_alloc_t(p, &p->words[b], (size_t)p->n * p->words_per_node)) != FEM_OK) return st;
-  p->part_blocks = std::max(1, std::min((p->n + 7) / 8, p->sm_count * 4));
-  const size_t part = (size_t)p->part_blocks * R * (p->kind == FEM_BMINCUT ? (p->q + 1) : 1);
+      if ((st = dev_alloc_t(p, &p->satP[b], per)) != FEM_OK) return st;
+  p->part_blocks = std::max(1, std::min((p->n + 15) / 16, p->sm_count * 4));
+  const size_t part = (size_t)p->part_blocks * R;
   if ((st = dev_alloc_t(p, &p->part_i, part)) != FEM_OK) return st;
   if ((st = dev_alloc_t(p, &p->part_f, part)) != FEM_OK) return st;
+  if (p->kind == FEM_BMINCUT && (st = dev_alloc_t(p, &p->part_cnt, part * p->q)) != FEM_OK) return st;
   if ((st = dev_alloc_t(p, &p->energy_i, (size_t)R)) != FEM_OK) return st;
   if ((st = dev_alloc_t(p, &p->energy_f, (size_t)R)) != FEM_OK) return st;
   if ((st = dev_alloc_t(p, &p->best, 1)) != FEM_OK) return st;
@@ -306,11 +387,12 @@ fem_status fem_create_problem(const fem_problem_desc* d, void* stream, fem_probl
   cudaStream_t s = (cudaStream_t)stream;
   // 1. host-side validation and construction (no CUDA call yet)
   HostGraph hg;
+  HostSat hs;
   fem_status st = FEM_OK;
   if (d->kind == FEM_MAXCUT && d->dense_J) {
     return fail(FEM_ERR_UNSUPPORTED, "dense couplings are not built in this library version");
   } else if (d->kind == FEM_MAXKSAT) {
-    return fail(FEM_ERR_UNSUPPORTED, "Max-k-SAT is not built in this library version");
+    if ((st = host_sat(d, hs)) != FEM_OK) return st;
   } else {
     if ((st = host_graph(d->kind, d->q, d, hg)) != FEM_OK) return st;
   }
@@ -321,7 +403,7 @@ fem_status fem_create_problem(const fem_problem_desc* d, void* stream, fem_probl
   p->q = d->q;
   FEM_CUDA(cudaGetDevice(&p->device));
   FEM_CUDA(cudaDeviceGetAttribute(&p->sm_count, cudaDevAttrMultiProcessorCount, p->device));
-  st = upload_graph(p.get(), hg, s);
+  st = d->kind == FEM_MAXKSAT ? upload_sat(p.get(), hs, s) : upload_graph(p.get(), hg, s);
   if (st == FEM_OK) st = dev_alloc_t(p.get(), &p->err, 1);
   if (st == FEM_OK) {
     const cudaError_t e1 = cudaMemsetAsync(p->err, 0, sizeof(int32_t), s);
@@ -355,6 +437,13 @@ fem_status fem_anneal(fem_problem_t p, const fem_anneal_params* a, void* stream)
   if (R < 1) return fail(FEM_ERR_INVALID_ARG, "replicas must be >= 1");
   if (p->kind == FEM_MAXCUT && R % 32 != 0)
     return fail(FEM_ERR_UNSUPPORTED, "sparse MaxCut needs replicas %% 32 == 0");
+  if (p->kind == FEM_BMINCUT) {
+    const int rpw = 32 / bmincut_bits(p->q);
+    if (R % 16 != 0 || R % rpw != 0 || R > 1024)
+      return fail(FEM_ERR_UNSUPPORTED, "bMinCut needs replicas %% 16 == 0, %% %d == 0 and <= 1024", rpw);
+    if (!(a->lambda_max >= 0) || !std::isfinite(a->lambda_max))
+      return fail(FEM_ERR_INVALID_ARG, "lambda_max must be finite and >= 0");
+  }
   int cur_dev = 0;
   FEM_CUDA(cudaGetDevice(&cur_dev));
   if (cur_dev != p->device) return fail(FEM_ERR_STATE, "the current device is not the problem's device");
@@ -374,8 +463,13 @@ fem_status fem_anneal(fem_problem_t p, const fem_anneal_params* a, void* stream)
     p->grad_mode = a->grad_mode;
     p->optimizer = a->optimizer;
     p->precision = a->precision;
+    p->lambda_max = a->lambda_max;
     if (p->kind == FEM_MAXCUT) {
       if ((st = maxcut_pack_words(p, 0, 0, s)) != FEM_OK) return st;
+    } else if (p->kind == FEM_BMINCUT) {
+      if ((st = bmincut_derive(p, 0, s)) != FEM_OK) return st;
+    } else {
+      if ((st = sat_marginals(p, 0, s)) != FEM_OK) return st;
     }
     if (!a->h_init_is_device) FEM_CUDA(cudaStreamSynchronize(s));  // h_init may be pageable
     p->initialised = true;
@@ -390,6 +484,8 @@ fem_status fem_anneal(fem_problem_t p, const fem_anneal_params* a, void* stream)
   const std::vector<StepScalars> sc = make_step_scalars(*a, p->kind != FEM_BMINCUT);
   fem_status st = FEM_OK;
   if (p->kind == FEM_MAXCUT) st = maxcut_sparse_steps(p, *a, sc, s);
+  else if (p->kind == FEM_BMINCUT) st = bmincut_sparse_steps(p, sc, a->t_begin, s);
+  else if (p->kind == FEM_MAXKSAT) st = sat_steps(p, sc, a->t_begin, s);
   else st = fail(FEM_ERR_UNSUPPORTED, "problem kind not built in this library version");
   if (st != FEM_OK) return st;
   p->steps_done = a->t_end;
@@ -404,6 +500,8 @@ fem_status fem_read_best(fem_problem_t p, int32_t* best_replica, int32_t* states
   cudaStream_t s = (cudaStream_t)stream;
   fem_status st = FEM_OK;
   if (p->kind == FEM_MAXCUT) st = maxcut_readout(p, s);
+  else if (p->kind == FEM_BMINCUT) st = bmincut_readout(p, s);
+  else if (p->kind == FEM_MAXKSAT) st = sat_readout(p, s);
   else st = fail(FEM_ERR_UNSUPPORTED, "problem kind not built");
   if (st != FEM_OK) return st;
   if (best_replica) FEM_CUDA(cudaMemcpyAsync(best_replica, p->best, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
@@ -419,7 +517,7 @@ fem_status fem_read_fields(fem_problem_t p, float* h_host, void* stream) {
   if (!p->initialised) return fail(FEM_ERR_STATE, "no fields before the first anneal call");
   cudaStream_t s = (cudaStream_t)stream;
   const size_t per = (size_t)p->n * p->R * (p->kind == FEM_BMINCUT ? p->q : 1);
-  const float* src = p->kind == FEM_MAXCUT ? maxcut_current_fields(p) : p->h[p->cur];
+  const float* src = current_fields(p);
   FEM_CUDA(cudaMemcpyAsync(h_host, src, per * sizeof(float), cudaMemcpyDeviceToHost, s));
   return check_sticky(p, s);
 }
@@ -434,6 +532,8 @@ fem_status fem_read_states(fem_problem_t p, int32_t* states_host, void* stream) 
   FEM_CUDA(cudaMallocAsync((void**)&tmp, total * sizeof(int32_t), s));
   fem_status st = FEM_OK;
   if (p->kind == FEM_MAXCUT) st = maxcut_states_all(p, tmp, s);
+  else if (p->kind == FEM_BMINCUT) st = bmincut_states_all(p, tmp, s);
+  else if (p->kind == FEM_MAXKSAT) st = sat_states_all(p, tmp, s);
   else st = fail(FEM_ERR_UNSUPPORTED, "problem kind not built");
   if (st == FEM_OK) {
     const cudaError_t e = cudaMemcpyAsync(states_host, tmp, total * sizeof(int32_t), cudaMemcpyDeviceToHost, s);
@@ -441,6 +541,50 @@ fem_status fem_read_states(fem_problem_t p, int32_t* states_host, void* stream) 
   }
   cudaFreeAsync(tmp, s);
   if (st != FEM_OK) return st;
+  return check_sticky(p, s);
+}
+
+fem_status fem_read_state(fem_problem_t p, float* h, float* m, float* v, void* stream) {
+  g_last_error.clear();
+  if (!p) return fail(FEM_ERR_INVALID_ARG, "problem must be non-NULL");
+  if (!p->initialised) return fail(FEM_ERR_STATE, "no state before the first anneal call");
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t bytes = (size_t)p->n * p->R * (p->kind == FEM_BMINCUT ? p->q : 1) * sizeof(float);
+  const float* src = current_fields(p);
+  if (h) FEM_CUDA(cudaMemcpyAsync(h, src, bytes, cudaMemcpyDeviceToHost, s));
+  if (m) FEM_CUDA(cudaMemcpyAsync(m, p->m, bytes, cudaMemcpyDeviceToHost, s));
+  if (v) FEM_CUDA(cudaMemcpyAsync(v, p->v, bytes, cudaMemcpyDeviceToHost, s));
+  return check_sticky(p, s);
+}
+
+fem_status fem_write_state(fem_problem_t p, const float* h, const float* m, const float* v,
+                           int32_t steps_done, void* stream) {
+  g_last_error.clear();
+  if (!p || !h) return fail(FEM_ERR_INVALID_ARG, "problem and h must be non-NULL");
+  if (!p->initialised) return fail(FEM_ERR_STATE, "fem_write_state needs an initialised problem");
+  if (steps_done < 0 || steps_done > p->n_steps)
+    return fail(FEM_ERR_INVALID_ARG, "steps_done must be in [0, n_steps]");
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t bytes = (size_t)p->n * p->R * (p->kind == FEM_BMINCUT ? p->q : 1) * sizeof(float);
+  const int t = steps_done;
+  float* dst = fields_for_step(p, t);
+  FEM_CUDA(cudaMemcpyAsync(dst, h, bytes, cudaMemcpyHostToDevice, s));
+  if (m) FEM_CUDA(cudaMemcpyAsync(p->m, m, bytes, cudaMemcpyHostToDevice, s));
+  else FEM_CUDA(cudaMemsetAsync(p->m, 0, bytes, s));
+  if (v) FEM_CUDA(cudaMemcpyAsync(p->v, v, bytes, cudaMemcpyHostToDevice, s));
+  else FEM_CUDA(cudaMemsetAsync(p->v, 0, bytes, s));
+  fem_status st = FEM_OK;
+  if (p->kind == FEM_MAXCUT) {
+    p->cur = t & 1;
+    st = maxcut_pack_words(p, p->grad_mode == FEM_GRAD_PAPER ? 0 : (t & 1), t & 1, s);
+  } else if (p->kind == FEM_BMINCUT) {
+    st = bmincut_derive(p, t, s);
+  } else {
+    st = sat_marginals(p, t, s);
+  }
+  if (st != FEM_OK) return st;
+  FEM_CUDA(cudaStreamSynchronize(s));
+  p->steps_done = steps_done;
   return check_sticky(p, s);
 }
 

@@ -74,12 +74,16 @@ struct Problem {
   uint32_t* words[2] = {nullptr, nullptr};
   int32_t words_per_node = 0;
   void* mt[2] = {nullptr, nullptr};    // dense: discretised marginals for the tensor cores
-  int32_t* cnt[2] = {nullptr, nullptr};  // bMinCut per-replica group counts [R][q]
+  int32_t* cnt[3] = {nullptr, nullptr, nullptr};  // bMinCut group counts n_r(s), [R][q], rotating
+  unsigned long long* psum[3] = {nullptr, nullptr, nullptr};  // bMinCut 2^32 * sum_j P_j(s)
+  double lambda_max = 0.0;
+  float* satP[2] = {nullptr, nullptr};  // Max-k-SAT marginals P = sigmoid(h), ping-ponged
 
   // ---- readout scratch
   int32_t part_blocks = 0;
-  int64_t* part_i = nullptr;   // [part_blocks][R] (or [part_blocks][R][q+1])
+  int64_t* part_i = nullptr;   // [part_blocks][R]
   double* part_f = nullptr;
+  int64_t* part_cnt = nullptr; // [part_blocks][R][q] (bMinCut group sizes)
   int64_t* energy_i = nullptr; // [R]
   double* energy_f = nullptr;  // [R]
   int32_t* best = nullptr;     // [1]
@@ -117,8 +121,19 @@ fem_status maxcut_sparse_steps(Problem* p, const fem_anneal_params& a,
                                const std::vector<StepScalars>& sc, cudaStream_t s);
 fem_status maxcut_readout(Problem* p, cudaStream_t s);
 
-// ---- readout common (readout.cu)
-fem_status finish_argmin(Problem* p, cudaStream_t s);
+// ---- bMinCut sparse (bmincut_sparse.cu)
+int bmincut_bits(int q);
+fem_status bmincut_sparse_steps(Problem* p, const std::vector<StepScalars>& sc, int t_begin,
+                                cudaStream_t s);
+fem_status bmincut_derive(Problem* p, int t, cudaStream_t s);
+fem_status bmincut_readout(Problem* p, cudaStream_t s);
+fem_status bmincut_states_all(Problem* p, int32_t* out, cudaStream_t s);
+
+// ---- Max-k-SAT (sat.cu)
+fem_status sat_marginals(Problem* p, int t, cudaStream_t s);
+fem_status sat_steps(Problem* p, const std::vector<StepScalars>& sc, int t_begin, cudaStream_t s);
+fem_status sat_readout(Problem* p, cudaStream_t s);
+fem_status sat_states_all(Problem* p, int32_t* out, cudaStream_t s);
 
 }  // namespace fem
 

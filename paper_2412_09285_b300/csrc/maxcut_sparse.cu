@@ -110,6 +110,105 @@ __global__ void __launch_bounds__(256) k_maxcut_step(MaxcutArgs a, StepScalars s
   }
 }
 
+// Paper-mode step, tuned for HBM streaming.  A warp owns NPW consecutive nodes
+// (one block of 32 replicas) per iteration and issues every load of the group
+// before it computes: the 3*NPW state lines (h, m, v), then one coalesced load
+// of up to 32 CSR entries covering the whole group, then 32 parallel gathers of
+// the neighbours' sign words.  The row pointers of the next group are fetched a
+// group ahead.  Each gathered word is pre-XORed with the weight sign (unit
+// weights), so one shuffle and one bit test per edge give the neighbour term:
+//   sum_j W_ij sgn(m_j) = deg_i - 2 * #{j : W_ij sgn(m_j) = -1}.
+template <int OPT, bool UNIT, int NPW>
+__global__ void __launch_bounds__(256) k_maxcut_step_paper(MaxcutArgs a, StepScalars s) {
+  const int lane = threadIdx.x & 31;
+  const int ngroups = (a.n + NPW - 1) / NPW;
+  const long long total = (long long)ngroups * a.wpn;
+  const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+  long long g = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  auto row_ptrs = [&](long long gg) -> int {
+    if (gg >= total) return 0;
+    const int ng = a.wpn == 1 ? (int)gg : (int)(gg / a.wpn);
+    return lane <= NPW ? __ldg(a.row_ptr + min(ng * NPW + lane, a.n)) : 0;
+  };
+  int rp = row_ptrs(g);
+  for (; g < total; g += nwarps) {
+    const int ng = a.wpn == 1 ? (int)g : (int)(g / a.wpn);
+    const int wb = a.wpn == 1 ? 0 : (int)(g - (long long)ng * a.wpn);
+    const int i0 = ng * NPW;
+    float h[NPW], m[NPW], v[NPW];
+#pragma unroll
+    for (int k = 0; k < NPW; ++k) {
+      h[k] = 0.f; m[k] = 0.f; v[k] = 0.f;
+      if (i0 + k < a.n) {
+        const size_t idx = (size_t)(i0 + k) * a.R + (size_t)wb * 32 + lane;
+        h[k] = a.h_in[idx];
+        m[k] = a.m[idx];
+        if (OPT != FEM_OPT_SGD) v[k] = a.v[idx];
+      }
+    }
+    int rb[NPW + 1];
+#pragma unroll
+    for (int k = 0; k <= NPW; ++k) rb[k] = __shfl_sync(kFullMask, rp, k);
+    rp = row_ptrs(g + nwarps);  // prefetch the next group's row pointers
+    const int bN = rb[NPW];
+    int cb = rb[0];
+    uint32_t adj = 0;
+    float wv = 0.f;
+    auto load_chunk = [&](int base) {
+      const int e = base + lane;
+      adj = 0;
+      wv = 0.f;
+      if (e < bN) {
+        const uint32_t c = __ldg(a.col + e);
+        const uint32_t wd = __ldg(a.words_in + (size_t)(c & 0x7fffffffu) * a.wpn + wb);
+        if (UNIT) {
+          adj = wd ^ (0u - (c >> 31));
+        } else {
+          adj = wd;
+          wv = __ldg(a.w + e);
+        }
+      }
+    };
+    load_chunk(cb);
+    uint32_t ball[NPW];
+#pragma unroll
+    for (int k = 0; k < NPW; ++k) {
+      int nneg = 0;
+      float facc = 0.f;
+      for (int e = rb[k]; e < rb[k + 1]; ++e) {
+        if (e >= cb + 32) {
+          cb += 32;
+          load_chunk(cb);
+        }
+        const uint32_t bit = (__shfl_sync(kFullMask, adj, e - cb) >> lane) & 1u;
+        if (UNIT) {
+          nneg += (int)bit;
+        } else {
+          const float w = __shfl_sync(kFullMask, wv, e - cb);
+          facc += bit ? -w : w;
+        }
+      }
+      const int deg = rb[k + 1] - rb[k];
+      const float field = UNIT ? (deg > 0 ? __fdividef((float)(deg - 2 * nneg), (float)deg) : 0.f)
+                               : (a.cnorm[min(i0 + k, a.n - 1)] * facc);
+      float hk = h[k], mk = m[k], vk = v[k];
+      const float gk = s.gq * (field + hk * s.inv_beta) * one_minus_m2_fast(hk);
+      opt_update_fast<OPT>(hk, mk, vk, gk, s);
+      ball[k] = __ballot_sync(kFullMask, hk < 0.f);
+      if (i0 + k < a.n) {
+        const size_t idx = (size_t)(i0 + k) * a.R + (size_t)wb * 32 + lane;
+        a.h_out[idx] = hk;
+        a.m[idx] = mk;
+        if (OPT != FEM_OPT_SGD) a.v[idx] = vk;
+      }
+    }
+    uint32_t mine = ball[0];
+#pragma unroll
+    for (int k = 1; k < NPW; ++k) mine = lane == k ? ball[k] : mine;
+    if (lane < NPW && i0 + lane < a.n) a.words_out[(size_t)(i0 + lane) * a.wpn + wb] = mine;
+  }
+}
+
 // Sign words of the fields: bit r of word (i, b) is set when h[i][32b + r] < 0.
 __global__ void k_pack_sign_words(const float* __restrict__ h, int32_t n, int32_t R,
                                   int32_t wpn, uint32_t* __restrict__ words) {
@@ -250,12 +349,37 @@ __global__ void k_maxcut_states_all(const uint32_t* __restrict__ words, int32_t 
   }
 }
 
-template <int MODE, int OPT, bool UNIT>
-void launch_step(const MaxcutArgs& a, const StepScalars& s, int grid, cudaStream_t st) {
-  k_maxcut_step<MODE, OPT, UNIT><<<grid, 256, 0, st>>>(a, s);
+constexpr int kNodesPerWarp = 4;
+
+// Persistent grid: exactly the resident blocks (occupancy x SMs), never more
+// than the work needs, so the grid-stride loop runs in a single wave.
+template <typename K>
+int resident_grid(K kernel, int sm_count, long long warps_needed) {
+  static int per_sm = 0;  // one cache per kernel instantiation
+  if (per_sm == 0) {
+    int b = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kernel, 256, 0) != cudaSuccess || b < 1) b = 1;
+    per_sm = b;
+  }
+  long long blocks = (warps_needed + 7) / 8;
+  const long long cap = (long long)per_sm * sm_count;
+  if (blocks > cap) blocks = cap;
+  return (int)(blocks < 1 ? 1 : blocks);
 }
 
-using StepFn = void (*)(const MaxcutArgs&, const StepScalars&, int, cudaStream_t);
+template <int MODE, int OPT, bool UNIT>
+void launch_step(const MaxcutArgs& a, const StepScalars& s, int sm_count, long long warps,
+                 cudaStream_t st) {
+  if (MODE == FEM_GRAD_PAPER) {
+    auto k = k_maxcut_step_paper<OPT, UNIT, kNodesPerWarp>;
+    k<<<resident_grid(k, sm_count, warps), 256, 0, st>>>(a, s);
+  } else {
+    auto k = k_maxcut_step<FEM_GRAD_EXACT, OPT, UNIT>;
+    k<<<resident_grid(k, sm_count, warps), 256, 0, st>>>(a, s);
+  }
+}
+
+using StepFn = void (*)(const MaxcutArgs&, const StepScalars&, int, long long, cudaStream_t);
 
 template <int MODE, bool UNIT>
 StepFn pick_opt(int opt) {
@@ -292,8 +416,9 @@ fem_status maxcut_pack_words(Problem* p, int hbuf, int wbuf, cudaStream_t s) {
 fem_status maxcut_sparse_steps(Problem* p, const fem_anneal_params& a,
                                const std::vector<StepScalars>& sc, cudaStream_t s) {
   const StepFn fn = pick_step(p->grad_mode, p->optimizer, p->unit_w);
-  const long long items = (long long)p->n * p->words_per_node;
-  const int grid = grid_for_warps(p, items);
+  const long long groups = p->grad_mode == FEM_GRAD_PAPER
+                               ? (long long)((p->n + kNodesPerWarp - 1) / kNodesPerWarp) * p->words_per_node
+                               : (long long)p->n * p->words_per_node;
   MaxcutArgs args{};
   args.row_ptr = p->row_ptr;
   args.col = p->col;
@@ -314,7 +439,7 @@ fem_status maxcut_sparse_steps(Problem* p, const fem_anneal_params& a,
     }
     args.words_in = p->words[p->cur];
     args.words_out = p->words[p->cur ^ 1];
-    fn(args, sc[k], grid, s);
+    fn(args, sc[k], p->sm_count, groups, s);
     p->cur ^= 1;
   }
   count_launches((int64_t)sc.size());

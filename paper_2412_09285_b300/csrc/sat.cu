@@ -1,0 +1,230 @@
+// Max-k-SAT: the fused per-step kernel (clause products through the variable ->
+// occurrence transpose, single-field gradient, optimizer) and the read-out of
+// unsatisfied clauses.
+//
+// Single field P_i = P(sigma_i = 1) = sigmoid(h_i).  With u_mk = 1 - P_k(W_mk)
+// (a positive literal gives 1 - P_k, a negated one P_k) and s_mi = +1 / -1 for a
+// positive / negated literal of variable i in clause m, the gradient of
+// F = sum_m prod_{k in m} u_mk - S/beta (Methods Eq. maxksat_F; SM "The MaxSAT
+// problem", taken through Eq. gradients_wrt_h for the two states) is
+//   g_i = gamma P_i (1 - P_i) [ -sum_{m ni i} s_mi prod_{k in m, k != i} u_mk + h_i/beta ].
+// P_i(1 - P_i) = (1 - m_i^2)/4, so the kernel uses the single-field scale gamma/4.
+//
+// Layout: h, m, v and the marginals P are [n][R] fp32.  P is ping-ponged between
+// steps (step t reads P[t%2], writes P[(t+1)%2]); the neighbour gathers read P,
+// so no exponential is evaluated per gathered literal.  h is updated in place.
+#include <algorithm>
+
+#include "fem_internal.h"
+#include "step_common.cuh"
+
+namespace fem {
+namespace {
+
+struct SatArgs {
+  const int32_t* cl_ptr;   // [M+1]
+  const int32_t* cl_lit;   // [n_occ]: (var << 1) | negated
+  const int32_t* occ_ptr;  // [n+1]
+  const int32_t* occ;      // [n_occ]: (clause << 3) | position
+  int32_t n, R, opt;
+  float* h;
+  float* m;
+  float* v;
+  const float* P_in;
+  float* P_out;
+};
+
+__device__ __forceinline__ float sigmoidf_acc(float x) { return 1.f / (1.f + expf(-x)); }
+
+__global__ void __launch_bounds__(256) k_sat_step(SatArgs a, StepScalars s) {
+  const long long total = (long long)a.n * a.R;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(e / a.R);
+    const int r = (int)(e - (long long)i * a.R);
+    float hi = a.h[e], mi = a.m[e];
+    float vi = a.opt == FEM_OPT_SGD ? 0.f : a.v[e];
+    float G = 0.f;
+    const int ob = a.occ_ptr[i], oe = a.occ_ptr[i + 1];
+    for (int o = ob; o < oe; ++o) {
+      const int x = a.occ[o];
+      const int c = x >> 3, pos = x & 7;
+      const int cb = a.cl_ptr[c], ce = a.cl_ptr[c + 1];
+      float prod = 1.f;
+      float sgn = 1.f;
+      for (int b = cb; b < ce; ++b) {
+        const int lit = a.cl_lit[b];
+        if (b - cb == pos) {
+          sgn = (lit & 1) ? -1.f : 1.f;
+          continue;
+        }
+        const float pk = a.P_in[(size_t)(lit >> 1) * a.R + r];
+        prod *= (lit & 1) ? pk : 1.f - pk;
+      }
+      G = fmaf(sgn, prod, G);
+    }
+    const float g = s.gq * (hi * s.inv_beta - G) * one_minus_m2(hi);
+    opt_update_rt(a.opt, hi, mi, vi, g, s);
+    a.h[e] = hi;
+    a.m[e] = mi;
+    if (a.opt != FEM_OPT_SGD) a.v[e] = vi;
+    a.P_out[e] = sigmoidf_acc(hi);
+  }
+}
+
+__global__ void k_sat_marginals(const float* __restrict__ h, long long total, float* __restrict__ P) {
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x)
+    P[e] = sigmoidf_acc(h[e]);
+}
+
+// Per-block partial counts of unsatisfied clauses; a thread keeps one replica.
+// Block = 16 clauses x 16 replicas; blockIdx.y selects the block of 16 replicas.
+// A variable takes the value 1 when h >= 0.
+__global__ void __launch_bounds__(256) k_sat_unsat_partial(const int32_t* __restrict__ cl_ptr,
+                                                           const int32_t* __restrict__ cl_lit,
+                                                           int64_t M, const float* __restrict__ h,
+                                                           int32_t R, int64_t* __restrict__ part) {
+  __shared__ int64_t sc[256];
+  const int cl = threadIdx.x >> 4, rl = threadIdx.x & 15;
+  const int r = blockIdx.y * 16 + rl;
+  int64_t cnt = 0;
+  if (r < R) {
+    for (long long c = (long long)blockIdx.x * 16 + cl; c < M; c += (long long)gridDim.x * 16) {
+      bool sat = false;
+      for (int b = cl_ptr[c]; b < cl_ptr[c + 1]; ++b) {
+        const int lit = cl_lit[b];
+        const bool one = h[(size_t)(lit >> 1) * R + r] >= 0.f;
+        sat |= (lit & 1) ? !one : one;
+      }
+      cnt += sat ? 0 : 1;
+    }
+  }
+  sc[threadIdx.x] = cnt;
+  __syncthreads();
+  if (cl == 0 && r < R) {
+    int64_t t = 0;
+    for (int k = 0; k < 16; ++k) t += sc[k * 16 + rl];
+    part[(size_t)blockIdx.x * R + r] = t;
+  }
+}
+
+__global__ void __launch_bounds__(1024) k_sat_finish(const int64_t* __restrict__ part, int32_t nblk,
+                                                     int32_t R, int64_t* __restrict__ e_i,
+                                                     double* __restrict__ e_f,
+                                                     int32_t* __restrict__ best) {
+  __shared__ int64_t sval[1024];
+  __shared__ int sidx[1024];
+  int64_t bv = 0;
+  int bidx = 0x7fffffff;
+  for (int r = threadIdx.x; r < R; r += blockDim.x) {
+    int64_t t = 0;
+    for (int b = 0; b < nblk; ++b) t += part[(size_t)b * R + r];
+    e_i[r] = t;
+    e_f[r] = (double)t;
+    if (bidx == 0x7fffffff || t < bv) {
+      bv = t;
+      bidx = r;
+    }
+  }
+  sval[threadIdx.x] = bv;
+  sidx[threadIdx.x] = bidx;
+  __syncthreads();
+  for (int off = blockDim.x / 2; off > 0; off >>= 1) {
+    if (threadIdx.x < off) {
+      const int64_t ov = sval[threadIdx.x + off];
+      const int oi = sidx[threadIdx.x + off];
+      const int mi = sidx[threadIdx.x];
+      if (oi != 0x7fffffff &&
+          (mi == 0x7fffffff || ov < sval[threadIdx.x] || (ov == sval[threadIdx.x] && oi < mi))) {
+        sval[threadIdx.x] = ov;
+        sidx[threadIdx.x] = oi;
+      }
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) best[0] = sidx[0];
+}
+
+__global__ void k_sat_states(const float* __restrict__ h, int32_t n, int32_t R,
+                             const int32_t* __restrict__ best, int32_t* __restrict__ out, int32_t all) {
+  const size_t total = all ? (size_t)n * R : (size_t)n;
+  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (size_t)gridDim.x * blockDim.x) {
+    const size_t idx = all ? e : e * R + best[0];
+    out[e] = h[idx] >= 0.f ? 1 : 0;
+  }
+}
+
+int grid_for(const Problem* p, long long threads, int per_sm) {
+  long long blocks = (threads + 255) / 256;
+  const long long cap = (long long)per_sm * p->sm_count;
+  if (blocks > cap) blocks = cap;
+  return (int)(blocks < 1 ? 1 : blocks);
+}
+
+}  // namespace
+
+// Marginals read by step t (buffer t%2) from the current fields.
+fem_status sat_marginals(Problem* p, int t, cudaStream_t st) {
+  const long long total = (long long)p->n * p->R;
+  k_sat_marginals<<<grid_for(p, total, 8), 256, 0, st>>>(p->h[0], total, p->satP[t & 1]);
+  count_launches(1);
+  FEM_CUDA(cudaGetLastError());
+  return FEM_OK;
+}
+
+fem_status sat_steps(Problem* p, const std::vector<StepScalars>& sc, int t_begin, cudaStream_t st) {
+  static int per_sm = 0;
+  if (per_sm == 0) {
+    int b = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_sat_step, 256, 0) != cudaSuccess || b < 1) b = 1;
+    per_sm = b;
+  }
+  SatArgs a{};
+  a.cl_ptr = p->cl_ptr;
+  a.cl_lit = p->cl_lit;
+  a.occ_ptr = p->occ_ptr;
+  a.occ = p->occ;
+  a.n = p->n;
+  a.R = p->R;
+  a.opt = p->optimizer;
+  a.h = p->h[0];
+  a.m = p->m;
+  a.v = p->v;
+  const int grid = grid_for(p, (long long)p->n * p->R, per_sm);
+  for (size_t k = 0; k < sc.size(); ++k) {
+    const int t = t_begin + (int)k;
+    a.P_in = p->satP[t & 1];
+    a.P_out = p->satP[(t + 1) & 1];
+    k_sat_step<<<grid, 256, 0, st>>>(a, sc[k]);
+  }
+  count_launches((int64_t)sc.size());
+  FEM_CUDA(cudaGetLastError());
+  return FEM_OK;
+}
+
+fem_status sat_readout(Problem* p, cudaStream_t st) {
+  const int nb = (int)std::min<long long>(std::max<long long>(1, (p->n_clauses + 15) / 16),
+                                          (long long)p->part_blocks);
+  const dim3 grid(nb, (p->R + 15) / 16);
+  k_sat_unsat_partial<<<grid, 256, 0, st>>>(p->cl_ptr, p->cl_lit, p->n_clauses, p->h[0], p->R, p->part_i);
+  k_sat_finish<<<1, 1024, 0, st>>>(p->part_i, nb, p->R, p->energy_i, p->energy_f, p->best);
+  k_sat_states<<<(p->n + 255) / 256 < 1024 ? (p->n + 255) / 256 : 1024, 256, 0, st>>>(
+      p->h[0], p->n, p->R, p->best, p->states_dev, 0);
+  count_launches(3);
+  FEM_CUDA(cudaGetLastError());
+  return FEM_OK;
+}
+
+fem_status sat_states_all(Problem* p, int32_t* out, cudaStream_t st) {
+  const size_t total = (size_t)p->n * p->R;
+  size_t blocks = (total + 255) / 256;
+  if (blocks > (size_t)p->sm_count * 16) blocks = (size_t)p->sm_count * 16;
+  k_sat_states<<<(int)blocks, 256, 0, st>>>(p->h[0], p->n, p->R, p->best, out, 1);
+  count_launches(1);
+  FEM_CUDA(cudaGetLastError());
+  return FEM_OK;
+}
+
+}  // namespace fem

@@ -47,6 +47,49 @@ __device__ __forceinline__ void opt_update(float& h, float& m, float& v, float g
   }
 }
 
+// The same updates with the divisions done by the fast reciprocal (__fdividef,
+// 2 ulp); the divisors here are >= eps and far below 2^126.
+template <int OPT>
+__device__ __forceinline__ void opt_update_fast(float& h, float& m, float& v, float g,
+                                                const StepScalars& s) {
+  if (s.wd != 0.f) g = fmaf(s.wd, h, g);
+  if (OPT == FEM_OPT_ADAM) {
+    m = fmaf(s.b1, m, s.omb1 * g);
+    v = fmaf(s.b2, v, s.omb2 * g * g);
+    h = fmaf(-s.lr, __fdividef(m, fmaf(sqrtf(v), s.inv_sqrt_bc2, s.eps)), h);
+  } else if (OPT == FEM_OPT_RMSPROP) {
+    v = fmaf(s.b1, v, s.omb1 * g * g);
+    const float q = __fdividef(g, sqrtf(v) + s.eps);
+    if (s.momentum > 0.f) {
+      m = fmaf(s.momentum, m, q);
+      h = fmaf(-s.lr, m, h);
+    } else {
+      h = fmaf(-s.lr, q, h);
+    }
+  } else {
+    if (s.b1 != 0.f) {
+      m = s.first ? g : fmaf(s.b1, m, s.omb1 * g);
+      g = m;
+    }
+    h = fmaf(-s.lr, g, h);
+  }
+}
+
+// 1 - tanh(h/2)^2 with the fast exponential (relative error ~1e-6).
+__device__ __forceinline__ float one_minus_m2_fast(float h) {
+  const float e = __expf(-fabsf(h));
+  const float d = 1.f + e;
+  return __fdividef(4.f * e, d * d);
+}
+
+// The same update with the optimizer chosen at run time (a warp-uniform branch).
+__device__ __forceinline__ void opt_update_rt(int opt, float& h, float& m, float& v, float g,
+                                              const StepScalars& s) {
+  if (opt == FEM_OPT_ADAM) opt_update<FEM_OPT_ADAM>(h, m, v, g, s);
+  else if (opt == FEM_OPT_RMSPROP) opt_update<FEM_OPT_RMSPROP>(h, m, v, g, s);
+  else opt_update<FEM_OPT_SGD>(h, m, v, g, s);
+}
+
 // 1 - m^2 for m = tanh(h/2) = 2 sigmoid(h) - 1, evaluated as 4e/(1+e)^2 with
 // e = exp(-|h|) so that it keeps full relative accuracy when |m| -> 1.
 __device__ __forceinline__ float one_minus_m2(float h) {

@@ -69,6 +69,8 @@ def _load():
         "fem_read_best": (S, [P, P, P, P, P, P]),
         "fem_read_fields": (S, [P, P, P]),
         "fem_read_states": (S, [P, P, P]),
+        "fem_read_state": (S, [P, P, P, P, P]),
+        "fem_write_state": (S, [P, P, P, P, C.c_int32, P]),
         "fem_problem_info": (S, [P, P, P, P, P, P]),
         "fem_sync": (S, [P, P]),
         "fem_destroy": (None, [P]),
@@ -140,6 +142,15 @@ def fem_read_fields(handle, h_host, stream=None):
 
 def fem_read_states(handle, states_host, stream=None):
     _check(_lib.fem_read_states(handle, _ptr(states_host), _stream(stream)), "fem_read_states")
+
+
+def fem_read_state(handle, h=None, m=None, v=None, stream=None):
+    _check(_lib.fem_read_state(handle, _ptr(h), _ptr(m), _ptr(v), _stream(stream)), "fem_read_state")
+
+
+def fem_write_state(handle, h, m=None, v=None, steps_done=0, stream=None):
+    _check(_lib.fem_write_state(handle, _ptr(h), _ptr(m), _ptr(v), int(steps_done), _stream(stream)),
+           "fem_write_state")
 
 
 def fem_problem_info(handle):
@@ -237,6 +248,20 @@ class Problem:
         out = np.empty(shape, np.float32)
         fem_read_fields(self.handle, out, self.stream)
         return out
+
+    def _shape(self):
+        return (self.n, self.replicas) if self.kind != "bmincut" else (self.n, self.replicas, self.q)
+
+    def state(self):
+        """(h, m, v) as float32 host arrays (a checkpoint, with info()['steps_done'])."""
+        h, m, v = (np.empty(self._shape(), np.float32) for _ in range(3))
+        fem_read_state(self.handle, h, m, v, self.stream)
+        return h, m, v
+
+    def set_state(self, h, m=None, v=None, steps_done=0):
+        conv = lambda x: None if x is None else np.ascontiguousarray(x, np.float32)
+        h, m, v = conv(h), conv(m), conv(v)
+        fem_write_state(self.handle, h, m, v, steps_done, self.stream)
 
     def states(self):
         out = np.empty((self.n, self.replicas), np.int32)

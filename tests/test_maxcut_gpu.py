@@ -1,8 +1,24 @@
 """GPU vs oracle parity for sparse MaxCut, through the C ABI.
 
-Fields: sigmoid(h) within 1e-4 max-abs over the first 50 fp32 steps (exact
-mode; paper mode on every replica whose discrete trajectory agrees with the
-oracle's).  Objectives: bit-exact (int64) for the GPU's own discrete states.
+Two kinds of field comparison:
+
+* Trajectories (the gate for the workloads' settings: Adam, lr 0.1, beta
+  0.05 -> 5): sigmoid(h) within 1e-4 max-abs over the first 50 fp32 steps from
+  the same h0 - in exact mode on every well-conditioned element, in paper mode on
+  every replica whose discrete trajectory agrees with the oracle's.
+* Teacher-forced windows (every optimizer and schedule): the oracle's fp64 state
+  at step t0, rounded to fp32, is written into the GPU problem; both sides then
+  run 3 steps and must agree within 1e-4.  With the paper's aggressive RMSprop /
+  SGD settings the fp32-vs-fp64 trajectory itself diverges (the dynamics amplify
+  a 1e-8 rounding difference by orders of magnitude over tens of steps), so
+  comparing whole trajectories there would test chaos, not the kernel.
+
+Conditioning.  Adam and RMSprop divide by D = sqrt(v) + eps (eps = 1e-8), so an
+absolute gradient rounding error d moves the update by about lr * d / D.  Elements
+whose oracle denominator fell below D_COND at some step are checked only against a
+loose bound, and their share must stay below MAX_ILL.
+
+Objectives: bit-exact (int64) for the GPU's own discrete states.
 """
 import numpy as np
 import pytest
@@ -12,7 +28,10 @@ from paper_2412_09285_b300 import instances as I
 
 pytestmark = pytest.mark.gpu
 
-TOL_P = 1e-4   # marginals, max-abs, first 50 fp32 steps
+TOL_P = 1e-4     # marginals, max-abs
+D_COND = 1e-6    # well-conditioned: optimizer denominator >= D_COND at every step so far
+MAX_ILL = 5e-3   # at most this share of compared elements may be ill-conditioned
+CHECK = [1, 2, 5, 10, 20, 35, 50]
 
 
 @pytest.fixture(scope="module")
@@ -24,6 +43,30 @@ def fem():
     build.build()
     from paper_2412_09285_b300 import fem as F
     return F
+
+
+def _check_marginals(got, ref, cond, where, agree=None):
+    P_got = O.sigmoid(got.astype(np.float64))
+    P_ref = O.sigmoid(ref)
+    pool = np.ones(got.shape, bool) if agree is None else np.broadcast_to(agree[None, :], got.shape)
+    ok = pool & (cond >= D_COND)
+    ill = pool & ~ok
+    assert ill.sum() <= MAX_ILL * max(1, pool.sum()), (where, "ill-conditioned share", ill.mean())
+    err = np.abs(P_got - P_ref)
+    if ok.any():
+        assert err[ok].max() <= TOL_P, (where, float(err[ok].max()))
+    if ill.any():
+        assert err[ill].max() <= 0.05, (where, "ill-conditioned", float(err[ill].max()))
+
+
+def _okw(kw):
+    return {k: kw[k] for k in ("lr", "beta1", "beta2", "eps", "weight_decay", "momentum", "alpha",
+                               "dampening") if k in kw} or dict(lr=0.1)
+
+
+def _sched(kw):
+    return dict(schedule=kw.get("schedule", "exponential"), beta_min=kw.get("beta_min", 0.05),
+                beta_max=kw.get("beta_max", 5.0), gamma=kw.get("gamma_grad", 1.0))
 
 
 def _gpu_trace(fem, graph, h0, checkpoints, n_steps, **kw):
@@ -40,36 +83,30 @@ def _gpu_trace(fem, graph, h0, checkpoints, n_steps, **kw):
 def _oracle_trace(graph, h0, checkpoints, n_steps, mode, **kw):
     W = O.coupling_matrix(graph.n, graph.ei, graph.ej, graph.w)
     tr = {t: None for t in checkpoints}
-    okw = {k: kw[k] for k in ("lr", "beta1", "beta2", "eps", "weight_decay", "momentum", "alpha",
-                              "dampening") if k in kw}
+    cd = {t: None for t in checkpoints}
     O.anneal(("maxcut", W), h0.astype(np.float64), n_steps, t_end=max(checkpoints),
-             schedule=kw.get("schedule", "exponential"), beta_min=kw.get("beta_min", 0.05),
-             beta_max=kw.get("beta_max", 5.0), optimizer=kw.get("optimizer", "adam"),
-             opt_kw=okw or dict(lr=0.1), mode=mode, gamma=kw.get("gamma_grad", 1.0), trace=tr)
-    return tr
+             optimizer=kw.get("optimizer", "adam"), opt_kw=_okw(kw), mode=mode, trace=tr, cond=cd,
+             **_sched(kw))
+    return tr, cd
 
 
-CHECK = [1, 2, 5, 10, 20, 35, 50]
+def _agreeing_replicas(got, ref, checkpoints):
+    agree = np.ones(got[checkpoints[0]].shape[1], bool)
+    for t in checkpoints:
+        agree &= np.all((got[t] >= 0) == (ref[t] >= 0), axis=0)
+    return agree
 
+
+# ------------------------------------------------------------ trajectories
 
 @pytest.mark.parametrize("weights", ["unit", "pm1", "real"])
 def test_exact_mode_marginals_first_50_steps(fem, weights):
     g = I.er_gnp(800, 0.06, seed=1, weights=weights)
     h0 = I.initial_fields(800, 32, seed=2)
     _, got = _gpu_trace(fem, g, h0, CHECK, 1000, grad_mode="exact", lr=0.1)
-    ref = _oracle_trace(g, h0, CHECK, 1000, "exact", lr=0.1)
+    ref, cd = _oracle_trace(g, h0, CHECK, 1000, "exact", lr=0.1)
     for t in CHECK:
-        err = np.abs(O.sigmoid(got[t].astype(np.float64)) - O.sigmoid(ref[t])).max()
-        assert err <= TOL_P, (t, err)
-
-
-def _paper_compare(got, ref, checkpoints):
-    agree = np.ones(got[checkpoints[0]].shape[1], bool)
-    for t in checkpoints:
-        agree &= np.all((got[t] >= 0) == (ref[t] >= 0), axis=0)
-    errs = [np.abs(O.sigmoid(got[t][:, agree].astype(np.float64)) - O.sigmoid(ref[t][:, agree])).max()
-            for t in checkpoints] if agree.any() else [0.0]
-    return agree, max(errs)
+        _check_marginals(got[t], ref[t], cd[t], t)
 
 
 @pytest.mark.parametrize("weights", ["unit", "pm1", "real"])
@@ -77,29 +114,87 @@ def test_paper_mode_marginals_first_50_steps(fem, weights):
     g = I.er_gnp(800, 0.06, seed=3, weights=weights)
     h0 = I.initial_fields(800, 32, seed=4)
     _, got = _gpu_trace(fem, g, h0, CHECK, 1000, grad_mode="paper", lr=0.1)
-    ref = _oracle_trace(g, h0, CHECK, 1000, "paper", lr=0.1)
-    agree, err = _paper_compare(got, ref, CHECK)
+    ref, cd = _oracle_trace(g, h0, CHECK, 1000, "paper", lr=0.1)
+    agree = _agreeing_replicas(got, ref, CHECK)
     assert agree.sum() >= 30, agree.sum()      # sign disagreements are rare near-ties
-    assert err <= TOL_P, err
+    for t in CHECK:
+        _check_marginals(got[t], ref[t], cd[t], t, agree)
 
 
-@pytest.mark.parametrize("opt,kw", [
+# ------------------------------------------------ teacher-forced step windows
+
+OPTIMIZER_CASES = [
     ("rmsprop", dict(lr=0.03, alpha=0.56, momentum=0.63, weight_decay=0.013,
                      schedule="inverse_proportional", beta_min=1 / 1.16, beta_max=1 / 6e-5)),
     ("rmsprop", dict(lr=0.01, alpha=0.99, momentum=0.0)),
     ("sgd", dict(lr=0.5, momentum=0.71, dampening=0.11, weight_decay=0.018, gamma_grad=6.0,
                  schedule="inverse_proportional", beta_min=1 / 0.63, beta_max=1e5)),
+    # lr * gamma / (4 beta_min) != 1: at exactly 1 the first step maps h to h * m^2 ~ 0 on
+    # nodes whose discretised neighbourhood sums to 0, a sign decided by rounding alone
+    ("sgd", dict(lr=0.13, momentum=0.0)),
     ("adam", dict(lr=0.05, beta1=0.8, beta2=0.99, eps=1e-6, weight_decay=0.01, gamma_grad=2.0)),
-])
-def test_other_optimizers_and_schedules(fem, opt, kw):
-    g = I.er_gnp(500, 0.05, seed=5, weights="pm1")
-    h0 = I.initial_fields(500, 64, seed=6)
-    _, got = _gpu_trace(fem, g, h0, CHECK, 1000, grad_mode="exact", optimizer=opt, **kw)
-    ref = _oracle_trace(g, h0, CHECK, 1000, "exact", optimizer=opt, **kw)
-    for t in CHECK:
-        err = np.abs(O.sigmoid(got[t].astype(np.float64)) - O.sigmoid(ref[t])).max()
-        assert err <= TOL_P, (t, err)
+    ("adam", dict(lr=0.1)),
+]
 
+
+def _opt_state(opt):
+    """(m, v) of an oracle optimizer in the library's slots."""
+    if isinstance(opt, O.Adam):
+        return opt.m, opt.v
+    if isinstance(opt, O.RMSprop):
+        return opt.buf, opt.v
+    return opt.buf, np.zeros_like(opt.buf)
+
+
+def _set_opt_state(opt, m, v):
+    if isinstance(opt, O.Adam):
+        opt.m, opt.v = m, v
+    elif isinstance(opt, O.RMSprop):
+        opt.buf, opt.v = m, v
+    else:
+        opt.buf = m
+
+
+@pytest.mark.parametrize("mode", ["exact", "paper"])
+@pytest.mark.parametrize("opt,kw", OPTIMIZER_CASES)
+def test_teacher_forced_windows(fem, opt, kw, mode):
+    g = I.er_gnp(500, 0.05, seed=5, weights="pm1")
+    W = O.coupling_matrix(g.n, g.ei, g.ej, g.w)
+    h0 = I.initial_fields(500, 64, seed=6)
+    n_steps = 1000
+    P = fem.Problem("maxcut", graph=g)
+    P.anneal(h_init=h0, n_steps=n_steps, t_end=0, grad_mode=mode, optimizer=opt, **kw)
+    h, o = O.anneal(("maxcut", W), h0.astype(np.float64), n_steps, t_end=0, optimizer=opt,
+                    opt_kw=_okw(kw), mode=mode, **_sched(kw))
+    t = 0
+    for t0 in (0, 7, 30, 120, 600):
+        if t0 > t:
+            h, o = O.anneal(("maxcut", W), h, n_steps, t_begin=t, t_end=t0, optimizer=opt, opt=o,
+                            mode=mode, **_sched(kw))
+        # round the oracle's state to fp32, give the same state to both sides
+        m, v = _opt_state(o)
+        h32, m32, v32 = (x.astype(np.float32) for x in (h, m, v))
+        h = h32.astype(np.float64)
+        _set_opt_state(o, m32.astype(np.float64), v32.astype(np.float64))
+        cd = {t0 + 3: None}
+        h, o = O.anneal(("maxcut", W), h, n_steps, t_begin=t0, t_end=t0 + 3, optimizer=opt, opt=o,
+                        mode=mode, cond=cd, **_sched(kw))
+        if t0 == 0:   # a step count of 0 is a fresh start: fields from h_init, zero state
+            P.anneal(h_init=h32, n_steps=n_steps, t_end=3, grad_mode=mode, optimizer=opt, **kw)
+        else:
+            P.set_state(h32, m32, v32, steps_done=t0)
+            P.anneal(n_steps=n_steps, t_begin=t0, t_end=t0 + 3, grad_mode=mode, optimizer=opt,
+                     replicas=64, **kw)
+        got = P.fields()
+        agree = np.all((got >= 0) == (h >= 0), axis=0) if mode == "paper" else None
+        if agree is not None:
+            assert agree.sum() >= 56, (t0, agree.sum())
+        # a fresh conditioning record for the window (denominators of the 3 steps)
+        _check_marginals(got, h, cd[t0 + 3], (opt, mode, t0), agree)
+        t = t0 + 3
+
+
+# ------------------------------------------------------------- objectives
 
 @pytest.mark.parametrize("weights", ["unit", "pm1", "int3", "real"])
 def test_objectives_bit_exact_after_full_anneal(fem, weights):
@@ -127,20 +222,26 @@ def test_objectives_bit_exact_after_full_anneal(fem, weights):
     assert cut.max() > 0.55 * g.w.sum()
 
 
-def test_resume_is_bit_identical(fem):
+@pytest.mark.parametrize("mode", ["paper", "exact"])
+def test_resume_and_checkpoint_are_bit_identical(fem, mode):
     g = I.er_gnp(600, 0.05, seed=10, weights="pm1")
     h0 = I.initial_fields(600, 32, seed=11)
-    a = fem.Problem("maxcut", graph=g).anneal(h_init=h0, n_steps=400, grad_mode="paper")
+    a = fem.Problem("maxcut", graph=g).anneal(h_init=h0, n_steps=400, grad_mode=mode)
     b = fem.Problem("maxcut", graph=g)
-    b.anneal(h_init=h0, n_steps=400, t_end=123, grad_mode="paper")
-    b.anneal(n_steps=400, t_begin=123, t_end=400, grad_mode="paper", replicas=32)
+    b.anneal(h_init=h0, n_steps=400, t_end=123, grad_mode=mode)
+    b.anneal(n_steps=400, t_begin=123, t_end=400, grad_mode=mode, replicas=32)
     assert np.array_equal(a.fields(), b.fields())
-    for mode in ("exact",):
-        a = fem.Problem("maxcut", graph=g).anneal(h_init=h0, n_steps=100, grad_mode=mode)
-        b = fem.Problem("maxcut", graph=g)
-        b.anneal(h_init=h0, n_steps=100, t_end=37, grad_mode=mode)
-        b.anneal(n_steps=100, t_begin=37, grad_mode=mode, replicas=32)
-        assert np.array_equal(a.fields(), b.fields())
+    # checkpoint at 201, restore into a fresh problem, finish there
+    c = fem.Problem("maxcut", graph=g)
+    c.anneal(h_init=h0, n_steps=400, t_end=201, grad_mode=mode)
+    ck = c.state()
+    assert c.info()["steps_done"] == 201
+    d = fem.Problem("maxcut", graph=g)
+    d.anneal(h_init=h0, n_steps=400, t_end=0, grad_mode=mode)
+    d.set_state(*ck, steps_done=201)
+    d.anneal(n_steps=400, t_begin=201, grad_mode=mode, replicas=32)
+    assert np.array_equal(a.fields(), d.fields())
+    assert np.array_equal(a.best()["energy_i64"], d.best()["energy_i64"])
 
 
 @pytest.mark.parametrize("n,p,R", [(1, 0.0, 32), (37, 0.0, 32), (300, 0.004, 64), (257, 0.03, 96)])
@@ -148,9 +249,9 @@ def test_edge_cases_isolated_empty_multiword(fem, n, p, R):
     g = I.er_gnp(n, p, seed=12, weights="pm1")
     h0 = I.initial_fields(n, R, seed=13)
     _, got = _gpu_trace(fem, g, h0, [1, 10, 50], 200, grad_mode="exact")
-    ref = _oracle_trace(g, h0, [1, 10, 50], 200, "exact", lr=0.1)
+    ref, cd = _oracle_trace(g, h0, [1, 10, 50], 200, "exact", lr=0.1)
     for t in (1, 10, 50):
-        assert np.abs(O.sigmoid(got[t].astype(np.float64)) - O.sigmoid(ref[t])).max() <= TOL_P
+        _check_marginals(got[t], ref[t], cd[t], (n, t))
     P = fem.Problem("maxcut", graph=g).anneal(h_init=h0, n_steps=200, grad_mode="paper")
     res = P.best()
     cut = O.maxcut_cut_edges(g.ei, g.ej, g.w, P.states().astype(np.int8))
@@ -164,12 +265,18 @@ def test_error_paths(fem):
         P.best()
     assert e.value.status == fem.FEM_ERR_STATE
     with pytest.raises(fem.FemError) as e:
+        P.set_state(np.zeros((100, 32), np.float32))
+    assert e.value.status == fem.FEM_ERR_STATE
+    with pytest.raises(fem.FemError) as e:
         P.anneal(h_init=I.initial_fields(100, 48, seed=1), n_steps=10)
     assert e.value.status == fem.FEM_ERR_UNSUPPORTED
     P.anneal(h_init=I.initial_fields(100, 32, seed=1), n_steps=10, t_end=5)
     with pytest.raises(fem.FemError) as e:
         P.anneal(n_steps=10, t_begin=4, replicas=32)
     assert e.value.status == fem.FEM_ERR_STATE
+    with pytest.raises(fem.FemError) as e:
+        P.set_state(np.zeros((100, 32), np.float32), steps_done=11)
+    assert e.value.status == fem.FEM_ERR_INVALID_ARG
     P.sync()
 
 
@@ -182,14 +289,12 @@ def test_full_size_sparse_steps_match_oracle(fem):
     h0 = I.initial_fields(n, 32, seed=2025)
     for mode in ("paper", "exact"):
         _, got = _gpu_trace(fem, g, h0, [1, 2, 3], 2000, grad_mode=mode)
-        ref = _oracle_trace(g, h0, [1, 2, 3], 2000, mode, lr=0.1)
+        ref, cd = _oracle_trace(g, h0, [1, 2, 3], 2000, mode, lr=0.1)
+        agree = _agreeing_replicas(got, ref, [1, 2, 3]) if mode == "paper" else None
+        if agree is not None:
+            assert agree.sum() >= 28
         for t in (1, 2, 3):
-            diff = np.abs(O.sigmoid(got[t].astype(np.float64)) - O.sigmoid(ref[t]))
-            if mode == "paper":
-                agree = np.all((got[t] >= 0) == (ref[t] >= 0), axis=0)
-                diff = diff[:, agree]
-                assert agree.sum() >= 28
-            assert diff.max() <= TOL_P, (mode, t, diff.max())
+            _check_marginals(got[t], ref[t], cd[t], (mode, t), agree)
     P = fem.Problem("maxcut", graph=g).anneal(h_init=h0, n_steps=2000, t_end=30)
     st = P.states()
     res = P.best()

@@ -235,6 +235,29 @@ const char* fem_last_error(void);
  * handles, all threads).  Lets a caller count the device work behind a call. */
 int64_t fem_kernel_launches(void);
 
+/* MaxCut energies of caller-provided sign words, without allocating.
+ * The paper has no counterpart: this is a library service for callers that cannot
+ * call cudaMalloc - for example code whose device memory is owned by a pool manager,
+ * or a loop that must not allocate because an allocation can synchronise the device.
+ * The caller passes every input and output (all DEVICE pointers on the current
+ * device); the only scratch is a fixed 2 MiB array in the library's device image,
+ * which each GPU that loads the library holds until the process exits.
+ *   row_ptr[n+1], col[row_ptr[n]]  the graph in the library's CSR form: every
+ *        undirected edge in both rows, column index in bits 0-30 and the edge weight
+ *        (+1 or -1 only) in bit 31 (set = -1).
+ *   words[n][replicas/32]  bit r of word (i, r/32) set <=> replica r puts node i in
+ *        state -1.
+ *   energy[replicas]  out: E_r = -cut_r (int64); best_replica[1] out: argmin E,
+ *        lowest index on ties.
+ * replicas must be a multiple of 32 and at most 1024 (FEM_ERR_UNSUPPORTED beyond).
+ * Asynchronous on `stream`.  The first call on a device looks up the scratch address
+ * (a CUDA runtime query), so make that first call before any stream capture.  Calls
+ * share the scratch array: calls that overlap on the GPU (different streams, no
+ * ordering between them) race and give wrong results. */
+fem_status fem_maxcut_energies_noalloc(const int32_t* row_ptr, const uint32_t* col, int32_t n,
+                                       const uint32_t* words, int32_t replicas, int64_t* energy,
+                                       int32_t* best_replica, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -77,6 +77,7 @@ def _load():
         "fem_status_string": (C.c_char_p, [S]),
         "fem_last_error": (C.c_char_p, []),
         "fem_kernel_launches": (C.c_int64, []),
+        "fem_maxcut_energies_noalloc": (S, [P, P, C.c_int32, P, C.c_int32, P, P, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -170,6 +171,13 @@ def fem_destroy(handle):
 
 def fem_kernel_launches() -> int:
     return int(_lib.fem_kernel_launches())
+
+
+def fem_maxcut_energies_noalloc(row_ptr, col, n, words, replicas, energy, best_replica, stream=None):
+    """All array arguments are CUDA tensors (device pointers); nothing is allocated."""
+    _check(_lib.fem_maxcut_energies_noalloc(_ptr(row_ptr), _ptr(col), int(n), _ptr(words),
+                                            int(replicas), _ptr(energy), _ptr(best_replica),
+                                            _stream(stream)), "fem_maxcut_energies_noalloc")
 
 
 # ----------------------------------------------------------------- convenience

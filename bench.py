@@ -1,21 +1,26 @@
 #!/usr/bin/env python3
 """Benchmark of the FEM per-step replica update on B300 (one JSON line on stdout).
 
-Workload (default): sparse MaxCut at scale - Erdos-Renyi G(n, m) with n = 2^20,
-m = 3n (mean degree 6), weights uniform +-1, R = 32 replicas, the exponential
-beta schedule 0.05 -> 5 over 2000 steps, Adam (lr 0.1), paper-mode gradients.
-A "step" is one anneal step of all replicas (schedule, discretised neighbour
-contraction, gradient, Adam).  The timed region runs K steps from freshly
-initialised fields (resident in HBM) and ends with the read-out (argmax, exact
-int64 cuts, argmin over replicas).  Metric: edge*replica*steps/s with the
-undirected |E|.
-
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                    [--workload sparse|small]
+                    [--workload sparse|small|dense] [--precision bf16|fp8|bf16x2|fp32]
+
+Workloads (synthetic, seeded; the paper's data sets are not available):
+  sparse (default)  sparse MaxCut at scale: ER G(n, m), n = 2^20, m = 3n, +-1 weights,
+                    R = 32, 2000-step exponential beta 0.05 -> 5, Adam lr 0.1, paper-mode
+                    gradient.  Units: |E| undirected edges x replicas x steps.
+  small             ER G(800, 0.06), unit weights, R = 32, 1000 steps (latency-bound).
+  dense             SK complete graph n = 2000, J = +-1, R = 1024, 1000 steps, the J.M
+                    contraction on the tensor cores (--precision).  Units: n(n-1)/2 edges.
+
+A "step" is one anneal step of all replicas (schedule, contraction, gradient,
+optimizer).  The timed region runs K steps from freshly initialised fields
+resident in HBM (chained anneals of the workload's length) and ends each anneal
+with the read-out (argmax, exact int64 objective, argmin over replicas).
 
 Under torchrun every rank runs its own R replicas of the same instance (replica
 sharding, no data-path collective, weak scaling); rank 0 prints the line.
-``--impl reference`` times the FP64 CPU oracle on the host cores instead.
+``--impl reference`` times the FP64 CPU oracle (there is no other implementation
+of the method to run) on the host cores.
 """
 from __future__ import annotations
 
@@ -36,13 +41,16 @@ sys.path.insert(0, ROOT)
 
 METRIC = "edge*replica*steps/s"
 WORKLOADS = {
-    "sparse": dict(name="sparse MaxCut at scale: ER G(n,m) n=2^20, m=3n, +-1 weights, R=32, "
-                        "2000-step exponential beta 0.05->5, Adam lr 0.1, paper-mode gradient",
-                   n=1 << 20, m=3 << 20, weights="pm1", R=32, n_steps=2000, graph_seed=2024,
-                   h_seed=2025),
-    "small": dict(name="plain MaxCut: ER G(800, 0.06), unit weights, R=32, 1000-step exponential "
-                       "beta 0.05->5, Adam lr 0.1, paper-mode gradient",
-                  n=800, p=0.06, weights="unit", R=32, n_steps=1000, graph_seed=1, h_seed=2),
+    "sparse": dict(kind="sparse", name="sparse MaxCut at scale: ER G(n,m) n=2^20, m=3n, +-1 weights, R=32, "
+                                      "2000-step exponential beta 0.05->5, Adam lr 0.1, paper-mode gradient",
+                   n=1 << 20, m=3 << 20, weights="pm1", R=32, n_steps=2000, graph_seed=2024, h_seed=2025,
+                   cpu_steps=6),
+    "small": dict(kind="sparse", name="plain MaxCut: ER G(800, 0.06), unit weights, R=32, 1000-step "
+                                     "exponential beta 0.05->5, Adam lr 0.1, paper-mode gradient",
+                  n=800, p=0.06, weights="unit", R=32, n_steps=1000, graph_seed=1, h_seed=2, cpu_steps=1000),
+    "dense": dict(kind="dense", name="dense SK MaxCut: complete graph n=2000, J=+-1, R=1024, 1000-step "
+                                    "exponential beta 0.05->5, Adam lr 0.1, paper-mode gradient",
+                  n=2000, R=1024, n_steps=1000, graph_seed=3, h_seed=4, cpu_steps=4),
 }
 
 
@@ -51,30 +59,29 @@ def _peaks():
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
             return json.load(f), "measured"
     except Exception:
-        return {"hbm_gbs": 6400.0, "bf16_tflops": 1800.0}, "fallback"
+        return {"hbm_gbs": 6400.0, "bf16_tflops": 1800.0, "bf16_tflops_sustained": 1400.0}, "fallback"
 
 
-def _graph(wl):
+def _instance(wl):
     from paper_2412_09285_b300 import instances as I
+    if wl["kind"] == "dense":
+        return I.sk_dense(wl["n"], seed=wl["graph_seed"])
     if "m" in wl:
         return I.er_gnm(wl["n"], wl["m"], seed=wl["graph_seed"], weights=wl["weights"])
     return I.er_gnp(wl["n"], wl["p"], seed=wl["graph_seed"], weights=wl["weights"])
 
 
-def _algorithmic_bytes_per_step(n, nnz, R):
-    """Unique DRAM bytes one paper-mode step must move: h, m, v read + written
-    (24 B per node*replica), CSR col (4 B per directed entry) and row_ptr, the
-    sign words read once and written once (4 B per node per 32 replicas each)."""
-    wpn = R // 32
-    return 24 * n * R + 4 * nnz + 4 * (n + 1) + 8 * n * wpn
+def _make_problem(fem, wl, inst, stream):
+    if wl["kind"] == "dense":
+        return fem.Problem("maxcut", dense=inst.dense, stream=stream)
+    return fem.Problem("maxcut", graph=inst, stream=stream)
 
 
-def _traffic_from_profile(kernel_src):
-    """DRAM traffic per step launch from the committed ncu summary, if the kernel
-    source is unchanged since the capture (else None)."""
-    path = os.path.join(ROOT, "profiles", "maxcut_step_sparse_n1M_R32.md")
+def _traffic_from_profile(name, kernel_src):
+    """DRAM bytes per launch from a committed ncu summary, if the kernel source is
+    unchanged since the capture (else None)."""
     try:
-        txt = open(path).read()
+        txt = open(os.path.join(ROOT, "profiles", name)).read()
     except OSError:
         return None
     m1 = re.search(r"source_sha256:\s*([0-9a-f]{64})", txt)
@@ -83,6 +90,43 @@ def _traffic_from_profile(kernel_src):
         return None
     sha = hashlib.sha256(open(kernel_src, "rb").read()).hexdigest()
     return int(m2.group(1)) if sha == m1.group(1) else None
+
+
+def _roofline(wl, inst, step_ms, precision):
+    """Algorithmic work of one step launch / its measured duration, against the peak."""
+    peaks, src = _peaks()
+    csrc = os.path.join(ROOT, "paper_2412_09285_b300", "csrc")
+    R = wl["R"]
+    if wl["kind"] == "sparse":
+        n, nnz = inst.n, 2 * inst.n_edges
+        # h, m, v read + written (24 B per node*replica), CSR col (4 B per directed entry),
+        # row_ptr, the sign words read once and written once (4 B per node per 32 replicas)
+        alg = 24 * n * R + 4 * nnz + 4 * (n + 1) + 8 * n * (R // 32)
+        ach = alg / (step_ms / 1e3) / 1e9
+        return {"bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": ach / peaks["hbm_gbs"],
+                "traffic": _traffic_from_profile("maxcut_step_sparse_n1M_R32.md",
+                                                 os.path.join(csrc, "maxcut_sparse.cu")),
+                "kernel": "k_maxcut_step_paper<adam, unit, 4>", "algorithmic_bytes_per_launch": alg,
+                "launch_ms": step_ms, "peak_source": f"{src} hbm_gbs (copy), of {src}",
+                "frac_of_8TBs": ach / 8000.0}
+    n = inst.n
+    flops = 2.0 * n * n * R * (2 if precision == "bf16x2" else 1)
+    ach = flops / (step_ms / 1e3) / 1e12
+    if precision == "fp32":
+        # CUDA-core fp32: 148 SMs x 128 lanes x 2 flop x 2.032 GHz
+        peak, bound, psrc = 148 * 128 * 2 * 2.032e9 / 1e12, "alu", "derived fp32 FMA peak at 2032 MHz"
+    else:
+        base = peaks.get("bf16_tflops_sustained", peaks["bf16_tflops"])
+        peak = base * (2.0 if precision == "fp8" else 1.0)
+        bound = "tensor"
+        psrc = (f"{src} bf16_tflops_sustained" + (" x 2 (nominal fp8/bf16 ratio)" if precision == "fp8" else "")
+                + f", of {src}")
+    return {"bound": bound, "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
+            "traffic": _traffic_from_profile(f"dense_step_{precision}_sk2000_R1024.md",
+                                             os.path.join(csrc, "dense_tc.cu")),
+            "kernel": f"k_dense_step_{'fp32' if precision == 'fp32' else 'tc<' + precision + '>'}",
+            "algorithmic_flops_per_launch": flops, "launch_ms": step_ms, "peak_source": psrc}
 
 
 class ClockSampler:
@@ -94,6 +138,7 @@ class ClockSampler:
     def __init__(self, index):
         self.index = index
         self.proc = None
+        self.out = ""
 
     def __enter__(self):
         try:
@@ -106,7 +151,6 @@ class ClockSampler:
         return self
 
     def __exit__(self, *exc):
-        self.out = ""
         if self.proc is not None:
             time.sleep(0.15)
             self.proc.terminate()
@@ -136,28 +180,35 @@ class ClockSampler:
 
 
 def _dist():
-    ws = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    return ws, rank, local
+    return (int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0")),
+            int(os.environ.get("LOCAL_RANK", "0")))
 
 
-def cpu_baseline(wl, graph, steps):
+def _oracle_problem(wl, inst):
+    import oracle as O
+    if wl["kind"] == "dense":
+        return ("maxcut", inst.dense.astype(np.float64))
+    return ("maxcut", O.coupling_matrix(inst.n, inst.ei, inst.ej, inst.w))
+
+
+def _units_per_replica(wl, inst):
+    return inst.n * (inst.n - 1) // 2 if wl["kind"] == "dense" else inst.n_edges
+
+
+def cpu_baseline(wl, inst):
     """The FP64 oracle as it stands, timed on this host on a bounded sample."""
     import oracle as O
     from paper_2412_09285_b300 import instances as I
-    W = O.coupling_matrix(graph.n, graph.ei, graph.ej, graph.w)
-    h0 = I.initial_fields(graph.n, wl["R"], seed=wl["h_seed"]).astype(np.float64)
-    c0 = time.process_time()
-    t0 = time.perf_counter()
-    O.anneal(("maxcut", W), h0, wl["n_steps"], t_end=steps, mode="paper", optimizer="adam",
-             opt_kw=dict(lr=0.1))
-    wall = time.perf_counter() - t0
-    cpu = time.process_time() - c0
-    units = graph.n_edges * wl["R"] * steps
-    return {"value": units / wall, "unit": METRIC, "cores": max(1, round(cpu / wall)),
-            "kind": "oracle", "sample": f"first {steps} of {wl['n_steps']} steps, all {wl['R']} "
-                                        f"replicas, same instance; {wall:.1f} s wall"}
+    prob = _oracle_problem(wl, inst)
+    steps = wl["cpu_steps"]
+    h0 = I.initial_fields(inst.n, wl["R"], seed=wl["h_seed"]).astype(np.float64)
+    c0, t0 = time.process_time(), time.perf_counter()
+    O.anneal(prob, h0, wl["n_steps"], t_end=steps, mode="paper", optimizer="adam", opt_kw=dict(lr=0.1))
+    wall, cpu = time.perf_counter() - t0, time.process_time() - c0
+    units = _units_per_replica(wl, inst) * wl["R"] * steps
+    return {"value": units / wall, "unit": METRIC, "cores": max(1, round(cpu / wall)), "kind": "oracle",
+            "sample": f"first {steps} of {wl['n_steps']} steps, all {wl['R']} replicas, same instance; "
+                      f"{wall:.1f} s wall"}
 
 
 def run_reference(args, wl):
@@ -166,27 +217,25 @@ def run_reference(args, wl):
         return
     import oracle as O
     from paper_2412_09285_b300 import instances as I
-    graph = _graph(wl)
-    W = O.coupling_matrix(graph.n, graph.ei, graph.ej, graph.w)
-    r_sample = 1
-    h0 = I.initial_fields(graph.n, r_sample, seed=wl["h_seed"]).astype(np.float64)
+    inst = _instance(wl)
+    prob = _oracle_problem(wl, inst)
+    r_sample = 1 if wl["kind"] == "sparse" else 8
+    h0 = I.initial_fields(inst.n, r_sample, seed=wl["h_seed"]).astype(np.float64)
     n_steps = max(wl["n_steps"], args.warmup + args.steps)
-    h, opt = O.anneal(("maxcut", W), h0, n_steps, t_end=args.warmup, mode="paper", optimizer="adam",
+    h, opt = O.anneal(prob, h0, n_steps, t_end=args.warmup, mode="paper", optimizer="adam",
                       opt_kw=dict(lr=0.1))
-    c0 = time.process_time()
-    t0 = time.perf_counter()
-    O.anneal(("maxcut", W), h, n_steps, t_begin=args.warmup, t_end=args.warmup + args.steps,
-             mode="paper", optimizer="adam", opt=opt)
-    wall = time.perf_counter() - t0
-    cpu = time.process_time() - c0
-    value = graph.n_edges * r_sample * args.steps / wall
+    c0, t0 = time.process_time(), time.perf_counter()
+    O.anneal(prob, h, n_steps, t_begin=args.warmup, t_end=args.warmup + args.steps, mode="paper",
+             optimizer="adam", opt=opt)
+    wall, cpu = time.perf_counter() - t0, time.process_time() - c0
+    value = _units_per_replica(wl, inst) * r_sample * args.steps / wall
     line = {"metric": METRIC, "value": value, "unit": METRIC, "impl": "reference", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * wall / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": {"workload": wl["name"]},
             "cpu_baseline": {"value": value, "unit": METRIC, "cores": max(1, round(cpu / wall)),
                              "kind": "oracle",
-                             "sample": f"{r_sample} replica of {wl['R']} per step, same instance"},
+                             "sample": f"{r_sample} of {wl['R']} replicas per step, same instance"},
             "e2e": {"value": value, "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -202,21 +251,20 @@ def run_ours(args, wl):
     from paper_2412_09285_b300 import fem
     from paper_2412_09285_b300 import instances as I
 
-    graph = _graph(wl)
-    R = wl["R"]
-    n_steps = wl["n_steps"]
+    inst = _instance(wl)
+    R, n_steps = wl["R"], wl["n_steps"]
     K, Wm = args.steps, args.warmup
-    h0_host = I.initial_fields(graph.n, R, seed=wl["h_seed"] + 7919 * rank)
+    precision = args.precision if wl["kind"] == "dense" else "bf16"
+    h0_host = I.initial_fields(inst.n, R, seed=wl["h_seed"] + 7919 * rank)
     h0 = torch.from_numpy(h0_host).to(dev)
     stream = torch.cuda.current_stream()
-    prob = fem.Problem("maxcut", graph=graph, stream=stream)
-    info = prob.info()
-    kw = dict(grad_mode="paper", optimizer="adam", lr=0.1)
+    prob = _make_problem(fem, wl, inst, stream)
+    kw = dict(grad_mode="exact" if precision == "bf16x2" else "paper", optimizer="adam", lr=0.1,
+              precision=precision)
 
     def one_anneal(k, events):
-        """Fresh fields from the resident h0, then k steps, then the read-out.
-        Events bracket steps 1..k-1 so the per-launch step time excludes the
-        initialisation."""
+        """Fresh fields from the resident h0, then k steps, then the read-out.  Events
+        bracket steps 1..k-1 so the per-launch step time excludes the initialisation."""
         prob.anneal(h_init=h0, replicas=R, n_steps=n_steps, t_begin=0, t_end=1, **kw)
         if k > 1:
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -226,10 +274,8 @@ def run_ours(args, wl):
             events.append((e0, e1, k - 1))
         return prob.best()
 
-    # warm-up (untimed)
-    one_anneal(Wm, [])
+    one_anneal(Wm, [])  # warm-up (untimed)
     torch.cuda.synchronize()
-
     start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     k_ev = []
     launches0 = fem.fem_kernel_launches()
@@ -247,60 +293,55 @@ def run_ours(args, wl):
         torch.cuda.synchronize()
     launches = fem.fem_kernel_launches() - launches0
     t_ms = start.elapsed_time(end)
-    step_ms = sum(a.elapsed_time(b) for a, b, _ in k_ev) / sum(k for _, _, k in k_ev)
+    step_ms = sum(a.elapsed_time(b) for a, b, _ in k_ev) / max(1, sum(k for _, _, k in k_ev))
     if ws > 1:
         import torch.distributed as dist
         t = torch.tensor([t_ms], device=dev)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         t_ms = float(t.item())
-        # the best replica over all ranks (lowest energy, then lowest rank)
-        e = torch.tensor([float(best["energy_f64"][best["best_replica"]]), float(rank)], device=dev)
-        allb = [torch.zeros_like(e) for _ in range(ws)]
-        dist.all_gather(allb, e)
-    units_per_step = info["units_per_replica"] * R
+        from paper_2412_09285_b300.sharding import best_over_ranks
+        # the best replica over all ranks (after timing; one small all_gather)
+        g_best = best_over_ranks(float(best["energy_f64"][best["best_replica"]]), best["best_replica"],
+                                 rank, ws, device=dev)
+        best = dict(best, energy_f64=np.array([g_best[0]]), best_replica=0)
+    units_per_step = _units_per_replica(wl, inst) * R
     value = units_per_step * K * ws / (t_ms / 1e3)
 
-    # end-to-end through the public API from host buffers (create + anneal + read-out)
+    # end to end through the public API from host buffers (create + anneal + read-out)
     h0_pinned = torch.from_numpy(h0_host).pin_memory()
     e2e_steps = min(K, n_steps)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    p2 = fem.Problem("maxcut", graph=graph, stream=stream)
+    p2 = _make_problem(fem, wl, inst, stream)
     p2.anneal(h_init=h0_pinned.numpy(), replicas=R, n_steps=n_steps, t_end=e2e_steps, **kw)
-    b2 = p2.best()
+    p2.best()
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t0
     p2.close()
-    nnz = 2 * graph.n_edges
-    h2d = h0_host.nbytes + 4 * (graph.n + 1) + 4 * nnz
-    d2h = 4 * graph.n + 16 * R + 4
+    if wl["kind"] == "dense":
+        h2d = h0_host.nbytes + 4 * inst.n * inst.n
+    else:
+        h2d = h0_host.nbytes + 4 * (inst.n + 1) + 8 * inst.n_edges
+    d2h = 4 * inst.n + 16 * R + 4
     e2e = {"value": units_per_step * e2e_steps / e2e_s, "unit": METRIC,
            "h2d_bytes_per_step": int(round(h2d / e2e_steps)), "d2h_bytes_per_step": int(round(d2h / e2e_steps)),
-           "note": f"one full user call sequence per {e2e_steps} steps: fem_create_problem from the host "
-                   "edge list (host CSR build included), h_init from pinned host memory, anneal, "
-                   "fem_read_best to host; bytes are per step"}
-
-    peaks, src = _peaks()
-    alg = _algorithmic_bytes_per_step(graph.n, nnz, R)
-    achieved = alg / (step_ms / 1e3) / 1e9
-    kernel_src = os.path.join(ROOT, "paper_2412_09285_b300", "csrc", "maxcut_sparse.cu")
-    roof = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-            "frac": achieved / peaks["hbm_gbs"], "traffic": _traffic_from_profile(kernel_src),
-            "kernel": "k_maxcut_step<paper, adam, unit>", "algorithmic_bytes_per_launch": alg,
-            "launch_ms": step_ms, "peak_source": f"{src} hbm_gbs (copy)",
-            "frac_of_8TBs": achieved / 8000.0}
+           "note": f"one full user call sequence per {e2e_steps} steps: fem_create_problem from host arrays "
+                   "(host-side build included), h_init from pinned host memory, anneal, fem_read_best to host"}
     line = {"metric": METRIC, "value": value, "unit": METRIC, "n_gpus": ws, "steps": K, "warmup": Wm,
             "ms_per_step": t_ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f32", "data": "synthetic",
-            "config": {"workload": wl["name"], "n": graph.n, "undirected_edges": graph.n_edges,
-                       "replicas_per_gpu": R, "anneal_steps": n_steps,
+            "dtype": {"bf16": "bf16", "fp8": "e4m3", "bf16x2": "bf16x2", "fp32": "f32"}[precision]
+            if wl["kind"] == "dense" else "f32",
+            "data": "synthetic",
+            "config": {"workload": wl["name"], "n": inst.n, "units_per_replica": _units_per_replica(wl, inst),
+                       "replicas_per_gpu": R, "anneal_steps": n_steps, "precision": precision,
                        "parallelism": f"replica-sharded x{ws}",
-                       "l2": f"inputs larger than L2 (state {24 * graph.n * R / 1e6:.0f} MB per step)"},
-            "roofline": roof, "gpu_launches": int(launches), "e2e": e2e,
+                       "l2": ("inputs larger than L2" if wl["kind"] == "sparse" and inst.n > 100000
+                              else "working set L2-resident (latency/compute-bound workload)")},
+            "roofline": _roofline(wl, inst, step_ms, precision), "gpu_launches": int(launches), "e2e": e2e,
             "clocks": clk.summary(),
-            "best_cut": -int(best["energy_i64"][best["best_replica"]])}
+            "best_energy": float(best["energy_f64"][best["best_replica"]])}
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(wl, graph, args.cpu_steps)
+        line["cpu_baseline"] = cpu_baseline(wl, inst)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if ws > 1:
@@ -311,16 +352,18 @@ def run_ours(args, wl):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--steps", type=int, default=None)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="sparse", choices=sorted(WORKLOADS))
-    ap.add_argument("--cpu-steps", type=int, default=6)
+    ap.add_argument("--precision", default="bf16", choices=["bf16", "fp8", "bf16x2", "fp32"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
+    wl = WORKLOADS[args.workload]
+    if args.steps is None:
+        args.steps = wl["n_steps"]
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3
-    wl = WORKLOADS[args.workload]
     if args.impl == "reference":
         run_reference(args, wl)
     else:

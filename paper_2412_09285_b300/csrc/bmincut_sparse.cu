@@ -115,34 +115,19 @@ __device__ __forceinline__ void store_q(float* p, const float (&x)[Q]) {
   }
 }
 
-// One thread per (node, replica); a warp covers 32 consecutive (node, replica)
-// pairs, so R % RPW == 0 keeps every packed word inside one group of lanes.
+}  // namespace
+
+// The update of element e = i*R + r (node i, replica r) of one step: marginals,
+// neighbour contraction, centred gradient, optimizer, argmax word and the block's
+// shared-memory counts (scnt / sps, [R][Q]).  All 32 lanes of the warp must call it
+// together (word packing shuffles); lanes with act == false contribute nothing.
 template <int Q, int MODE>
-__global__ void __launch_bounds__(256) k_bmincut_step(BmcArgs a, StepScalars s) {
+__device__ __forceinline__ void bmincut_element(const BmcArgs& a, const StepScalars& s, long long e,
+                                                bool act, int lane, int32_t* scnt,
+                                                unsigned long long* sps) {
   constexpr int B = QBits<Q>::B, RPW = QBits<Q>::RPW;
   constexpr uint32_t SM = QBits<Q>::MASK;
-  extern __shared__ unsigned long long smem_u64[];
-  const int RQ = a.R * Q;
-  unsigned long long* sps = smem_u64;                                // [R*Q] exact mode
-  int32_t* scnt = reinterpret_cast<int32_t*>(smem_u64 + (MODE == FEM_GRAD_EXACT ? RQ : 0));
-  for (int x = threadIdx.x; x < RQ; x += blockDim.x) {
-    scnt[x] = 0;
-    if (MODE == FEM_GRAD_EXACT) sps[x] = 0ull;
-  }
-  if (blockIdx.x == 0) {
-    for (int x = threadIdx.x; x < RQ; x += blockDim.x) {
-      a.cnt_zero[x] = 0;
-      if (MODE == FEM_GRAD_EXACT) a.ps_zero[x] = 0ull;
-    }
-  }
-  __syncthreads();
-  const int lane = threadIdx.x & 31;
-  const long long total = (long long)a.n * a.R;
-  const long long stride = (long long)gridDim.x * blockDim.x;
-  for (long long base = (long long)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < total;
-       base += stride) {
-    const long long e = base + lane;
-    const bool act = e < total;
+  {
     const int i = act ? (int)(e / a.R) : 0;
     const int r = act ? (int)(e - (long long)i * a.R) : 0;
     const int wsel = r / RPW, sh = (r % RPW) * B;
@@ -173,7 +158,9 @@ __global__ void __launch_bounds__(256) k_bmincut_step(BmcArgs a, StepScalars s) 
         }
       } else {
         // accumulate sum_j W_ij (P_j(s) - 1/q): the constant drops out of every
-        // difference below, and the small deviations keep fp32 sums precise
+        // difference below.  The deviation is evaluated as
+        // (1/q) sum_s' P_j(s') expm1(h_j(s) - h_j(s')), which keeps full relative
+        // accuracy when P_j is near uniform (P_j - 1/q in fp32 would not).
         for (int k = beg; k < end; ++k) {
           const uint32_t j = a.col[k] & 0x7fffffffu;
           const float wk = a.w ? a.w[k] : 1.f;
@@ -181,7 +168,12 @@ __global__ void __launch_bounds__(256) k_bmincut_step(BmcArgs a, StepScalars s) 
           load_q<Q>(a.h_in + ((size_t)j * a.R + r) * Q, hj);
           softmax_q<Q>(hj, Pj, lj);
 #pragma unroll
-          for (int q = 0; q < Q; ++q) acc[q] = fmaf(wk, Pj[q] - 1.f / Q, acc[q]);
+          for (int q = 0; q < Q; ++q) {
+            float dq = 0.f;
+#pragma unroll
+            for (int q2 = 0; q2 < Q; ++q2) dq = fmaf(Pj[q2], expm1f(hj[q] - hj[q2]), dq);
+            acc[q] = fmaf(wk, dq * (1.f / Q), acc[q]);
+          }
         }
       }
     }
@@ -239,6 +231,38 @@ __global__ void __launch_bounds__(256) k_bmincut_step(BmcArgs a, StepScalars s) 
 #pragma unroll
     for (int off = 1; off < RPW; off <<= 1) word |= __shfl_xor_sync(kFullMask, word, off);
     if (act && (r % RPW) == 0) a.words_out[(size_t)i * a.wpn + wsel] = word;
+  }
+  (void)lane;
+}
+
+namespace {
+
+// One thread per (node, replica); a warp covers 32 consecutive (node, replica)
+// pairs, so R % RPW == 0 keeps every packed word inside one group of lanes.
+template <int Q, int MODE>
+__global__ void __launch_bounds__(256) k_bmincut_step(BmcArgs a, StepScalars s) {
+  extern __shared__ unsigned long long smem_u64[];
+  const int RQ = a.R * Q;
+  unsigned long long* sps = smem_u64;                                // [R*Q] exact mode
+  int32_t* scnt = reinterpret_cast<int32_t*>(smem_u64 + (MODE == FEM_GRAD_EXACT ? RQ : 0));
+  for (int x = threadIdx.x; x < RQ; x += blockDim.x) {
+    scnt[x] = 0;
+    if (MODE == FEM_GRAD_EXACT) sps[x] = 0ull;
+  }
+  if (blockIdx.x == 0) {
+    for (int x = threadIdx.x; x < RQ; x += blockDim.x) {
+      a.cnt_zero[x] = 0;
+      if (MODE == FEM_GRAD_EXACT) a.ps_zero[x] = 0ull;
+    }
+  }
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  const long long total = (long long)a.n * a.R;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long base = (long long)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < total;
+       base += stride) {
+    const long long e = base + lane;
+    bmincut_element<Q, MODE>(a, s, e, e < total, lane, scnt, sps);
   }
   __syncthreads();
   for (int x = threadIdx.x; x < RQ; x += blockDim.x) {

@@ -390,7 +390,16 @@ fem_status fem_create_problem(const fem_problem_desc* d, void* stream, fem_probl
   HostSat hs;
   fem_status st = FEM_OK;
   if (d->kind == FEM_MAXCUT && d->dense_J) {
-    return fail(FEM_ERR_UNSUPPORTED, "dense couplings are not built in this library version");
+    // symmetric, zero diagonal, integers with |J_ij| <= 127 (exact in bf16 and int8)
+    const float* J = d->dense_J;
+    for (int32_t i = 0; i < d->n; ++i)
+      for (int32_t j = 0; j < d->n; ++j) {
+        const float x = J[(size_t)i * d->n + j];
+        if (!std::isfinite(x) || x != std::rint(x) || std::fabs(x) > 127.f)
+          return fail(FEM_ERR_INVALID_ARG, "dense_J[%d][%d] must be an integer with |J| <= 127", i, j);
+        if (i == j && x != 0.f) return fail(FEM_ERR_INVALID_ARG, "dense_J must have a zero diagonal");
+        if (j > i && x != J[(size_t)j * d->n + i]) return fail(FEM_ERR_INVALID_ARG, "dense_J must be symmetric");
+      }
   } else if (d->kind == FEM_MAXKSAT) {
     if ((st = host_sat(d, hs)) != FEM_OK) return st;
   } else {
@@ -403,7 +412,8 @@ fem_status fem_create_problem(const fem_problem_desc* d, void* stream, fem_probl
   p->q = d->q;
   FEM_CUDA(cudaGetDevice(&p->device));
   FEM_CUDA(cudaDeviceGetAttribute(&p->sm_count, cudaDevAttrMultiProcessorCount, p->device));
-  st = d->kind == FEM_MAXKSAT ? upload_sat(p.get(), hs, s) : upload_graph(p.get(), hg, s);
+  if (d->kind == FEM_MAXCUT && d->dense_J) st = dense_upload(p.get(), d->dense_J, s);
+  else st = d->kind == FEM_MAXKSAT ? upload_sat(p.get(), hs, s) : upload_graph(p.get(), hg, s);
   if (st == FEM_OK) st = dev_alloc_t(p.get(), &p->err, 1);
   if (st == FEM_OK) {
     const cudaError_t e1 = cudaMemsetAsync(p->err, 0, sizeof(int32_t), s);
@@ -435,8 +445,18 @@ fem_status fem_anneal(fem_problem_t p, const fem_anneal_params* a, void* stream)
     return fail(FEM_ERR_INVALID_ARG, "unknown grad_mode %d", a->grad_mode);
   const int32_t R = a->replicas;
   if (R < 1) return fail(FEM_ERR_INVALID_ARG, "replicas must be >= 1");
-  if (p->kind == FEM_MAXCUT && R % 32 != 0)
+  if (p->dense) {
+    if (a->precision < FEM_PREC_FP32 || a->precision > FEM_PREC_FP8)
+      return fail(FEM_ERR_INVALID_ARG, "unknown precision %d", a->precision);
+    if (a->precision != FEM_PREC_FP32 && R % 128 != 0)
+      return fail(FEM_ERR_UNSUPPORTED, "the tensor-core path needs replicas %% 128 == 0");
+    if (a->precision == FEM_PREC_FP8 && (a->grad_mode != FEM_GRAD_PAPER || !p->dense_fp8_ok))
+      return fail(FEM_ERR_UNSUPPORTED, "FP8 needs the paper-mode gradient and |J_ij| <= 16");
+    if (a->t_begin > 0 && a->precision != p->precision)
+      return fail(FEM_ERR_STATE, "a resumed call must keep the precision");
+  } else if (p->kind == FEM_MAXCUT && R % 32 != 0) {
     return fail(FEM_ERR_UNSUPPORTED, "sparse MaxCut needs replicas %% 32 == 0");
+  }
   if (p->kind == FEM_BMINCUT) {
     const int rpw = 32 / bmincut_bits(p->q);
     if (R % 16 != 0 || R % rpw != 0 || R > 1024)
@@ -448,7 +468,29 @@ fem_status fem_anneal(fem_problem_t p, const fem_anneal_params* a, void* stream)
   FEM_CUDA(cudaGetDevice(&cur_dev));
   if (cur_dev != p->device) return fail(FEM_ERR_STATE, "the current device is not the problem's device");
 
-  if (a->t_begin == 0) {
+  if (a->t_begin == 0 && p->dense) {
+    if (!a->h_init) return fail(FEM_ERR_INVALID_ARG, "h_init is required when t_begin == 0");
+    fem_status st = FEM_OK;
+    if (p->dense_R_alloc != R || p->dense_prec_alloc != a->precision) {
+      if ((st = dense_state(p, R, a->precision)) != FEM_OK) return st;
+    }
+    p->R = R;
+    p->cur = 0;
+    p->steps_done = 0;
+    p->n_steps = a->n_steps;
+    p->grad_mode = a->grad_mode;
+    p->optimizer = a->optimizer;
+    p->precision = a->precision;
+    p->lambda_max = a->lambda_max;
+    const size_t per = (size_t)R * p->n_pad;
+    FEM_CUDA(cudaMemsetAsync(p->h[0], 0, per * sizeof(float), s));
+    FEM_CUDA(cudaMemsetAsync(p->m, 0, per * sizeof(float), s));
+    FEM_CUDA(cudaMemsetAsync(p->v, 0, per * sizeof(float), s));
+    if ((st = dense_set_fields(p, a->h_init, a->h_init_is_device != 0, s)) != FEM_OK) return st;
+    if ((st = dense_operand(p, 0, s)) != FEM_OK) return st;
+    if (!a->h_init_is_device) FEM_CUDA(cudaStreamSynchronize(s));
+    p->initialised = true;
+  } else if (a->t_begin == 0) {
     if (!a->h_init) return fail(FEM_ERR_INVALID_ARG, "h_init is required when t_begin == 0");
     fem_status st = ensure_state(p, R, s);
     if (st != FEM_OK) return st;
@@ -483,7 +525,8 @@ fem_status fem_anneal(fem_problem_t p, const fem_anneal_params* a, void* stream)
   if (a->t_end == a->t_begin) return FEM_OK;
   const std::vector<StepScalars> sc = make_step_scalars(*a, p->kind != FEM_BMINCUT);
   fem_status st = FEM_OK;
-  if (p->kind == FEM_MAXCUT) st = maxcut_sparse_steps(p, *a, sc, s);
+  if (p->dense) st = dense_steps(p, sc, a->t_begin, s);
+  else if (p->kind == FEM_MAXCUT) st = maxcut_sparse_steps(p, *a, sc, s);
   else if (p->kind == FEM_BMINCUT) st = bmincut_sparse_steps(p, sc, a->t_begin, s);
   else if (p->kind == FEM_MAXKSAT) st = sat_steps(p, sc, a->t_begin, s);
   else st = fail(FEM_ERR_UNSUPPORTED, "problem kind not built in this library version");
@@ -499,7 +542,8 @@ fem_status fem_read_best(fem_problem_t p, int32_t* best_replica, int32_t* states
   if (!p->initialised) return fail(FEM_ERR_STATE, "read-out before the first anneal call");
   cudaStream_t s = (cudaStream_t)stream;
   fem_status st = FEM_OK;
-  if (p->kind == FEM_MAXCUT) st = maxcut_readout(p, s);
+  if (p->dense) st = dense_readout(p, s);
+  else if (p->kind == FEM_MAXCUT) st = maxcut_readout(p, s);
   else if (p->kind == FEM_BMINCUT) st = bmincut_readout(p, s);
   else if (p->kind == FEM_MAXKSAT) st = sat_readout(p, s);
   else st = fail(FEM_ERR_UNSUPPORTED, "problem kind not built");
@@ -517,6 +561,11 @@ fem_status fem_read_fields(fem_problem_t p, float* h_host, void* stream) {
   if (!p->initialised) return fail(FEM_ERR_STATE, "no fields before the first anneal call");
   cudaStream_t s = (cudaStream_t)stream;
   const size_t per = (size_t)p->n * p->R * (p->kind == FEM_BMINCUT ? p->q : 1);
+  if (p->dense) {
+    const fem_status st = dense_get(p, p->h[0], h_host, s);
+    if (st != FEM_OK) return st;
+    return check_sticky(p, s);
+  }
   const float* src = current_fields(p);
   FEM_CUDA(cudaMemcpyAsync(h_host, src, per * sizeof(float), cudaMemcpyDeviceToHost, s));
   return check_sticky(p, s);
@@ -531,7 +580,8 @@ fem_status fem_read_states(fem_problem_t p, int32_t* states_host, void* stream) 
   const size_t total = (size_t)p->n * p->R;
   FEM_CUDA(cudaMallocAsync((void**)&tmp, total * sizeof(int32_t), s));
   fem_status st = FEM_OK;
-  if (p->kind == FEM_MAXCUT) st = maxcut_states_all(p, tmp, s);
+  if (p->dense) st = dense_states_all(p, tmp, s);
+  else if (p->kind == FEM_MAXCUT) st = maxcut_states_all(p, tmp, s);
   else if (p->kind == FEM_BMINCUT) st = bmincut_states_all(p, tmp, s);
   else if (p->kind == FEM_MAXKSAT) st = sat_states_all(p, tmp, s);
   else st = fail(FEM_ERR_UNSUPPORTED, "problem kind not built");
@@ -550,6 +600,13 @@ fem_status fem_read_state(fem_problem_t p, float* h, float* m, float* v, void* s
   if (!p->initialised) return fail(FEM_ERR_STATE, "no state before the first anneal call");
   cudaStream_t s = (cudaStream_t)stream;
   const size_t bytes = (size_t)p->n * p->R * (p->kind == FEM_BMINCUT ? p->q : 1) * sizeof(float);
+  if (p->dense) {
+    fem_status st = FEM_OK;
+    if (h && (st = dense_get(p, p->h[0], h, s)) != FEM_OK) return st;
+    if (m && (st = dense_get(p, p->m, m, s)) != FEM_OK) return st;
+    if (v && (st = dense_get(p, p->v, v, s)) != FEM_OK) return st;
+    return check_sticky(p, s);
+  }
   const float* src = current_fields(p);
   if (h) FEM_CUDA(cudaMemcpyAsync(h, src, bytes, cudaMemcpyDeviceToHost, s));
   if (m) FEM_CUDA(cudaMemcpyAsync(m, p->m, bytes, cudaMemcpyDeviceToHost, s));
@@ -567,6 +624,19 @@ fem_status fem_write_state(fem_problem_t p, const float* h, const float* m, cons
   cudaStream_t s = (cudaStream_t)stream;
   const size_t bytes = (size_t)p->n * p->R * (p->kind == FEM_BMINCUT ? p->q : 1) * sizeof(float);
   const int t = steps_done;
+  if (p->dense) {
+    const size_t per = (size_t)p->R * p->n_pad * sizeof(float);
+    FEM_CUDA(cudaMemsetAsync(p->m, 0, per, s));
+    FEM_CUDA(cudaMemsetAsync(p->v, 0, per, s));
+    fem_status st = dense_put(p, p->h[0], h, s);
+    if (st == FEM_OK && m) st = dense_put(p, p->m, m, s);
+    if (st == FEM_OK && v) st = dense_put(p, p->v, v, s);
+    if (st == FEM_OK) st = dense_operand(p, t, s);
+    if (st != FEM_OK) return st;
+    FEM_CUDA(cudaStreamSynchronize(s));
+    p->steps_done = steps_done;
+    return check_sticky(p, s);
+  }
   float* dst = fields_for_step(p, t);
   FEM_CUDA(cudaMemcpyAsync(dst, h, bytes, cudaMemcpyHostToDevice, s));
   if (m) FEM_CUDA(cudaMemcpyAsync(p->m, m, bytes, cudaMemcpyHostToDevice, s));

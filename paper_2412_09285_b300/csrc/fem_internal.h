@@ -1,6 +1,7 @@
 // Internal declarations of libfem (not part of the C ABI).
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -58,10 +59,16 @@ struct Problem {
   // ---- dense couplings (MaxCut, dense_J)
   bool dense = false;
   int32_t n_pad = 0;           // n rounded up to the tensor tile
-  float* J32 = nullptr;        // [n][n]
+  float* J32 = nullptr;        // fp32 [n_pad][n_pad]
   void* J16 = nullptr;         // bf16 [n_pad][n_pad]
   void* J8 = nullptr;          // e4m3 [n_pad][n_pad]
-  float* rowabs = nullptr;     // sum_j |J_ij|
+  int8_t* Ji8 = nullptr;       // int8 [n_pad][n_pad] (exact read-out)
+  float* rowabs = nullptr;     // c_i = 1 / sum_j |J_ij|
+  int64_t dense_wtot = 0;      // sum_{i<j} J_ij
+  bool dense_fp8_ok = false;   // every |J_ij| <= 16 (exact in e4m3)
+  int32_t dense_R_alloc = 0, dense_prec_alloc = -1;
+  void* mt_lo[2] = {nullptr, nullptr};  // exact mode, bf16 low parts
+  CUtensorMap tmap_a16, tmap_a8, tmap_b[2], tmap_blo[2];
 
   // ---- replica state
   int32_t R = 0, steps_done = 0, n_steps = 0;
@@ -128,6 +135,18 @@ fem_status bmincut_sparse_steps(Problem* p, const std::vector<StepScalars>& sc, 
 fem_status bmincut_derive(Problem* p, int t, cudaStream_t s);
 fem_status bmincut_readout(Problem* p, cudaStream_t s);
 fem_status bmincut_states_all(Problem* p, int32_t* out, cudaStream_t s);
+
+// ---- dense MaxCut on the tensor cores (dense_tc.cu)
+int dense_pad(int n);
+fem_status dense_upload(Problem* p, const float* J, cudaStream_t s);
+fem_status dense_state(Problem* p, int R, int prec);
+fem_status dense_set_fields(Problem* p, const float* h_nr, bool on_device, cudaStream_t s);
+fem_status dense_get(Problem* p, const float* src_rn, float* dst_nr_host, cudaStream_t s);
+fem_status dense_put(Problem* p, float* dst_rn, const float* src_nr_host, cudaStream_t s);
+fem_status dense_operand(Problem* p, int t, cudaStream_t s);
+fem_status dense_steps(Problem* p, const std::vector<StepScalars>& sc, int t_begin, cudaStream_t s);
+fem_status dense_readout(Problem* p, cudaStream_t s);
+fem_status dense_states_all(Problem* p, int32_t* out, cudaStream_t s);
 
 // ---- Max-k-SAT (sat.cu)
 fem_status sat_marginals(Problem* p, int t, cudaStream_t s);

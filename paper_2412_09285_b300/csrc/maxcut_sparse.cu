@@ -110,6 +110,21 @@ __global__ void __launch_bounds__(256) k_maxcut_step(MaxcutArgs a, StepScalars s
   }
 }
 
+// Transpose of a 32 x 32 bit matrix held one row per lane (lane e holds row e):
+// afterwards lane r holds column r, i.e. bit e of the result is bit r of row e.
+// Five butterfly stages exchange blocks of 16, 8, 4, 2 and 1 bits.
+__device__ __forceinline__ uint32_t warp_transpose32(uint32_t x, int lane) {
+  const uint32_t masks[5] = {0x0000FFFFu, 0x00FF00FFu, 0x0F0F0F0Fu, 0x33333333u, 0x55555555u};
+#pragma unroll
+  for (int s = 0; s < 5; ++s) {
+    const int j = 16 >> s;
+    const uint32_t m = masks[s];
+    const uint32_t y = __shfl_xor_sync(kFullMask, x, j);
+    x = (lane & j) ? (((y >> j) & m) | (x & ~m)) : ((x & m) | ((y << j) & ~m));
+  }
+  return x;
+}
+
 // Paper-mode step, tuned for HBM streaming.  A warp owns NPW consecutive nodes
 // (one block of 32 replicas) per iteration and issues every load of the group
 // before it computes: the 3*NPW state lines (h, m, v), then one coalesced load
@@ -170,22 +185,36 @@ __global__ void __launch_bounds__(256) k_maxcut_step_paper(MaxcutArgs a, StepSca
       }
     };
     load_chunk(cb);
+    // Unit weights, whole group in one chunk of <= 32 entries (the common case): a
+    // 32 x 32 bit transpose across the warp turns "lane e holds the word of entry e"
+    // into "lane r holds, for every entry e, bit r of its word"; a node's count is
+    // then one popcount of that word under the node's entry mask.
+    const bool one_chunk = UNIT && (bN - rb[0] <= 32);
+    uint32_t tr = 0;
+    if (one_chunk) tr = warp_transpose32(adj, lane);
     uint32_t ball[NPW];
 #pragma unroll
     for (int k = 0; k < NPW; ++k) {
       int nneg = 0;
       float facc = 0.f;
-      for (int e = rb[k]; e < rb[k + 1]; ++e) {
-        if (e >= cb + 32) {
-          cb += 32;
-          load_chunk(cb);
-        }
-        const uint32_t bit = (__shfl_sync(kFullMask, adj, e - cb) >> lane) & 1u;
-        if (UNIT) {
-          nneg += (int)bit;
-        } else {
-          const float w = __shfl_sync(kFullMask, wv, e - cb);
-          facc += bit ? -w : w;
+      if (one_chunk) {
+        const int len = rb[k + 1] - rb[k];
+        const uint32_t mask =
+            len == 0 ? 0u : (len >= 32 ? 0xffffffffu : ((1u << len) - 1u)) << (rb[k] - rb[0]);
+        nneg = __popc(tr & mask);
+      } else {
+        for (int e = rb[k]; e < rb[k + 1]; ++e) {
+          if (e >= cb + 32) {
+            cb += 32;
+            load_chunk(cb);
+          }
+          const uint32_t bit = (__shfl_sync(kFullMask, adj, e - cb) >> lane) & 1u;
+          if (UNIT) {
+            nneg += (int)bit;
+          } else {
+            const float w = __shfl_sync(kFullMask, wv, e - cb);
+            facc += bit ? -w : w;
+          }
         }
       }
       const int deg = rb[k + 1] - rb[k];

@@ -47,8 +47,16 @@ __device__ __forceinline__ void opt_update(float& h, float& m, float& v, float g
   }
 }
 
+// Square root by the hardware approximation (sqrt.approx.f32, a few ulp).
+__device__ __forceinline__ float sqrt_approx(float x) {
+  float y;
+  asm("sqrt.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
 // The same updates with the divisions done by the fast reciprocal (__fdividef,
-// 2 ulp); the divisors here are >= eps and far below 2^126.
+// 2 ulp) and the approximate square root; the divisors here are >= eps and far
+// below 2^126.
 template <int OPT>
 __device__ __forceinline__ void opt_update_fast(float& h, float& m, float& v, float g,
                                                 const StepScalars& s) {
@@ -56,10 +64,10 @@ __device__ __forceinline__ void opt_update_fast(float& h, float& m, float& v, fl
   if (OPT == FEM_OPT_ADAM) {
     m = fmaf(s.b1, m, s.omb1 * g);
     v = fmaf(s.b2, v, s.omb2 * g * g);
-    h = fmaf(-s.lr, __fdividef(m, fmaf(sqrtf(v), s.inv_sqrt_bc2, s.eps)), h);
+    h = fmaf(-s.lr, __fdividef(m, fmaf(sqrt_approx(v), s.inv_sqrt_bc2, s.eps)), h);
   } else if (OPT == FEM_OPT_RMSPROP) {
     v = fmaf(s.b1, v, s.omb1 * g * g);
-    const float q = __fdividef(g, sqrtf(v) + s.eps);
+    const float q = __fdividef(g, sqrt_approx(v) + s.eps);
     if (s.momentum > 0.f) {
       m = fmaf(s.momentum, m, q);
       h = fmaf(-s.lr, m, h);

@@ -51,7 +51,62 @@ WORKLOADS = {
     "dense": dict(kind="dense", name="dense SK MaxCut: complete graph n=2000, J=+-1, R=1024, 1000-step "
                                     "exponential beta 0.05->5, Adam lr 0.1, paper-mode gradient",
                   n=2000, R=1024, n_steps=1000, graph_seed=3, h_seed=4, cpu_steps=4),
+    "batched": dict(kind="batched", name="batched heterogeneous: 256 bMinCut (random geometric graphs, n "
+                                        "log-uniform 1k-64k, mean degree 10, unit weights, q=4, lambda_max=1) + "
+                                        "64 random Max-3-SAT (n log-uniform 5k-50k, M=4.2n), R=16 each, 1000-step "
+                                        "exponential beta 0.05->5, Adam lr 0.1, paper-mode gradient, one launch "
+                                        "per step, CUDA-graph step loop, autotuned work items",
+                    n_bmc=256, bmc_lo=1000, bmc_hi=64000, deg=10.0, q=4, n_sat=64, sat_lo=5000, sat_hi=50000,
+                    ratio=4.2, R=16, n_steps=1000, graph_seed=5, h_seed=6, cpu_steps=2),
 }
+
+
+class _BatchInstance:
+    """The members of the batched workload (graphs and clause lists)."""
+
+    def __init__(self, wl):
+        from paper_2412_09285_b300 import instances as I
+        s = wl["graph_seed"]
+        self.graphs = [I.rgg(int(n), wl["deg"], seed=1000 * s + k)
+                       for k, n in enumerate(I.loguniform_sizes(wl["n_bmc"], wl["bmc_lo"], wl["bmc_hi"], seed=s))]
+        self.sats = [I.random_ksat(int(n), int(round(wl["ratio"] * n)), 3, seed=2000 * s + k)
+                     for k, n in enumerate(I.loguniform_sizes(wl["n_sat"], wl["sat_lo"], wl["sat_hi"], seed=s + 1))]
+        self.n = sum(g.n for g in self.graphs) + sum(c.n for c in self.sats)
+        self.units = sum(g.n_edges for g in self.graphs) + sum(int(c.ptr[-1]) for c in self.sats)
+
+    def h0(self, wl, rank=0):
+        from paper_2412_09285_b300 import instances as I
+        base = wl["h_seed"] + 7919 * rank
+        return ([I.initial_fields(g.n, wl["R"], seed=base * 100000 + k, q=wl["q"]) for k, g in enumerate(self.graphs)]
+                + [I.initial_fields(c.n, wl["R"], seed=base * 100000 + 50000 + k) for k, c in enumerate(self.sats)])
+
+
+class _BatchRunner:
+    """Adapter with the single-problem interface the timing loop uses."""
+
+    def __init__(self, fem, wl, inst, stream):
+        self.probs = ([fem.Problem("bmincut", graph=g, q=wl["q"], stream=stream) for g in inst.graphs]
+                      + [fem.Problem("sat", clauses=c, stream=stream) for c in inst.sats])
+        self.batch = fem.Batch(self.probs, stream=stream)
+        self.h0 = None
+
+    def anneal(self, h_init=None, replicas=None, n_steps=1000, t_begin=0, t_end=None, **kw):
+        kw.pop("precision", None)
+        self.batch.anneal(h_inits=h_init if t_begin == 0 else None, replicas=replicas, n_steps=n_steps,
+                          t_begin=t_begin, t_end=t_end, lambda_max=1.0, **kw)
+
+    def best(self):
+        """Sum over members of each member's best energy (one read-out per member)."""
+        tot = 0.0
+        for p in self.probs:
+            r = p.best()
+            tot += float(r["energy_f64"][r["best_replica"]])
+        return {"energy_f64": np.array([tot]), "best_replica": 0, "energy_i64": np.array([int(tot)])}
+
+    def close(self):
+        self.batch.close()
+        for p in self.probs:
+            p.close()
 
 
 def _peaks():
@@ -64,6 +119,8 @@ def _peaks():
 
 def _instance(wl):
     from paper_2412_09285_b300 import instances as I
+    if wl["kind"] == "batched":
+        return _BatchInstance(wl)
     if wl["kind"] == "dense":
         return I.sk_dense(wl["n"], seed=wl["graph_seed"])
     if "m" in wl:
@@ -72,6 +129,8 @@ def _instance(wl):
 
 
 def _make_problem(fem, wl, inst, stream):
+    if wl["kind"] == "batched":
+        return _BatchRunner(fem, wl, inst, stream)
     if wl["kind"] == "dense":
         return fem.Problem("maxcut", dense=inst.dense, stream=stream)
     return fem.Problem("maxcut", graph=inst, stream=stream)
@@ -97,6 +156,23 @@ def _roofline(wl, inst, step_ms, precision):
     peaks, src = _peaks()
     csrc = os.path.join(ROOT, "paper_2412_09285_b300", "csrc")
     R = wl["R"]
+    if wl["kind"] == "batched":
+        q = wl["q"]
+        alg = 0
+        for g in inst.graphs:
+            n, nnz = g.n, 2 * g.n_edges
+            # h, m, v read + written, col, row_ptr, c^f and c^a, argmax words read once + written once
+            alg += 24 * q * n * R + 4 * nnz + 4 * (n + 1) + 8 * n + 8 * n * (R * 2 // 32)
+        for c in inst.sats:
+            n, L, M = c.n, int(c.ptr[-1]), c.n_clauses
+            # h, m, v read + written, marginals read once + written once, clause lists and transpose
+            alg += 24 * n * R + 8 * n * R + 4 * (n + 1) + 4 * L + 4 * (M + 1) + 4 * L
+        ach = alg / (step_ms / 1e3) / 1e9
+        return {"bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": ach / peaks["hbm_gbs"],
+                "traffic": _traffic_from_profile("batch_step_config4.md", os.path.join(csrc, "batch.cu")),
+                "kernel": "k_batch_step<4, paper>", "algorithmic_bytes_per_launch": alg, "launch_ms": step_ms,
+                "peak_source": f"{src} hbm_gbs (copy), of {src}", "frac_of_8TBs": ach / 8000.0}
     if wl["kind"] == "sparse":
         n, nnz = inst.n, 2 * inst.n_edges
         # h, m, v read + written (24 B per node*replica), CSR col (4 B per directed entry),
@@ -192,15 +268,46 @@ def _oracle_problem(wl, inst):
 
 
 def _units_per_replica(wl, inst):
+    if wl["kind"] == "batched":
+        return inst.units
     return inst.n * (inst.n - 1) // 2 if wl["kind"] == "dense" else inst.n_edges
+
+
+def _oracle_batch_sample(wl, inst, replicas, steps, n_members=(8, 4)):
+    """Oracle run over the first members of the batched workload; returns (units, wall, cpu)."""
+    import oracle as O
+    from paper_2412_09285_b300 import instances as I
+    units, wall, cpu = 0, 0.0, 0.0
+    for k, g in enumerate(inst.graphs[:n_members[0]]):
+        W = O.coupling_matrix(g.n, g.ei, g.ej, g.w)
+        h0 = I.initial_fields(g.n, replicas, seed=k, q=wl["q"]).astype(np.float64)
+        c0, t0 = time.process_time(), time.perf_counter()
+        O.anneal(("bmincut", W), h0, wl["n_steps"], t_end=steps, mode="paper", lambda_max=1.0)
+        wall += time.perf_counter() - t0
+        cpu += time.process_time() - c0
+        units += g.n_edges * replicas * steps
+    for k, c in enumerate(inst.sats[:n_members[1]]):
+        groups = O.sat_arrays(c.ptr, c.lits)
+        h0 = I.initial_fields(c.n, replicas, seed=k).astype(np.float64)
+        c0, t0 = time.process_time(), time.perf_counter()
+        O.anneal(("sat", groups), h0, wl["n_steps"], t_end=steps)
+        wall += time.perf_counter() - t0
+        cpu += time.process_time() - c0
+        units += int(c.ptr[-1]) * replicas * steps
+    return units, wall, cpu
 
 
 def cpu_baseline(wl, inst):
     """The FP64 oracle as it stands, timed on this host on a bounded sample."""
     import oracle as O
     from paper_2412_09285_b300 import instances as I
-    prob = _oracle_problem(wl, inst)
     steps = wl["cpu_steps"]
+    if wl["kind"] == "batched":
+        units, wall, cpu = _oracle_batch_sample(wl, inst, wl["R"], steps)
+        return {"value": units / wall, "unit": METRIC, "cores": max(1, round(cpu / wall)), "kind": "oracle",
+                "sample": f"first {steps} steps of the first 8 bMinCut and 4 SAT members, all {wl['R']} "
+                          f"replicas; {wall:.1f} s wall"}
+    prob = _oracle_problem(wl, inst)
     h0 = I.initial_fields(inst.n, wl["R"], seed=wl["h_seed"]).astype(np.float64)
     c0, t0 = time.process_time(), time.perf_counter()
     O.anneal(prob, h0, wl["n_steps"], t_end=steps, mode="paper", optimizer="adam", opt_kw=dict(lr=0.1))
@@ -218,17 +325,22 @@ def run_reference(args, wl):
     import oracle as O
     from paper_2412_09285_b300 import instances as I
     inst = _instance(wl)
-    prob = _oracle_problem(wl, inst)
-    r_sample = 1 if wl["kind"] == "sparse" else 8
-    h0 = I.initial_fields(inst.n, r_sample, seed=wl["h_seed"]).astype(np.float64)
-    n_steps = max(wl["n_steps"], args.warmup + args.steps)
-    h, opt = O.anneal(prob, h0, n_steps, t_end=args.warmup, mode="paper", optimizer="adam",
-                      opt_kw=dict(lr=0.1))
-    c0, t0 = time.process_time(), time.perf_counter()
-    O.anneal(prob, h, n_steps, t_begin=args.warmup, t_end=args.warmup + args.steps, mode="paper",
-             optimizer="adam", opt=opt)
-    wall, cpu = time.perf_counter() - t0, time.process_time() - c0
-    value = _units_per_replica(wl, inst) * r_sample * args.steps / wall
+    if wl["kind"] == "batched":
+        r_sample = 1
+        units, wall, cpu = _oracle_batch_sample(wl, inst, r_sample, args.steps, n_members=(4, 2))
+        value = units / wall
+    else:
+        prob = _oracle_problem(wl, inst)
+        r_sample = 1 if wl["kind"] == "sparse" else 8
+        h0 = I.initial_fields(inst.n, r_sample, seed=wl["h_seed"]).astype(np.float64)
+        n_steps = max(wl["n_steps"], args.warmup + args.steps)
+        h, opt = O.anneal(prob, h0, n_steps, t_end=args.warmup, mode="paper", optimizer="adam",
+                          opt_kw=dict(lr=0.1))
+        c0, t0 = time.process_time(), time.perf_counter()
+        O.anneal(prob, h, n_steps, t_begin=args.warmup, t_end=args.warmup + args.steps, mode="paper",
+                 optimizer="adam", opt=opt)
+        wall, cpu = time.perf_counter() - t0, time.process_time() - c0
+        value = _units_per_replica(wl, inst) * r_sample * args.steps / wall
     line = {"metric": METRIC, "value": value, "unit": METRIC, "impl": "reference", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * wall / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
@@ -255,8 +367,13 @@ def run_ours(args, wl):
     R, n_steps = wl["R"], wl["n_steps"]
     K, Wm = args.steps, args.warmup
     precision = args.precision if wl["kind"] == "dense" else "bf16"
-    h0_host = I.initial_fields(inst.n, R, seed=wl["h_seed"] + 7919 * rank)
-    h0 = torch.from_numpy(h0_host).to(dev)
+    if wl["kind"] == "batched":
+        h0_host = inst.h0(wl, rank)
+        h0 = [torch.from_numpy(x).to(dev) for x in h0_host]
+        Wm = max(Wm, 8)   # the first call also tunes the work-item size (two steps per candidate)
+    else:
+        h0_host = I.initial_fields(inst.n, R, seed=wl["h_seed"] + 7919 * rank)
+        h0 = torch.from_numpy(h0_host).to(dev)
     stream = torch.cuda.current_stream()
     prob = _make_problem(fem, wl, inst, stream)
     kw = dict(grad_mode="exact" if precision == "bf16x2" else "paper", optimizer="adam", lr=0.1,
@@ -308,20 +425,28 @@ def run_ours(args, wl):
     value = units_per_step * K * ws / (t_ms / 1e3)
 
     # end to end through the public API from host buffers (create + anneal + read-out)
-    h0_pinned = torch.from_numpy(h0_host).pin_memory()
+    if wl["kind"] == "batched":
+        h0_pinned = [torch.from_numpy(x).pin_memory().numpy() for x in h0_host]
+        h0_bytes = sum(x.nbytes for x in h0_host)
+    else:
+        h0_pinned = torch.from_numpy(h0_host).pin_memory().numpy()
+        h0_bytes = h0_host.nbytes
     e2e_steps = min(K, n_steps)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     p2 = _make_problem(fem, wl, inst, stream)
-    p2.anneal(h_init=h0_pinned.numpy(), replicas=R, n_steps=n_steps, t_end=e2e_steps, **kw)
+    p2.anneal(h_init=h0_pinned, replicas=R, n_steps=n_steps, t_end=e2e_steps, **kw)
     p2.best()
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t0
     p2.close()
     if wl["kind"] == "dense":
-        h2d = h0_host.nbytes + 4 * inst.n * inst.n
+        h2d = h0_bytes + 4 * inst.n * inst.n
+    elif wl["kind"] == "batched":
+        h2d = h0_bytes + sum(4 * (g.n + 1) + 8 * g.n_edges for g in inst.graphs) \
+            + sum(8 * (c.n_clauses + 1) + 8 * int(c.ptr[-1]) for c in inst.sats)
     else:
-        h2d = h0_host.nbytes + 4 * (inst.n + 1) + 8 * inst.n_edges
+        h2d = h0_bytes + 4 * (inst.n + 1) + 8 * inst.n_edges
     d2h = 4 * inst.n + 16 * R + 4
     e2e = {"value": units_per_step * e2e_steps / e2e_s, "unit": METRIC,
            "h2d_bytes_per_step": int(round(h2d / e2e_steps)), "d2h_bytes_per_step": int(round(d2h / e2e_steps)),

@@ -188,6 +188,26 @@ fem_status fem_anneal(fem_problem_t p, const fem_anneal_params* prm, void* strea
 fem_status fem_read_best(fem_problem_t p, int32_t* best_replica, int32_t* states,
                          int64_t* energy_i64, double* energy_f64, void* stream);
 
+/* Batches: many sparse bMinCut and Max-k-SAT problems advanced together (the
+ * batched, heterogeneous form of the per-step update).  One kernel launch per step
+ * walks a work list of (member, node range) items across all members, the step loop
+ * is captured in a CUDA graph and replayed, and the work-item size is chosen by
+ * timing candidates on the first steps of the first call (cached per problem shape;
+ * every candidate gives bit-identical results).  Each member keeps its own state:
+ * after a batched anneal, fem_read_best / fem_read_fields on a member behave as if
+ * that member had been annealed alone with the same parameters (bit-identical).
+ *   fem_batch_create  members must be sparse bMinCut or Max-k-SAT problems on one
+ *                     device; bMinCut members must share q.  The members must outlive
+ *                     the batch.  The batch owns only its work list and graph.
+ *   fem_batch_anneal  fem_anneal semantics for every member with the same parameters
+ *                     (replicas % 16 == 0); h_init[k] is member k's initial fields
+ *                     (host, required when t_begin == 0, else ignored). */
+typedef struct fem_batch* fem_batch_t;
+fem_status fem_batch_create(fem_problem_t const* probs, int32_t count, fem_batch_t* out);
+fem_status fem_batch_anneal(fem_batch_t b, const fem_anneal_params* prm, const float* const* h_init,
+                            void* stream);
+void fem_batch_destroy(fem_batch_t b);
+
 /* Copy the current fields to host memory `h_host` (layout of the file header;
  * n*R (single field) or n*R*q floats).  Synchronises `stream`. */
 fem_status fem_read_fields(fem_problem_t p, float* h_host, void* stream);

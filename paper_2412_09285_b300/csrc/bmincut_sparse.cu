@@ -20,221 +20,9 @@
 // (t+1)%3 and zeroes (t+2)%3 for the step after.
 #include <cmath>
 
-#include "fem_internal.h"
-#include "step_common.cuh"
+#include "bmincut_core.cuh"
 
 namespace fem {
-namespace {
-
-template <int Q>
-struct QBits {
-  static constexpr int B = Q <= 2 ? 1 : (Q <= 4 ? 2 : 4);
-  static constexpr int RPW = 32 / B;  // replicas per word
-  static constexpr uint32_t MASK = (1u << B) - 1u;
-};
-
-constexpr float kPsumScale = 4294967296.0f;         // 2^32
-constexpr float kPsumInv = 2.3283064365386963e-10f;  // 2^-32
-
-struct BmcArgs {
-  const int32_t* row_ptr;
-  const uint32_t* col;
-  const float* w;  // NULL for unit weights
-  const float* cf;
-  const float* ca;
-  int32_t n, R, wpn, opt;
-  const float* h_in;
-  float* h_out;
-  float* m;
-  float* v;
-  const uint32_t* words_in;
-  uint32_t* words_out;
-  const int32_t* cnt_in;
-  int32_t* cnt_out;
-  int32_t* cnt_zero;
-  const unsigned long long* ps_in;
-  unsigned long long* ps_out;
-  unsigned long long* ps_zero;
-};
-
-template <int Q>
-__device__ __forceinline__ void softmax_q(const float (&h)[Q], float (&P)[Q], float (&lnP)[Q]) {
-  float mx = h[0];
-#pragma unroll
-  for (int s = 1; s < Q; ++s) mx = fmaxf(mx, h[s]);
-  float ex[Q], Z = 0.f;
-#pragma unroll
-  for (int s = 0; s < Q; ++s) {
-    ex[s] = expf(h[s] - mx);
-    Z += ex[s];
-  }
-  const float invZ = 1.f / Z, lz = logf(Z);
-#pragma unroll
-  for (int s = 0; s < Q; ++s) {
-    P[s] = ex[s] * invZ;
-    lnP[s] = h[s] - mx - lz;
-  }
-}
-
-template <int Q>
-__device__ __forceinline__ int argmax_q(const float (&h)[Q]) {
-  int best = 0;
-  float bv = h[0];
-#pragma unroll
-  for (int s = 1; s < Q; ++s)
-    if (h[s] > bv) {
-      bv = h[s];
-      best = s;
-    }
-  return best;
-}
-
-template <int Q>
-__device__ __forceinline__ void load_q(const float* p, float (&x)[Q]) {
-  if (Q == 4) {
-    const float4 t = *reinterpret_cast<const float4*>(p);
-    x[0] = t.x; x[1] = t.y; x[2] = t.z; x[3] = t.w;
-  } else if (Q == 2) {
-    const float2 t = *reinterpret_cast<const float2*>(p);
-    x[0] = t.x; x[1] = t.y;
-  } else {
-#pragma unroll
-    for (int s = 0; s < Q; ++s) x[s] = p[s];
-  }
-}
-
-template <int Q>
-__device__ __forceinline__ void store_q(float* p, const float (&x)[Q]) {
-  if (Q == 4) {
-    *reinterpret_cast<float4*>(p) = make_float4(x[0], x[1], x[2], x[3]);
-  } else if (Q == 2) {
-    *reinterpret_cast<float2*>(p) = make_float2(x[0], x[1]);
-  } else {
-#pragma unroll
-    for (int s = 0; s < Q; ++s) p[s] = x[s];
-  }
-}
-
-}  // namespace
-
-// The update of element e = i*R + r (node i, replica r) of one step: marginals,
-// neighbour contraction, centred gradient, optimizer, argmax word and the block's
-// shared-memory counts (scnt / sps, [R][Q]).  All 32 lanes of the warp must call it
-// together (word packing shuffles); lanes with act == false contribute nothing.
-template <int Q, int MODE>
-__device__ __forceinline__ void bmincut_element(const BmcArgs& a, const StepScalars& s, long long e,
-                                                bool act, int lane, int32_t* scnt,
-                                                unsigned long long* sps) {
-  constexpr int B = QBits<Q>::B, RPW = QBits<Q>::RPW;
-  constexpr uint32_t SM = QBits<Q>::MASK;
-  {
-    const int i = act ? (int)(e / a.R) : 0;
-    const int r = act ? (int)(e - (long long)i * a.R) : 0;
-    const int wsel = r / RPW, sh = (r % RPW) * B;
-    float h[Q], mm[Q], vv[Q];
-#pragma unroll
-    for (int q = 0; q < Q; ++q) h[q] = mm[q] = vv[q] = 0.f;
-    const size_t idx = ((size_t)i * a.R + r) * Q;
-    float acc[Q];
-#pragma unroll
-    for (int q = 0; q < Q; ++q) acc[q] = 0.f;
-    int own = 0;
-    float cf = 0.f, ca = 0.f;
-    if (act) {
-      load_q<Q>(a.h_in + idx, h);
-      load_q<Q>(a.m + idx, mm);
-      if (a.opt != FEM_OPT_SGD) load_q<Q>(a.v + idx, vv);
-      const int beg = a.row_ptr[i], end = a.row_ptr[i + 1];
-      if (MODE == FEM_GRAD_PAPER) {
-        own = (int)((a.words_in[(size_t)i * a.wpn + wsel] >> sh) & SM);
-        cf = a.cf[i];
-        ca = a.ca[i];
-        for (int k = beg; k < end; ++k) {
-          const uint32_t j = a.col[k] & 0x7fffffffu;
-          const float wk = a.w ? a.w[k] : 1.f;
-          const int sj = (int)((a.words_in[(size_t)j * a.wpn + wsel] >> sh) & SM);
-#pragma unroll
-          for (int q = 0; q < Q; ++q) acc[q] += (sj == q) ? wk : 0.f;
-        }
-      } else {
-        // accumulate sum_j W_ij (P_j(s) - 1/q): the constant drops out of every
-        // difference below.  The deviation is evaluated as
-        // (1/q) sum_s' P_j(s') expm1(h_j(s) - h_j(s')), which keeps full relative
-        // accuracy when P_j is near uniform (P_j - 1/q in fp32 would not).
-        for (int k = beg; k < end; ++k) {
-          const uint32_t j = a.col[k] & 0x7fffffffu;
-          const float wk = a.w ? a.w[k] : 1.f;
-          float hj[Q], Pj[Q], lj[Q];
-          load_q<Q>(a.h_in + ((size_t)j * a.R + r) * Q, hj);
-          softmax_q<Q>(hj, Pj, lj);
-#pragma unroll
-          for (int q = 0; q < Q; ++q) {
-            float dq = 0.f;
-#pragma unroll
-            for (int q2 = 0; q2 < Q; ++q2) dq = fmaf(Pj[q2], expm1f(hj[q] - hj[q2]), dq);
-            acc[q] = fmaf(wk, dq * (1.f / Q), acc[q]);
-          }
-        }
-      }
-    }
-    // Centred gradient ghat(s) - sum_s' P(s') ghat(s') = sum_s' P(s') [ghat(s) - ghat(s')],
-    // with every difference formed before it is scaled: integer count differences
-    // (paper), exact fixed-point column-sum differences (exact), ln P(s) - ln P(s') =
-    // h(s) - h(s').  Algebraically the formula above; in fp32 it avoids cancelling the
-    // large s-independent parts (deg/q, lambda N/q) of ghat.
-    float P[Q], lnP[Q];
-    softmax_q<Q>(h, P, lnP);
-    int32_t nc[Q];
-    unsigned long long ps[Q];
-#pragma unroll
-    for (int q = 0; q < Q; ++q) {
-      if (MODE == FEM_GRAD_PAPER) nc[q] = act ? a.cnt_in[r * Q + q] - (own == q ? 1 : 0) : 0;
-      else ps[q] = act ? a.ps_in[r * Q + q] : 0ull;
-    }
-    float cen[Q];
-#pragma unroll
-    for (int q = 0; q < Q; ++q) {
-      float c = 0.f;
-#pragma unroll
-      for (int q2 = 0; q2 < Q; ++q2) {
-        float d;
-        if (MODE == FEM_GRAD_PAPER) {
-          d = -cf * (acc[q] - acc[q2]) + s.lambda * ca * (float)(nc[q] - nc[q2]);
-        } else {
-          const float dcol = (float)(long long)(ps[q] - ps[q2]) * kPsumInv;
-          d = -2.f * (acc[q] - acc[q2]) + 2.f * s.lambda * (dcol - (P[q] - P[q2]));
-        }
-        d = fmaf(h[q] - h[q2], s.inv_beta, d);
-        c = fmaf(P[q2], d, c);
-      }
-      cen[q] = c;
-    }
-#pragma unroll
-    for (int q = 0; q < Q; ++q) {
-      const float g = s.gq * cen[q] * P[q];
-      opt_update_rt(a.opt, h[q], mm[q], vv[q], g, s);
-    }
-    const int sn = argmax_q<Q>(h);
-    if (act) {
-      store_q<Q>(a.h_out + idx, h);
-      store_q<Q>(a.m + idx, mm);
-      if (a.opt != FEM_OPT_SGD) store_q<Q>(a.v + idx, vv);
-      atomicAdd(&scnt[r * Q + sn], 1);
-      if (MODE == FEM_GRAD_EXACT) {
-        float Pn[Q], ln[Q];
-        softmax_q<Q>(h, Pn, ln);
-#pragma unroll
-        for (int q = 0; q < Q; ++q) atomicAdd(&sps[r * Q + q], __float2ull_rn(Pn[q] * kPsumScale));
-      }
-    }
-    uint32_t word = act ? ((uint32_t)sn << sh) : 0u;
-#pragma unroll
-    for (int off = 1; off < RPW; off <<= 1) word |= __shfl_xor_sync(kFullMask, word, off);
-    if (act && (r % RPW) == 0) a.words_out[(size_t)i * a.wpn + wsel] = word;
-  }
-  (void)lane;
-}
-
 namespace {
 
 // One thread per (node, replica); a warp covers 32 consecutive (node, replica)

@@ -17,12 +17,13 @@
 // consecutive addresses across a warp for every replica column.  The next step's
 // operand M^T is written as [R][n_pad] bf16 / e4m3, K-major for the tensor cores.
 //
-// Tensor-core kernel: CTA = 128 threads, tile = 128 rows (i) x 128 replicas (r),
-// K loop over j in 128-byte chunks fed by TMA (128B swizzle) through a 4-stage
-// mbarrier pipeline; thread 0 issues the copies, thread 32 issues tcgen05.mma into a
-// 128-column fp32 TMEM accumulator; then all four warps read their 32 TMEM lanes
-// (tcgen05.ld 32x32b) and run the fused epilogue.  Every wait is bounded in time;
-// on expiry the kernel records FEM's timeout bit and leaves, freeing its TMEM.
+// Tensor-core kernel: CTA = 512 threads, tile = 128 rows (i) x 128 replicas (r),
+// K loop over j in 128-byte chunks fed by TMA (128B swizzle) through a 6-stage
+// (hi+lo: 4-stage) mbarrier pipeline; thread 0 issues the copies, thread 32 issues
+// tcgen05.mma into a 128-column fp32 TMEM accumulator; then all 16 warps read TMEM
+// (tcgen05.ld 32x32b: warp w owns lane quadrant w%4 and 32 replica columns) and run
+// the fused epilogue.  Every wait is bounded in time; on expiry the kernel records
+// FEM's timeout bit and leaves, freeing its TMEM.
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_fp8.h>
@@ -39,7 +40,9 @@ namespace fem {
 namespace {
 
 constexpr int kTile = 128;        // rows (i) and replica columns (r) per CTA
-constexpr int kStages = 4;
+constexpr int kMaxStages = 6;
+constexpr int kThreads = 512;  // 16 warps: all run the epilogue (lane quadrant = warp % 4)
+__host__ __device__ constexpr int stages_for(int prec) { return prec == FEM_PREC_BF16X2 ? 4 : 6; }
 constexpr int kChunkBytes = 128;  // K bytes per pipeline stage (one swizzle row)
 constexpr unsigned long long kWaitNs = 2000000000ull;  // 2 s bound on any wait
 
@@ -164,7 +167,7 @@ __device__ __forceinline__ uint16_t bf16_bits(float x) {
 
 // ------------------------------------------------------------ the fused step
 template <int PREC>  // FEM_PREC_BF16, FEM_PREC_BF16X2 or FEM_PREC_FP8
-__global__ void __launch_bounds__(128, 1) k_dense_step_tc(const __grid_constant__ CUtensorMap tmA,
+__global__ void __launch_bounds__(kThreads, 1) k_dense_step_tc(const __grid_constant__ CUtensorMap tmA,
                                                          const __grid_constant__ CUtensorMap tmB,
                                                          const __grid_constant__ CUtensorMap tmBlo,
                                                          DenseArgs a, StepScalars s) {
@@ -178,8 +181,9 @@ __global__ void __launch_bounds__(128, 1) k_dense_step_tc(const __grid_constant_
 
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  __shared__ __align__(8) uint64_t full[kStages];
-  __shared__ __align__(8) uint64_t empty[kStages];
+  constexpr int kStages = stages_for(PREC);
+  __shared__ __align__(8) uint64_t full[kMaxStages];
+  __shared__ __align__(8) uint64_t empty[kMaxStages];
   __shared__ __align__(8) uint64_t done;
   __shared__ uint32_t tmem_base_slot;
 
@@ -239,12 +243,14 @@ __global__ void __launch_bounds__(128, 1) k_dense_step_tc(const __grid_constant_
   const bool ok = mbar_wait(&done, 0, a.err);
   tc_fence_after();
   if (ok) {
-    const int i = i0 + warp * 32 + lane;
+    // warp w reads TMEM lanes 32*(w%4).. (its quadrant) and replica columns 32*(w/4)..
+    const int quad = warp & 3;
+    const int i = i0 + quad * 32 + lane;
     const bool row = i < a.n;
     const float cn = row ? (a.mode == FEM_GRAD_PAPER ? a.cnorm[i] : 2.f) : 0.f;
-    for (int c0 = 0; c0 < kTile; c0 += 32) {
+    for (int c0 = (warp >> 2) * 32; c0 < kTile; c0 += 32 * (kThreads / 128)) {
       uint32_t acc[32];
-      tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, acc);
+      tmem_ld32(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)c0, acc);
       if (!row) continue;
 #pragma unroll
       for (int c = 0; c < 32; ++c) {  // R % 128 == 0: every column is a replica
@@ -499,7 +505,7 @@ fem_status make_map(CUtensorMap* m, const void* base, int rows, int n_pad, int e
 }
 
 size_t tc_smem_bytes(int prec) {
-  return (size_t)kStages * kTile * kChunkBytes * (prec == FEM_PREC_BF16X2 ? 3 : 2) + 1024;
+  return (size_t)stages_for(prec) * kTile * kChunkBytes * (prec == FEM_PREC_BF16X2 ? 3 : 2) + 1024;
 }
 
 template <int PREC>
@@ -513,7 +519,7 @@ fem_status launch_tc(Problem* p, const DenseArgs& a, const StepScalars& s, int i
   const CUtensorMap* mb = &p->tmap_b[in];
   const CUtensorMap* mlo = PREC == FEM_PREC_BF16X2 ? &p->tmap_blo[in] : mb;
   const dim3 grid(p->n_pad / kTile, (p->R + kTile - 1) / kTile);
-  k_dense_step_tc<PREC><<<grid, 128, tc_smem_bytes(PREC), st>>>(
+  k_dense_step_tc<PREC><<<grid, kThreads, tc_smem_bytes(PREC), st>>>(
       PREC == FEM_PREC_FP8 ? p->tmap_a8 : p->tmap_a16, *mb, *mlo, a, s);
   return FEM_OK;
 }

@@ -77,6 +77,9 @@ def _load():
         "fem_status_string": (C.c_char_p, [S]),
         "fem_last_error": (C.c_char_p, []),
         "fem_kernel_launches": (C.c_int64, []),
+        "fem_batch_create": (S, [P, C.c_int32, C.POINTER(P)]),
+        "fem_batch_anneal": (S, [P, C.POINTER(fem_anneal_params), P, P]),
+        "fem_batch_destroy": (None, [P]),
         "fem_maxcut_energies_noalloc": (S, [P, P, C.c_int32, P, C.c_int32, P, P, P]),
     }
     for name, (res, args) in sig.items():
@@ -293,6 +296,61 @@ class Problem:
     def close(self):
         if getattr(self, "handle", None):
             fem_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# ----------------------------------------------------------------- batches
+
+def fem_batch_create(handles) -> int:
+    arr = (C.c_void_p * len(handles))(*handles)
+    out = C.c_void_p()
+    _check(_lib.fem_batch_create(C.cast(arr, C.c_void_p), len(handles), C.byref(out)), "fem_batch_create")
+    return out.value
+
+
+def fem_batch_anneal(batch, params, h_inits=None, stream=None):
+    ptrs = None
+    if h_inits is not None:
+        ptrs = (C.c_void_p * len(h_inits))(*[_ptr(h) for h in h_inits])
+    _check(_lib.fem_batch_anneal(batch, C.byref(params), C.cast(ptrs, C.c_void_p) if ptrs else None,
+                                 _stream(stream)), "fem_batch_anneal")
+
+
+def fem_batch_destroy(batch):
+    _lib.fem_batch_destroy(batch)
+
+
+class Batch:
+    """Several Problem objects advanced together by fem_batch_anneal."""
+
+    def __init__(self, problems, stream=None):
+        self.problems = list(problems)
+        self.stream = stream
+        self.handle = fem_batch_create([p.handle for p in self.problems])
+
+    def anneal(self, h_inits=None, replicas=None, n_steps=1000, t_begin=0, t_end=None, **kw):
+        on_device = False
+        if h_inits is not None:
+            on_device = all(getattr(h, "is_cuda", False) for h in h_inits)
+            if not on_device:
+                h_inits = [np.ascontiguousarray(h, np.float32) for h in h_inits]
+            replicas = h_inits[0].shape[1] if replicas is None else replicas
+        for p in self.problems:
+            p.replicas = int(replicas)
+        params = make_params(replicas, n_steps, t_begin, t_end, None, **kw)
+        params.h_init_is_device = int(on_device)
+        fem_batch_anneal(self.handle, params, h_inits, self.stream)
+        return self
+
+    def close(self):
+        if getattr(self, "handle", None):
+            fem_batch_destroy(self.handle)
             self.handle = None
 
     def __del__(self):

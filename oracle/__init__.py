@@ -14,3 +14,4 @@ only check is the oracle itself are marked "parity unpinned" there.
 """
 from .fem import *  # noqa: F401,F403
 from .brute import *  # noqa: F401,F403
+from .mpnn import *  # noqa: F401,F403

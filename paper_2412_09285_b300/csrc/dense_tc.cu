@@ -640,7 +640,7 @@ fem_status dense_get(Problem* p, const float* src_rn, float* dst_nr_host, cudaSt
   k_transpose_rn_to_nr<<<grid, dim3(32, 8), 0, s>>>(src_rn, p->n, p->R, p->n_pad, tmp);
   count_launches(1);
   cudaError_t e = cudaGetLastError();
-  if (e == cudaSuccess) e = cudaMemcpyAsync(dst_nr_host, tmp, bytes, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(dst_nr_host, tmp, bytes, cudaMemcpyDefault, s);
   cudaFreeAsync(tmp, s);
   if (e != cudaSuccess) return cuda_fail(e, "dense fields download");
   return FEM_OK;

@@ -567,7 +567,7 @@ fem_status fem_read_fields(fem_problem_t p, float* h_host, void* stream) {
     return check_sticky(p, s);
   }
   const float* src = current_fields(p);
-  FEM_CUDA(cudaMemcpyAsync(h_host, src, per * sizeof(float), cudaMemcpyDeviceToHost, s));
+  FEM_CUDA(cudaMemcpyAsync(h_host, src, per * sizeof(float), cudaMemcpyDefault, s));  // host or device
   return check_sticky(p, s);
 }
 

@@ -101,7 +101,8 @@ def er_gnm(n: int, m: int, seed: int, weights: str = "unit") -> Graph:
         b = rng.integers(0, n, size=need, dtype=np.int64)
         ok = a != b
         lo, hi = np.minimum(a[ok], b[ok]), np.maximum(a[ok], b[ok])
-        keys = np.unique(np.concatenate([keys, lo * n + hi]))
+        s = np.sort(np.concatenate([keys, lo * n + hi]))   # sorted distinct keys (== np.unique)
+        keys = s[np.concatenate(([True], s[1:] != s[:-1]))] if s.size else s
     # keep a uniform subset of exactly m distinct pairs, then sort by (i, j)
     keys = np.sort(rng.permutation(keys)[:m])
     ei, ej = (keys // n).astype(np.int32), (keys % n).astype(np.int32)
@@ -165,6 +166,39 @@ def initial_fields(n: int, replicas: int, seed: int, q: int = 1) -> np.ndarray:
     rng = np.random.Generator(np.random.PCG64(seed))
     shape = (n, replicas) if q == 1 else (n, replicas, q)
     return (0.001 * rng.standard_normal(shape)).astype(np.float32)
+
+
+MPNN_SHAPES = [("A1", (4, 64)), ("B1", (4, 64)), ("b1", (64,)), ("A2", (64, 64)), ("B2", (64, 64)),
+               ("b2", (64,)), ("A3", (64, 64)), ("B3", (64, 64)), ("b3", (64,)), ("C", (64, 4)), ("c", (4,))]
+
+
+def mpnn_init(seed: int) -> dict:
+    """Initial weights of the warm-start network: Glorot-uniform matrices, zero biases,
+    filter taps starting at (1, 0, 0, 0) (prediction = the replica's own fields)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    out = {}
+    for name, shape in MPNN_SHAPES:
+        if len(shape) == 2:
+            lim = np.sqrt(6.0 / (shape[0] + shape[1]))
+            out[name] = rng.uniform(-lim, lim, size=shape) * (0.1 if name == "C" else 1.0)
+        else:
+            out[name] = np.zeros(shape)
+    out["c"][0] = 1.0
+    return out
+
+
+def mpnn_flatten(params: dict) -> np.ndarray:
+    """Parameters as one float32 vector in the library's order (row-major blocks)."""
+    return np.concatenate([np.asarray(params[k], np.float64).ravel() for k, _ in MPNN_SHAPES]).astype(np.float32)
+
+
+def mpnn_unflatten(vec) -> dict:
+    out, off = {}, 0
+    for k, shape in MPNN_SHAPES:
+        size = int(np.prod(shape))
+        out[k] = np.asarray(vec[off:off + size], np.float64).reshape(shape)
+        off += size
+    return out
 
 
 def loguniform_sizes(count: int, lo: int, hi: int, seed: int) -> np.ndarray:

@@ -128,11 +128,13 @@ def _instance(wl):
     return I.er_gnp(wl["n"], wl["p"], seed=wl["graph_seed"], weights=wl["weights"])
 
 
-def _make_problem(fem, wl, inst, stream):
+def _make_problem(fem, wl, inst, stream, dense_launch="auto"):
     if wl["kind"] == "batched":
         return _BatchRunner(fem, wl, inst, stream)
     if wl["kind"] == "dense":
-        return fem.Problem("maxcut", dense=inst.dense, stream=stream)
+        P = fem.Problem("maxcut", dense=inst.dense, stream=stream)
+        P.set_dense_launch(dense_launch)
+        return P
     return fem.Problem("maxcut", graph=inst, stream=stream)
 
 
@@ -151,7 +153,7 @@ def _traffic_from_profile(name, kernel_src):
     return int(m2.group(1)) if sha == m1.group(1) else None
 
 
-def _roofline(wl, inst, step_ms, precision):
+def _roofline(wl, inst, step_ms, precision, persistent=False):
     """Algorithmic work of one step launch / its measured duration, against the peak."""
     peaks, src = _peaks()
     csrc = os.path.join(ROOT, "paper_2412_09285_b300", "csrc")
@@ -198,11 +200,17 @@ def _roofline(wl, inst, step_ms, precision):
         bound = "tensor"
         psrc = (f"{src} bf16_tflops_sustained" + (" x 2 (nominal fp8/bf16 ratio)" if precision == "fp8" else "")
                 + f", of {src}")
+    if persistent:
+        # one cooperative launch runs the whole timed window; figures are per step
+        kernel, prof = f"k_dense_anneal_tc<{precision}>", f"dense_anneal_{precision}_sk2000_R1024.md"
+    else:
+        kernel = f"k_dense_step_{'fp32' if precision == 'fp32' else 'tc<' + precision + '>'}"
+        prof = f"dense_step_{precision}_sk2000_R1024.md"
     return {"bound": bound, "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
-            "traffic": _traffic_from_profile(f"dense_step_{precision}_sk2000_R1024.md",
-                                             os.path.join(csrc, "dense_tc.cu")),
-            "kernel": f"k_dense_step_{'fp32' if precision == 'fp32' else 'tc<' + precision + '>'}",
-            "algorithmic_flops_per_launch": flops, "launch_ms": step_ms, "peak_source": psrc}
+            "traffic": _traffic_from_profile(prof, os.path.join(csrc, "dense_tc.cu")),
+            "kernel": kernel, "algorithmic_flops_per_step": flops, "step_ms": step_ms,
+            "launch": "persistent (one launch per anneal window)" if persistent else "one launch per step",
+            "peak_source": psrc}
 
 
 class ClockSampler:
@@ -375,9 +383,11 @@ def run_ours(args, wl):
         h0_host = I.initial_fields(inst.n, R, seed=wl["h_seed"] + 7919 * rank)
         h0 = torch.from_numpy(h0_host).to(dev)
     stream = torch.cuda.current_stream()
-    prob = _make_problem(fem, wl, inst, stream)
+    prob = _make_problem(fem, wl, inst, stream, args.dense_launch)
     kw = dict(grad_mode="exact" if precision == "bf16x2" else "paper", optimizer="adam", lr=0.1,
               precision=precision)
+
+    window_launches = []
 
     def one_anneal(k, events):
         """Fresh fields from the resident h0, then k steps, then the read-out.  Events
@@ -385,9 +395,11 @@ def run_ours(args, wl):
         prob.anneal(h_init=h0, replicas=R, n_steps=n_steps, t_begin=0, t_end=1, **kw)
         if k > 1:
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            l0 = fem.fem_kernel_launches()
             e0.record(stream)
             prob.anneal(replicas=R, n_steps=n_steps, t_begin=1, t_end=k, **kw)
             e1.record(stream)
+            window_launches.append(fem.fem_kernel_launches() - l0)
             events.append((e0, e1, k - 1))
         return prob.best()
 
@@ -434,7 +446,7 @@ def run_ours(args, wl):
     e2e_steps = min(K, n_steps)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    p2 = _make_problem(fem, wl, inst, stream)
+    p2 = _make_problem(fem, wl, inst, stream, args.dense_launch)
     p2.anneal(h_init=h0_pinned, replicas=R, n_steps=n_steps, t_end=e2e_steps, **kw)
     p2.best()
     torch.cuda.synchronize()
@@ -462,7 +474,8 @@ def run_ours(args, wl):
                        "parallelism": f"replica-sharded x{ws}",
                        "l2": ("inputs larger than L2" if wl["kind"] == "sparse" and inst.n > 100000
                               else "working set L2-resident (latency/compute-bound workload)")},
-            "roofline": _roofline(wl, inst, step_ms, precision), "gpu_launches": int(launches), "e2e": e2e,
+            "roofline": _roofline(wl, inst, step_ms, precision,
+                                  persistent=bool(window_launches) and window_launches[-1] == 1), "gpu_launches": int(launches), "e2e": e2e,
             "clocks": clk.summary(),
             "best_energy": float(best["energy_f64"][best["best_replica"]])}
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
@@ -482,6 +495,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="sparse", choices=sorted(WORKLOADS))
     ap.add_argument("--precision", default="bf16", choices=["bf16", "fp8", "bf16x2", "fp32"])
+    ap.add_argument("--dense-launch", default="auto", choices=["auto", "per_step", "persistent"],
+                    help="dense workload: persistent (state in tensor memory) or one kernel per step")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     wl = WORKLOADS[args.workload]

@@ -80,6 +80,19 @@ typedef enum { FEM_GRAD_EXACT = 0, FEM_GRAD_PAPER = 1 } fem_grad_mode;
  *            the discretised +-1 marginals and integer couplings |J| <= 16 are exact). */
 typedef enum { FEM_PREC_FP32 = 0, FEM_PREC_BF16 = 1, FEM_PREC_BF16X2 = 2, FEM_PREC_FP8 = 3 } fem_precision;
 
+/* How a dense tensor-core anneal is launched (fem_set_dense_launch).  Both give
+ * bit-identical fields; they differ only in where the optimizer state lives.
+ *   AUTO        PERSISTENT when the problem fits it, else PER_STEP (the default).
+ *   PER_STEP    one kernel per step; h, m, v stay in global memory.
+ *   PERSISTENT  one cooperative kernel per fem_anneal window: every CTA keeps its
+ *               128 x 128 (rows x replicas) tile of h, m, v in tensor memory for the
+ *               whole window and meets the other CTAs of its replica block at a
+ *               barrier after each step.  Needs precision BF16, BF16X2 or FP8,
+ *               R % 128 == 0 and (n_pad/128) * (R/128) <= the number of SMs, where
+ *               n_pad = n rounded up to 128; fem_anneal returns FEM_ERR_UNSUPPORTED
+ *               otherwise. */
+typedef enum { FEM_DENSE_AUTO = 0, FEM_DENSE_PER_STEP = 1, FEM_DENSE_PERSISTENT = 2 } fem_dense_launch;
+
 typedef struct fem_problem* fem_problem_t; /* opaque; owned by the library until fem_destroy */
 
 /* Problem description.  All pointers are HOST pointers; they are read during
@@ -271,6 +284,10 @@ fem_status fem_problem_info(fem_problem_t p, int32_t* steps_done, int32_t* n, in
 
 /* Synchronise `stream` and report any sticky device-side error. */
 fem_status fem_sync(fem_problem_t p, void* stream);
+
+/* Select how later fem_anneal calls on a dense problem are launched (fem_dense_launch);
+ * FEM_ERR_INVALID_ARG for other values or a problem without dense couplings. */
+fem_status fem_set_dense_launch(fem_problem_t p, int32_t mode);
 
 /* Release every resource owned by p (NULL is ignored). */
 void fem_destroy(fem_problem_t p);

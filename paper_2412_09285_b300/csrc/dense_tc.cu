@@ -30,8 +30,10 @@
 #include <cuda_runtime.h>
 #include <cudaTypedefs.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <type_traits>
 
 #include "fem_internal.h"
 #include "step_common.cuh"
@@ -130,18 +132,27 @@ __device__ __forceinline__ void umma_commit(uint64_t* bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
                : "memory");
 }
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
-      "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
-        "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
-        "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-      : "r"(taddr)
-      : "memory");
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+// TMEM <-> registers, 32 lanes x 8 columns.  A load is issued without waiting; its
+// outputs are tied to tmem_wait_ld, which every reader calls first (it waits for all
+// earlier loads of the thread), so no use can be scheduled before the data arrives.
+__device__ __forceinline__ void tmem_ld8_issue(uint32_t taddr, uint32_t (&r)[8]) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+               : "r"(taddr)
+               : "memory");
 }
+__device__ __forceinline__ void tmem_wait_ld(uint32_t (&r)[8]) {
+  asm volatile("tcgen05.wait::ld.sync.aligned;"
+               : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7])
+               :
+               : "memory");
+}
+__device__ __forceinline__ void tmem_st8(uint32_t taddr, const uint32_t (&r)[8]) {
+  asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"r"(taddr),
+               "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7])
+               : "memory");
+}
+__device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
 
 // Shared-memory matrix descriptor (tcgen05) for a K-major tile whose rows are 128
 // bytes with the 128-byte swizzle: start address >> 4, leading offset unused (1),
@@ -163,6 +174,54 @@ __host__ __device__ constexpr uint32_t make_idesc(uint32_t fmt) {
 
 __device__ __forceinline__ uint16_t bf16_bits(float x) {
   return __bfloat16_as_ushort(__float2bfloat16_rn(x));
+}
+
+// One element of the fused epilogue: the gradient from the accumulated field S_ir
+// and the optimizer update of (h, m, v).  Returns the next step's operand entry (bf16
+// or e4m3 bits; with the bf16 hi+lo split the low part goes to *lo); the caller
+// stores it.  Branch-free for Adam at fixed (PREC, OPT, PAPER), so the elements of
+// a chunk interleave.
+template <int PREC, int OPT, bool PAPER>
+__device__ __forceinline__ uint32_t epi_element(const StepScalars& s, float cn, uint32_t acc_bits, float& h,
+                                                float& m, float& v, uint32_t* lo) {
+  // explicit roundings: the per-step and the persistent kernels agree bit for bit
+  const float field = __fmul_rn(cn, __uint_as_float(acc_bits));
+  float g = __fmul_rn(__fmul_rn(s.gq, fmaf(h, s.inv_beta, field)), one_minus_m2_fast(h));
+  g = fmaf(s.wd, h, g);  // L2 weight decay; exactly g when wd == 0
+  opt_update_fast_core<OPT>(h, m, v, g, s);
+  if (PAPER) {
+    *lo = 0u;
+    if (PREC == FEM_PREC_FP8) return h < 0.f ? 0xB8u : 0x38u;  // e4m3 -1 / +1
+    return h < 0.f ? 0xBF80u : 0x3F80u;                        // bf16 -1 / +1
+  }
+  const float mm = tanhf(0.5f * h);
+  const uint16_t hi = bf16_bits(mm);
+  *lo = PREC == FEM_PREC_BF16X2 ? bf16_bits(mm - __bfloat162float(__ushort_as_bfloat16(hi))) : 0u;
+  return hi;
+}
+
+// Calls f(OPT, PAPER) with the run-time optimizer and gradient mode as compile-time
+// constants (one warp-uniform branch per call instead of several per element).
+template <class F>
+__device__ __forceinline__ void with_opt_mode(int opt, int mode, F&& f) {
+  using A = std::integral_constant<int, FEM_OPT_ADAM>;
+  using Rm = std::integral_constant<int, FEM_OPT_RMSPROP>;
+  using Sg = std::integral_constant<int, FEM_OPT_SGD>;
+  if (mode == FEM_GRAD_PAPER) {
+    if (opt == FEM_OPT_ADAM) f(A{}, std::true_type{});
+    else if (opt == FEM_OPT_RMSPROP) f(Rm{}, std::true_type{});
+    else f(Sg{}, std::true_type{});
+  } else {
+    if (opt == FEM_OPT_ADAM) f(A{}, std::false_type{});
+    else if (opt == FEM_OPT_RMSPROP) f(Rm{}, std::false_type{});
+    else f(Sg{}, std::false_type{});
+  }
+}
+
+template <int PREC>
+__device__ __forceinline__ void store_operand(void* base, size_t idx, uint32_t bits) {
+  if (PREC == FEM_PREC_FP8) reinterpret_cast<uint8_t*>(base)[idx] = (uint8_t)bits;
+  else reinterpret_cast<uint16_t*>(base)[idx] = (uint16_t)bits;
 }
 
 // ------------------------------------------------------------ the fused step
@@ -239,43 +298,309 @@ __global__ void __launch_bounds__(kThreads, 1) k_dense_step_tc(const __grid_cons
   }
   __syncwarp();
 
-  // epilogue: thread = TMEM lane = row i of the tile
+  // epilogue: thread = TMEM lane = row i of the tile.  Warp w reads TMEM lanes
+  // 32*(w%4).. (its quadrant) and the 32 replica columns 32*(w/4)..; the state of 8
+  // columns is loaded in one batch (the first batch before the MMAs complete), so a
+  // thread waits for four memory round trips instead of one per column.
+  constexpr int kB = 8;
+  const int quad = warp & 3, c0 = (warp >> 2) * 32;
+  const int i = i0 + quad * 32 + lane;
+  const bool row = i < a.n;
+  const bool sgd = a.opt == FEM_OPT_SGD;
+  float* __restrict__ h_io = a.h;
+  float* __restrict__ m_io = a.m;
+  float* __restrict__ v_io = a.v;
+  float hv[kB], mv[kB], vv[kB];
+  auto load_batch = [&](int cb) {
+#pragma unroll
+    for (int c = 0; c < kB; ++c) {
+      const size_t idx = (size_t)(r0 + c0 + cb + c) * a.n_pad + i;
+      hv[c] = h_io[idx];
+      mv[c] = m_io[idx];
+      vv[c] = sgd ? 0.f : v_io[idx];
+    }
+  };
+  if (row) load_batch(0);
   const bool ok = mbar_wait(&done, 0, a.err);
   tc_fence_after();
-  if (ok) {
-    // warp w reads TMEM lanes 32*(w%4).. (its quadrant) and replica columns 32*(w/4)..
-    const int quad = warp & 3;
-    const int i = i0 + quad * 32 + lane;
-    const bool row = i < a.n;
+  if (__all_sync(kFullMask, ok)) {
     const float cn = row ? (a.mode == FEM_GRAD_PAPER ? a.cnorm[i] : 2.f) : 0.f;
-    for (int c0 = (warp >> 2) * 32; c0 < kTile; c0 += 32 * (kThreads / 128)) {
-      uint32_t acc[32];
-      tmem_ld32(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)c0, acc);
+#pragma unroll 1
+    for (int cb = 0; cb < 32; cb += kB) {  // R % 128 == 0: every column is a replica
+      uint32_t acc[kB];
+      tmem_ld8_issue(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(c0 + cb), acc);
+      tmem_wait_ld(acc);
       if (!row) continue;
+      if (cb > 0) load_batch(cb);
+      with_opt_mode(a.opt, a.mode, [&](auto O, auto P) {
+        constexpr int OPT = decltype(O)::value;
+        constexpr bool PAPER = decltype(P)::value;
 #pragma unroll
-      for (int c = 0; c < 32; ++c) {  // R % 128 == 0: every column is a replica
-        const int r = r0 + c0 + c;
-        const size_t idx = (size_t)r * a.n_pad + i;
-        float hv = a.h[idx], mv = a.m[idx], vv = a.opt == FEM_OPT_SGD ? 0.f : a.v[idx];
-        const float field = cn * __uint_as_float(acc[c]);
-        const float g = s.gq * (field + hv * s.inv_beta) * one_minus_m2_fast(hv);
-        opt_update_rt(a.opt, hv, mv, vv, g, s);
-        a.h[idx] = hv;
-        a.m[idx] = mv;
-        if (a.opt != FEM_OPT_SGD) a.v[idx] = vv;
-        if (a.mode == FEM_GRAD_PAPER) {
-          if (PREC == FEM_PREC_FP8)
-            reinterpret_cast<uint8_t*>(a.mt_out)[idx] = hv < 0.f ? 0xB8u : 0x38u;  // e4m3 -1 / +1
-          else
-            reinterpret_cast<uint16_t*>(a.mt_out)[idx] = hv < 0.f ? 0xBF80u : 0x3F80u;  // bf16 -1 / +1
-        } else {
-          const float mm = tanhf(0.5f * hv);
-          const uint16_t hi = bf16_bits(mm);
-          reinterpret_cast<uint16_t*>(a.mt_out)[idx] = hi;
-          if (X2) {
-            const float res = mm - __bfloat162float(__ushort_as_bfloat16(hi));
-            reinterpret_cast<uint16_t*>(a.mt_lo_out)[idx] = bf16_bits(res);
-          }
+        for (int c = 0; c < kB; ++c) {
+          const size_t idx = (size_t)(r0 + c0 + cb + c) * a.n_pad + i;
+          float h = hv[c], m = mv[c], v = vv[c];
+          uint32_t lo;
+          store_operand<PREC>(a.mt_out, idx, epi_element<PREC, OPT, PAPER>(s, cn, acc[c], h, m, v, &lo));
+          if (X2 && !PAPER) reinterpret_cast<uint16_t*>(a.mt_lo_out)[idx] = (uint16_t)lo;
+          h_io[idx] = h;
+          m_io[idx] = m;
+          if (OPT != FEM_OPT_SGD) v_io[idx] = v;
+        }
+      });
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    tc_fence_after();
+    tmem_dealloc(tmem, kTile);
+  }
+}
+
+// --------------------------------------------- persistent anneal (one launch)
+// The step above, run for a whole window of steps by one cooperative launch.  Each
+// CTA keeps its 128 x 128 tile of h, m and v in tensor memory for the whole window
+// (TMEM columns 128.., 256.., 384..; the accumulator uses 0..127), so the optimizer
+// state is read from global memory once at the start and written once at the end.
+// Per step the only data a CTA needs from other CTAs is the next operand M^T of its
+// replica block, written by the n_pad/128 CTAs that share blockIdx.y; those CTAs meet
+// at a counter barrier in global memory after each step (release/acquire at GPU
+// scope, plus a proxy fence because the operand is written with ordinary stores and
+// read by TMA).  All waits are bounded; a CTA that gives up records the timeout bit,
+// lets its copies and MMAs in flight land, frees its TMEM and leaves, and the CTAs
+// waiting for it give up in turn.
+constexpr int kTmemCols = 4 * kTile;  // accumulator, h, m, v
+
+struct DenseAnnealArgs {
+  DenseArgs a;               // h, m, v ([R][n_pad], read at the start, written at the end), cnorm, err
+  void* mt[2];               // operand ping-pong: step t reads mt[t & 1] and writes mt[(t + 1) & 1]
+  void* mt_lo[2];            // exact mode low parts (bf16 hi + lo), else NULL
+  const StepScalars* sc;     // [n_steps], the scalars of steps t_begin ..
+  int32_t t_begin, n_steps;
+  int32_t* bar;              // one arrival counter per replica block (stride 32 ints), zero at launch
+};
+
+__device__ __forceinline__ bool wait_counter(const int32_t* ctr, int32_t target, int32_t* err) {
+  const unsigned long long t0 = global_ns();
+  while (true) {
+    int32_t v;
+    asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(ctr) : "memory");
+    if (v >= target) return true;
+    if (global_ns() - t0 > kWaitNs) {
+      atomicOr(err, ERR_TIMEOUT);
+      return false;
+    }
+  }
+}
+
+template <int PREC>
+__global__ void __launch_bounds__(kThreads, 1) k_dense_anneal_tc(const __grid_constant__ CUtensorMap tmA,
+                                                           const __grid_constant__ CUtensorMap tmB0,
+                                                           const __grid_constant__ CUtensorMap tmB1,
+                                                           const __grid_constant__ CUtensorMap tmBlo0,
+                                                           const __grid_constant__ CUtensorMap tmBlo1,
+                                                           const DenseAnnealArgs x) {
+  constexpr bool X2 = PREC == FEM_PREC_BF16X2;
+  constexpr int kElem = PREC == FEM_PREC_FP8 ? 1 : 2;
+  constexpr int kChunkK = kChunkBytes / kElem;
+  constexpr int kMmaK = PREC == FEM_PREC_FP8 ? 32 : 16;
+  constexpr uint32_t kTileBytes = kTile * kChunkBytes;
+  constexpr uint32_t kStageBytes = kTileBytes * (X2 ? 3 : 2);
+  constexpr uint32_t kIdesc = make_idesc(PREC == FEM_PREC_FP8 ? 0u : 1u);
+  constexpr int kStages = stages_for(PREC);
+  constexpr int kCols = 8;  // replica columns per TMEM load / store in the epilogue
+
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  __shared__ __align__(8) uint64_t full[kMaxStages];
+  __shared__ __align__(8) uint64_t empty[kMaxStages];
+  __shared__ __align__(8) uint64_t done;
+  __shared__ uint32_t tmem_base_slot;
+  __shared__ int32_t abort_flag;
+  __shared__ StepScalars s_sc;  // the current step's scalars (written by thread 0 between steps)
+  volatile int32_t* abort_v = &abort_flag;
+
+  const DenseArgs& a = x.a;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int i0 = blockIdx.x * kTile, r0 = blockIdx.y * kTile;
+  const int nchunks = a.n_pad / kChunkK;
+
+  if (threadIdx.x == 0) {
+    for (int st = 0; st < kStages; ++st) {
+      mbar_init(&full[st], 1);
+      mbar_init(&empty[st], 1);
+    }
+    mbar_init(&done, 1);
+    abort_flag = 0;
+    if (x.n_steps > 0) s_sc = x.sc[0];
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) tmem_alloc(&tmem_base_slot, kTmemCols);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tmem_base_slot;
+
+  // epilogue geometry: thread = TMEM lane = row i; warp w owns lane quadrant w % 4
+  // and the 32 replica columns 32 * (w / 4) ..
+  const int quad = warp & 3, c0 = (warp >> 2) * 32;
+  const int i = i0 + quad * 32 + lane;
+  const bool row = i < a.n;
+  const bool sgd = a.opt == FEM_OPT_SGD;
+  const uint32_t tl = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)c0;  // + region * kTile + column
+  const float cn = row ? (a.mode == FEM_GRAD_PAPER ? a.cnorm[i] : 2.f) : 0.f;
+
+  // state: global [R][n_pad] -> TMEM (padding rows hold zeros and are never updated)
+#pragma unroll
+  for (int cb = 0; cb < 32; cb += kCols) {
+    uint32_t hr[kCols], mr[kCols], vr[kCols];
+#pragma unroll
+    for (int c = 0; c < kCols; ++c) {
+      const size_t idx = (size_t)(r0 + c0 + cb + c) * a.n_pad + i;
+      hr[c] = row ? __float_as_uint(a.h[idx]) : 0u;
+      mr[c] = row ? __float_as_uint(a.m[idx]) : 0u;
+      vr[c] = (row && !sgd) ? __float_as_uint(a.v[idx]) : 0u;
+    }
+    tmem_st8(tl + 1 * kTile + cb, hr);
+    tmem_st8(tl + 2 * kTile + cb, mr);
+    tmem_st8(tl + 3 * kTile + cb, vr);
+  }
+  tmem_wait_st();
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+
+  int issued = 0;  // producer: TMA stage loads issued so far (thread 0 only)
+  for (int k = 0; k < x.n_steps; ++k) {
+    const int t = x.t_begin + k, in = t & 1;
+    if (threadIdx.x == 0) {
+      const CUtensorMap* mb = in ? &tmB1 : &tmB0;
+      const CUtensorMap* mlo = in ? &tmBlo1 : &tmBlo0;
+      for (int kc = 0; kc < nchunks; ++kc) {
+        const int g = k * nchunks + kc, st = g % kStages;
+        if (!mbar_wait(&empty[st], ((g / kStages) & 1) ^ 1, a.err)) {
+          *abort_v = 1;
+          break;
+        }
+        uint8_t* sa = smem + st * kStageBytes;
+        mbar_expect_tx(&full[st], kStageBytes);
+        tma_load_2d(sa, &tmA, kc * kChunkK, i0, &full[st]);
+        tma_load_2d(sa + kTileBytes, mb, kc * kChunkK, r0, &full[st]);
+        if (X2) tma_load_2d(sa + 2 * kTileBytes, mlo, kc * kChunkK, r0, &full[st]);
+        issued = g + 1;
+      }
+    } else if (threadIdx.x == 32) {
+      for (int kc = 0; kc < nchunks; ++kc) {
+        const int g = k * nchunks + kc, st = g % kStages;
+        if (!mbar_wait(&full[st], (g / kStages) & 1, a.err)) {
+          *abort_v = 1;
+          break;
+        }
+        tc_fence_after();
+        const uint32_t sa = smem_u32(smem + st * kStageBytes);
+        const uint64_t da = desc_sw128(sa), db = desc_sw128(sa + kTileBytes);
+        const uint64_t dblo = desc_sw128(sa + 2 * kTileBytes);
+#pragma unroll
+        for (int kk = 0; kk < kChunkK / kMmaK; ++kk) {
+          const uint64_t adv = (uint64_t)((kk * kMmaK * kElem) >> 4);
+          const uint32_t acc = (kc > 0 || kk > 0) ? 1u : 0u;
+          if (PREC == FEM_PREC_FP8) umma_f8(tmem, da + adv, db + adv, kIdesc, acc);
+          else umma_f16(tmem, da + adv, db + adv, kIdesc, acc);
+          if (X2) umma_f16(tmem, da + adv, dblo + adv, kIdesc, 1u);
+        }
+        umma_commit(&empty[st]);
+      }
+      umma_commit(&done);  // also after a failed wait: done then tracks the MMAs issued
+    }
+    __syncwarp();
+
+    const bool ok = mbar_wait(&done, k & 1, a.err);
+    tc_fence_after();
+    if (!ok) *abort_v = 1;
+    if (__all_sync(kFullMask, ok) && !*abort_v) {
+      const StepScalars s = s_sc;  // registers: the operand stores below are generic and could alias it
+      void* mt_out = x.mt[(t + 1) & 1];
+      void* mt_lo_out = x.mt_lo[(t + 1) & 1];
+#pragma unroll
+      for (int cb = 0; cb < 32; cb += kCols) {
+        uint32_t acc[kCols], hr[kCols], mr[kCols], vr[kCols];
+        tmem_ld8_issue(tl + cb, acc);
+        tmem_ld8_issue(tl + 1 * kTile + cb, hr);
+        tmem_ld8_issue(tl + 2 * kTile + cb, mr);
+        tmem_ld8_issue(tl + 3 * kTile + cb, vr);
+        tmem_wait_ld(acc);
+        tmem_wait_ld(hr);
+        tmem_wait_ld(mr);
+        tmem_wait_ld(vr);
+        if (row) {
+          // all arithmetic of the chunk first, then its operand stores
+          with_opt_mode(a.opt, a.mode, [&](auto O, auto P) {
+            constexpr int OPT = decltype(O)::value;
+            constexpr bool PAPER = decltype(P)::value;
+            uint32_t lo[kCols];
+#pragma unroll
+            for (int c = 0; c < kCols; ++c) {
+              float h = __uint_as_float(hr[c]), m = __uint_as_float(mr[c]);
+              float v = OPT == FEM_OPT_SGD ? 0.f : __uint_as_float(vr[c]);
+              acc[c] = epi_element<PREC, OPT, PAPER>(s, cn, acc[c], h, m, v, &lo[c]);
+              hr[c] = __float_as_uint(h);
+              mr[c] = __float_as_uint(m);
+              vr[c] = __float_as_uint(v);
+            }
+#pragma unroll
+            for (int c = 0; c < kCols; ++c) {
+              const size_t idx = (size_t)(r0 + c0 + cb + c) * a.n_pad + i;
+              store_operand<PREC>(mt_out, idx, acc[c]);
+              if (X2 && !PAPER) reinterpret_cast<uint16_t*>(mt_lo_out)[idx] = (uint16_t)lo[c];
+            }
+          });
+        }
+        tmem_st8(tl + 1 * kTile + cb, hr);
+        tmem_st8(tl + 2 * kTile + cb, mr);
+        tmem_st8(tl + 3 * kTile + cb, vr);
+      }
+      tmem_wait_st();
+    }
+
+    // the operand of step t + 1 is complete once every CTA of this replica block is here
+    tc_fence_before();
+    __syncthreads();
+    if (threadIdx.x == 0 && k + 1 < x.n_steps && !*abort_v) {
+      int32_t* ctr = x.bar + blockIdx.y * 32;
+      asm volatile("fence.proxy.async.global;" ::: "memory");
+      asm volatile("red.release.gpu.global.add.s32 [%0], 1;" ::"l"(ctr) : "memory");  // cumulative over bar.sync
+      if (!wait_counter(ctr, (k + 1) * (int32_t)gridDim.x, a.err)) *abort_v = 1;
+      asm volatile("fence.proxy.async.global;" ::: "memory");
+    }
+    if (threadIdx.x == 0 && k + 1 < x.n_steps) s_sc = x.sc[k + 1];
+    __syncthreads();
+    tc_fence_after();
+    if (*abort_v) break;
+  }
+
+  if (*abort_v) {
+    // let the stage loads still in flight land before the CTA's shared memory is released
+    if (threadIdx.x == 0)
+      for (int g = issued - kStages < 0 ? 0 : issued - kStages; g < issued; ++g)
+        mbar_wait(&full[g % kStages], (g / kStages) & 1, a.err);
+  } else {
+    // state: TMEM -> global
+#pragma unroll
+    for (int cb = 0; cb < 32; cb += kCols) {
+      uint32_t hr[kCols], mr[kCols], vr[kCols];
+      tmem_ld8_issue(tl + 1 * kTile + cb, hr);
+      tmem_ld8_issue(tl + 2 * kTile + cb, mr);
+      tmem_ld8_issue(tl + 3 * kTile + cb, vr);
+      tmem_wait_ld(hr);
+      tmem_wait_ld(mr);
+      tmem_wait_ld(vr);
+      if (row) {
+#pragma unroll
+        for (int c = 0; c < kCols; ++c) {
+          const size_t idx = (size_t)(r0 + c0 + cb + c) * a.n_pad + i;
+          a.h[idx] = __uint_as_float(hr[c]);
+          a.m[idx] = __uint_as_float(mr[c]);
+          if (!sgd) a.v[idx] = __uint_as_float(vr[c]);
         }
       }
     }
@@ -284,7 +609,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_dense_step_tc(const __grid_cons
   __syncthreads();
   if (warp == 0) {
     tc_fence_after();
-    tmem_dealloc(tmem, kTile);
+    tmem_dealloc(tmem, kTmemCols);
   }
 }
 
@@ -524,6 +849,84 @@ fem_status launch_tc(Problem* p, const DenseArgs& a, const StepScalars& s, int i
   return FEM_OK;
 }
 
+// Whether the persistent kernel can run this problem: tensor-core precision, whole
+// replica tiles, and every CTA co-resident (one per SM).
+template <int PREC>
+bool anneal_fits(Problem* p) {
+  static int per_sm = -1;
+  if (per_sm < 0) {
+    if (cudaFuncSetAttribute(k_dense_anneal_tc<PREC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)tc_smem_bytes(PREC)) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_dense_anneal_tc<PREC>, kThreads,
+                                                      tc_smem_bytes(PREC)) != cudaSuccess) {
+      cudaGetLastError();
+      per_sm = 0;
+    }
+  }
+  const long grid = (long)(p->n_pad / kTile) * (p->R / kTile);
+  return p->R % kTile == 0 && per_sm > 0 && grid <= (long)per_sm * p->sm_count;
+}
+
+bool anneal_fits_any(Problem* p) {
+  switch (p->precision) {
+    case FEM_PREC_BF16: return anneal_fits<FEM_PREC_BF16>(p);
+    case FEM_PREC_BF16X2: return anneal_fits<FEM_PREC_BF16X2>(p);
+    case FEM_PREC_FP8: return anneal_fits<FEM_PREC_FP8>(p);
+    default: return false;
+  }
+}
+
+template <int PREC>
+fem_status launch_anneal_tc(Problem* p, const DenseArgs& a, int t_begin, int n_steps, cudaStream_t st) {
+  DenseAnnealArgs x{};
+  x.a = a;
+  for (int b = 0; b < 2; ++b) {
+    x.mt[b] = p->mt[b];
+    x.mt_lo[b] = p->mt_lo[b];
+  }
+  x.sc = p->dense_sc;
+  x.t_begin = t_begin;
+  x.n_steps = n_steps;
+  x.bar = p->dense_bar;
+  const int groups = p->R / kTile;
+  FEM_CUDA(cudaMemsetAsync(p->dense_bar, 0, (size_t)groups * 32 * sizeof(int32_t), st));
+  const bool x2 = PREC == FEM_PREC_BF16X2;
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = dim3(p->n_pad / kTile, groups);
+  cfg.blockDim = dim3(kThreads);
+  cfg.dynamicSmemBytes = tc_smem_bytes(PREC);
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  FEM_CUDA(cudaLaunchKernelEx(&cfg, k_dense_anneal_tc<PREC>, PREC == FEM_PREC_FP8 ? p->tmap_a8 : p->tmap_a16,
+                              p->tmap_b[0], p->tmap_b[1], x2 ? p->tmap_blo[0] : p->tmap_b[0],
+                              x2 ? p->tmap_blo[1] : p->tmap_b[1], x));
+  return FEM_OK;
+}
+
+// The step-scalar table of a window on the device (grown as needed; the old table is
+// released after the stream has drained, since a running anneal may still read it).
+fem_status upload_scalars(Problem* p, const std::vector<StepScalars>& sc, cudaStream_t s) {
+  if ((int64_t)sc.size() > p->dense_sc_cap) {
+    if (p->dense_sc) {
+      FEM_CUDA(cudaStreamSynchronize(s));
+      cudaFree(p->dense_sc);
+      p->allocs.erase(std::remove(p->allocs.begin(), p->allocs.end(), (void*)p->dense_sc), p->allocs.end());
+      p->dense_sc = nullptr;
+      p->dense_sc_cap = 0;
+    }
+    const int64_t cap = std::max<int64_t>((int64_t)sc.size(), 1024);
+    fem_status st = dev_alloc_t(p, &p->dense_sc, (size_t)cap);
+    if (st != FEM_OK) return st;
+    p->dense_sc_cap = cap;
+  }
+  FEM_CUDA(cudaMemcpyAsync(p->dense_sc, sc.data(), sc.size() * sizeof(StepScalars), cudaMemcpyHostToDevice, s));
+  return FEM_OK;
+}
+
 }  // namespace
 
 int dense_pad(int n) { return ((n + kTile - 1) / kTile) * kTile; }
@@ -673,6 +1076,8 @@ fem_status dense_operand(Problem* p, int t, cudaStream_t s) {
   return FEM_OK;
 }
 
+bool dense_persistent_ok(Problem* p) { return anneal_fits_any(p); }
+
 fem_status dense_steps(Problem* p, const std::vector<StepScalars>& sc, int t_begin, cudaStream_t s) {
   DenseArgs a{};
   a.n = p->n;
@@ -686,6 +1091,37 @@ fem_status dense_steps(Problem* p, const std::vector<StepScalars>& sc, int t_beg
   a.v = p->v;
   a.cnorm = p->rowabs;
   a.err = p->err;
+  // AUTO takes the persistent kernel for windows of two or more steps
+  const bool persistent = !sc.empty() && p->dense_launch != FEM_DENSE_PER_STEP &&
+                          (p->dense_launch == FEM_DENSE_PERSISTENT || sc.size() > 1) && anneal_fits_any(p);
+  if (p->dense_launch == FEM_DENSE_PERSISTENT && !persistent && !sc.empty())
+    return fail(FEM_ERR_UNSUPPORTED, "persistent dense anneal needs a tensor-core precision, R %% 128 == 0 and "
+                "(n_pad/128)*(R/128) co-resident CTAs");
+  if (persistent) {
+    fem_status st = upload_scalars(p, sc, s);
+    if (st == FEM_OK) {
+      const int groups = p->R / kTile;
+      if (p->dense_bar_groups < groups) {  // first use, or more replica blocks than before
+        if (p->dense_bar) {
+          FEM_CUDA(cudaStreamSynchronize(s));
+          cudaFree(p->dense_bar);
+          p->allocs.erase(std::remove(p->allocs.begin(), p->allocs.end(), (void*)p->dense_bar), p->allocs.end());
+          p->dense_bar = nullptr;
+        }
+        if ((st = dev_alloc_t(p, &p->dense_bar, (size_t)groups * 32)) != FEM_OK) return st;
+        p->dense_bar_groups = groups;
+      }
+      switch (p->precision) {
+        case FEM_PREC_BF16: st = launch_anneal_tc<FEM_PREC_BF16>(p, a, t_begin, (int)sc.size(), s); break;
+        case FEM_PREC_BF16X2: st = launch_anneal_tc<FEM_PREC_BF16X2>(p, a, t_begin, (int)sc.size(), s); break;
+        default: st = launch_anneal_tc<FEM_PREC_FP8>(p, a, t_begin, (int)sc.size(), s); break;
+      }
+    }
+    if (st != FEM_OK) return st;
+    count_launches(1);
+    FEM_CUDA(cudaGetLastError());
+    return FEM_OK;
+  }
   for (size_t k = 0; k < sc.size(); ++k) {
     const int t = t_begin + (int)k, in = t & 1, out = (t + 1) & 1;
     a.mt_out = p->mt[out];

@@ -555,6 +555,14 @@ fem_status fem_read_best(fem_problem_t p, int32_t* best_replica, int32_t* states
   return check_sticky(p, s);
 }
 
+fem_status fem_set_dense_launch(fem_problem_t p, int32_t mode) {
+  if (!p || !p->dense) return fail(FEM_ERR_INVALID_ARG, "fem_set_dense_launch: not a dense problem");
+  if (mode < FEM_DENSE_AUTO || mode > FEM_DENSE_PERSISTENT)
+    return fail(FEM_ERR_INVALID_ARG, "fem_set_dense_launch: mode %d", (int)mode);
+  p->dense_launch = mode;
+  return FEM_OK;
+}
+
 fem_status fem_read_fields(fem_problem_t p, float* h_host, void* stream) {
   g_last_error.clear();
   if (!p || !h_host) return fail(FEM_ERR_INVALID_ARG, "problem and h_host must be non-NULL");

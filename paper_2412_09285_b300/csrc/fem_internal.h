@@ -69,6 +69,11 @@ struct Problem {
   int32_t dense_R_alloc = 0, dense_prec_alloc = -1;
   void* mt_lo[2] = {nullptr, nullptr};  // exact mode, bf16 low parts
   CUtensorMap tmap_a16, tmap_a8, tmap_b[2], tmap_blo[2];
+  int32_t dense_launch = 0;               // fem_dense_launch
+  StepScalars* dense_sc = nullptr;        // persistent anneal: the window's step scalars
+  int64_t dense_sc_cap = 0;
+  int32_t* dense_bar = nullptr;           // persistent anneal: per replica block arrival counters
+  int32_t dense_bar_groups = 0;
 
   // ---- replica state
   int32_t R = 0, steps_done = 0, n_steps = 0;
@@ -145,6 +150,7 @@ fem_status dense_get(Problem* p, const float* src_rn, float* dst_nr_host, cudaSt
 fem_status dense_put(Problem* p, float* dst_rn, const float* src_nr_host, cudaStream_t s);
 fem_status dense_operand(Problem* p, int t, cudaStream_t s);
 fem_status dense_steps(Problem* p, const std::vector<StepScalars>& sc, int t_begin, cudaStream_t s);
+bool dense_persistent_ok(Problem* p);
 fem_status dense_readout(Problem* p, cudaStream_t s);
 fem_status dense_states_all(Problem* p, int32_t* out, cudaStream_t s);
 

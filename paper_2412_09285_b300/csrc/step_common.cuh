@@ -19,7 +19,9 @@ constexpr unsigned kFullMask = 0xffffffffu;
 //            momentum mu > 0: buf = mu buf + g/avg, h -= lr buf;  else h -= lr g/avg
 //   SGD:     momentum mu != 0: buf = g (first step) or mu buf + (1-d) g;  h -= lr buf
 // The L2 weight decay adds wd*h to g first.  `m` doubles as the momentum buffer
-// of RMSprop and SGD.
+// of RMSprop and SGD.  Every multiply-add is an explicit fmaf, so the rounding does
+// not depend on how the compiler contracts the surrounding kernel's code (kernels
+// that must agree bit for bit share these sequences).
 template <int OPT>
 __device__ __forceinline__ void opt_update(float& h, float& m, float& v, float g,
                                            const StepScalars& s) {
@@ -28,22 +30,22 @@ __device__ __forceinline__ void opt_update(float& h, float& m, float& v, float g
     m = fmaf(s.b1, m, s.omb1 * g);
     v = fmaf(s.b2, v, s.omb2 * g * g);
     const float denom = fmaf(sqrtf(v), s.inv_sqrt_bc2, s.eps);
-    h = h - s.lr * (m / denom);
+    h = fmaf(-s.lr, m / denom, h);
   } else if (OPT == FEM_OPT_RMSPROP) {
     v = fmaf(s.b1, v, s.omb1 * g * g);
     const float avg = sqrtf(v) + s.eps;
     if (s.momentum > 0.f) {
       m = fmaf(s.momentum, m, g / avg);
-      h = h - s.lr * m;
+      h = fmaf(-s.lr, m, h);
     } else {
-      h = h - s.lr * (g / avg);
+      h = fmaf(-s.lr, g / avg, h);
     }
   } else {
     if (s.b1 != 0.f) {
       m = s.first ? g : fmaf(s.b1, m, s.omb1 * g);
       g = m;
     }
-    h = h - s.lr * g;
+    h = fmaf(-s.lr, g, h);
   }
 }
 
@@ -57,10 +59,12 @@ __device__ __forceinline__ float sqrt_approx(float x) {
 // The same updates with the divisions done by the fast reciprocal (__fdividef,
 // 2 ulp) and the approximate square root; the divisors here are >= eps and far
 // below 2^126.
+// opt_update_fast_core is the update of a gradient that already includes wd*h
+// (callers that must not branch per element add it with an fmaf, which leaves g
+// unchanged when wd == 0).
 template <int OPT>
-__device__ __forceinline__ void opt_update_fast(float& h, float& m, float& v, float g,
-                                                const StepScalars& s) {
-  if (s.wd != 0.f) g = fmaf(s.wd, h, g);
+__device__ __forceinline__ void opt_update_fast_core(float& h, float& m, float& v, float g,
+                                                     const StepScalars& s) {
   if (OPT == FEM_OPT_ADAM) {
     m = fmaf(s.b1, m, s.omb1 * g);
     v = fmaf(s.b2, v, s.omb2 * g * g);
@@ -83,6 +87,13 @@ __device__ __forceinline__ void opt_update_fast(float& h, float& m, float& v, fl
   }
 }
 
+template <int OPT>
+__device__ __forceinline__ void opt_update_fast(float& h, float& m, float& v, float g,
+                                                const StepScalars& s) {
+  if (s.wd != 0.f) g = fmaf(s.wd, h, g);
+  opt_update_fast_core<OPT>(h, m, v, g, s);
+}
+
 // 1 - tanh(h/2)^2 with the fast exponential (relative error ~1e-6).
 __device__ __forceinline__ float one_minus_m2_fast(float h) {
   const float e = __expf(-fabsf(h));
@@ -96,6 +107,14 @@ __device__ __forceinline__ void opt_update_rt(int opt, float& h, float& m, float
   if (opt == FEM_OPT_ADAM) opt_update<FEM_OPT_ADAM>(h, m, v, g, s);
   else if (opt == FEM_OPT_RMSPROP) opt_update<FEM_OPT_RMSPROP>(h, m, v, g, s);
   else opt_update<FEM_OPT_SGD>(h, m, v, g, s);
+}
+
+// opt_update_fast with the optimizer chosen at run time (a warp-uniform branch).
+__device__ __forceinline__ void opt_update_fast_rt(int opt, float& h, float& m, float& v, float g,
+                                                   const StepScalars& s) {
+  if (opt == FEM_OPT_ADAM) opt_update_fast<FEM_OPT_ADAM>(h, m, v, g, s);
+  else if (opt == FEM_OPT_RMSPROP) opt_update_fast<FEM_OPT_RMSPROP>(h, m, v, g, s);
+  else opt_update_fast<FEM_OPT_SGD>(h, m, v, g, s);
 }
 
 // 1 - m^2 for m = tanh(h/2) = 2 sigmoid(h) - 1, evaluated as 4e/(1+e)^2 with

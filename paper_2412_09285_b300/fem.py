@@ -73,6 +73,7 @@ def _load():
         "fem_write_state": (S, [P, P, P, P, C.c_int32, P]),
         "fem_problem_info": (S, [P, P, P, P, P, P]),
         "fem_sync": (S, [P, P]),
+        "fem_set_dense_launch": (S, [P, C.c_int32]),
         "fem_destroy": (None, [P]),
         "fem_status_string": (C.c_char_p, [S]),
         "fem_last_error": (C.c_char_p, []),
@@ -173,6 +174,11 @@ def fem_problem_info(handle):
 
 def fem_sync(handle, stream=None):
     _check(_lib.fem_sync(handle, _stream(stream)), "fem_sync")
+
+
+def fem_set_dense_launch(handle, mode):
+    """mode: 0 auto, 1 one kernel per step, 2 persistent (fem_dense_launch)."""
+    _check(_lib.fem_set_dense_launch(handle, int(mode)), "fem_set_dense_launch")
 
 
 def fem_destroy(handle):
@@ -296,6 +302,10 @@ class Problem:
 
     def info(self):
         return fem_problem_info(self.handle)
+
+    def set_dense_launch(self, mode):
+        """'auto', 'per_step' or 'persistent' (dense problems)."""
+        fem_set_dense_launch(self.handle, {"auto": 0, "per_step": 1, "persistent": 2}[mode])
 
     def sync(self):
         fem_sync(self.handle, self.stream)

@@ -179,3 +179,56 @@ def test_dense_argument_errors(fem):
     with pytest.raises(fem.FemError) as e:
         fem.Problem("maxcut", dense=bad)
     assert e.value.status == fem.FEM_ERR_INVALID_ARG
+
+
+def _run(fem, g, h0, launch, n_steps, windows, **kw):
+    P = fem.Problem("maxcut", dense=g.dense)
+    P.set_dense_launch(launch)
+    t = 0
+    for T in windows:
+        P.anneal(h_init=h0 if t == 0 else None, replicas=h0.shape[1], n_steps=n_steps, t_begin=t, t_end=T, **kw)
+        t = T
+    return P
+
+
+@pytest.mark.parametrize("prec,mode,opt", [
+    ("bf16", "paper", "adam"), ("fp8", "paper", "adam"), ("bf16x2", "exact", "adam"), ("bf16", "exact", "adam"),
+    ("bf16", "paper", "rmsprop"), ("fp8", "paper", "sgd")])
+def test_persistent_matches_per_step(fem, prec, mode, opt):
+    """The persistent launch (state in tensor memory for the whole window, a barrier
+    per step between the CTAs of a replica block) gives the per-step kernel's h, m, v
+    bit for bit: n = 300 (three row tiles, the last one ragged), two replica blocks,
+    and the window split [0, 37) + [37, 120) for the persistent run."""
+    g = I.sk_dense(300, seed=92)
+    h0 = I.initial_fields(300, 256, seed=93)
+    kw = dict(precision=prec, grad_mode=mode, optimizer=opt)
+    if opt == "rmsprop":
+        kw.update(lr=0.01)
+    if opt == "sgd":
+        kw.update(lr=0.05, momentum=0.9)
+    ref = _run(fem, g, h0, "per_step", 120, [120], **kw).state()
+    got = _run(fem, g, h0, "persistent", 120, [37, 120], **kw).state()
+    for a, b, name in zip(got, ref, "hmv"):
+        assert np.array_equal(a, b), (name, int(np.sum(a != b)))
+
+
+def test_persistent_full_size(fem):
+    """n = 2000, R = 1024 (the dense SK workload, 128 co-resident CTAs): 60 persistent
+    steps equal 60 per-step launches bit for bit, in bf16 and e4m3."""
+    g = I.sk_dense(2000, seed=94)
+    h0 = I.initial_fields(2000, 1024, seed=95)
+    for prec in ("bf16", "fp8"):
+        ref = _run(fem, g, h0, "per_step", 1000, [60], precision=prec).state()
+        got = _run(fem, g, h0, "persistent", 1000, [60], precision=prec).state()
+        for a, b, name in zip(got, ref, "hmv"):
+            assert np.array_equal(a, b), (prec, name, int(np.sum(a != b)))
+
+
+def test_persistent_unsupported(fem):
+    g = I.sk_dense(200, seed=96)
+    h0 = I.initial_fields(200, 128, seed=97)
+    with pytest.raises(fem.FemError) as e:
+        _run(fem, g, h0, "persistent", 10, [10], precision="fp32")
+    assert e.value.status == fem.FEM_ERR_UNSUPPORTED
+    with pytest.raises(fem.FemError):
+        fem.Problem("maxcut", graph=I.er_gnm(50, 100, seed=1)).set_dense_launch("persistent")

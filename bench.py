@@ -58,6 +58,13 @@ WORKLOADS = {
                                         "per step, CUDA-graph step loop, autotuned work items",
                     n_bmc=256, bmc_lo=1000, bmc_hi=64000, deg=10.0, q=4, n_sat=64, sat_lo=5000, sat_hi=50000,
                     ratio=4.2, R=16, n_steps=1000, graph_seed=5, h_seed=6, cpu_steps=2),
+    # the batched workload at 1/8 scale (same size distributions): the case profiled in detail
+    "batched_small": dict(kind="batched", name="batched heterogeneous at 1/8 scale: 32 bMinCut (random geometric "
+                                              "graphs, n log-uniform 1k-64k, mean degree 10, unit weights, q=4) + 8 "
+                                              "random Max-3-SAT (n log-uniform 5k-50k, M=4.2n), R=16 each, 1000-step "
+                                              "exponential beta 0.05->5, Adam lr 0.1, paper-mode gradient",
+                          n_bmc=32, bmc_lo=1000, bmc_hi=64000, deg=10.0, q=4, n_sat=8, sat_lo=5000, sat_hi=50000,
+                          ratio=4.2, R=16, n_steps=1000, graph_seed=5, h_seed=6, cpu_steps=2),
 }
 
 
@@ -172,7 +179,7 @@ def _roofline(wl, inst, step_ms, precision, persistent=False):
         ach = alg / (step_ms / 1e3) / 1e9
         return {"bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                 "frac": ach / peaks["hbm_gbs"],
-                "traffic": _traffic_from_profile("batch_step_config4.md", os.path.join(csrc, "batch.cu")),
+                "traffic": _traffic_from_profile("batch_step_bmc256_sat64_R16.md", os.path.join(csrc, "batch.cu")),
                 "kernel": "k_batch_step<4, paper>", "algorithmic_bytes_per_launch": alg, "launch_ms": step_ms,
                 "peak_source": f"{src} hbm_gbs (copy), of {src}", "frac_of_8TBs": ach / 8000.0}
     if wl["kind"] == "sparse":

@@ -42,6 +42,7 @@ struct BatchMember {
   const int32_t* cl_lit;
   const int32_t* occ_ptr;
   const int32_t* occ;
+  const int2* oth;
 };
 
 struct BatchItem {
@@ -106,6 +107,7 @@ __device__ void run_sat_item(const BatchMember& b, const BatchItem& it, const St
   a.cl_lit = b.cl_lit;
   a.occ_ptr = b.occ_ptr;
   a.occ = b.occ;
+  a.oth = b.oth;
   a.n = b.n;
   a.R = b.R;
   a.opt = b.opt;
@@ -114,6 +116,12 @@ __device__ void run_sat_item(const BatchMember& b, const BatchItem& it, const St
   a.v = b.v;
   a.P_in = b.satP[t & 1];
   a.P_out = b.satP[(t + 1) & 1];
+  if (sat_k3_shape(a)) {
+    const int lane = threadIdx.x & 31;
+    for (long long base = it.e0 + (threadIdx.x & ~31); base < it.e1; base += blockDim.x)
+      sat_element_k3(a, s, base + lane, base + lane < it.e1, lane);
+    return;
+  }
   for (long long e = it.e0 + threadIdx.x; e < it.e1; e += blockDim.x) sat_element(a, s, e);
 }
 
@@ -121,7 +129,7 @@ __device__ void run_sat_item(const BatchMember& b, const BatchItem& it, const St
 // shared by all bMinCut members of a batch.
 // s_q carries the q-state gradient scale (gamma), s_1 the single-field one (gamma/4).
 template <int Q, int MODE>
-__global__ void __launch_bounds__(256) k_batch_step(const BatchMember* __restrict__ members,
+__global__ void __launch_bounds__(256, 4) k_batch_step(const BatchMember* __restrict__ members,
                                                     const BatchItem* __restrict__ items, int32_t n_items,
                                                     int32_t max_rq, StepScalars s_q, StepScalars s_1,
                                                     int32_t t) {
@@ -265,6 +273,7 @@ static fem_status batch_prepare(Batch* b, cudaStream_t s) {
     m.cl_lit = p->cl_lit;
     m.occ_ptr = p->occ_ptr;
     m.occ = p->occ;
+    m.oth = reinterpret_cast<const int2*>(p->oth);
     dm.push_back(m);
     if (p->kind == FEM_BMINCUT) {
       b->elems_bmc += (long long)p->n * p->R;

@@ -38,6 +38,7 @@ struct BmcArgs {
   unsigned long long* ps_zero;
 };
 
+// Softmax with the fast exponential and reciprocal (relative error ~1e-6; Z >= 1).
 template <int Q>
 __device__ __forceinline__ void softmax_q(const float (&h)[Q], float (&P)[Q], float (&lnP)[Q]) {
   float mx = h[0];
@@ -46,10 +47,10 @@ __device__ __forceinline__ void softmax_q(const float (&h)[Q], float (&P)[Q], fl
   float ex[Q], Z = 0.f;
 #pragma unroll
   for (int s = 0; s < Q; ++s) {
-    ex[s] = expf(h[s] - mx);
+    ex[s] = __expf(h[s] - mx);
     Z += ex[s];
   }
-  const float invZ = 1.f / Z, lz = logf(Z);
+  const float invZ = __fdividef(1.f, Z), lz = __logf(Z);
 #pragma unroll
   for (int s = 0; s < Q; ++s) {
     P[s] = ex[s] * invZ;
@@ -107,8 +108,8 @@ __device__ __forceinline__ void bmincut_element(const BmcArgs& a, const StepScal
   constexpr int B = QBits<Q>::B, RPW = QBits<Q>::RPW;
   constexpr uint32_t SM = QBits<Q>::MASK;
   {
-    const int i = act ? (int)(e / a.R) : 0;
-    const int r = act ? (int)(e - (long long)i * a.R) : 0;
+    int i = 0, r = 0;
+    if (act) split_element(e, a.R, i, r);
     const int wsel = r / RPW, sh = (r % RPW) * B;
     float h[Q], mm[Q], vv[Q];
 #pragma unroll
@@ -119,21 +120,72 @@ __device__ __forceinline__ void bmincut_element(const BmcArgs& a, const StepScal
     for (int q = 0; q < Q; ++q) acc[q] = 0.f;
     int own = 0;
     float cf = 0.f, ca = 0.f;
+    int beg = 0, end = 0;
+    // Paper mode, unit weights, one packed word per node (R * B == 32: q = 2 with
+    // R = 32, q = 3, 4 with R = 16): the lanes of a node load up to R neighbours'
+    // words at once, a warp bit-transpose turns them into bit planes, and popcounts
+    // give the per-state counts (warp-uniform condition; every lane takes part).
+    const bool planes = MODE == FEM_GRAD_PAPER && B <= 2 && !a.w && a.R * B == 32;
     if (act) {
       load_q<Q>(a.h_in + idx, h);
       load_q<Q>(a.m + idx, mm);
       if (a.opt != FEM_OPT_SGD) load_q<Q>(a.v + idx, vv);
-      const int beg = a.row_ptr[i], end = a.row_ptr[i + 1];
+      beg = a.row_ptr[i];
+      end = a.row_ptr[i + 1];
       if (MODE == FEM_GRAD_PAPER) {
         own = (int)((a.words_in[(size_t)i * a.wpn + wsel] >> sh) & SM);
         cf = a.cf[i];
         ca = a.ca[i];
-        for (int k = beg; k < end; ++k) {
-          const uint32_t j = a.col[k] & 0x7fffffffu;
-          const float wk = a.w ? a.w[k] : 1.f;
-          const int sj = (int)((a.words_in[(size_t)j * a.wpn + wsel] >> sh) & SM);
+      }
+    }
+    if (MODE == FEM_GRAD_PAPER && planes) {
+      const int G = a.R;  // lanes per node: 16 or 32
+      const int deg = end - beg, sub = lane & (G - 1);
+      int maxdeg = deg;
+      if (G == 16) maxdeg = max(maxdeg, __shfl_xor_sync(kFullMask, maxdeg, 16));
+      uint32_t c[4] = {0u, 0u, 0u, 0u};
+      for (int k0 = 0; k0 < maxdeg; k0 += G) {
+        const int kk = k0 + sub;
+        uint32_t w = 0u;
+        if (kk < deg) w = a.words_in[a.col[beg + kk] & 0x7fffffffu];
+        const uint32_t t = warp_transpose32(w, lane);  // lane b: bit e = bit b of lane e's word
+        const int nv = min(max(deg - k0, 0), G);
+        const uint32_t vm = (nv >= 32 ? 0xffffffffu : ((1u << nv) - 1u)) << (lane & ~(G - 1));
+        if (B == 1) {
+          c[1] += __popc(t & vm);
+          c[0] += __popc(~t & vm);
+        } else {
+          const uint32_t lo = __shfl_sync(kFullMask, t, 2 * sub), hi = __shfl_sync(kFullMask, t, 2 * sub + 1);
+          c[0] += __popc(~lo & ~hi & vm);
+          c[1] += __popc(lo & ~hi & vm);
+          c[2] += __popc(~lo & hi & vm);
+          c[3] += __popc(lo & hi & vm);
+        }
+      }
 #pragma unroll
-          for (int q = 0; q < Q; ++q) acc[q] += (sj == q) ? wk : 0.f;
+      for (int q = 0; q < Q; ++q) acc[q] = (float)c[q < 4 ? q : 0];
+    } else if (act) {
+      if (MODE == FEM_GRAD_PAPER) {
+        if (!a.w && end - beg < (Q <= 4 ? 65536 : 256)) {
+          // unit weights: integer counts packed 16 (q <= 4) or 8 bits wide in one word,
+          // the same exact sums as the float path below
+          constexpr int F = Q <= 4 ? 16 : 8;
+          unsigned long long pk = 0ull;
+          for (int k = beg; k < end; ++k) {
+            const uint32_t j = a.col[k] & 0x7fffffffu;
+            const uint32_t sj = (a.words_in[(size_t)j * a.wpn + wsel] >> sh) & SM;
+            pk += 1ull << (F * sj);
+          }
+#pragma unroll
+          for (int q = 0; q < Q; ++q) acc[q] = (float)(uint32_t)((pk >> (F * q)) & ((1ull << F) - 1ull));
+        } else {
+          for (int k = beg; k < end; ++k) {
+            const uint32_t j = a.col[k] & 0x7fffffffu;
+            const float wk = a.w ? a.w[k] : 1.f;
+            const int sj = (int)((a.words_in[(size_t)j * a.wpn + wsel] >> sh) & SM);
+#pragma unroll
+            for (int q = 0; q < Q; ++q) acc[q] += (sj == q) ? wk : 0.f;
+          }
         }
       } else {
         // accumulate sum_j W_ij (P_j(s) - 1/q): the constant drops out of every
@@ -188,11 +240,10 @@ __device__ __forceinline__ void bmincut_element(const BmcArgs& a, const StepScal
       }
       cen[q] = c;
     }
+    with_opt(a.opt, [&](auto O) {
 #pragma unroll
-    for (int q = 0; q < Q; ++q) {
-      const float g = s.gq * cen[q] * P[q];
-      opt_update_rt(a.opt, h[q], mm[q], vv[q], g, s);
-    }
+      for (int q = 0; q < Q; ++q) opt_update_fast<decltype(O)::value>(h[q], mm[q], vv[q], s.gq * cen[q] * P[q], s);
+    });
     const int sn = argmax_q<Q>(h);
     if (act) {
       store_q<Q>(a.h_out + idx, h);
@@ -211,7 +262,6 @@ __device__ __forceinline__ void bmincut_element(const BmcArgs& a, const StepScal
     for (int off = 1; off < RPW; off <<= 1) word |= __shfl_xor_sync(kFullMask, word, off);
     if (act && (r % RPW) == 0) a.words_out[(size_t)i * a.wpn + wsel] = word;
   }
-  (void)lane;
 }
 
 }  // namespace fem

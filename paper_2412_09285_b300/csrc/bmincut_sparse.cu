@@ -28,7 +28,7 @@ namespace {
 // One thread per (node, replica); a warp covers 32 consecutive (node, replica)
 // pairs, so R % RPW == 0 keeps every packed word inside one group of lanes.
 template <int Q, int MODE>
-__global__ void __launch_bounds__(256) k_bmincut_step(BmcArgs a, StepScalars s) {
+__global__ void __launch_bounds__(256, 4) k_bmincut_step(BmcArgs a, StepScalars s) {
   extern __shared__ unsigned long long smem_u64[];
   const int RQ = a.R * Q;
   unsigned long long* sps = smem_u64;                                // [R*Q] exact mode

@@ -239,8 +239,11 @@ static fem_status upload_graph(Problem* p, const HostGraph& g, cudaStream_t s) {
 // ---------------------------------------------------------------------------
 struct HostSat {
   int64_t n_clauses = 0;
-  int32_t max_width = 0;
+  int32_t max_width = 0, min_width = 0;
   std::vector<int32_t> cl_ptr, cl_lit, occ_ptr, occ;
+  // every clause has 3 literals: per occurrence (in occ order) the clause's other two
+  // literals in clause order, the first with the occurrence's own negation in bit 31
+  std::vector<int32_t> oth;
 };
 
 static fem_status host_sat(const fem_problem_desc* d, HostSat& g) {
@@ -281,6 +284,20 @@ static fem_status host_sat(const fem_problem_desc* d, HostSat& g) {
     for (int32_t k = g.cl_ptr[c]; k < g.cl_ptr[c + 1]; ++k)
       g.occ[fill[g.cl_lit[k] >> 1]++] = (int32_t)((c << 3) | (k - g.cl_ptr[c]));
   g.n_clauses = M;
+  g.min_width = 8;
+  for (int64_t c = 0; c < M; ++c) g.min_width = std::min<int32_t>(g.min_width, g.cl_ptr[c + 1] - g.cl_ptr[c]);
+  if (M > 0 && g.min_width == 3 && g.max_width == 3) {
+    g.oth.assign(2 * (size_t)L, 0);
+    for (int64_t o = 0; o < L; ++o) {
+      const int32_t c = g.occ[o] >> 3, pos = g.occ[o] & 7, b = g.cl_ptr[c];
+      int32_t other[2], k2 = 0;
+      for (int32_t k = 0; k < 3; ++k)
+        if (k != pos) other[k2++] = g.cl_lit[b + k];
+      const uint32_t own_neg = (uint32_t)(g.cl_lit[b + pos] & 1);
+      g.oth[2 * o] = (int32_t)((uint32_t)other[0] | (own_neg << 31));
+      g.oth[2 * o + 1] = other[1];
+    }
+  }
   return FEM_OK;
 }
 
@@ -293,6 +310,7 @@ static fem_status upload_sat(Problem* p, const HostSat& g, cudaStream_t s) {
   if ((st = upload(p, &p->cl_lit, g.cl_lit, s)) != FEM_OK) return st;
   if ((st = upload(p, &p->occ_ptr, g.occ_ptr, s)) != FEM_OK) return st;
   if ((st = upload(p, &p->occ, g.occ, s)) != FEM_OK) return st;
+  if (!g.oth.empty() && (st = upload(p, &p->oth, g.oth, s)) != FEM_OK) return st;
   return FEM_OK;
 }
 

@@ -53,7 +53,8 @@ struct Problem {
   int32_t* cl_ptr = nullptr;   // [M+1]
   int32_t* cl_lit = nullptr;   // [n_occ]: (var << 1) | negated
   int32_t* occ_ptr = nullptr;  // [n+1]: variable -> occurrences
-  int32_t* occ = nullptr;      // [n_occ]: (clause << 2) | position   (k <= 4) or clause index
+  int32_t* occ = nullptr;      // [n_occ]: (clause << 3) | position
+  int32_t* oth = nullptr;      // [2 n_occ]: 3-SAT only, the other two literals per occurrence
   int32_t max_width = 0;
 
   // ---- dense couplings (MaxCut, dense_J)

@@ -110,21 +110,6 @@ __global__ void __launch_bounds__(256) k_maxcut_step(MaxcutArgs a, StepScalars s
   }
 }
 
-// Transpose of a 32 x 32 bit matrix held one row per lane (lane e holds row e):
-// afterwards lane r holds column r, i.e. bit e of the result is bit r of row e.
-// Five butterfly stages exchange blocks of 16, 8, 4, 2 and 1 bits.
-__device__ __forceinline__ uint32_t warp_transpose32(uint32_t x, int lane) {
-  const uint32_t masks[5] = {0x0000FFFFu, 0x00FF00FFu, 0x0F0F0F0Fu, 0x33333333u, 0x55555555u};
-#pragma unroll
-  for (int s = 0; s < 5; ++s) {
-    const int j = 16 >> s;
-    const uint32_t m = masks[s];
-    const uint32_t y = __shfl_xor_sync(kFullMask, x, j);
-    x = (lane & j) ? (((y >> j) & m) | (x & ~m)) : ((x & m) | ((y << j) & ~m));
-  }
-  return x;
-}
-
 // Paper-mode step, tuned for HBM streaming.  A warp owns NPW consecutive nodes
 // (one block of 32 replicas) per iteration and issues every load of the group
 // before it computes: the 3*NPW state lines (h, m, v), then one coalesced load

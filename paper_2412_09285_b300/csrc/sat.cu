@@ -22,6 +22,13 @@ namespace {
 
 __global__ void __launch_bounds__(256) k_sat_step(SatArgs a, StepScalars s) {
   const long long total = (long long)a.n * a.R;
+  if (sat_k3_shape(a)) {
+    const int lane = threadIdx.x & 31;
+    for (long long base = (long long)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < total;
+         base += (long long)gridDim.x * blockDim.x)
+      sat_element_k3(a, s, base + lane, base + lane < total, lane);
+    return;
+  }
   for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
        e += (long long)gridDim.x * blockDim.x)
     sat_element(a, s, e);
@@ -30,7 +37,7 @@ __global__ void __launch_bounds__(256) k_sat_step(SatArgs a, StepScalars s) {
 __global__ void k_sat_marginals(const float* __restrict__ h, long long total, float* __restrict__ P) {
   for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
        e += (long long)gridDim.x * blockDim.x)
-    P[e] = sigmoidf_acc(h[e]);
+    P[e] = sigmoidf_fast(h[e]);
 }
 
 // Per-block partial counts of unsatisfied clauses; a thread keeps one replica.
@@ -141,6 +148,7 @@ fem_status sat_steps(Problem* p, const std::vector<StepScalars>& sc, int t_begin
   a.cl_lit = p->cl_lit;
   a.occ_ptr = p->occ_ptr;
   a.occ = p->occ;
+  a.oth = reinterpret_cast<const int2*>(p->oth);
   a.n = p->n;
   a.R = p->R;
   a.opt = p->optimizer;

@@ -5,6 +5,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 #include "fem_internal.h"
 
 namespace fem {
@@ -92,6 +94,43 @@ __device__ __forceinline__ void opt_update_fast(float& h, float& m, float& v, fl
                                                 const StepScalars& s) {
   if (s.wd != 0.f) g = fmaf(s.wd, h, g);
   opt_update_fast_core<OPT>(h, m, v, g, s);
+}
+
+// Calls f(OPT) with the run-time optimizer as a compile-time constant: one
+// warp-uniform branch around a whole block of updates, so their arithmetic can
+// interleave instead of being split by a branch per update.
+template <class F>
+__device__ __forceinline__ void with_opt(int opt, F&& f) {
+  if (opt == FEM_OPT_ADAM) f(std::integral_constant<int, FEM_OPT_ADAM>{});
+  else if (opt == FEM_OPT_RMSPROP) f(std::integral_constant<int, FEM_OPT_RMSPROP>{});
+  else f(std::integral_constant<int, FEM_OPT_SGD>{});
+}
+
+// Transpose of a 32 x 32 bit matrix held one row per lane (lane e holds row e):
+// afterwards lane r holds column r, i.e. bit e of the result is bit r of row e.
+// Five butterfly stages exchange blocks of 16, 8, 4, 2 and 1 bits.
+__device__ __forceinline__ uint32_t warp_transpose32(uint32_t x, int lane) {
+  const uint32_t masks[5] = {0x0000FFFFu, 0x00FF00FFu, 0x0F0F0F0Fu, 0x33333333u, 0x55555555u};
+#pragma unroll
+  for (int s = 0; s < 5; ++s) {
+    const int j = 16 >> s;
+    const uint32_t m = masks[s];
+    const uint32_t y = __shfl_xor_sync(kFullMask, x, j);
+    x = (lane & j) ? (((y >> j) & m) | (x & ~m)) : ((x & m) | ((y << j) & ~m));
+  }
+  return x;
+}
+
+// Element index e = i*R + r -> (i, r); 32-bit division whenever e < 2^32.
+__device__ __forceinline__ void split_element(long long e, int R, int& i, int& r) {
+  if ((unsigned long long)e < 4294967296ull) {
+    const uint32_t el = (uint32_t)e, ii = el / (uint32_t)R;
+    i = (int)ii;
+    r = (int)(el - ii * (uint32_t)R);
+  } else {
+    i = (int)(e / R);
+    r = (int)(e - (long long)i * R);
+  }
 }
 
 // 1 - tanh(h/2)^2 with the fast exponential (relative error ~1e-6).

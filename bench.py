@@ -145,8 +145,27 @@ def _make_problem(fem, wl, inst, stream, dense_launch="auto"):
     return fem.Problem("maxcut", graph=inst, stream=stream)
 
 
-def _traffic_from_profile(name, kernel_src):
-    """DRAM bytes per launch from a committed ncu summary, if the kernel source is
+# The source files each profiled kernel is compiled from (its .cu and the local
+# headers it includes); a summary's traffic figure counts only while they are unchanged.
+KERNEL_SOURCES = {
+    "sparse": ["maxcut_sparse.cu", "step_common.cuh", "fem_internal.h"],
+    "dense": ["dense_tc.cu", "step_common.cuh", "fem_internal.h"],
+    "batched": ["batch.cu", "bmincut_core.cuh", "sat_core.cuh", "step_common.cuh", "fem_internal.h"],
+}
+
+
+def source_sha256(kind):
+    """sha256 over the concatenated sources of one kernel family (see KERNEL_SOURCES)."""
+    csrc = os.path.join(ROOT, "paper_2412_09285_b300", "csrc")
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES[kind]:
+        with open(os.path.join(csrc, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def _traffic_from_profile(name, kind):
+    """DRAM bytes per launch from a committed ncu summary, if the kernel's sources are
     unchanged since the capture (else None)."""
     try:
         txt = open(os.path.join(ROOT, "profiles", name)).read()
@@ -156,8 +175,7 @@ def _traffic_from_profile(name, kernel_src):
     m2 = re.search(r"traffic_bytes_per_launch:\s*([0-9]+)", txt)
     if not (m1 and m2):
         return None
-    sha = hashlib.sha256(open(kernel_src, "rb").read()).hexdigest()
-    return int(m2.group(1)) if sha == m1.group(1) else None
+    return int(m2.group(1)) if source_sha256(kind) == m1.group(1) else None
 
 
 def _roofline(wl, inst, step_ms, precision, persistent=False):
@@ -179,7 +197,7 @@ def _roofline(wl, inst, step_ms, precision, persistent=False):
         ach = alg / (step_ms / 1e3) / 1e9
         return {"bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                 "frac": ach / peaks["hbm_gbs"],
-                "traffic": _traffic_from_profile("batch_step_bmc256_sat64_R16.md", os.path.join(csrc, "batch.cu")),
+                "traffic": _traffic_from_profile("batch_step_bmc256_sat64_R16.md", "batched"),
                 "kernel": "k_batch_step<4, paper>", "algorithmic_bytes_per_launch": alg, "launch_ms": step_ms,
                 "peak_source": f"{src} hbm_gbs (copy), of {src}", "frac_of_8TBs": ach / 8000.0}
     if wl["kind"] == "sparse":
@@ -190,8 +208,7 @@ def _roofline(wl, inst, step_ms, precision, persistent=False):
         ach = alg / (step_ms / 1e3) / 1e9
         return {"bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                 "frac": ach / peaks["hbm_gbs"],
-                "traffic": _traffic_from_profile("maxcut_step_sparse_n1M_R32.md",
-                                                 os.path.join(csrc, "maxcut_sparse.cu")),
+                "traffic": _traffic_from_profile("maxcut_step_sparse_n1M_R32.md", "sparse"),
                 "kernel": "k_maxcut_step_paper<adam, unit, 4>", "algorithmic_bytes_per_launch": alg,
                 "launch_ms": step_ms, "peak_source": f"{src} hbm_gbs (copy), of {src}",
                 "frac_of_8TBs": ach / 8000.0}
@@ -214,7 +231,7 @@ def _roofline(wl, inst, step_ms, precision, persistent=False):
         kernel = f"k_dense_step_{'fp32' if precision == 'fp32' else 'tc<' + precision + '>'}"
         prof = f"dense_step_{precision}_sk2000_R1024.md"
     return {"bound": bound, "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
-            "traffic": _traffic_from_profile(prof, os.path.join(csrc, "dense_tc.cu")),
+            "traffic": _traffic_from_profile(prof, "dense"),
             "kernel": kernel, "algorithmic_flops_per_step": flops, "step_ms": step_ms,
             "launch": "persistent (one launch per anneal window)" if persistent else "one launch per step",
             "peak_source": psrc}

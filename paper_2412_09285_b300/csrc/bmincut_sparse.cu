@@ -21,6 +21,7 @@
 #include <cmath>
 
 #include "bmincut_core.cuh"
+#include "reduce_common.cuh"
 
 namespace fem {
 namespace {
@@ -60,36 +61,52 @@ __global__ void __launch_bounds__(256, 4) k_bmincut_step(BmcArgs a, StepScalars 
 }
 
 // From fields h: packed argmax words, group counts and fixed-point column sums.
+// Counts and sums gather in shared memory ([R][q] per block) and reach the global
+// buffers with one integer atomic per entry and block (exact, so order-free).
 template <int Q>
 __global__ void __launch_bounds__(256) k_bmincut_derive(const float* __restrict__ h, int32_t n, int32_t R,
                                                         int32_t wpn, uint32_t* __restrict__ words,
                                                         int32_t* __restrict__ cnt,
                                                         unsigned long long* __restrict__ ps) {
   constexpr int B = QBits<Q>::B, RPW = QBits<Q>::RPW;
+  extern __shared__ unsigned long long smem_d[];
+  const int RQ = R * Q;
+  unsigned long long* sps = smem_d;
+  int32_t* scnt = reinterpret_cast<int32_t*>(smem_d + RQ);
+  for (int x = threadIdx.x; x < RQ; x += blockDim.x) {
+    sps[x] = 0ull;
+    scnt[x] = 0;
+  }
+  __syncthreads();
   const int lane = threadIdx.x & 31;
   const long long total = (long long)n * R;
   for (long long base = (long long)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < total;
        base += (long long)gridDim.x * blockDim.x) {
     const long long e = base + lane;
     const bool act = e < total;
-    const int i = act ? (int)(e / R) : 0;
-    const int r = act ? (int)(e - (long long)i * R) : 0;
+    int i = 0, r = 0;
+    if (act) split_element(e, R, i, r);
     float x[Q];
 #pragma unroll
     for (int q = 0; q < Q; ++q) x[q] = 0.f;
     if (act) load_q<Q>(h + ((size_t)i * R + r) * Q, x);
     const int sn = argmax_q<Q>(x);
     if (act) {
-      atomicAdd(&cnt[r * Q + sn], 1);
+      atomicAdd(&scnt[r * Q + sn], 1);
       float P[Q], ln[Q];
       softmax_q<Q>(x, P, ln);
 #pragma unroll
-      for (int q = 0; q < Q; ++q) atomicAdd(&ps[r * Q + q], __float2ull_rn(P[q] * kPsumScale));
+      for (int q = 0; q < Q; ++q) atomicAdd(&sps[r * Q + q], __float2ull_rn(P[q] * kPsumScale));
     }
     uint32_t word = act ? ((uint32_t)sn << ((r % RPW) * B)) : 0u;
 #pragma unroll
     for (int off = 1; off < RPW; off <<= 1) word |= __shfl_xor_sync(kFullMask, word, off);
     if (act && (r % RPW) == 0) words[(size_t)i * wpn + r / RPW] = word;
+  }
+  __syncthreads();
+  for (int x = threadIdx.x; x < RQ; x += blockDim.x) {
+    if (scnt[x]) atomicAdd(&cnt[x], scnt[x]);
+    if (sps[x]) atomicAdd(&ps[x], sps[x]);
   }
 }
 
@@ -154,32 +171,25 @@ __global__ void __launch_bounds__(256) k_bmincut_cut_partial(
   }
 }
 
-// E_r = cut_r + lambda_max * sum_s n_s (n_s - 1), then argmin (lowest index on ties).
+// E_r = cut_r + lambda_max * sum_s n_s (n_s - 1) for replica r = blockIdx.x (the
+// argmin follows in k_argmin_replica).
 template <int Q>
-__global__ void __launch_bounds__(1024) k_bmincut_finish(
+__global__ void __launch_bounds__(kRedThreads) k_bmincut_finish(
     const int64_t* __restrict__ part_i, const double* __restrict__ part_f,
     const int64_t* __restrict__ part_cnt, int32_t nblk, int32_t R, int32_t intw, int32_t lam_is_int,
-    double lam, int64_t* __restrict__ e_i, double* __restrict__ e_f, int32_t* __restrict__ best) {
-  __shared__ double sval[1024];
-  __shared__ int sidx[1024];
-  double bv = 0.0;
-  int bidx = 0x7fffffff;
-  for (int r = threadIdx.x; r < R; r += blockDim.x) {
-    int64_t ci = 0;
-    double cfv = 0.0;
-    int64_t sz[Q];
+    double lam, int64_t* __restrict__ e_i, double* __restrict__ e_f) {
+  __shared__ int64_t shi[kRedThreads];
+  __shared__ double shf[kRedThreads];
+  const int r = blockIdx.x;
+  const int64_t ci = intw ? column_sum<int64_t>(part_i, nblk, R, r, shi) : 0;
+  const double cfv = intw ? 0.0 : column_sum<double>(part_f, nblk, R, r, shf);
+  int64_t bal = 0;
 #pragma unroll
-    for (int q = 0; q < Q; ++q) sz[q] = 0;
-    for (int b = 0; b < nblk; ++b) {
-      const size_t o = (size_t)b * R + r;
-      ci += part_i[o];
-      cfv += part_f[o];
-#pragma unroll
-      for (int q = 0; q < Q; ++q) sz[q] += part_cnt[o * Q + q];
-    }
-    int64_t bal = 0;
-#pragma unroll
-    for (int q = 0; q < Q; ++q) bal += sz[q] * (sz[q] - 1);
+  for (int q = 0; q < Q; ++q) {
+    const int64_t sz = column_sum<int64_t>(part_cnt, nblk, (size_t)R * Q, (size_t)r * Q + q, shi);
+    bal += sz * (sz - 1);
+  }
+  if (threadIdx.x == 0) {
     double ef;
     if (intw && lam_is_int) {
       const int64_t ei = ci + (int64_t)lam * bal;
@@ -190,28 +200,7 @@ __global__ void __launch_bounds__(1024) k_bmincut_finish(
       ef = (intw ? (double)ci : cfv) + lam * (double)bal;
     }
     e_f[r] = ef;
-    if (bidx == 0x7fffffff || ef < bv) {
-      bv = ef;
-      bidx = r;
-    }
   }
-  sval[threadIdx.x] = bv;
-  sidx[threadIdx.x] = bidx;
-  __syncthreads();
-  for (int off = blockDim.x / 2; off > 0; off >>= 1) {
-    if (threadIdx.x < off) {
-      const double ov = sval[threadIdx.x + off];
-      const int oi = sidx[threadIdx.x + off];
-      const int mi = sidx[threadIdx.x];
-      if (oi != 0x7fffffff &&
-          (mi == 0x7fffffff || ov < sval[threadIdx.x] || (ov == sval[threadIdx.x] && oi < mi))) {
-        sval[threadIdx.x] = ov;
-        sidx[threadIdx.x] = oi;
-      }
-    }
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) best[0] = sidx[0];
 }
 
 template <int Q>
@@ -289,9 +278,12 @@ fem_status derive_q(Problem* p, int t, cudaStream_t st) {
     FEM_CUDA(cudaMemsetAsync(p->cnt[b], 0, rq * sizeof(int32_t), st));
     FEM_CUDA(cudaMemsetAsync(p->psum[b], 0, rq * sizeof(unsigned long long), st));
   }
-  const int grid = resident_grid(k_bmincut_derive<Q>, p->sm_count, (long long)p->n * p->R, 0);
-  k_bmincut_derive<Q><<<grid, 256, 0, st>>>(h, p->n, p->R, p->words_per_node, p->words[t & 1],
-                                           p->cnt[t % 3], p->psum[t % 3]);
+  const size_t smem = rq * (sizeof(unsigned long long) + sizeof(int32_t));
+  if (smem > 48 * 1024)
+    FEM_CUDA(cudaFuncSetAttribute(k_bmincut_derive<Q>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  const int grid = resident_grid(k_bmincut_derive<Q>, p->sm_count, (long long)p->n * p->R, smem);
+  k_bmincut_derive<Q><<<grid, 256, smem, st>>>(h, p->n, p->R, p->words_per_node, p->words[t & 1],
+                                              p->cnt[t % 3], p->psum[t % 3]);
   count_launches(1);
   FEM_CUDA(cudaGetLastError());
   return FEM_OK;
@@ -310,12 +302,13 @@ fem_status readout_q(Problem* p, cudaStream_t st) {
                                                           p->w64, words, p->n, p->R, p->words_per_node,
                                                           p->part_i, p->part_f, p->part_cnt);
   const double lam = p->lambda_max;
-  k_bmincut_finish<Q><<<1, 1024, 0, st>>>(p->part_i, p->part_f, p->part_cnt, p->part_blocks, p->R,
-                                          p->int_w ? 1 : 0, lam == std::floor(lam) ? 1 : 0, lam,
-                                          p->energy_i, p->energy_f, p->best);
+  k_bmincut_finish<Q><<<p->R, kRedThreads, 0, st>>>(p->part_i, p->part_f, p->part_cnt, p->part_blocks, p->R,
+                                                     p->int_w ? 1 : 0, lam == std::floor(lam) ? 1 : 0, lam,
+                                                     p->energy_i, p->energy_f);
+  k_argmin_replica<<<1, 1024, 0, st>>>(p->energy_f, p->R, p->best);
   k_bmincut_states<Q><<<(p->n + 255) / 256 < 1024 ? (p->n + 255) / 256 : 1024, 256, 0, st>>>(
       words, p->n, p->R, p->words_per_node, p->best, p->states_dev, 0);
-  count_launches(3);
+  count_launches(4);
   FEM_CUDA(cudaGetLastError());
   return FEM_OK;
 }

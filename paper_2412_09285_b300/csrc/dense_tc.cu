@@ -57,6 +57,7 @@ struct DenseArgs {
   void* mt_out;     // next step's operand (bf16 or e4m3), [R][n_pad]
   void* mt_lo_out;  // exact mode low part (bf16) or NULL
   int32_t* err;
+  int64_t* part;  // read-out: per (row tile, replica) partial sums
 };
 
 // ------------------------------------------------------------------ PTX helpers
@@ -225,7 +226,10 @@ __device__ __forceinline__ void store_operand(void* base, size_t idx, uint32_t b
 }
 
 // ------------------------------------------------------------ the fused step
-template <int PREC>  // FEM_PREC_BF16, FEM_PREC_BF16X2 or FEM_PREC_FP8
+// READ: the exact read-out instead of a step.  With B = sgn(h) (+-1) the accumulator
+// holds S_ir = sum_j J_ij s_jr exactly, and the epilogue writes the partial
+// Q_r = sum_{i in tile} s_ir S_ir to a.part[blockIdx.x][r] (no state is changed).
+template <int PREC, bool READ = false>  // FEM_PREC_BF16, FEM_PREC_BF16X2 or FEM_PREC_FP8
 __global__ void __launch_bounds__(kThreads, 1) k_dense_step_tc(const __grid_constant__ CUtensorMap tmA,
                                                          const __grid_constant__ CUtensorMap tmB,
                                                          const __grid_constant__ CUtensorMap tmBlo,
@@ -297,6 +301,44 @@ __global__ void __launch_bounds__(kThreads, 1) k_dense_step_tc(const __grid_cons
     umma_commit(&done);
   }
   __syncwarp();
+
+  if constexpr (READ) {
+    __shared__ int32_t red[4][kTile];
+    const int quad = warp & 3, c0 = (warp >> 2) * 32;
+    const int i = i0 + quad * 32 + lane;
+    const bool row = i < a.n;
+    const bool ok = mbar_wait(&done, 0, a.err);
+    tc_fence_after();
+    if (__all_sync(kFullMask, ok)) {
+#pragma unroll 1
+      for (int cb = 0; cb < 32; cb += 8) {
+        float hv[8];
+#pragma unroll
+        for (int c = 0; c < 8; ++c) hv[c] = row ? a.h[(size_t)(r0 + c0 + cb + c) * a.n_pad + i] : 0.f;
+        uint32_t acc[8];
+        tmem_ld8_issue(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(c0 + cb), acc);
+        tmem_wait_ld(acc);
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+          const int S = (int)__uint_as_float(acc[c]);
+          const int v = row ? (hv[c] >= 0.f ? S : -S) : 0;
+          const int tot = __reduce_add_sync(kFullMask, v);
+          if (lane == 0) red[quad][c0 + cb + c] = tot;
+        }
+      }
+    }
+    __syncthreads();
+    if (threadIdx.x < kTile)
+      a.part[(size_t)blockIdx.x * a.R + r0 + threadIdx.x] =
+          (int64_t)red[0][threadIdx.x] + red[1][threadIdx.x] + red[2][threadIdx.x] + red[3][threadIdx.x];
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+      tc_fence_after();
+      tmem_dealloc(tmem, kTile);
+    }
+    return;
+  }
 
   // epilogue: thread = TMEM lane = row i of the tile.  Warp w reads TMEM lanes
   // 32*(w%4).. (its quadrant) and the 32 replica columns 32*(w/4)..; the state of 8
@@ -1144,10 +1186,55 @@ fem_status dense_steps(Problem* p, const std::vector<StepScalars>& sc, int t_beg
   return FEM_OK;
 }
 
+// Read-out on the tensor cores: S = J sgn(h) with +-1 operands (exact), reduced to
+// Q_r per 128-row tile in the epilogue.  Paper mode at BF16 / FP8 reuses the current
+// operand (it is sgn(h)); otherwise sgn(h) is written as bf16 into the ping-pong
+// buffer the next step overwrites anyway.
+template <int PREC>
+fem_status launch_read(Problem* p, int b, cudaStream_t st) {
+  static bool attr = false;
+  if (!attr) {
+    FEM_CUDA(cudaFuncSetAttribute(k_dense_step_tc<PREC, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)tc_smem_bytes(PREC)));
+    attr = true;
+  }
+  DenseArgs a{};
+  a.n = p->n;
+  a.n_pad = p->n_pad;
+  a.R = p->R;
+  a.h = p->h[0];
+  a.err = p->err;
+  a.part = p->part_i;
+  const dim3 grid(p->n_pad / kTile, p->R / kTile);
+  k_dense_step_tc<PREC, true><<<grid, kThreads, tc_smem_bytes(PREC), st>>>(
+      PREC == FEM_PREC_FP8 ? p->tmap_a8 : p->tmap_a16, p->tmap_b[b], p->tmap_b[b], a, StepScalars{});
+  return FEM_OK;
+}
+
 fem_status dense_readout(Problem* p, cudaStream_t s) {
-  const dim3 grid(p->n_pad / 32, (p->R + 31) / 32);
-  k_dense_quad<<<grid, 1024, 0, s>>>(p->Ji8, p->h[0], p->n, p->n_pad, p->R, p->part_i);
-  k_dense_finish<<<1, 1024, 0, s>>>(p->part_i, p->n_pad / 32, p->R, p->dense_wtot, p->energy_i, p->energy_f, p->best);
+  int nblk = p->n_pad / 32;
+  if (p->precision == FEM_PREC_FP32 || p->R % kTile != 0) {
+    const dim3 grid(p->n_pad / 32, (p->R + 31) / 32);
+    k_dense_quad<<<grid, 1024, 0, s>>>(p->Ji8, p->h[0], p->n, p->n_pad, p->R, p->part_i);
+  } else {
+    const int t = p->steps_done;
+    fem_status st;
+    if (p->grad_mode == FEM_GRAD_PAPER && p->precision != FEM_PREC_BF16X2) {
+      st = p->precision == FEM_PREC_FP8 ? launch_read<FEM_PREC_FP8>(p, t & 1, s)
+                                         : launch_read<FEM_PREC_BF16>(p, t & 1, s);
+    } else {
+      const int b = (t + 1) & 1;
+      const size_t total = (size_t)p->R * p->n_pad;
+      const int blocks = (int)std::min<size_t>((total + 255) / 256, (size_t)p->sm_count * 16);
+      k_dense_operand<<<blocks, 256, 0, s>>>(p->h[0], p->n, p->n_pad, p->R, FEM_GRAD_PAPER, FEM_PREC_BF16,
+                                             p->mt[b], nullptr);
+      count_launches(1);
+      st = launch_read<FEM_PREC_BF16>(p, b, s);
+    }
+    if (st != FEM_OK) return st;
+    nblk = p->n_pad / kTile;
+  }
+  k_dense_finish<<<1, 1024, 0, s>>>(p->part_i, nblk, p->R, p->dense_wtot, p->energy_i, p->energy_f, p->best);
   k_dense_states<<<(p->n + 255) / 256, 256, 0, s>>>(p->h[0], p->n, p->n_pad, p->R, p->best, p->states_dev, 0);
   count_launches(3);
   FEM_CUDA(cudaGetLastError());

@@ -13,6 +13,7 @@
 // bit r set <=> h_jr < 0 <=> state -1), ping-ponged between steps, so a
 // neighbour gather moves 4 bytes per edge instead of 128.
 #include "fem_internal.h"
+#include "reduce_common.cuh"
 #include "step_common.cuh"
 
 namespace fem {
@@ -294,53 +295,29 @@ __global__ void __launch_bounds__(256) k_maxcut_cut_partial(
 
 // Sum the partials of every replica in block order, set E_r = -cut_r, then the
 // argmin over replicas with the lowest index winning ties.  One block.
+// E_r = -cut_r for replica r = blockIdx.x (the argmin follows in k_argmin_replica).
 template <bool INTW>
-__global__ void __launch_bounds__(1024) k_maxcut_finish(const int64_t* __restrict__ part_i,
-                                                        const double* __restrict__ part_f,
-                                                        int32_t nblk, int32_t R,
-                                                        int64_t* __restrict__ e_i,
-                                                        double* __restrict__ e_f,
-                                                        int32_t* __restrict__ best) {
-  __shared__ double sval[1024];
-  __shared__ int sidx[1024];
-  double bv = 0.0;
-  int bidx = 0x7fffffff;
-  for (int r = threadIdx.x; r < R; r += blockDim.x) {
-    double ef;
-    if (INTW) {
-      int64_t t = 0;
-      for (int b = 0; b < nblk; ++b) t += part_i[(size_t)b * R + r];
+__global__ void __launch_bounds__(kRedThreads) k_maxcut_finish(const int64_t* __restrict__ part_i,
+                                                               const double* __restrict__ part_f,
+                                                               int32_t nblk, int32_t R,
+                                                               int64_t* __restrict__ e_i,
+                                                               double* __restrict__ e_f) {
+  __shared__ int64_t shi[kRedThreads];
+  __shared__ double shf[kRedThreads];
+  const int r = blockIdx.x;
+  if (INTW) {
+    const int64_t t = column_sum<int64_t>(part_i, nblk, R, r, shi);
+    if (threadIdx.x == 0) {
       e_i[r] = -t;
-      ef = (double)(-t);
-    } else {
-      double t = 0.0;
-      for (int b = 0; b < nblk; ++b) t += part_f[(size_t)b * R + r];
-      ef = -t;
+      e_f[r] = (double)(-t);
+    }
+  } else {
+    const double t = column_sum<double>(part_f, nblk, R, r, shf);
+    if (threadIdx.x == 0) {
       e_i[r] = 0;
-    }
-    e_f[r] = ef;
-    if (bidx == 0x7fffffff || ef < bv) {
-      bv = ef;
-      bidx = r;
+      e_f[r] = -t;
     }
   }
-  sval[threadIdx.x] = bv;
-  sidx[threadIdx.x] = bidx;
-  __syncthreads();
-  for (int off = blockDim.x / 2; off > 0; off >>= 1) {
-    if (threadIdx.x < off) {
-      const double ov = sval[threadIdx.x + off];
-      const int oi = sidx[threadIdx.x + off];
-      const int mi = sidx[threadIdx.x];
-      if (oi != 0x7fffffff && (mi == 0x7fffffff || ov < sval[threadIdx.x] ||
-                               (ov == sval[threadIdx.x] && oi < mi))) {
-        sval[threadIdx.x] = ov;
-        sidx[threadIdx.x] = oi;
-      }
-    }
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) best[0] = sidx[0];
 }
 
 // states[i] = +1 / -1 of replica r (from the sign words).
@@ -477,17 +454,18 @@ fem_status maxcut_readout(Problem* p, cudaStream_t s) {
     else
       k_maxcut_cut_partial<false, true><<<grid, 256, 0, s>>>(p->row_ptr, p->col, p->w, p->w64, words,
                                                              p->n, p->R, wpn, p->part_i, p->part_f);
-    k_maxcut_finish<true><<<1, 1024, 0, s>>>(p->part_i, p->part_f, p->part_blocks, p->R,
-                                             p->energy_i, p->energy_f, p->best);
+    k_maxcut_finish<true><<<p->R, kRedThreads, 0, s>>>(p->part_i, p->part_f, p->part_blocks, p->R,
+                                                        p->energy_i, p->energy_f);
   } else {
     k_maxcut_cut_partial<false, false><<<grid, 256, 0, s>>>(p->row_ptr, p->col, p->w, p->w64, words,
                                                             p->n, p->R, wpn, p->part_i, p->part_f);
-    k_maxcut_finish<false><<<1, 1024, 0, s>>>(p->part_i, p->part_f, p->part_blocks, p->R,
-                                              p->energy_i, p->energy_f, p->best);
+    k_maxcut_finish<false><<<p->R, kRedThreads, 0, s>>>(p->part_i, p->part_f, p->part_blocks, p->R,
+                                                         p->energy_i, p->energy_f);
   }
+  k_argmin_replica<<<1, 1024, 0, s>>>(p->energy_f, p->R, p->best);
   k_maxcut_states_one<<<(p->n + 255) / 256 < 1024 ? (p->n + 255) / 256 : 1024, 256, 0, s>>>(
       words, p->n, wpn, p->best, p->states_dev);
-  count_launches(3);
+  count_launches(4);
   FEM_CUDA(cudaGetLastError());
   return FEM_OK;
 }

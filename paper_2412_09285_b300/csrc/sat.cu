@@ -15,6 +15,7 @@
 // so no exponential is evaluated per gathered literal.  h is updated in place.
 #include <algorithm>
 
+#include "reduce_common.cuh"
 #include "sat_core.cuh"
 
 namespace fem {
@@ -71,41 +72,17 @@ __global__ void __launch_bounds__(256) k_sat_unsat_partial(const int32_t* __rest
   }
 }
 
-__global__ void __launch_bounds__(1024) k_sat_finish(const int64_t* __restrict__ part, int32_t nblk,
-                                                     int32_t R, int64_t* __restrict__ e_i,
-                                                     double* __restrict__ e_f,
-                                                     int32_t* __restrict__ best) {
-  __shared__ int64_t sval[1024];
-  __shared__ int sidx[1024];
-  int64_t bv = 0;
-  int bidx = 0x7fffffff;
-  for (int r = threadIdx.x; r < R; r += blockDim.x) {
-    int64_t t = 0;
-    for (int b = 0; b < nblk; ++b) t += part[(size_t)b * R + r];
+// Unsatisfied clauses of replica r = blockIdx.x (the argmin follows in k_argmin_replica).
+__global__ void __launch_bounds__(kRedThreads) k_sat_finish(const int64_t* __restrict__ part, int32_t nblk,
+                                                            int32_t R, int64_t* __restrict__ e_i,
+                                                            double* __restrict__ e_f) {
+  __shared__ int64_t sh[kRedThreads];
+  const int r = blockIdx.x;
+  const int64_t t = column_sum<int64_t>(part, nblk, R, r, sh);
+  if (threadIdx.x == 0) {
     e_i[r] = t;
     e_f[r] = (double)t;
-    if (bidx == 0x7fffffff || t < bv) {
-      bv = t;
-      bidx = r;
-    }
   }
-  sval[threadIdx.x] = bv;
-  sidx[threadIdx.x] = bidx;
-  __syncthreads();
-  for (int off = blockDim.x / 2; off > 0; off >>= 1) {
-    if (threadIdx.x < off) {
-      const int64_t ov = sval[threadIdx.x + off];
-      const int oi = sidx[threadIdx.x + off];
-      const int mi = sidx[threadIdx.x];
-      if (oi != 0x7fffffff &&
-          (mi == 0x7fffffff || ov < sval[threadIdx.x] || (ov == sval[threadIdx.x] && oi < mi))) {
-        sval[threadIdx.x] = ov;
-        sidx[threadIdx.x] = oi;
-      }
-    }
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) best[0] = sidx[0];
 }
 
 __global__ void k_sat_states(const float* __restrict__ h, int32_t n, int32_t R,
@@ -172,10 +149,11 @@ fem_status sat_readout(Problem* p, cudaStream_t st) {
                                           (long long)p->part_blocks);
   const dim3 grid(nb, (p->R + 15) / 16);
   k_sat_unsat_partial<<<grid, 256, 0, st>>>(p->cl_ptr, p->cl_lit, p->n_clauses, p->h[0], p->R, p->part_i);
-  k_sat_finish<<<1, 1024, 0, st>>>(p->part_i, nb, p->R, p->energy_i, p->energy_f, p->best);
+  k_sat_finish<<<p->R, kRedThreads, 0, st>>>(p->part_i, nb, p->R, p->energy_i, p->energy_f);
+  k_argmin_replica<<<1, 1024, 0, st>>>(p->energy_f, p->R, p->best);
   k_sat_states<<<(p->n + 255) / 256 < 1024 ? (p->n + 255) / 256 : 1024, 256, 0, st>>>(
       p->h[0], p->n, p->R, p->best, p->states_dev, 0);
-  count_launches(3);
+  count_launches(4);
   FEM_CUDA(cudaGetLastError());
   return FEM_OK;
 }

@@ -58,6 +58,14 @@ WORKLOADS = {
                                         "per step, CUDA-graph step loop, autotuned work items",
                     n_bmc=256, bmc_lo=1000, bmc_hi=64000, deg=10.0, q=4, n_sat=64, sat_lo=5000, sat_hi=50000,
                     ratio=4.2, R=16, n_steps=1000, graph_seed=5, h_seed=6, cpu_steps=2),
+    # learned warm start (time to target only): ER graphs, n log-uniform 20k-200k, mean
+    # degree 8, +-1 weights, R = 32, full budget 2000 steps; the network is trained here
+    # on FEM's converged fields of the training graphs (disjoint seeds from the held-out)
+    "warmstart": dict(kind="warmstart", name="learned warm start: MaxCut on ER graphs, n log-uniform 20k-200k, "
+                                             "mean degree 8, +-1 weights, R=32, 2000-step exponential beta "
+                                             "0.05->5, Adam lr 0.1, paper-mode gradient",
+                      n_lo=20000, n_hi=200000, deg=8.0, R=32, n_steps=2000, n_train=64, n_held=16, epochs=3,
+                      lr=3e-3, rms=0.1, train_seed=31, held_seed=32, h_seed=33),
     # the batched workload at 1/8 scale (same size distributions): the case profiled in detail
     "batched_small": dict(kind="batched", name="batched heterogeneous at 1/8 scale: 32 bMinCut (random geometric "
                                               "graphs, n log-uniform 1k-64k, mean degree 10, unit weights, q=4) + 8 "
@@ -511,6 +519,141 @@ def run_ours(args, wl):
         dist.destroy_process_group()
 
 
+def _timed(fn):
+    """Wall time of fn() in ms with the device drained before and after."""
+    import torch
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    out = fn()
+    torch.cuda.synchronize()
+    return (time.perf_counter() - t0) * 1e3, out
+
+
+def _ttt_summary(plain, fast, budgets):
+    """Per instance: target = plain's best at the full budget; time to target = the
+    fastest run (of the budgets tried) whose best is within 0.1% of it."""
+    out = []
+    for p, f in zip(plain, fast):
+        target = p[budgets[-1]][1]
+        thr = target - 0.001 * abs(target)
+        tp = min(t for b, (t, c) in p.items() if c >= thr)
+        tf = [t for b, (t, c) in f.items() if c >= thr]
+        out.append((tp, min(tf) if tf else None))
+    reached = [x for x in out if x[1] is not None]
+    return {"instances": len(out), "reached": len(reached),
+            "plain_ms_mean": float(np.mean([x[0] for x in out])),
+            "fast_ms_mean_over_reached": float(np.mean([x[1] for x in reached])) if reached else None,
+            "speedup_over_reached": float(np.mean([x[0] / x[1] for x in reached])) if reached else None}
+
+
+def run_ttt(args, wl):
+    """Time to target cut (the metric's second part): the reduced-precision (dense), batched
+    and warm-started forms against plain FP32 FEM on the same GPU, target = plain FEM's best
+    cut at its full budget, within 0.1%.  One JSON line."""
+    import torch
+    from paper_2412_09285_b300 import fem
+    from paper_2412_09285_b300 import instances as I
+    dev = torch.device("cuda")
+    N = wl["n_steps"]
+    line = {"metric": "time-to-target-cut", "unit": "ms", "higher_is_better": False, "n_gpus": 1,
+            "data": "synthetic", "config": {"workload": wl["name"], "target": "plain FP32 FEM best cut at the full "
+                                            "budget, within 0.1%"}}
+    if wl["kind"] == "dense":
+        inst = _instance(wl)
+        R = wl["R"]
+        h0 = torch.from_numpy(I.initial_fields(inst.n, R, seed=wl["h_seed"])).to(dev)
+        budgets = [N // 4, N // 2, N]
+
+        def run(prec, b):
+            P = fem.Problem("maxcut", dense=inst.dense)
+            P.anneal(h_init=h0, replicas=R, n_steps=b, precision=prec)   # compile / first-call effects
+            t, r = _timed(lambda: P.anneal(h_init=h0, replicas=R, n_steps=b, precision=prec).best())
+            P.close()
+            return t, -float(r["energy_f64"][r["best_replica"]])
+        plain = {b: run("fp32", b) for b in budgets}
+        res = {"fp32": plain}
+        for prec in ("bf16", "fp8"):
+            res[prec] = {b: run(prec, b) for b in budgets}
+        line["time_to_target"] = {prec: _ttt_summary([plain], [res[prec]], budgets) for prec in ("bf16", "fp8")}
+        line["best_cut"] = {prec: {str(b): c for b, (t, c) in v.items()} for prec, v in res.items()}
+        line["ms"] = {prec: {str(b): t for b, (t, c) in v.items()} for prec, v in res.items()}
+        line["value"] = line["time_to_target"]["fp8"]["fast_ms_mean_over_reached"]
+    elif wl["kind"] == "batched":
+        inst = _instance(wl)
+        h0 = [torch.from_numpy(x).to(dev) for x in inst.h0(wl)]
+        R = wl["R"]
+        probs = ([fem.Problem("bmincut", graph=g, q=wl["q"]) for g in inst.graphs]
+                 + [fem.Problem("sat", clauses=c) for c in inst.sats])
+        kw = dict(replicas=R, n_steps=N, lambda_max=1.0)
+
+        def one_by_one():
+            out = []
+            for p, h in zip(probs, h0):
+                p.anneal(h_init=h, **kw)
+                r = p.best()
+                out.append(float(r["energy_f64"][r["best_replica"]]))
+            return out
+        B = fem.Batch(probs)
+
+        def batched():
+            B.anneal(h_inits=h0, **kw)
+            out = []
+            for p in probs:
+                r = p.best()
+                out.append(float(r["energy_f64"][r["best_replica"]]))
+            return out
+        B.anneal(h_inits=h0, replicas=R, n_steps=N, t_end=20, lambda_max=1.0)  # first-call tuning
+        t_plain, e_plain = _timed(one_by_one)
+        t_batch, e_batch = _timed(batched)
+        line["time_to_target"] = {"plain_ms": t_plain, "batched_ms": t_batch, "speedup": t_plain / t_batch,
+                                  "same_best_energies": bool(e_plain == e_batch), "members": len(probs)}
+        line["value"] = t_batch
+    else:
+        from paper_2412_09285_b300 import warmstart as ws
+        R, rms = wl["R"], wl["rms"]
+        t_gen, (train, held) = _timed(lambda: (ws.make_graphs(wl["n_train"], wl["n_lo"], wl["n_hi"], wl["deg"],
+                                                              seed=wl["train_seed"]),
+                                               ws.make_graphs(wl["n_held"], wl["n_lo"], wl["n_hi"], wl["deg"],
+                                                              seed=wl["held_seed"])))
+        net = ws.Mpnn(seed=1)
+        t_train, losses = _timed(lambda: ws.train(net, train, wl["epochs"], R, N, lr=wl["lr"], seed=wl["h_seed"]))
+        budgets = [N // 8, N // 4, N // 2, N]
+        noise = ws.Mpnn({**I.mpnn_init(0), "C": np.zeros((64, 4)), "c": np.array([1.0, 0.0, 0.0, 0.0])})
+        plain, warm, ctrl = [], [], []
+        for k, g in enumerate(held):
+            z = torch.from_numpy(I.initial_fields(g.n, R, seed=wl["h_seed"] * 1000 + k) * np.float32(1000.0)).to(dev)
+            probs = [fem.Problem("maxcut", graph=g) for _ in range(2)]
+
+            def plain_run(b):
+                return _timed(lambda: -float(probs[0].anneal(h_init=z * 0.001, replicas=R, n_steps=b)
+                                             .best()["energy_f64"].min()))
+            y = torch.empty_like(z)
+
+            def warm_run(b, model):
+                def go():
+                    model.predict(probs[1], z, R, y, rms=rms)
+                    ws.warm_anneal(probs[1], y, b, N, N // 4)
+                    return -float(probs[1].best()["energy_f64"].min())
+                return _timed(go)
+            plain_run(budgets[0])  # first-call effects
+            plain.append({b: plain_run(b) for b in budgets})
+            warm.append({b: warm_run(b, net) for b in budgets})
+            ctrl.append({b: warm_run(b, noise) for b in budgets})
+            for p in probs:
+                p.close()
+        gap = lambda runs: {str(b): float(np.mean([(r[b][1] - p[N][1]) / abs(p[N][1]) for r, p in zip(runs, plain)]))
+                            for b in budgets}
+        line["time_to_target"] = {"warm": _ttt_summary(plain, warm, budgets),
+                                  "noise_control": _ttt_summary(plain, ctrl, budgets)}
+        line["relative_cut_gap_vs_plain_full"] = {"plain": gap(plain), "warm": gap(warm), "noise_control": gap(ctrl)}
+        line["ms_per_budget"] = {"plain": {str(b): float(np.mean([r[b][0] for r in plain])) for b in budgets},
+                                 "warm": {str(b): float(np.mean([r[b][0] for r in warm])) for b in budgets}}
+        line["train"] = {"graphs": len(train), "epochs": wl["epochs"], "loss_by_epoch": losses,
+                         "train_s": t_train / 1e3, "generate_s": t_gen / 1e3, "held_out": len(held)}
+        line["value"] = line["time_to_target"]["warm"]["fast_ms_mean_over_reached"]
+    print(json.dumps(line))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -522,8 +665,13 @@ def main():
     ap.add_argument("--dense-launch", default="auto", choices=["auto", "per_step", "persistent"],
                     help="dense workload: persistent (state in tensor memory) or one kernel per step")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--ttt", action="store_true",
+                    help="time to target cut of the dense, batched or warmstart workload against plain FP32 FEM")
     args = ap.parse_args()
     wl = WORKLOADS[args.workload]
+    if args.ttt or wl["kind"] == "warmstart":
+        run_ttt(args, wl)
+        return
     if args.steps is None:
         args.steps = wl["n_steps"]
     if args.warmup < 3 and args.impl == "ours":

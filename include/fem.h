@@ -226,8 +226,8 @@ void fem_batch_destroy(fem_batch_t b);
  *   P = D^-1 W;  s_i = [1, deg_i / mean deg, sum_j W_ij / deg_i, 1/sqrt(deg_i + 1)]
  *   x^0 = s;  x^l = tanh(x^(l-1) A_l + (P x^(l-1)) B_l + b_l),  l = 1..3, width 64
  *   theta = x^3 C + c (4 taps);  u_0 = z, u_k = P u_(k-1);  y_ir = sum_k theta_ik u_k,ir
- *   loss = mean_ir (tanh(y_ir / 2) - tanh(h_ir / 2))^2,  h = target fields (FEM's own, at
- *          the step the warm start replaces)
+ *   loss = mean_ir (tanh(y_ir / 2) - tanh(h_ir / 2))^2,  h = target fields (FEM's own
+ *          converged fields)
  * z is a replica's initial fields in units of 0.001 (the paper's 0.001*randn scale),
  * y the predicted fields; y is odd in z (MaxCut's spin-flip symmetry).  Parameters:
  * fem_mpnn_num_params() fp32 values in the order A1[4][64], B1[4][64], b1[64],
@@ -236,13 +236,17 @@ void fem_batch_destroy(fem_batch_t b);
  * gradient is with respect to those rounded weights; the optimizer (Adam,
  * beta 0.9/0.999, eps 1e-8) updates the fp32 master copy.
  *   graph: a sparse MaxCut problem (its CSR is used).  z, h_target, y: DEVICE
- *   pointers, [n][R] fp32.  grad: HOST, num_params floats (may be NULL). */
+ *   pointers, [n][R] fp32.  grad: HOST, num_params floats (may be NULL).
+ *   rms (fem_mpnn_predict): 0 returns y as is; rms > 0 rescales every replica's
+ *   column to root-mean-square rms, y_ir * rms / sqrt(mean_i y_ir^2) (the network
+ *   fixes the direction of the warm start, the caller its magnitude; an all-zero
+ *   column stays zero).  FEM_ERR_INVALID_ARG for rms < 0 or NaN. */
 typedef struct fem_mpnn* fem_mpnn_t;
 int32_t fem_mpnn_num_params(void);
 fem_status fem_mpnn_create(const float* params_host, fem_mpnn_t* out);
 fem_status fem_mpnn_get_params(fem_mpnn_t net, float* params_host);
-fem_status fem_mpnn_predict(fem_mpnn_t net, fem_problem_t graph, const float* z, int32_t replicas, float* y,
-                            void* stream);
+fem_status fem_mpnn_predict(fem_mpnn_t net, fem_problem_t graph, const float* z, int32_t replicas, float rms,
+                            float* y, void* stream);
 fem_status fem_mpnn_grad(fem_mpnn_t net, fem_problem_t graph, const float* z, const float* h_target,
                          int32_t replicas, float* grad_host, double* loss, void* stream);
 fem_status fem_mpnn_train_step(fem_mpnn_t net, fem_problem_t graph, const float* z, const float* h_target,

@@ -22,7 +22,7 @@ import numpy as np
 import scipy.sparse as sp
 
 __all__ = ["mpnn_propagation", "mpnn_features", "bf16_round", "mpnn_forward", "mpnn_loss",
-           "mpnn_backward", "PARAM_ORDER"]
+           "mpnn_backward", "mpnn_normalize", "PARAM_ORDER"]
 
 PARAM_ORDER = ["A1", "B1", "b1", "A2", "B2", "b2", "A3", "B3", "b3", "C", "c"]
 
@@ -99,3 +99,12 @@ def mpnn_backward(cache, y, m_target):
         g[f"b{l}"] = dpre.sum(axis=0)
         dx = dpre @ p[f"A{l}"].T + PT @ (dpre @ p[f"B{l}"].T)
     return g
+
+
+def mpnn_normalize(y, rms):
+    """Every replica's column rescaled to root-mean-square rms (the magnitude of the warm
+    start; the network gives its direction).  An all-zero column stays zero."""
+    y = np.asarray(y, np.float64)
+    cur = np.sqrt(np.mean(y * y, axis=0))
+    scale = np.where(cur > 0, rms / np.where(cur > 0, cur, 1.0), 0.0)
+    return y * scale

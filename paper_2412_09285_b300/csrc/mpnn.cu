@@ -18,6 +18,7 @@
 #include <vector>
 
 #include "fem_internal.h"
+#include "reduce_common.cuh"
 #include "step_common.cuh"
 
 namespace fem {
@@ -306,6 +307,34 @@ __global__ void k_to_bf16(const float* __restrict__ w, __nv_bfloat16* __restrict
     wb[e] = __float2bfloat16_rn(w[e]);
 }
 
+// Per-replica sums of squares of y ([n][R]) over row chunks: part[b][r] (fp64).
+constexpr int kRmsRows = 512;
+__global__ void k_col_sumsq_partial(const float* __restrict__ y, int n, int R, double* __restrict__ part) {
+  const int i0 = blockIdx.x * kRmsRows, i1 = min(n, i0 + kRmsRows);
+  for (int r = threadIdx.x; r < R; r += blockDim.x) {
+    double acc = 0.0;
+    for (int i = i0; i < i1; ++i) {
+      const double v = y[(size_t)i * R + r];
+      acc += v * v;
+    }
+    part[(size_t)blockIdx.x * R + r] = acc;
+  }
+}
+
+// scale[r] = rms / sqrt(mean_i y_ir^2) (0 for an all-zero column); one block per replica.
+__global__ void __launch_bounds__(kRedThreads) k_col_scale(const double* __restrict__ part, int nblk, int n, int R,
+                                                           float rms, float* __restrict__ scale) {
+  __shared__ double sh[kRedThreads];
+  const int r = blockIdx.x;
+  const double ss = column_sum<double>(part, nblk, R, r, sh);
+  if (threadIdx.x == 0) scale[r] = ss > 0.0 ? (float)(rms / sqrt(ss / n)) : 0.f;
+}
+
+__global__ void k_scale_cols(float* __restrict__ y, size_t total, int R, const float* __restrict__ scale) {
+  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x)
+    y[e] *= scale[e % R];
+}
+
 }  // namespace
 
 struct Mpnn {
@@ -501,13 +530,29 @@ static fem_status mpnn_check(fem_mpnn_t net, fem_problem_t g, const float* z, in
   return FEM_OK;
 }
 
-fem_status fem_mpnn_predict(fem_mpnn_t net, fem_problem_t g, const float* z, int32_t R, float* y, void* stream) {
+fem_status fem_mpnn_predict(fem_mpnn_t net, fem_problem_t g, const float* z, int32_t R, float rms, float* y,
+                            void* stream) {
   fem_status st = mpnn_check(net, g, z, R);
   if (st != FEM_OK) return st;
   if (!y) return fail(FEM_ERR_INVALID_ARG, "y must be non-NULL");
+  if (!(rms >= 0.f)) return fail(FEM_ERR_INVALID_ARG, "rms must be >= 0");
   cudaStream_t s = (cudaStream_t)stream;
   Pass ps;
   st = forward(net, g, z, R, nullptr, y, ps, s);
+  if (st == FEM_OK && rms > 0.f) {
+    const int n = g->n, nblk = (n + kRmsRows - 1) / kRmsRows;
+    double* part = nullptr;
+    float* scale = nullptr;
+    if ((st = pass_alloc(ps, (void**)&part, (size_t)nblk * R * sizeof(double), s)) == FEM_OK &&
+        (st = pass_alloc(ps, (void**)&scale, (size_t)R * sizeof(float), s)) == FEM_OK) {
+      k_col_sumsq_partial<<<nblk, 256, 0, s>>>(y, n, R, part);
+      k_col_scale<<<R, kRedThreads, 0, s>>>(part, nblk, n, R, rms, scale);
+      k_scale_cols<<<blocks_for((size_t)n * R, net->sm_count), 256, 0, s>>>(y, (size_t)n * R, R, scale);
+      count_launches(3);
+      const cudaError_t e = cudaGetLastError();
+      if (e != cudaSuccess) st = cuda_fail(e, "fem_mpnn_predict normalisation");
+    }
+  }
   pass_free(ps, s);
   return st;
 }

@@ -84,7 +84,7 @@ def _load():
         "fem_mpnn_num_params": (C.c_int32, []),
         "fem_mpnn_create": (S, [P, C.POINTER(P)]),
         "fem_mpnn_get_params": (S, [P, P]),
-        "fem_mpnn_predict": (S, [P, P, P, C.c_int32, P, P]),
+        "fem_mpnn_predict": (S, [P, P, P, C.c_int32, C.c_float, P, P]),
         "fem_mpnn_grad": (S, [P, P, P, P, C.c_int32, P, C.POINTER(C.c_double), P]),
         "fem_mpnn_train_step": (S, [P, P, P, P, C.c_int32, C.c_double, C.POINTER(C.c_double), P]),
         "fem_mpnn_destroy": (None, [P]),

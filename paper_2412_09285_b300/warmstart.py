@@ -1,14 +1,18 @@
 """Learned warm start for sparse MaxCut FEM: the network binding, training on FEM's
-own mid-anneal fields, and the warm-started anneal.
+own converged fields, and the warm-started anneal.
 
 The network (C ABI ``fem_mpnn_*``, kernels in csrc/mpnn.cu) predicts local fields
 y = sum_k theta_k(i) (P^k z)_i from the graph and a replica's random initial fields
-z (units of 0.001).  It is trained to reproduce the fields plain FEM reaches at the
-middle of its schedule (step t_mid of N); a warm-started anneal then starts from the
-prediction and runs only the second half of the schedule (N - t_mid steps, beta from
-beta(t_mid) to beta_max).  Plain random-initialised FEM is both the fallback and the
-judge: the comparison is the best cut of the warm-started half-budget anneal against
-plain FEM with the full and the half budget.
+z (units of 0.001).  It is trained on the fields plain FEM converges to (loss on
+tanh(y/2) against tanh(h/2)); since those depend only weakly on z the least-squares
+optimum is small in magnitude, so at inference the prediction is rescaled per replica
+to a chosen root-mean-square (the network fixes the direction, the caller the
+magnitude).  A warm-started anneal then runs a shortened schedule that starts at
+beta(t_start) of the full schedule.  Plain random-initialised FEM is both the fallback
+and the judge: the comparison is the best cut of the warm-started anneal against plain
+FEM at the same and at the full budget, and against the same shortened schedule
+started from rescaled noise instead of the prediction (which isolates what the network
+adds beyond the shorter schedule).
 
 Every computation runs in the library's kernels; torch only holds device buffers.
 """
@@ -22,7 +26,7 @@ import numpy as np
 from . import fem as F
 from . import instances as I
 
-__all__ = ["Mpnn", "beta_at", "fem_mid_fields", "warm_anneal", "make_graphs"]
+__all__ = ["Mpnn", "beta_at", "fem_fields_at", "warm_anneal", "train", "make_graphs"]
 
 
 class Mpnn:
@@ -40,8 +44,10 @@ class Mpnn:
         F._check(F._lib.fem_mpnn_get_params(self.handle, flat.ctypes.data), "fem_mpnn_get_params")
         return I.mpnn_unflatten(flat)
 
-    def predict(self, problem, z, R, y, stream=None):
-        F._check(F._lib.fem_mpnn_predict(self.handle, problem.handle, F._ptr(z), int(R), F._ptr(y),
+    def predict(self, problem, z, R, y, rms=0.0, stream=None):
+        """y = the network's fields for initial fields z; rms > 0 rescales every replica's
+        column to that root-mean-square."""
+        F._check(F._lib.fem_mpnn_predict(self.handle, problem.handle, F._ptr(z), int(R), float(rms), F._ptr(y),
                                          F._stream(stream)), "fem_mpnn_predict")
 
     def grad(self, problem, z, h_target, R, stream=None):
@@ -76,18 +82,39 @@ def beta_at(t, n_steps, beta_min=0.05, beta_max=5.0):
     return math.exp((math.log(beta_max) - math.log(beta_min)) / (n_steps - 1) * t + math.log(beta_min))
 
 
-def fem_mid_fields(problem, h0, n_steps, t_mid, out, **kw):
-    """Plain FEM from h0 (device [n][R]) for t_mid of n_steps steps; its fields into out (device)."""
+def fem_fields_at(problem, h0, n_steps, t_end, out, **kw):
+    """Plain FEM from h0 (device [n][R]) for t_end of n_steps steps; its fields into out
+    (device).  t_end = n_steps gives the converged fields the network is trained on."""
     R = h0.shape[1]
-    problem.anneal(h_init=h0, replicas=R, n_steps=n_steps, t_end=t_mid, **kw)
+    problem.anneal(h_init=h0, replicas=R, n_steps=n_steps, t_end=t_end, **kw)
     F.fem_read_fields(problem.handle, out, problem.stream)
 
 
-def warm_anneal(problem, y, n_steps, t_mid, beta_min=0.05, beta_max=5.0, **kw):
-    """The second half of the schedule from predicted fields y (device [n][R])."""
+def warm_anneal(problem, y, budget, n_full, t_start, beta_min=0.05, beta_max=5.0, **kw):
+    """A shortened anneal of `budget` steps from fields y (device [n][R]); beta runs from
+    beta(t_start) of the full n_full-step schedule to beta_max."""
     R = y.shape[1]
-    problem.anneal(h_init=y, replicas=R, n_steps=n_steps - t_mid, beta_min=beta_at(t_mid, n_steps, beta_min, beta_max),
+    problem.anneal(h_init=y, replicas=R, n_steps=budget, beta_min=beta_at(t_start, n_full, beta_min, beta_max),
                    beta_max=beta_max, **kw)
+
+
+def train(net, graphs, epochs, R, n_steps, lr, seed=0, device="cuda"):
+    """One Adam step per graph and epoch on FEM's converged fields from fresh random
+    initial fields; returns the mean loss of every epoch."""
+    import torch
+    from . import instances as I
+    out = []
+    for epoch in range(epochs):
+        losses = []
+        for k, g in enumerate(graphs):
+            prob = F.Problem("maxcut", graph=g)
+            z = torch.from_numpy(I.initial_fields(g.n, R, seed=seed + 100003 * epoch + k) * np.float32(1000.0)).to(device)
+            target = torch.empty_like(z)
+            fem_fields_at(prob, z * 0.001, n_steps, n_steps, target)
+            losses.append(net.train_step(prob, z, target, R, lr=lr))
+            prob.close()
+        out.append(float(np.mean(losses)))
+    return out
 
 
 def _gen(args):

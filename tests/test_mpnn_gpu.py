@@ -1,5 +1,6 @@
-"""The warm-start network on the GPU against its FP64 oracle (forward, gradients),
-and what the trained network gains over plain random-initialised FEM."""
+"""The warm-start network on the GPU against its FP64 oracle (forward, gradients,
+rescaled prediction), and what the trained network gains over plain random-initialised
+FEM and over the shortened schedule without it."""
 import numpy as np
 import pytest
 
@@ -71,56 +72,59 @@ def test_gradients_match_oracle(env):
         assert err <= 1e-3 * scale + 1e-9, (name, err, scale)
 
 
+def test_predict_rms_matches_oracle(env):
+    fem, ws, torch = env
+    g, prob, z, ht, P, feats, zd, _ = _case(fem, torch)
+    params = _params(13)
+    net = ws.Mpnn(params)
+    y = torch.empty_like(zd)
+    net.predict(prob, zd, z.shape[1], y, rms=0.1)
+    torch.cuda.synchronize()
+    y_ref = O.mpnn_normalize(O.mpnn_forward(params, P, feats, z.astype(np.float64))[0], 0.1)
+    err = np.abs(y.cpu().numpy() - y_ref).max() / np.abs(y_ref).max()
+    assert err <= 1e-4, err
+    with pytest.raises(fem.FemError):
+        net.predict(prob, zd, z.shape[1], y, rms=-1.0)
+
+
 def test_training_and_warm_start_gain(env):
-    """Train on FEM's own mid-anneal fields of small ER graphs, then compare on
-    held-out graphs: warm start + second half of the schedule vs plain FEM with the
-    half and the full budget (best cut over 32 replicas).  The gains are printed, not
-    asserted: the test requires the training loss to fall and the held-out predictions
-    to agree in sign with FEM's mid-anneal fields more often than not."""
+    """Train on FEM's converged fields of small ER graphs (+-1 weights, mean degree 8),
+    then on held-out graphs compare best cuts (32 replicas) of
+      * the warm start: the prediction rescaled to rms 0.1, then a quarter-length
+        schedule from beta(N/4) of the full one,
+      * the same schedule from random fields of the same rms (the control: what the
+        shortened schedule gives without the network),
+      * plain FEM with the same budget and with the full budget N.
+    The numbers are printed; the test requires the training loss to fall and the warm
+    start to beat the control on average over the held-out graphs."""
     fem, ws, torch = env
     dev = torch.device("cuda")
-    R, N, t_mid = 32, 400, 200
-    train = ws.make_graphs(24, 1500, 4000, 8.0, seed=7)
+    R, N = 32, 400
+    train = ws.make_graphs(32, 1500, 4000, 8.0, seed=7)
     held = ws.make_graphs(8, 1500, 4000, 8.0, seed=8)
     net = ws.Mpnn(seed=1)
-    first, last = [], []
-    for epoch in range(6):
-        for k, g in enumerate(train):
-            prob = fem.Problem("maxcut", graph=g)
-            z = I.initial_fields(g.n, R, seed=10000 * epoch + k) * np.float32(1000.0)
-            zd = torch.from_numpy(z).to(dev)
-            h0 = zd * 0.001
-            ht = torch.empty_like(zd)
-            ws.fem_mid_fields(prob, h0, N, t_mid, ht)
-            loss = net.train_step(prob, zd, ht, R, lr=3e-3)
-            (first if epoch == 0 else last if epoch == 5 else []).append(loss)
-    assert np.mean(last) < 0.9 * np.mean(first), (np.mean(first), np.mean(last))
-    gains = {}
-    agree, rel_loss = [], []
+    losses = ws.train(net, train, 8, R, N, lr=3e-3, seed=11)
+    assert losses[-1] < losses[0], losses
     cut = lambda r: -int(r["energy_i64"].min())
+    res = {}
     for k, g in enumerate(held):
-        z = I.initial_fields(g.n, R, seed=777 + k) * np.float32(1000.0)
-        zd = torch.from_numpy(z).to(dev)
-        h0 = zd * 0.001
-        pf = fem.Problem("maxcut", graph=g)
-        ht = torch.empty_like(zd)
-        ws.fem_mid_fields(pf, h0, N, t_mid, ht)
-        pf.anneal(replicas=R, n_steps=N, t_begin=t_mid)
-        full = pf.best()
-        half = fem.Problem("maxcut", graph=g).anneal(h_init=h0, replicas=R, n_steps=N - t_mid).best()
-        y = torch.empty_like(zd)
-        net.predict(pf, zd, R, y)
-        yy, tt = y.cpu().numpy(), ht.cpu().numpy()
-        agree.append(np.mean(np.sign(yy) == np.sign(tt)))
-        rel_loss.append(np.mean((np.tanh(yy / 2) - np.tanh(tt / 2)) ** 2) / np.mean(np.tanh(tt / 2) ** 2))
-        for start in (t_mid, t_mid // 2, 0):     # warm anneal of N - t_mid steps from beta(start)
-            prob = fem.Problem("maxcut", graph=g)
-            prob.anneal(h_init=y, replicas=R, n_steps=N - t_mid, beta_min=ws.beta_at(start, N))
-            gains.setdefault(start, []).append((cut(prob.best()) - cut(half), cut(prob.best()) - cut(full)))
-    print(f"\nheld-out: sign agreement of predicted vs FEM mid fields {np.mean(agree):.3f}, "
-          f"loss / loss of the zero prediction {np.mean(rel_loss):.3f}")
-    for start, v in gains.items():
-        v = np.array(v)
-        print(f"warm start + {N - t_mid} steps from beta(t={start}): best cut vs plain half budget "
-              f"{v[:, 0].mean():+.1f}, vs plain full budget {v[:, 1].mean():+.1f}")
-    assert np.mean(agree) > 0.5
+        z = torch.from_numpy(I.initial_fields(g.n, R, seed=777 + k) * np.float32(1000.0)).to(dev)
+        pf = fem.Problem("maxcut", graph=g).anneal(h_init=z * 0.001, replicas=R, n_steps=N)
+        full = cut(pf.best())
+        y = torch.empty_like(z)
+        net.predict(pf, z, R, y, rms=0.1)
+        zn = torch.empty_like(z)
+        ws.Mpnn(I.mpnn_init(0) | {"C": np.zeros((64, 4)), "c": np.array([1.0, 0.0, 0.0, 0.0])}).predict(
+            pf, z, R, zn, rms=0.1)  # taps (1, 0, 0, 0): the noise itself, rescaled by the same kernels
+        b = N // 4
+        for name, h in (("warm", y), ("control", zn)):
+            p = fem.Problem("maxcut", graph=g)
+            ws.warm_anneal(p, h, b, N, N // 4)
+            res.setdefault(name, []).append(cut(p.best()) - full)
+        plain = fem.Problem("maxcut", graph=g).anneal(h_init=z * 0.001, replicas=R, n_steps=b)
+        res.setdefault("plain", []).append(cut(plain.best()) - full)
+    print(f"\ntraining loss by epoch: {[round(x, 4) for x in losses]}")
+    for name, v in res.items():
+        print(f"{name:8s} ({N // 4} steps): best cut minus plain FEM's at {N} steps, mean {np.mean(v):+.1f}, "
+              f"per graph {v}")
+    assert np.mean(res["warm"]) > np.mean(res["control"])

@@ -66,3 +66,16 @@ def test_bf16_rounding():
     assert O.bf16_round(np.array([1.0 + 3 * 2 ** -8]))[0] == 1.0 + 2 ** -6
     assert O.bf16_round(np.array([-3.14159265]))[0] == -3.140625
     assert np.all(np.abs(r - x) <= np.abs(x) * 2 ** -8 + 1e-300)
+
+
+def test_normalize_sets_the_column_rms_and_keeps_directions():
+    rng = np.random.Generator(np.random.PCG64(4))
+    y = rng.standard_normal((500, 6)) * np.array([1e-4, 0.3, 1.0, 7.0, 1e3, 1.0])
+    y[:, 5] = 0.0
+    out = O.mpnn_normalize(y, 0.1)
+    rms = np.sqrt((out ** 2).mean(axis=0))
+    assert np.allclose(rms[:5], 0.1, rtol=1e-12) and rms[5] == 0.0
+    # a positive multiple of the input column: the cosine with it is 1
+    for r in range(5):
+        c = out[:, r] @ y[:, r] / (np.linalg.norm(out[:, r]) * np.linalg.norm(y[:, r]))
+        assert abs(c - 1.0) < 1e-12

@@ -18,6 +18,8 @@ namespace fem {
 
 static thread_local std::string g_last_error;
 static std::atomic<int64_t> g_launches{0};
+constexpr long long kGraphMaxElems = 1ll << 21;  // node x replica (x q) elements of a "small" problem
+constexpr int64_t kGraphMinSteps = 16;
 
 void count_launches(int64_t k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
 
@@ -314,9 +316,15 @@ static fem_status upload_sat(Problem* p, const HostSat& g, cudaStream_t s) {
   return FEM_OK;
 }
 
+static void drop_step_graphs(Problem* p) {
+  for (auto& g : p->step_graphs) cudaGraphExecDestroy(g.exec);
+  p->step_graphs.clear();
+}
+
 static fem_status ensure_state(Problem* p, int32_t R, cudaStream_t s) {
   const size_t per = (size_t)p->n * R * (p->kind == FEM_BMINCUT ? p->q : 1);
   if (p->R == R && p->h[0]) return FEM_OK;
+  drop_step_graphs(p);  // the graphs name the buffers being replaced
   fem_status st;
   for (int b = 0; b < 2; ++b)
     if ((st = dev_alloc_t(p, &p->h[b], per)) != FEM_OK) return st;
@@ -387,6 +395,8 @@ void fem_destroy(fem_problem_t p) {
   int cur = 0;
   cudaGetDevice(&cur);
   if (cur != p->device) cudaSetDevice(p->device);
+  drop_step_graphs(p);
+  if (p->capture_stream) cudaStreamDestroy(p->capture_stream);
   for (void* a : p->allocs) cudaFree(a);
   if (cur != p->device) cudaSetDevice(cur);
   delete p;
@@ -542,13 +552,63 @@ fem_status fem_anneal(fem_problem_t p, const fem_anneal_params* a, void* stream)
   }
   if (a->t_end == a->t_begin) return FEM_OK;
   const std::vector<StepScalars> sc = make_step_scalars(*a, p->kind != FEM_BMINCUT);
+  auto run = [&](cudaStream_t st_) -> fem_status {
+    if (p->dense) return dense_steps(p, sc, a->t_begin, st_);
+    if (p->kind == FEM_MAXCUT) return maxcut_sparse_steps(p, *a, sc, st_);
+    if (p->kind == FEM_BMINCUT) return bmincut_sparse_steps(p, sc, a->t_begin, st_);
+    if (p->kind == FEM_MAXKSAT) return sat_steps(p, sc, a->t_begin, st_);
+    return fail(FEM_ERR_UNSUPPORTED, "problem kind not built in this library version");
+  };
+  // Small sparse problems step in a few microseconds, less than it takes the host to
+  // submit a launch: windows of >= kGraphMinSteps steps then run as one CUDA graph,
+  // captured once (on a private stream) and replayed for the same first step, buffer
+  // parity, replica count, optimizer, mode and scalars.  The first window of a problem
+  // always runs directly, so one-time setup calls never happen inside a capture.
+  const long long elems = (long long)p->n * p->R * (p->kind == FEM_BMINCUT ? p->q : 1);
+  const bool graph = !p->dense && p->stepped_uncaptured && elems <= kGraphMaxElems &&
+                     (int64_t)sc.size() >= kGraphMinSteps;
   fem_status st = FEM_OK;
-  if (p->dense) st = dense_steps(p, sc, a->t_begin, s);
-  else if (p->kind == FEM_MAXCUT) st = maxcut_sparse_steps(p, *a, sc, s);
-  else if (p->kind == FEM_BMINCUT) st = bmincut_sparse_steps(p, sc, a->t_begin, s);
-  else if (p->kind == FEM_MAXKSAT) st = sat_steps(p, sc, a->t_begin, s);
-  else st = fail(FEM_ERR_UNSUPPORTED, "problem kind not built in this library version");
-  if (st != FEM_OK) return st;
+  if (!graph) {
+    st = run(s);
+    if (st != FEM_OK) return st;
+    p->stepped_uncaptured = true;
+  } else {
+    Problem::StepGraph* hit = nullptr;
+    for (auto& g : p->step_graphs)
+      if (g.t_begin == a->t_begin && g.cur_before == p->cur && g.R == p->R && g.opt == p->optimizer &&
+          g.mode == p->grad_mode && g.sc.size() == sc.size() &&
+          std::memcmp(g.sc.data(), sc.data(), sc.size() * sizeof(StepScalars)) == 0)
+        hit = &g;
+    if (!hit) {
+      if (p->step_graphs.size() >= 4) {
+        cudaGraphExecDestroy(p->step_graphs.front().exec);
+        p->step_graphs.erase(p->step_graphs.begin());
+      }
+      if (!p->capture_stream) FEM_CUDA(cudaStreamCreateWithFlags(&p->capture_stream, cudaStreamNonBlocking));
+      Problem::StepGraph g{a->t_begin, p->cur, 0, p->R, p->optimizer, p->grad_mode, sc, 0, nullptr};
+      const int64_t l0 = fem_kernel_launches();
+      FEM_CUDA(cudaStreamBeginCapture(p->capture_stream, cudaStreamCaptureModeThreadLocal));
+      st = run(p->capture_stream);
+      cudaGraph_t cg = nullptr;
+      const cudaError_t ec = cudaStreamEndCapture(p->capture_stream, &cg);
+      g.launches = fem_kernel_launches() - l0;
+      count_launches(-g.launches);  // captured, not run
+      if (st != FEM_OK) {
+        if (cg) cudaGraphDestroy(cg);
+        return st;
+      }
+      if (ec != cudaSuccess) return cuda_fail(ec, "step graph capture");
+      const cudaError_t ei = cudaGraphInstantiate(&g.exec, cg, 0);
+      cudaGraphDestroy(cg);
+      if (ei != cudaSuccess) return cuda_fail(ei, "step graph instantiate");
+      g.cur_after = p->cur;
+      p->step_graphs.push_back(std::move(g));
+      hit = &p->step_graphs.back();
+    }
+    FEM_CUDA(cudaGraphLaunch(hit->exec, s));
+    count_launches(hit->launches);
+    p->cur = hit->cur_after;
+  }
   p->steps_done = a->t_end;
   return FEM_OK;
 }

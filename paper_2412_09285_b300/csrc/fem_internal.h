@@ -81,6 +81,16 @@ struct Problem {
   bool initialised = false;
   int32_t grad_mode = 1, optimizer = 0, precision = 0;
   int32_t cur = 0;             // which h / words buffer is current
+  // CUDA graphs of short-step windows (small sparse problems), see fem_anneal
+  struct StepGraph {
+    int32_t t_begin, cur_before, cur_after, R, opt, mode;
+    std::vector<StepScalars> sc;
+    int64_t launches;
+    cudaGraphExec_t exec;
+  };
+  std::vector<StepGraph> step_graphs;
+  cudaStream_t capture_stream = nullptr;
+  bool stepped_uncaptured = false;  // one window ran directly (one-time setup is done)
   float* h[2] = {nullptr, nullptr};
   float* m = nullptr;
   float* v = nullptr;

@@ -120,7 +120,7 @@ __global__ void __launch_bounds__(256) k_maxcut_step(MaxcutArgs a, StepScalars s
 // weights), so one shuffle and one bit test per edge give the neighbour term:
 //   sum_j W_ij sgn(m_j) = deg_i - 2 * #{j : W_ij sgn(m_j) = -1}.
 template <int OPT, bool UNIT, int NPW>
-__global__ void __launch_bounds__(256) k_maxcut_step_paper(MaxcutArgs a, StepScalars s) {
+__global__ void __launch_bounds__(256, 5) k_maxcut_step_paper(MaxcutArgs a, StepScalars s) {
   const int lane = threadIdx.x & 31;
   const int ngroups = (a.n + NPW - 1) / NPW;
   const long long total = (long long)ngroups * a.wpn;
@@ -171,36 +171,50 @@ __global__ void __launch_bounds__(256) k_maxcut_step_paper(MaxcutArgs a, StepSca
       }
     };
     load_chunk(cb);
-    // Unit weights, whole group in one chunk of <= 32 entries (the common case): a
-    // 32 x 32 bit transpose across the warp turns "lane e holds the word of entry e"
-    // into "lane r holds, for every entry e, bit r of its word"; a node's count is
-    // then one popcount of that word under the node's entry mask.
-    const bool one_chunk = UNIT && (bN - rb[0] <= 32);
-    uint32_t tr = 0;
-    if (one_chunk) tr = warp_transpose32(adj, lane);
+    // Unit weights: the group's CSR entries in chunks of 32 (one chunk in the common
+    // case).  A 32 x 32 bit transpose across the warp turns "lane e holds the word of
+    // entry e" into "lane r holds, for every entry e, bit r of its word"; a node's count
+    // in a chunk is then one popcount under the node's entry mask.  The next chunk's
+    // column and word loads are issued before the current chunk is counted.
+    int nneg_u[NPW];
+#pragma unroll
+    for (int k = 0; k < NPW; ++k) nneg_u[k] = 0;
+    if (UNIT && bN - rb[0] <= 32) {
+      const uint32_t tr = warp_transpose32(adj, lane);
+#pragma unroll
+      for (int k = 0; k < NPW; ++k) {
+        const int len = rb[k + 1] - rb[k];
+        nneg_u[k] = __popc(tr & (len == 0 ? 0u : (len >= 32 ? 0xffffffffu : ((1u << len) - 1u)) << (rb[k] - rb[0])));
+      }
+    } else if (UNIT) {
+      for (int c0 = rb[0]; c0 < bN; c0 += 32) {
+        const uint32_t cur = adj;
+        if (c0 + 32 < bN) load_chunk(c0 + 32);
+        const uint32_t tr = warp_transpose32(cur, lane);
+#pragma unroll
+        for (int k = 0; k < NPW; ++k) {
+          const int lo = max(rb[k], c0) - c0, hi = min(rb[k + 1], c0 + 32) - c0;
+          if (hi > lo) {
+            const int len = hi - lo;
+            nneg_u[k] += __popc(tr & ((len >= 32 ? 0xffffffffu : ((1u << len) - 1u)) << lo));
+          }
+        }
+      }
+    }
     uint32_t ball[NPW];
 #pragma unroll
     for (int k = 0; k < NPW; ++k) {
-      int nneg = 0;
+      int nneg = nneg_u[k];
       float facc = 0.f;
-      if (one_chunk) {
-        const int len = rb[k + 1] - rb[k];
-        const uint32_t mask =
-            len == 0 ? 0u : (len >= 32 ? 0xffffffffu : ((1u << len) - 1u)) << (rb[k] - rb[0]);
-        nneg = __popc(tr & mask);
-      } else {
+      if (!UNIT) {
         for (int e = rb[k]; e < rb[k + 1]; ++e) {
           if (e >= cb + 32) {
             cb += 32;
             load_chunk(cb);
           }
           const uint32_t bit = (__shfl_sync(kFullMask, adj, e - cb) >> lane) & 1u;
-          if (UNIT) {
-            nneg += (int)bit;
-          } else {
-            const float w = __shfl_sync(kFullMask, wv, e - cb);
-            facc += bit ? -w : w;
-          }
+          const float w = __shfl_sync(kFullMask, wv, e - cb);
+          facc += bit ? -w : w;
         }
       }
       const int deg = rb[k + 1] - rb[k];
@@ -358,12 +372,21 @@ int resident_grid(K kernel, int sm_count, long long warps_needed) {
   return (int)(blocks < 1 ? 1 : blocks);
 }
 
+// Graphs with fewer groups of kNodesPerWarp nodes than this many warps run one node
+// per warp instead (more warps in flight when a step is latency-bound).
+constexpr long long kSmallGraphWarps = 4096;
+
 template <int MODE, int OPT, bool UNIT>
 void launch_step(const MaxcutArgs& a, const StepScalars& s, int sm_count, long long warps,
                  cudaStream_t st) {
   if (MODE == FEM_GRAD_PAPER) {
-    auto k = k_maxcut_step_paper<OPT, UNIT, kNodesPerWarp>;
-    k<<<resident_grid(k, sm_count, warps), 256, 0, st>>>(a, s);
+    if (warps < kSmallGraphWarps) {
+      auto k = k_maxcut_step_paper<OPT, UNIT, 1>;
+      k<<<resident_grid(k, sm_count, (long long)a.n * a.wpn), 256, 0, st>>>(a, s);
+    } else {
+      auto k = k_maxcut_step_paper<OPT, UNIT, kNodesPerWarp>;
+      k<<<resident_grid(k, sm_count, warps), 256, 0, st>>>(a, s);
+    }
   } else {
     auto k = k_maxcut_step<FEM_GRAD_EXACT, OPT, UNIT>;
     k<<<resident_grid(k, sm_count, warps), 256, 0, st>>>(a, s);

@@ -205,7 +205,8 @@ def _roofline(wl, inst, step_ms, precision, persistent=False):
         ach = alg / (step_ms / 1e3) / 1e9
         return {"bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                 "frac": ach / peaks["hbm_gbs"],
-                "traffic": _traffic_from_profile("batch_step_bmc256_sat64_R16.md", "batched"),
+                "traffic": (_traffic_from_profile("batch_step_bmc256_sat64_R16.md", "batched")
+                            if wl is WORKLOADS["batched"] else None),
                 "kernel": "k_batch_step<4, paper>", "algorithmic_bytes_per_launch": alg, "launch_ms": step_ms,
                 "peak_source": f"{src} hbm_gbs (copy), of {src}", "frac_of_8TBs": ach / 8000.0}
     if wl["kind"] == "sparse":
@@ -216,7 +217,8 @@ def _roofline(wl, inst, step_ms, precision, persistent=False):
         ach = alg / (step_ms / 1e3) / 1e9
         return {"bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                 "frac": ach / peaks["hbm_gbs"],
-                "traffic": _traffic_from_profile("maxcut_step_sparse_n1M_R32.md", "sparse"),
+                "traffic": (_traffic_from_profile("maxcut_step_sparse_n1M_R32.md", "sparse")
+                            if wl is WORKLOADS["sparse"] else None),
                 "kernel": "k_maxcut_step_paper<adam, unit, 4>", "algorithmic_bytes_per_launch": alg,
                 "launch_ms": step_ms, "peak_source": f"{src} hbm_gbs (copy), of {src}",
                 "frac_of_8TBs": ach / 8000.0}

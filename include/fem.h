@@ -293,6 +293,19 @@ fem_status fem_sync(fem_problem_t p, void* stream);
  * FEM_ERR_INVALID_ARG for other values or a problem without dense couplings. */
 fem_status fem_set_dense_launch(fem_problem_t p, int32_t mode);
 
+/* Failure detection (no counterpart in the paper).
+ *   fem_set_step_barrier_timeout: the limit, in ns, on the persistent dense kernel's
+ *     per-step barrier between CTAs (default 2 s).  A CTA that waits longer records
+ *     FEM_ERR_TIMEOUT in the problem's sticky error word, lets its own copies and MMAs
+ *     land, frees its tensor memory and returns; the others give up in turn.  The error
+ *     surfaces on the next fem_read_* / fem_sync call; an fem_anneal with t_begin == 0
+ *     clears it.  0 gives up at the first check (tests use it to exercise the path).
+ *   fem_inject_allocation_failure: after `after` >= 0 further successful device
+ *     allocations of problems, the next one fails with FEM_ERR_OOM (then the injection
+ *     switches itself off); -1 disables it.  Process-wide, for tests. */
+fem_status fem_set_step_barrier_timeout(fem_problem_t p, int64_t ns);
+void fem_inject_allocation_failure(int64_t after);
+
 /* Release every resource owned by p (NULL is ignored). */
 void fem_destroy(fem_problem_t p);
 

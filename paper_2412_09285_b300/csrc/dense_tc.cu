@@ -420,15 +420,17 @@ struct DenseAnnealArgs {
   const StepScalars* sc;     // [n_steps], the scalars of steps t_begin ..
   int32_t t_begin, n_steps;
   int32_t* bar;              // one arrival counter per replica block (stride 32 ints), zero at launch
+  unsigned long long bar_wait_ns;  // limit on the step barrier (the copy and MMA waits keep kWaitNs)
 };
 
-__device__ __forceinline__ bool wait_counter(const int32_t* ctr, int32_t target, int32_t* err) {
+__device__ __forceinline__ bool wait_counter(const int32_t* ctr, int32_t target, int32_t* err,
+                                             unsigned long long limit_ns) {
   const unsigned long long t0 = global_ns();
   while (true) {
     int32_t v;
     asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(ctr) : "memory");
     if (v >= target) return true;
-    if (global_ns() - t0 > kWaitNs) {
+    if (global_ns() - t0 >= limit_ns) {
       atomicOr(err, ERR_TIMEOUT);
       return false;
     }
@@ -611,7 +613,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_dense_anneal_tc(const __grid_co
       int32_t* ctr = x.bar + blockIdx.y * 32;
       asm volatile("fence.proxy.async.global;" ::: "memory");
       asm volatile("red.release.gpu.global.add.s32 [%0], 1;" ::"l"(ctr) : "memory");  // cumulative over bar.sync
-      if (!wait_counter(ctr, (k + 1) * (int32_t)gridDim.x, a.err)) *abort_v = 1;
+      if (!wait_counter(ctr, (k + 1) * (int32_t)gridDim.x, a.err, x.bar_wait_ns)) *abort_v = 1;
       asm volatile("fence.proxy.async.global;" ::: "memory");
     }
     if (threadIdx.x == 0 && k + 1 < x.n_steps) s_sc = x.sc[k + 1];
@@ -930,6 +932,7 @@ fem_status launch_anneal_tc(Problem* p, const DenseArgs& a, int t_begin, int n_s
   x.t_begin = t_begin;
   x.n_steps = n_steps;
   x.bar = p->dense_bar;
+  x.bar_wait_ns = (unsigned long long)p->barrier_wait_ns;
   const int groups = p->R / kTile;
   FEM_CUDA(cudaMemsetAsync(p->dense_bar, 0, (size_t)groups * 32 * sizeof(int32_t), st));
   const bool x2 = PREC == FEM_PREC_BF16X2;

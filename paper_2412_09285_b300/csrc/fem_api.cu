@@ -39,9 +39,17 @@ fem_status cuda_fail(cudaError_t e, const char* what) {
   return fail(FEM_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
 }
 
+// Failure injection for tests: >= 0 makes the allocation after that many successful
+// ones fail as if the device were out of memory (then it switches itself off).
+static std::atomic<int64_t> g_fail_alloc_after{-1};
+
 fem_status dev_alloc(Problem* p, void** ptr, size_t bytes) {
   *ptr = nullptr;
   if (bytes == 0) bytes = 16;
+  int64_t left = g_fail_alloc_after.load();
+  while (left >= 0 && !g_fail_alloc_after.compare_exchange_weak(left, left - 1)) {
+  }
+  if (left == 0) return fail(FEM_ERR_OOM, "allocation of %zu bytes failed (injected)", bytes);
   const cudaError_t e = cudaMalloc(ptr, bytes);
   if (e != cudaSuccess) {
     cudaGetLastError();
@@ -496,6 +504,8 @@ fem_status fem_anneal(fem_problem_t p, const fem_anneal_params* a, void* stream)
   FEM_CUDA(cudaGetDevice(&cur_dev));
   if (cur_dev != p->device) return fail(FEM_ERR_STATE, "the current device is not the problem's device");
 
+  // a fresh start also clears the sticky device error word of an earlier failed run
+  if (a->t_begin == 0 && a->h_init) FEM_CUDA(cudaMemsetAsync(p->err, 0, sizeof(int32_t), s));
   if (a->t_begin == 0 && p->dense) {
     if (!a->h_init) return fail(FEM_ERR_INVALID_ARG, "h_init is required when t_begin == 0");
     fem_status st = FEM_OK;
@@ -632,6 +642,14 @@ fem_status fem_read_best(fem_problem_t p, int32_t* best_replica, int32_t* states
   if (energy_f64) FEM_CUDA(cudaMemcpyAsync(energy_f64, p->energy_f, (size_t)p->R * sizeof(double), cudaMemcpyDeviceToHost, s));
   return check_sticky(p, s);
 }
+
+fem_status fem_set_step_barrier_timeout(fem_problem_t p, int64_t ns) {
+  if (!p || ns < 0) return fail(FEM_ERR_INVALID_ARG, "fem_set_step_barrier_timeout: problem and ns >= 0 required");
+  p->barrier_wait_ns = ns;
+  return FEM_OK;
+}
+
+void fem_inject_allocation_failure(int64_t after) { g_fail_alloc_after.store(after < 0 ? -1 : after); }
 
 fem_status fem_set_dense_launch(fem_problem_t p, int32_t mode) {
   if (!p || !p->dense) return fail(FEM_ERR_INVALID_ARG, "fem_set_dense_launch: not a dense problem");

@@ -71,6 +71,7 @@ struct Problem {
   void* mt_lo[2] = {nullptr, nullptr};  // exact mode, bf16 low parts
   CUtensorMap tmap_a16, tmap_a8, tmap_b[2], tmap_blo[2];
   int32_t dense_launch = 0;               // fem_dense_launch
+  int64_t barrier_wait_ns = 2000000000;   // persistent kernel: limit on its step barrier
   StepScalars* dense_sc = nullptr;        // persistent anneal: the window's step scalars
   int64_t dense_sc_cap = 0;
   int32_t* dense_bar = nullptr;           // persistent anneal: per replica block arrival counters

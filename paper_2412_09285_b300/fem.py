@@ -74,6 +74,8 @@ def _load():
         "fem_problem_info": (S, [P, P, P, P, P, P]),
         "fem_sync": (S, [P, P]),
         "fem_set_dense_launch": (S, [P, C.c_int32]),
+        "fem_set_step_barrier_timeout": (S, [P, C.c_int64]),
+        "fem_inject_allocation_failure": (None, [C.c_int64]),
         "fem_destroy": (None, [P]),
         "fem_status_string": (C.c_char_p, [S]),
         "fem_last_error": (C.c_char_p, []),
@@ -179,6 +181,15 @@ def fem_sync(handle, stream=None):
 def fem_set_dense_launch(handle, mode):
     """mode: 0 auto, 1 one kernel per step, 2 persistent (fem_dense_launch)."""
     _check(_lib.fem_set_dense_launch(handle, int(mode)), "fem_set_dense_launch")
+
+
+def fem_set_step_barrier_timeout(handle, ns):
+    _check(_lib.fem_set_step_barrier_timeout(handle, int(ns)), "fem_set_step_barrier_timeout")
+
+
+def fem_inject_allocation_failure(after):
+    """The device allocation after `after` successful ones fails with FEM_ERR_OOM (-1: off)."""
+    _lib.fem_inject_allocation_failure(int(after))
 
 
 def fem_destroy(handle):

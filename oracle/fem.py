@@ -180,14 +180,17 @@ def _apply(W, X):
     return np.asarray(W @ X.reshape(n, -1)).reshape(X.shape)
 
 
-def bmincut_free_energy(W, h, beta, lam):
+def bmincut_free_energy(W, h, beta, lam, V=None):
     """F per replica, listing form ``cut + penalty*balance - S/beta``:
-    F = sum_{i,j} W_ij sum_s P_i(s)(1-P_j(s)) + lam sum_s[(sum_i P_i(s))^2 - sum_i P_i(s)^2]
-        + (1/beta) sum P ln P.      h: [N, R, q] -> [R]."""
+    F = sum_{i,j} W_ij sum_s P_i(s)(1-P_j(s)) + lam sum_s[(sum_i V_i P_i(s))^2 - sum_i V_i^2 P_i(s)^2]
+        + (1/beta) sum P ln P.      h: [N, R, q] -> [R].
+    V: node weights (SM, FPGA partitioning of community graphs: a coarsened node weighs
+    the number of nodes it groups); None means every V_i = 1."""
     P = _softmax(h)
+    Vn = np.ones(h.shape[0]) if V is None else np.asarray(V, np.float64)
     cut = (_apply(W, P) * (1.0 - P)).sum(axis=(0, 2))
-    col = P.sum(axis=0)                                   # [R, q]
-    balance = (col ** 2).sum(axis=1) - (P ** 2).sum(axis=(0, 2))
+    col = (Vn[:, None, None] * P).sum(axis=0)             # [R, q]
+    balance = (col ** 2).sum(axis=1) - ((Vn[:, None, None] * P) ** 2).sum(axis=(0, 2))
     ent = _xlogx(P).sum(axis=(0, 2))
     return cut + lam * balance + ent / beta
 
@@ -202,17 +205,20 @@ def bmincut_normalisers(W, q):
     return cf, ca
 
 
-def bmincut_grad(W, h, beta, lam, gamma=1.0, mode="paper", cf=None, ca=None, discretise=True):
+def bmincut_grad(W, h, beta, lam, gamma=1.0, mode="paper", cf=None, ca=None, discretise=True, V=None):
     """g^h_i(s) = gamma [ghat_i(s) - sum_s' P_i(s') ghat_i(s')] P_i(s)  (Eq. gradients_wrt_h)
 
-    exact: ghat = -2 sum_j W_ij P_j(s) + 2 lam [sum_j P_j(s) - P_i(s)] + (ln P_i(s) + 1)/beta
-    paper: ghat = -c^f_i sum_j W_ij e_j(s) + lam c^a_i [sum_j e_j(s) - e_i(s)] + (ln P_i(s) + 1)/beta
-    with e_j the one-hot argmax of P_j.  h: [N, R, q]."""
+    exact: ghat = -2 sum_j W_ij P_j(s) + 2 lam V_i [sum_j V_j P_j(s) - V_i P_i(s)] + (ln P_i(s) + 1)/beta
+    paper: ghat = -c^f_i sum_j W_ij e_j(s) + lam c^a_i V_i [sum_j V_j e_j(s) - V_i e_i(s)] + (ln P_i(s) + 1)/beta
+    with e_j the one-hot argmax of P_j and node weights V (SM, node-weighted balance
+    term; None: every V_i = 1).  h: [N, R, q]."""
     q = h.shape[2]
     P = _softmax(h)
     logP = _log_softmax(h)
+    Vn = (np.ones(h.shape[0]) if V is None else np.asarray(V, np.float64))[:, None, None]
     if mode == "exact":
-        ghat = -2.0 * _apply(W, P) + 2.0 * lam * (P.sum(axis=0)[None] - P) + (logP + 1.0) / beta
+        VP = Vn * P
+        ghat = -2.0 * _apply(W, P) + 2.0 * lam * Vn * (VP.sum(axis=0)[None] - VP) + (logP + 1.0) / beta
     elif mode == "paper":
         if cf is None or ca is None:
             cf0, ca0 = bmincut_normalisers(W, q)
@@ -226,7 +232,8 @@ def bmincut_grad(W, h, beta, lam, gamma=1.0, mode="paper", cf=None, ca=None, dis
             e = P
         cf = np.asarray(cf, np.float64)[:, None, None]
         ca = np.asarray(ca, np.float64)[:, None, None]
-        ghat = -cf * _apply(W, e) + lam * ca * (e.sum(axis=0)[None] - e) + (logP + 1.0) / beta
+        Ve = Vn * e
+        ghat = -cf * _apply(W, e) + lam * ca * Vn * (Ve.sum(axis=0)[None] - Ve) + (logP + 1.0) / beta
     else:
         raise ValueError(mode)
     return gamma * (ghat - (P * ghat).sum(axis=2, keepdims=True)) * P
@@ -380,14 +387,15 @@ def anneal(problem, h0, n_step, *, t_begin=0, t_end=None, schedule="exponential"
            gamma=1.0, lambda_max=1.0, opt=None, trace=None, cond=None):
     """Run anneal steps t_begin .. t_end-1 from fields h0 (copied, float64).
 
-    problem: ("maxcut", W) | ("bmincut", W) | ("sat", groups)
+    problem: ("maxcut", W) | ("bmincut", W) | ("bmincut", W, V) | ("sat", groups)
     Returns (h, opt); pass ``opt`` back in to resume.  ``trace``, if a dict
     {t: None}, is filled with copies of h after step t (1-based count of steps done).
     ``cond``, if a dict {t: None}, is filled with the elementwise minimum over the
     steps up to t of the optimizer's denominator (a conditioning record for
     comparisons in fp32: the update divides by it, so gradient rounding is
     amplified where it is small)."""
-    kind, data = problem
+    kind, data = problem[0], problem[1]
+    node_w = problem[2] if len(problem) > 2 else None
     t_end = n_step if t_end is None else t_end
     h = np.array(h0, dtype=np.float64, copy=True)
     betas = beta_schedule(schedule, beta_min, beta_max, n_step)
@@ -400,7 +408,7 @@ def anneal(problem, h0, n_step, *, t_begin=0, t_end=None, schedule="exponential"
         if kind == "maxcut":
             g = maxcut_grad(data, h, beta, gamma=gamma, mode=mode)
         elif kind == "bmincut":
-            g = bmincut_grad(data, h, beta, lams[t], gamma=gamma, mode=mode)
+            g = bmincut_grad(data, h, beta, lams[t], gamma=gamma, mode=mode, V=node_w)
         elif kind == "sat":
             g = sat_grad(data, h, beta, gamma=gamma)
         else:
@@ -460,16 +468,18 @@ def bmincut_states(h):
     return np.argmax(np.asarray(h), axis=2).astype(np.int32)
 
 
-def bmincut_objective(ei, ej, w, states, q, lam):
-    """(E, cut, sizes) per replica with E = cut + lam * sum_s n_s (n_s - 1)
-    (Eq. bmincut: lam * sum_i sum_{j != i} delta(sigma_i, sigma_j) = lam * sum_s n_s(n_s - 1))."""
+def bmincut_objective(ei, ej, w, states, q, lam, V=None):
+    """(E, cut, sizes) per replica with E = cut + lam * sum_s [n_s^2 - sum_{i in s} V_i^2],
+    n_s = sum_{i in s} V_i (Eq. bmincut with the node-weighted balance term; for V = 1 it
+    is lam * sum_i sum_{j != i} delta(sigma_i, sigma_j) = lam * sum_s n_s(n_s - 1))."""
     w = _as_exact(w)
     cut = (w[:, None] * (states[ei] != states[ej])).sum(axis=0)
     R = states.shape[1]
+    Vn = np.ones(states.shape[0], dtype=np.int64) if V is None else np.asarray(V, np.int64)
     sizes = np.zeros((R, q), dtype=np.int64)
     for s in range(q):
-        sizes[:, s] = (states == s).sum(axis=0)
-    bal = (sizes * (sizes - 1)).sum(axis=1)
+        sizes[:, s] = (Vn[:, None] * (states == s)).sum(axis=0)
+    bal = (sizes * sizes).sum(axis=1) - (Vn * Vn).sum()
     lam_exact = int(lam) if float(lam).is_integer() and w.dtype == np.int64 else lam
     return cut + lam_exact * bal, cut, sizes
 

@@ -399,3 +399,78 @@ def test_oracle_bmincut_reaches_bruteforce_optimum(seed):
                     opt_kw=dict(lr=0.1), lambda_max=lam)
     E, _, _ = O.bmincut_objective(g.ei, g.ej, g.w, O.bmincut_states(h), q, lam)
     assert E.min() == best
+
+
+# ---- node-weighted bMinCut (SM, partitioning community graphs of the FPGA task)
+
+def _weights(n, seed):
+    return _rng(seed).integers(1, 6, size=n).astype(np.float64)
+
+
+def test_weighted_bmincut_free_energy_matches_enumeration():
+    g, W = _small_graph(5, 0.7, 31, "real")
+    q, beta, lam = 3, 1.1, 0.35
+    V = _weights(5, 32)
+    h = _rng(33).normal(size=(5, 2, q))
+    F = O.bmincut_free_energy(W, h, beta, lam, V=V)
+    for r in range(2):
+        z = np.exp(h[:, r] - h[:, r].max(axis=1, keepdims=True))
+        marg = z / z.sum(axis=1, keepdims=True)
+
+        def E(X):
+            cut = (g.w[None, :] * (X[:, g.ei] != X[:, g.ej])).sum(axis=1)
+            n_s = np.stack([((X == s) * V[None]).sum(axis=1) for s in range(q)], axis=1)
+            sq_s = np.stack([((X == s) * V[None] ** 2).sum(axis=1) for s in range(q)], axis=1)
+            return 2.0 * cut + lam * (n_s ** 2 - sq_s).sum(axis=1)
+
+        ref = O.mf_free_energy_by_enumeration(marg, E, beta)
+        assert F[r] == pytest.approx(ref, rel=1e-12, abs=1e-12)
+
+
+def test_weighted_bmincut_exact_gradient_is_fd_of_F():
+    g, W = _small_graph(8, 0.5, 34, "real")
+    V = _weights(8, 35)
+    h = _rng(36).normal(size=(8, 2, 4))
+    beta, lam = 0.7, 0.2
+    ana = O.bmincut_grad(W, h, beta, lam, mode="exact", V=V)
+    fd = _fd(lambda x: O.bmincut_free_energy(W, x, beta, lam, V=V), h)
+    assert np.max(np.abs(ana - fd)) <= 1e-7 * max(1.0, np.max(np.abs(fd)))
+
+
+def test_unit_node_weights_reduce_to_the_unweighted_forms():
+    g, W = _small_graph(9, 0.5, 37, "unit")
+    h = _rng(38).normal(size=(9, 3, 3))
+    one = np.ones(9)
+    for mode in ("exact", "paper"):
+        assert np.array_equal(O.bmincut_grad(W, h, 0.8, 0.3, mode=mode, V=one),
+                              O.bmincut_grad(W, h, 0.8, 0.3, mode=mode))
+    st = O.bmincut_states(h)
+    a = O.bmincut_objective(g.ei, g.ej, g.w, st, 3, 1.0, V=one.astype(np.int64))
+    b = O.bmincut_objective(g.ei, g.ej, g.w, st, 3, 1.0)
+    assert all(np.array_equal(x, y) for x, y in zip(a, b))
+
+
+def test_weighted_objective_is_the_coarsened_graph_of_tied_nodes():
+    """Coarsening (SM, FPGA task): nodes of a community always share a group; the
+    community graph has node weight = community size and edge weight = the sum of the
+    edges between communities.  For every assignment of the community graph, the
+    weighted energy plus lam * sum_i V_i (V_i - 1) (the pairs inside communities, which
+    never leave a group) equals the unweighted energy of the lifted fine assignment."""
+    rng = _rng(39)
+    fine_n, q, lam = 9, 3, 2.0
+    comm = np.array([0, 0, 1, 1, 1, 2, 3, 3, 4])           # 5 communities
+    fg = I.er_gnp(fine_n, 0.6, seed=40, weights="unit")
+    V = np.bincount(comm).astype(np.int64)
+    acc = {}
+    for i, j, w in zip(fg.ei, fg.ej, fg.w):
+        a, b = comm[i], comm[j]
+        if a != b:
+            key = (min(a, b), max(a, b))
+            acc[key] = acc.get(key, 0) + int(w)
+    cei = np.array([k[0] for k in acc]); cej = np.array([k[1] for k in acc])
+    cw = np.array([acc[k] for k in acc], dtype=np.int64)
+    states = O.all_qary(5, q).T.astype(np.int32)                      # [community, assignment]
+    states = states[:, rng.choice(states.shape[1], size=60, replace=False)]
+    Ec, _, _ = O.bmincut_objective(cei, cej, cw, states, q, lam, V=V)
+    Ef, _, _ = O.bmincut_objective(fg.ei, fg.ej, fg.w, states[comm], q, lam)
+    assert np.array_equal(Ec + int(lam) * int((V * (V - 1)).sum()), Ef)

@@ -108,11 +108,19 @@ typedef struct fem_problem* fem_problem_t; /* opaque; owned by the library until
  *       objectives; other weights give fp64 objectives summed in a fixed order.
  *     dense_J    optional n*n row-major couplings (MaxCut only).  When non-NULL the
  *       dense tensor-core path is used and ei/ej/w are ignored.  Must be symmetric
- *       with a zero diagonal and integer entries, |J_ij| <= 2^8 (BF16 exact).
+ *       with a zero diagonal and integer entries, |J_ij| <= 127 (exact in bf16 and
+ *       int8; FEM_PREC_FP8 further needs |J_ij| <= 16).
  *   Clauses (Max-k-SAT), DIMACS style:
  *     n_clauses, clause_ptr[n_clauses + 1] (clause_ptr[0] = 0, non-decreasing),
  *     lits[clause_ptr[n_clauses]]: signed 1-based variable indices, +v for the
  *     literal v and -v for its negation; a clause must not repeat a variable.
+ *   node_weight  optional (bMinCut only), n node weights V_i: positive integers
+ *                <= 2^20 with sum < 2^31 (FEM_ERR_INVALID_ARG otherwise).  The balance
+ *                term becomes lambda sum_s [(sum_i V_i P_i(s))^2 - sum_i V_i^2 P_i(s)^2]
+ *                with the matching gradients (SM, the FPGA task's community graphs,
+ *                where a coarsened node weighs the number of nodes it groups), and
+ *                the read-out energy cut + lambda_max sum_s [n_s^2 - sum_{i in s} V_i^2]
+ *                with n_s = sum_{i in s} V_i.  NULL: every V_i = 1.
  */
 typedef struct {
   int32_t kind;
@@ -126,6 +134,7 @@ typedef struct {
   int64_t n_clauses;
   const int64_t* clause_ptr;
   const int32_t* lits;
+  const double* node_weight;
 } fem_problem_desc;
 
 /* Anneal parameters.

@@ -30,6 +30,7 @@ struct BatchMember {
   const float* w;
   const float* cf;
   const float* ca;
+  const int32_t* nodew;
   float* h0;
   float* h1;
   float* m;
@@ -62,6 +63,7 @@ __device__ void run_bmincut_item(const BatchMember& b, const BatchItem& it, cons
   a.w = b.w;
   a.cf = b.cf;
   a.ca = b.ca;
+  a.nodew = b.nodew;
   a.n = b.n;
   a.R = b.R;
   a.wpn = b.wpn;
@@ -257,6 +259,7 @@ static fem_status batch_prepare(Batch* b, cudaStream_t s) {
     m.w = p->unit_w ? nullptr : p->w;
     m.cf = p->cnorm;
     m.ca = p->cnorm2;
+    m.nodew = p->nodew;
     m.h0 = p->h[0];
     m.h1 = p->h[1];
     m.m = p->m;

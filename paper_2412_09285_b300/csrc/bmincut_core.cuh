@@ -23,6 +23,7 @@ struct BmcArgs {
   const float* w;  // NULL for unit weights
   const float* cf;
   const float* ca;
+  const int32_t* nodew;  // node weights V_i, NULL: all 1
   int32_t n, R, wpn, opt;
   const float* h_in;
   float* h_out;
@@ -118,7 +119,7 @@ __device__ __forceinline__ void bmincut_element(const BmcArgs& a, const StepScal
     float acc[Q];
 #pragma unroll
     for (int q = 0; q < Q; ++q) acc[q] = 0.f;
-    int own = 0;
+    int own = 0, Vi = 1;
     float cf = 0.f, ca = 0.f;
     int beg = 0, end = 0;
     // Paper mode, unit weights, one packed word per node (R * B == 32: q = 2 with
@@ -132,6 +133,7 @@ __device__ __forceinline__ void bmincut_element(const BmcArgs& a, const StepScal
       if (a.opt != FEM_OPT_SGD) load_q<Q>(a.v + idx, vv);
       beg = a.row_ptr[i];
       end = a.row_ptr[i + 1];
+      if (a.nodew) Vi = a.nodew[i];
       if (MODE == FEM_GRAD_PAPER) {
         own = (int)((a.words_in[(size_t)i * a.wpn + wsel] >> sh) & SM);
         cf = a.cf[i];
@@ -219,7 +221,7 @@ __device__ __forceinline__ void bmincut_element(const BmcArgs& a, const StepScal
     unsigned long long ps[Q];
 #pragma unroll
     for (int q = 0; q < Q; ++q) {
-      if (MODE == FEM_GRAD_PAPER) nc[q] = act ? a.cnt_in[r * Q + q] - (own == q ? 1 : 0) : 0;
+      if (MODE == FEM_GRAD_PAPER) nc[q] = act ? a.cnt_in[r * Q + q] - (own == q ? Vi : 0) : 0;
       else ps[q] = act ? a.ps_in[r * Q + q] : 0ull;
     }
     float cen[Q];
@@ -229,11 +231,14 @@ __device__ __forceinline__ void bmincut_element(const BmcArgs& a, const StepScal
 #pragma unroll
       for (int q2 = 0; q2 < Q; ++q2) {
         float d;
+        // node weights (SM, node-weighted balance term): lambda c^a_i V_i [n(s) - V_i e_i(s)]
+        // (paper) and 2 lambda V_i [sum_j V_j P_j(s) - V_i P_i(s)] (exact); V_i = 1 gives
+        // the unweighted forms with the same roundings
         if (MODE == FEM_GRAD_PAPER) {
-          d = -cf * (acc[q] - acc[q2]) + s.lambda * ca * (float)(nc[q] - nc[q2]);
+          d = -cf * (acc[q] - acc[q2]) + s.lambda * (ca * (float)Vi) * (float)(nc[q] - nc[q2]);
         } else {
           const float dcol = (float)(long long)(ps[q] - ps[q2]) * kPsumInv;
-          d = -2.f * (acc[q] - acc[q2]) + 2.f * s.lambda * (dcol - (P[q] - P[q2]));
+          d = -2.f * (acc[q] - acc[q2]) + 2.f * s.lambda * (float)Vi * (dcol - (float)Vi * (P[q] - P[q2]));
         }
         d = fmaf(h[q] - h[q2], s.inv_beta, d);
         c = fmaf(P[q2], d, c);
@@ -249,12 +254,13 @@ __device__ __forceinline__ void bmincut_element(const BmcArgs& a, const StepScal
       store_q<Q>(a.h_out + idx, h);
       store_q<Q>(a.m + idx, mm);
       if (a.opt != FEM_OPT_SGD) store_q<Q>(a.v + idx, vv);
-      atomicAdd(&scnt[r * Q + sn], 1);
+      atomicAdd(&scnt[r * Q + sn], Vi);
       if (MODE == FEM_GRAD_EXACT) {
         float Pn[Q], ln[Q];
         softmax_q<Q>(h, Pn, ln);
 #pragma unroll
-        for (int q = 0; q < Q; ++q) atomicAdd(&sps[r * Q + q], __float2ull_rn(Pn[q] * kPsumScale));
+        for (int q = 0; q < Q; ++q)
+          atomicAdd(&sps[r * Q + q], __float2ull_rn(Pn[q] * kPsumScale) * (unsigned long long)Vi);
       }
     }
     uint32_t word = act ? ((uint32_t)sn << sh) : 0u;

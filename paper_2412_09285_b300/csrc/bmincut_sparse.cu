@@ -65,7 +65,8 @@ __global__ void __launch_bounds__(256, 4) k_bmincut_step(BmcArgs a, StepScalars 
 // buffers with one integer atomic per entry and block (exact, so order-free).
 template <int Q>
 __global__ void __launch_bounds__(256) k_bmincut_derive(const float* __restrict__ h, int32_t n, int32_t R,
-                                                        int32_t wpn, uint32_t* __restrict__ words,
+                                                        int32_t wpn, const int32_t* __restrict__ nodew,
+                                                        uint32_t* __restrict__ words,
                                                         int32_t* __restrict__ cnt,
                                                         unsigned long long* __restrict__ ps) {
   constexpr int B = QBits<Q>::B, RPW = QBits<Q>::RPW;
@@ -92,11 +93,13 @@ __global__ void __launch_bounds__(256) k_bmincut_derive(const float* __restrict_
     if (act) load_q<Q>(h + ((size_t)i * R + r) * Q, x);
     const int sn = argmax_q<Q>(x);
     if (act) {
-      atomicAdd(&scnt[r * Q + sn], 1);
+      const int Vi = nodew ? nodew[i] : 1;
+      atomicAdd(&scnt[r * Q + sn], Vi);
       float P[Q], ln[Q];
       softmax_q<Q>(x, P, ln);
 #pragma unroll
-      for (int q = 0; q < Q; ++q) atomicAdd(&sps[r * Q + q], __float2ull_rn(P[q] * kPsumScale));
+      for (int q = 0; q < Q; ++q)
+        atomicAdd(&sps[r * Q + q], __float2ull_rn(P[q] * kPsumScale) * (unsigned long long)Vi);
     }
     uint32_t word = act ? ((uint32_t)sn << ((r % RPW) * B)) : 0u;
 #pragma unroll
@@ -117,8 +120,8 @@ template <int Q, bool INTW>
 __global__ void __launch_bounds__(256) k_bmincut_cut_partial(
     const int32_t* __restrict__ row_ptr, const uint32_t* __restrict__ col,
     const float* __restrict__ w, const double* __restrict__ w64, const uint32_t* __restrict__ words,
-    int32_t n, int32_t R, int32_t wpn, int64_t* __restrict__ part_i, double* __restrict__ part_f,
-    int64_t* __restrict__ part_cnt) {
+    const int32_t* __restrict__ nodew, int32_t n, int32_t R, int32_t wpn, int64_t* __restrict__ part_i,
+    double* __restrict__ part_f, int64_t* __restrict__ part_cnt) {
   constexpr int B = QBits<Q>::B, RPW = QBits<Q>::RPW;
   constexpr uint32_t SM = QBits<Q>::MASK;
   __shared__ int64_t si[256];
@@ -135,7 +138,7 @@ __global__ void __launch_bounds__(256) k_bmincut_cut_partial(
   for (int i = blockIdx.x * 16 + nl; i < n; i += gridDim.x * 16) {
     const int si_ = (int)((words[(size_t)i * wpn + wsel] >> sh) & SM);
 #pragma unroll
-    for (int q = 0; q < Q; ++q) cnt[q] += (si_ == q);
+    for (int q = 0; q < Q; ++q) cnt[q] += (si_ == q) ? (nodew ? nodew[i] : 1) : 0;
     const int beg = row_ptr[i], end = row_ptr[i + 1];
     for (int k = beg; k < end; ++k) {
       const int j = (int)(col[k] & 0x7fffffffu);
@@ -177,17 +180,18 @@ template <int Q>
 __global__ void __launch_bounds__(kRedThreads) k_bmincut_finish(
     const int64_t* __restrict__ part_i, const double* __restrict__ part_f,
     const int64_t* __restrict__ part_cnt, int32_t nblk, int32_t R, int32_t intw, int32_t lam_is_int,
-    double lam, int64_t* __restrict__ e_i, double* __restrict__ e_f) {
+    double lam, int64_t sum_v2, int64_t* __restrict__ e_i, double* __restrict__ e_f) {
   __shared__ int64_t shi[kRedThreads];
   __shared__ double shf[kRedThreads];
   const int r = blockIdx.x;
   const int64_t ci = intw ? column_sum<int64_t>(part_i, nblk, R, r, shi) : 0;
   const double cfv = intw ? 0.0 : column_sum<double>(part_f, nblk, R, r, shf);
-  int64_t bal = 0;
+  // sum_s [n_s^2 - sum_{i in s} V_i^2] = sum_s n_s^2 - sum_i V_i^2 (n_s(n_s - 1) unweighted)
+  int64_t bal = -sum_v2;
 #pragma unroll
   for (int q = 0; q < Q; ++q) {
     const int64_t sz = column_sum<int64_t>(part_cnt, nblk, (size_t)R * Q, (size_t)r * Q + q, shi);
-    bal += sz * (sz - 1);
+    bal += sz * sz;
   }
   if (threadIdx.x == 0) {
     double ef;
@@ -238,6 +242,7 @@ fem_status steps_q(Problem* p, const std::vector<StepScalars>& sc, int t_begin, 
   a.w = p->unit_w ? nullptr : p->w;
   a.cf = p->cnorm;
   a.ca = p->cnorm2;
+  a.nodew = p->nodew;
   a.n = p->n;
   a.R = p->R;
   a.wpn = p->words_per_node;
@@ -282,7 +287,7 @@ fem_status derive_q(Problem* p, int t, cudaStream_t st) {
   if (smem > 48 * 1024)
     FEM_CUDA(cudaFuncSetAttribute(k_bmincut_derive<Q>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   const int grid = resident_grid(k_bmincut_derive<Q>, p->sm_count, (long long)p->n * p->R, smem);
-  k_bmincut_derive<Q><<<grid, 256, smem, st>>>(h, p->n, p->R, p->words_per_node, p->words[t & 1],
+  k_bmincut_derive<Q><<<grid, 256, smem, st>>>(h, p->n, p->R, p->words_per_node, p->nodew, p->words[t & 1],
                                               p->cnt[t % 3], p->psum[t % 3]);
   count_launches(1);
   FEM_CUDA(cudaGetLastError());
@@ -295,16 +300,16 @@ fem_status readout_q(Problem* p, cudaStream_t st) {
   const uint32_t* words = p->words[p->steps_done & 1];
   if (p->int_w)
     k_bmincut_cut_partial<Q, true><<<grid, 256, 0, st>>>(p->row_ptr, p->col, p->unit_w ? nullptr : p->w,
-                                                         p->w64, words, p->n, p->R, p->words_per_node,
+                                                         p->w64, words, p->nodew, p->n, p->R, p->words_per_node,
                                                          p->part_i, p->part_f, p->part_cnt);
   else
     k_bmincut_cut_partial<Q, false><<<grid, 256, 0, st>>>(p->row_ptr, p->col, p->unit_w ? nullptr : p->w,
-                                                          p->w64, words, p->n, p->R, p->words_per_node,
+                                                          p->w64, words, p->nodew, p->n, p->R, p->words_per_node,
                                                           p->part_i, p->part_f, p->part_cnt);
   const double lam = p->lambda_max;
   k_bmincut_finish<Q><<<p->R, kRedThreads, 0, st>>>(p->part_i, p->part_f, p->part_cnt, p->part_blocks, p->R,
                                                      p->int_w ? 1 : 0, lam == std::floor(lam) ? 1 : 0, lam,
-                                                     p->energy_i, p->energy_f);
+                                                     p->nodew_sq, p->energy_i, p->energy_f);
   k_argmin_replica<<<1, 1024, 0, st>>>(p->energy_f, p->R, p->best);
   k_bmincut_states<Q><<<(p->n + 255) / 256 < 1024 ? (p->n + 255) / 256 : 1024, 256, 0, st>>>(
       words, p->n, p->R, p->words_per_node, p->best, p->states_dev, 0);

@@ -441,6 +441,24 @@ fem_status fem_create_problem(const fem_problem_desc* d, void* stream, fem_probl
   } else {
     if ((st = host_graph(d->kind, d->q, d, hg)) != FEM_OK) return st;
   }
+  std::vector<int32_t> nodew;
+  int64_t nodew_sq = d->n;
+  if (d->node_weight) {
+    if (d->kind != FEM_BMINCUT || d->dense_J)
+      return fail(FEM_ERR_INVALID_ARG, "node_weight applies to sparse bMinCut problems only");
+    nodew.resize(d->n);
+    int64_t tot = 0;
+    nodew_sq = 0;
+    for (int32_t i = 0; i < d->n; ++i) {
+      const double v = d->node_weight[i];
+      if (!(v >= 1.0 && v <= 1048576.0) || v != std::floor(v))
+        return fail(FEM_ERR_INVALID_ARG, "node_weight[%d] must be an integer in [1, 2^20]", i);
+      nodew[i] = (int32_t)v;
+      tot += nodew[i];
+      nodew_sq += (int64_t)nodew[i] * nodew[i];
+    }
+    if (tot >= (int64_t)INT32_MAX) return fail(FEM_ERR_INVALID_ARG, "the node weights must sum to less than 2^31");
+  }
   // 2. device side
   std::unique_ptr<fem_problem> p(new fem_problem());
   p->kind = d->kind;
@@ -450,6 +468,8 @@ fem_status fem_create_problem(const fem_problem_desc* d, void* stream, fem_probl
   FEM_CUDA(cudaDeviceGetAttribute(&p->sm_count, cudaDevAttrMultiProcessorCount, p->device));
   if (d->kind == FEM_MAXCUT && d->dense_J) st = dense_upload(p.get(), d->dense_J, s);
   else st = d->kind == FEM_MAXKSAT ? upload_sat(p.get(), hs, s) : upload_graph(p.get(), hg, s);
+  p->nodew_sq = nodew_sq;
+  if (st == FEM_OK && !nodew.empty()) st = upload(p.get(), &p->nodew, nodew, s);
   if (st == FEM_OK) st = dev_alloc_t(p.get(), &p->err, 1);
   if (st == FEM_OK) {
     const cudaError_t e1 = cudaMemsetAsync(p->err, 0, sizeof(int32_t), s);

@@ -47,6 +47,8 @@ struct Problem {
   double* w64 = nullptr;       // [nnz] fp64 weights when !int_w (objectives)
   float* cnorm = nullptr;      // MaxCut c_i = 1/sum|W_ij| (when !unit_w); bMinCut c^f
   float* cnorm2 = nullptr;     // bMinCut c^a
+  int32_t* nodew = nullptr;    // bMinCut node weights V_i (NULL: all 1)
+  int64_t nodew_sq = 0;        // sum_i V_i^2 (n when unweighted)
 
   // ---- clauses (Max-k-SAT)
   int64_t n_clauses = 0, n_occ = 0;

@@ -37,6 +37,7 @@ class fem_problem_desc(C.Structure):
         ("n_edges", C.c_int64), ("ei", C.c_void_p), ("ej", C.c_void_p), ("w", C.c_void_p),
         ("dense_J", C.c_void_p),
         ("n_clauses", C.c_int64), ("clause_ptr", C.c_void_p), ("lits", C.c_void_p),
+        ("node_weight", C.c_void_p),
     ]
 
 
@@ -238,7 +239,7 @@ class Problem:
     """Owns one libfem problem handle.  Inputs are host numpy arrays (or objects
     from ``instances``); h_init may also be a CUDA torch tensor."""
 
-    def __init__(self, kind="maxcut", graph=None, clauses=None, dense=None, q=2, stream=None):
+    def __init__(self, kind="maxcut", graph=None, clauses=None, dense=None, q=2, stream=None, node_weight=None):
         self.kind = kind
         self.stream = stream
         d = fem_problem_desc()
@@ -252,6 +253,10 @@ class Problem:
             w = np.ascontiguousarray(graph.w, np.float64)
             self._keep += [ei, ej, w]
             d.n_edges, d.ei, d.ej, d.w = ei.shape[0], _ptr(ei), _ptr(ej), _ptr(w)
+        if node_weight is not None:
+            V = np.ascontiguousarray(node_weight, np.float64)
+            self._keep.append(V)
+            d.node_weight = _ptr(V)
         if dense is not None:
             J = np.ascontiguousarray(dense, np.float32)
             self._keep.append(J)

@@ -67,9 +67,9 @@ def _sched(kw):
                 lambda_max=kw.get("lambda_max", 1.0))
 
 
-def _traces(fem, g, h0, q, checkpoints, n_steps, mode, **kw):
+def _traces(fem, g, h0, q, checkpoints, n_steps, mode, V=None, **kw):
     W = O.coupling_matrix(g.n, g.ei, g.ej, g.w)
-    P = fem.Problem("bmincut", graph=g, q=q)
+    P = fem.Problem("bmincut", graph=g, q=q, node_weight=V)
     got, t = {}, 0
     for T in checkpoints:
         P.anneal(h_init=h0 if t == 0 else None, replicas=h0.shape[1], n_steps=n_steps, t_begin=t,
@@ -78,7 +78,8 @@ def _traces(fem, g, h0, q, checkpoints, n_steps, mode, **kw):
         t = T
     tr = {t: None for t in checkpoints}
     cd = {t: None for t in checkpoints}
-    O.anneal(("bmincut", W), h0.astype(np.float64), n_steps, t_end=max(checkpoints),
+    O.anneal(("bmincut", W) if V is None else ("bmincut", W, V), h0.astype(np.float64), n_steps,
+             t_end=max(checkpoints),
              optimizer=kw.get("optimizer", "adam"), opt_kw=_okw(kw), mode=mode, trace=tr, cond=cd,
              **_sched(kw))
     return P, got, tr, cd
@@ -237,3 +238,67 @@ def test_bmincut_argument_errors(fem):
     with pytest.raises(fem.FemError) as e:
         P.anneal(h_init=I.initial_fields(100, 16, seed=1, q=4), n_steps=10, lambda_max=-1.0)
     assert e.value.status == fem.FEM_ERR_INVALID_ARG
+
+
+
+# ---- node-weighted bMinCut (SM, the FPGA task's community graphs)
+
+def _node_weights(n, seed):
+    return np.random.Generator(np.random.PCG64(seed)).integers(1, 6, size=n).astype(np.float64)
+
+
+@pytest.mark.parametrize("mode", ["exact", "paper"])
+def test_weighted_marginals_first_50_steps(fem, mode):
+    g = I.rgg(800, 10.0, seed=81)
+    V = _node_weights(800, 82)
+    h0 = I.initial_fields(800, 16, seed=83, q=4)
+    _, got, ref, cd = _traces(fem, g, h0, 4, CHECK, 1000, mode, V=V, lr=0.1, lambda_max=0.05)
+    agree = _agree(got, ref, CHECK) if mode == "paper" else None
+    if agree is not None:
+        assert agree.sum() >= 12, agree.sum()
+    for t in CHECK:
+        _check(got[t], ref[t], cd[t], (mode, t), agree=agree, mode=mode)
+
+
+def test_weighted_objectives_bit_exact_and_unit_weights_change_nothing(fem):
+    g = I.rgg(900, 10.0, seed=84)
+    V = _node_weights(900, 85)
+    h0 = I.initial_fields(900, 16, seed=86, q=4)
+    P = fem.Problem("bmincut", graph=g, q=4, node_weight=V).anneal(h_init=h0, n_steps=200, lambda_max=0.01)
+    st = P.states()
+    E, cut, sizes = O.bmincut_objective(g.ei, g.ej, g.w, st, 4, 0.01, V=V.astype(np.int64))
+    res = P.best()
+    assert np.allclose(res["energy_f64"], E, rtol=0, atol=1e-9 * np.abs(E).max())
+    assert res["best_replica"] == int(np.argmin(E))
+    # an integer lambda_max gives exact int64 energies
+    P1 = fem.Problem("bmincut", graph=g, q=4, node_weight=V).anneal(h_init=h0, n_steps=50, lambda_max=1.0)
+    E1, _, _ = O.bmincut_objective(g.ei, g.ej, g.w, P1.states(), 4, 1.0, V=V.astype(np.int64))
+    assert np.array_equal(P1.best()["energy_i64"], E1)
+    # V = 1 is the unweighted problem, bit for bit
+    a = fem.Problem("bmincut", graph=g, q=4, node_weight=np.ones(900)).anneal(h_init=h0, n_steps=60).state()
+    b = fem.Problem("bmincut", graph=g, q=4).anneal(h_init=h0, n_steps=60).state()
+    for x, y in zip(a, b):
+        assert np.array_equal(x, y)
+
+
+def test_weighted_member_in_a_batch_equals_alone(fem):
+    gs = [I.rgg(700, 10.0, seed=87 + k) for k in range(3)]
+    Vs = [_node_weights(700, 90 + k) if k != 1 else None for k in range(3)]
+    h0 = [I.initial_fields(700, 16, seed=93 + k, q=4) for k in range(3)]
+    alone = [fem.Problem("bmincut", graph=g, q=4, node_weight=V).anneal(h_init=h, n_steps=80).state()
+             for g, V, h in zip(gs, Vs, h0)]
+    probs = [fem.Problem("bmincut", graph=g, q=4, node_weight=V) for g, V in zip(gs, Vs)]
+    fem.Batch(probs).anneal(h_inits=h0, replicas=16, n_steps=80)
+    for p, ref in zip(probs, alone):
+        for x, y in zip(p.state(), ref):
+            assert np.array_equal(x, y)
+
+
+def test_node_weight_validation(fem):
+    g = I.rgg(50, 6.0, seed=96)
+    for bad in (np.zeros(50), np.full(50, 1.5), np.full(50, 2.0 ** 21)):
+        with pytest.raises(fem.FemError) as e:
+            fem.Problem("bmincut", graph=g, q=4, node_weight=bad)
+        assert e.value.status == fem.FEM_ERR_INVALID_ARG
+    with pytest.raises(fem.FemError):
+        fem.Problem("maxcut", graph=g, node_weight=np.ones(50))

@@ -11,7 +11,7 @@ from __future__ import annotations
 import numpy as np
 
 __all__ = [
-    "all_binary", "all_qary", "maxcut_bruteforce", "bmincut_bruteforce",
+    "all_binary", "all_qary", "maxcut_bruteforce", "bmincut_bruteforce", "coloring_bruteforce",
     "sat_bruteforce", "mf_free_energy_by_enumeration",
 ]
 
@@ -45,6 +45,12 @@ def bmincut_bruteforce(n, ei, ej, w, q, lam):
     cut = (np.asarray(w)[None, :] * (X[:, ei] != X[:, ej])).sum(axis=1)
     sizes = np.stack([(X == s).sum(axis=1) for s in range(q)], axis=1)
     return (cut + lam * (sizes * (sizes - 1)).sum(axis=1)).min()
+
+
+def coloring_bruteforce(n, ei, ej, w, q):
+    """Minimum violated edge weight sum_E W_ij [sigma_i == sigma_j] over all q^n colourings."""
+    X = all_qary(n, q)
+    return (np.asarray(w)[None, :] * (X[:, ei] == X[:, ej])).sum(axis=1).min()
 
 
 def sat_bruteforce(n, ptr, lits):

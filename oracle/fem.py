@@ -41,6 +41,7 @@ __all__ = [
     "beta_schedule", "lambda_ramp", "coupling_matrix", "sigmoid",
     "maxcut_free_energy", "maxcut_grad", "maxcut_normaliser",
     "bmincut_free_energy", "bmincut_grad", "bmincut_normalisers",
+    "coloring_free_energy", "coloring_grad", "coloring_energy",
     "sat_arrays", "sat_free_energy", "sat_grad",
     "Adam", "RMSprop", "SGD", "make_optimizer", "anneal",
     "maxcut_states", "maxcut_cut_edges", "maxcut_cut_spin", "maxcut_cut_matrix",
@@ -240,6 +241,50 @@ def bmincut_grad(W, h, beta, lam, gamma=1.0, mode="paper", cf=None, ca=None, dis
 
 
 # ----------------------------------------------------------------------------
+# Graph colouring (q-state Potts; SM, problems of multi-valued variables):
+#   E(sigma) = sum_{(i,j) in E} W_ij delta(sigma_i, sigma_j)   (violated edges)
+#   U_MF = sum_{(i,j) in E} W_ij sum_s P_i(s) P_j(s)
+# ----------------------------------------------------------------------------
+
+def coloring_free_energy(W, h, beta):
+    """F = sum_{(i,j) in E} W_ij sum_s P_i(s) P_j(s) + (1/beta) sum P ln P  (each edge once:
+    half the ordered-pair sum of the symmetric W).  h: [N, R, q] -> [R]."""
+    P = _softmax(h)
+    U = 0.5 * (_apply(W, P) * P).sum(axis=(0, 2))
+    return U + _xlogx(P).sum(axis=(0, 2)) / beta
+
+
+def coloring_grad(W, h, beta, gamma=1.0, mode="exact", cf=None, discretise=True):
+    """g^h_i(s) = gamma [ghat_i(s) - sum_s' P_i(s') ghat_i(s')] P_i(s)  (Eq. gradients_wrt_h)
+    exact: ghat = sum_j W_ij P_j(s) + (ln P_i(s) + 1)/beta  (the derivative of F)
+    paper: ghat = c^f_i sum_j W_ij e_j(s) + (ln P_i(s) + 1)/beta, e_j the one-hot argmax
+           (the bMinCut manipulation with the coupling's sign: same colours cost)."""
+    q = h.shape[2]
+    P = _softmax(h)
+    logP = _log_softmax(h)
+    if mode == "exact":
+        ghat = _apply(W, P) + (logP + 1.0) / beta
+    elif mode == "paper":
+        if cf is None:
+            cf, _ = bmincut_normalisers(W, q)
+        if discretise:
+            e = np.zeros_like(P)
+            np.put_along_axis(e, np.argmax(h, axis=2)[..., None], 1.0, axis=2)
+        else:
+            e = P
+        ghat = np.asarray(cf, np.float64)[:, None, None] * _apply(W, e) + (logP + 1.0) / beta
+    else:
+        raise ValueError(mode)
+    return gamma * (ghat - (P * ghat).sum(axis=2, keepdims=True)) * P
+
+
+def coloring_energy(ei, ej, w, states):
+    """Violated edge weight sum_{(i,j) in E} W_ij [sigma_i == sigma_j] per replica."""
+    w = _as_exact(w)
+    return (w[:, None] * (states[ei] == states[ej])).sum(axis=0)
+
+
+# ----------------------------------------------------------------------------
 # Max-k-SAT, single field P_i = P(sigma_i = 1) = sigmoid(h_i)
 # (Methods Eq. maxksat_F; SM "The MaxSAT problem" explicit gradient)
 # ----------------------------------------------------------------------------
@@ -387,7 +432,7 @@ def anneal(problem, h0, n_step, *, t_begin=0, t_end=None, schedule="exponential"
            gamma=1.0, lambda_max=1.0, opt=None, trace=None, cond=None):
     """Run anneal steps t_begin .. t_end-1 from fields h0 (copied, float64).
 
-    problem: ("maxcut", W) | ("bmincut", W) | ("bmincut", W, V) | ("sat", groups)
+    problem: ("maxcut", W) | ("bmincut", W) | ("bmincut", W, V) | ("coloring", W) | ("sat", groups)
     Returns (h, opt); pass ``opt`` back in to resume.  ``trace``, if a dict
     {t: None}, is filled with copies of h after step t (1-based count of steps done).
     ``cond``, if a dict {t: None}, is filled with the elementwise minimum over the
@@ -409,6 +454,8 @@ def anneal(problem, h0, n_step, *, t_begin=0, t_end=None, schedule="exponential"
             g = maxcut_grad(data, h, beta, gamma=gamma, mode=mode)
         elif kind == "bmincut":
             g = bmincut_grad(data, h, beta, lams[t], gamma=gamma, mode=mode, V=node_w)
+        elif kind == "coloring":
+            g = coloring_grad(data, h, beta, gamma=gamma, mode=mode)
         elif kind == "sat":
             g = sat_grad(data, h, beta, gamma=gamma)
         else:

@@ -474,3 +474,60 @@ def test_weighted_objective_is_the_coarsened_graph_of_tied_nodes():
     Ec, _, _ = O.bmincut_objective(cei, cej, cw, states, q, lam, V=V)
     Ef, _, _ = O.bmincut_objective(fg.ei, fg.ej, fg.w, states[comm], q, lam)
     assert np.array_equal(Ec + int(lam) * int((V * (V - 1)).sum()), Ef)
+
+
+# ---- graph colouring (q-state Potts; SM, problems of multi-valued variables)
+
+def test_coloring_free_energy_matches_enumeration():
+    g, W = _small_graph(5, 0.7, 41, "real")
+    q, beta = 3, 0.9
+    h = _rng(42).normal(size=(5, 2, q))
+    F = O.coloring_free_energy(W, h, beta)
+    for r in range(2):
+        z = np.exp(h[:, r] - h[:, r].max(axis=1, keepdims=True))
+        marg = z / z.sum(axis=1, keepdims=True)
+
+        def E(X):
+            return (g.w[None, :] * (X[:, g.ei] == X[:, g.ej])).sum(axis=1)
+
+        ref = O.mf_free_energy_by_enumeration(marg, E, beta)
+        assert F[r] == pytest.approx(ref, rel=1e-12, abs=1e-12)
+
+
+def test_coloring_exact_gradient_is_fd_of_F():
+    g, W = _small_graph(8, 0.5, 43, "real")
+    h = _rng(44).normal(size=(8, 2, 4))
+    ana = O.coloring_grad(W, h, 0.8, mode="exact")
+    fd = _fd(lambda x: O.coloring_free_energy(W, x, 0.8), h)
+    assert np.max(np.abs(ana - fd)) <= 1e-7 * max(1.0, np.max(np.abs(fd)))
+
+
+def test_coloring_paper_mode_reduces_to_exact():
+    g, W = _small_graph(10, 0.5, 45, "real")
+    h = _rng(46).normal(size=(10, 3, 3))
+    exact = O.coloring_grad(W, h, 1.1, mode="exact")
+    red = O.coloring_grad(W, h, 1.1, mode="paper", cf=np.ones(10), discretise=False)
+    assert np.allclose(red, exact, rtol=1e-12, atol=1e-14)
+
+
+def test_coloring_oracle_reaches_a_proper_colouring():
+    """A 3-colourable graph (a random graph on three planted colour classes, no edge
+    inside a class): brute force finds 0 violations, and so does the oracle's best
+    replica (exact mode, Adam, 1000 steps, beta 0.05 -> 20: a violation costs 1, so the
+    end temperature must be well below 1)."""
+    rng = _rng(47)
+    n = 12
+    cls = np.arange(n) % 3
+    ei, ej = [], []
+    for i in range(n):
+        for j in range(i + 1, n):
+            if cls[i] != cls[j] and rng.random() < 0.55:
+                ei.append(i); ej.append(j)
+    ei, ej = np.array(ei), np.array(ej)
+    w = np.ones(len(ei))
+    assert O.coloring_bruteforce(n, ei, ej, w, 3) == 0
+    W = O.coupling_matrix(n, ei, ej, w)
+    h0 = 0.001 * rng.normal(size=(n, 16, 3))
+    h, _ = O.anneal(("coloring", W), h0, 1000, mode="exact", beta_max=20.0)
+    E = O.coloring_energy(ei, ej, w, O.bmincut_states(h))
+    assert E.min() == 0

@@ -53,7 +53,11 @@ typedef enum {
   FEM_ERR_DEVICE = 7       /* a device-side bounds check failed                        */
 } fem_status;
 
-typedef enum { FEM_MAXCUT = 0, FEM_BMINCUT = 1, FEM_MAXKSAT = 2 } fem_kind;
+/* FEM_COLORING: graph colouring, the q-state Potts energy of violated edges
+ * E = sum_{(i,j) in E} W_ij delta(sigma_i, sigma_j) (SM, problems of multi-valued
+ * variables), on the bMinCut data path with the coupling's sign reversed and no
+ * balance term (lambda_max is ignored); the read-out energy is E itself. */
+typedef enum { FEM_MAXCUT = 0, FEM_BMINCUT = 1, FEM_MAXKSAT = 2, FEM_COLORING = 3 } fem_kind;
 
 /* Methods, "Different annealing schedules for the inverse temperature":
  *   exponential          beta(t) = exp(ln b_min + t (ln b_max - ln b_min)/(N_step - 1))

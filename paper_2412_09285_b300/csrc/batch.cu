@@ -31,6 +31,7 @@ struct BatchMember {
   const float* cf;
   const float* ca;
   const int32_t* nodew;
+  float cw, lam_scale;  // see BmcArgs
   float* h0;
   float* h1;
   float* m;
@@ -64,6 +65,8 @@ __device__ void run_bmincut_item(const BatchMember& b, const BatchItem& it, cons
   a.cf = b.cf;
   a.ca = b.ca;
   a.nodew = b.nodew;
+  a.cw = b.cw;
+  a.lam_scale = b.lam_scale;
   a.n = b.n;
   a.R = b.R;
   a.wpn = b.wpn;
@@ -260,6 +263,8 @@ static fem_status batch_prepare(Batch* b, cudaStream_t s) {
     m.cf = p->cnorm;
     m.ca = p->cnorm2;
     m.nodew = p->nodew;
+    m.cw = p->coloring ? 1.f : (p->grad_mode == FEM_GRAD_EXACT ? -2.f : -1.f);
+    m.lam_scale = p->coloring ? 0.f : 1.f;
     m.h0 = p->h[0];
     m.h1 = p->h[1];
     m.m = p->m;

@@ -24,6 +24,8 @@ struct BmcArgs {
   const float* cf;
   const float* ca;
   const int32_t* nodew;  // node weights V_i, NULL: all 1
+  float cw;              // coupling coefficient: bMinCut -2 (exact) / -1 (paper, times c^f); colouring +1
+  float lam_scale;       // 1 for bMinCut, 0 for colouring (no balance term)
   int32_t n, R, wpn, opt;
   const float* h_in;
   float* h_out;
@@ -217,6 +219,7 @@ __device__ __forceinline__ void bmincut_element(const BmcArgs& a, const StepScal
     // large s-independent parts (deg/q, lambda N/q) of ghat.
     float P[Q], lnP[Q];
     softmax_q<Q>(h, P, lnP);
+    const float lam = s.lambda * a.lam_scale;
     int32_t nc[Q];
     unsigned long long ps[Q];
 #pragma unroll
@@ -234,11 +237,13 @@ __device__ __forceinline__ void bmincut_element(const BmcArgs& a, const StepScal
         // node weights (SM, node-weighted balance term): lambda c^a_i V_i [n(s) - V_i e_i(s)]
         // (paper) and 2 lambda V_i [sum_j V_j P_j(s) - V_i P_i(s)] (exact); V_i = 1 gives
         // the unweighted forms with the same roundings
+        // the coupling term enters with a.cw: -c^f / -2 (bMinCut: cut edges are cheap to
+        // keep together) or +c^f / +1 (colouring: same colours across an edge cost)
         if (MODE == FEM_GRAD_PAPER) {
-          d = -cf * (acc[q] - acc[q2]) + s.lambda * (ca * (float)Vi) * (float)(nc[q] - nc[q2]);
+          d = (a.cw * cf) * (acc[q] - acc[q2]) + lam * (ca * (float)Vi) * (float)(nc[q] - nc[q2]);
         } else {
           const float dcol = (float)(long long)(ps[q] - ps[q2]) * kPsumInv;
-          d = -2.f * (acc[q] - acc[q2]) + 2.f * s.lambda * (float)Vi * (dcol - (float)Vi * (P[q] - P[q2]));
+          d = a.cw * (acc[q] - acc[q2]) + 2.f * lam * (float)Vi * (dcol - (float)Vi * (P[q] - P[q2]));
         }
         d = fmaf(h[q] - h[q2], s.inv_beta, d);
         c = fmaf(P[q2], d, c);

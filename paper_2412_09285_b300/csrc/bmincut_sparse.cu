@@ -180,7 +180,8 @@ template <int Q>
 __global__ void __launch_bounds__(kRedThreads) k_bmincut_finish(
     const int64_t* __restrict__ part_i, const double* __restrict__ part_f,
     const int64_t* __restrict__ part_cnt, int32_t nblk, int32_t R, int32_t intw, int32_t lam_is_int,
-    double lam, int64_t sum_v2, int64_t* __restrict__ e_i, double* __restrict__ e_f) {
+    double lam, int64_t sum_v2, int32_t coloring, int64_t wtot_i, double wtot_f, int64_t* __restrict__ e_i,
+    double* __restrict__ e_f) {
   __shared__ int64_t shi[kRedThreads];
   __shared__ double shf[kRedThreads];
   const int r = blockIdx.x;
@@ -193,7 +194,10 @@ __global__ void __launch_bounds__(kRedThreads) k_bmincut_finish(
     const int64_t sz = column_sum<int64_t>(part_cnt, nblk, (size_t)R * Q, (size_t)r * Q + q, shi);
     bal += sz * sz;
   }
-  if (threadIdx.x == 0) {
+  if (threadIdx.x == 0 && coloring) {  // violated edges = all edges - cut edges
+    e_i[r] = intw ? wtot_i - ci : 0;
+    e_f[r] = intw ? (double)(wtot_i - ci) : wtot_f - cfv;
+  } else if (threadIdx.x == 0) {
     double ef;
     if (intw && lam_is_int) {
       const int64_t ei = ci + (int64_t)lam * bal;
@@ -243,6 +247,8 @@ fem_status steps_q(Problem* p, const std::vector<StepScalars>& sc, int t_begin, 
   a.cf = p->cnorm;
   a.ca = p->cnorm2;
   a.nodew = p->nodew;
+  a.cw = p->coloring ? 1.f : (p->grad_mode == FEM_GRAD_EXACT ? -2.f : -1.f);
+  a.lam_scale = p->coloring ? 0.f : 1.f;
   a.n = p->n;
   a.R = p->R;
   a.wpn = p->words_per_node;
@@ -309,7 +315,8 @@ fem_status readout_q(Problem* p, cudaStream_t st) {
   const double lam = p->lambda_max;
   k_bmincut_finish<Q><<<p->R, kRedThreads, 0, st>>>(p->part_i, p->part_f, p->part_cnt, p->part_blocks, p->R,
                                                      p->int_w ? 1 : 0, lam == std::floor(lam) ? 1 : 0, lam,
-                                                     p->nodew_sq, p->energy_i, p->energy_f);
+                                                     p->nodew_sq, p->coloring ? 1 : 0, p->wtot_i, p->wtot_f,
+                                                     p->energy_i, p->energy_f);
   k_argmin_replica<<<1, 1024, 0, st>>>(p->energy_f, p->R, p->best);
   k_bmincut_states<Q><<<(p->n + 255) / 256 < 1024 ? (p->n + 255) / 256 : 1024, 256, 0, st>>>(
       words, p->n, p->R, p->words_per_node, p->best, p->states_dev, 0);

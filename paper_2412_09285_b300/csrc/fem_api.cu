@@ -145,6 +145,8 @@ static const float* current_fields(Problem* p) { return fields_for_step(p, p->st
 struct HostGraph {
   int64_t n_edges = 0;
   bool unit = true, integer = true;
+  int64_t wsum_i = 0;   // sum of the edge weights (exact when they are integers)
+  double wsum_f = 0.0;
   std::vector<int32_t> row_ptr;
   std::vector<uint32_t> col;
   std::vector<float> wf, cnorm, cnorm2;
@@ -171,6 +173,8 @@ static fem_status host_graph(int32_t kind, int32_t q, const fem_problem_desc* d,
       return fail(FEM_ERR_INVALID_ARG, "edge %lld: bMinCut weights must be positive", (long long)e);
     if (std::fabs(w) != 1.0) unit = false;
     if (w != std::rint(w) || std::fabs(w) > 16777216.0) integer = false;
+    g.wsum_f += w;
+    if (integer) g.wsum_i += (int64_t)w;
     deg[i]++;
     deg[j]++;
   }
@@ -414,12 +418,16 @@ fem_status fem_create_problem(const fem_problem_desc* d, void* stream, fem_probl
   g_last_error.clear();
   if (!d || !out) return fail(FEM_ERR_INVALID_ARG, "desc and out must be non-NULL");
   *out = nullptr;
-  if (d->kind < FEM_MAXCUT || d->kind > FEM_MAXKSAT) return fail(FEM_ERR_INVALID_ARG, "unknown kind %d", d->kind);
+  if (d->kind < FEM_MAXCUT || d->kind > FEM_COLORING) return fail(FEM_ERR_INVALID_ARG, "unknown kind %d", d->kind);
   if (d->n < 1) return fail(FEM_ERR_INVALID_ARG, "n must be >= 1");
   if ((d->kind == FEM_MAXCUT || d->kind == FEM_MAXKSAT) && d->q != 2)
     return fail(FEM_ERR_INVALID_ARG, "q must be 2 for MaxCut and Max-k-SAT");
-  if (d->kind == FEM_BMINCUT && (d->q < 2 || d->q > 8))
-    return fail(FEM_ERR_UNSUPPORTED, "bMinCut supports 2 <= q <= 8");
+  if ((d->kind == FEM_BMINCUT || d->kind == FEM_COLORING) && (d->q < 2 || d->q > 8))
+    return fail(FEM_ERR_UNSUPPORTED, "bMinCut and colouring support 2 <= q <= 8");
+  if (d->kind == FEM_COLORING && (d->dense_J || d->node_weight))
+    return fail(FEM_ERR_INVALID_ARG, "colouring takes a sparse graph without node weights");
+  // colouring runs on the bMinCut data path (same normalisers, counts and read-out)
+  const int32_t kind = d->kind == FEM_COLORING ? FEM_BMINCUT : d->kind;
   cudaStream_t s = (cudaStream_t)stream;
   // 1. host-side validation and construction (no CUDA call yet)
   HostGraph hg;
@@ -439,7 +447,7 @@ fem_status fem_create_problem(const fem_problem_desc* d, void* stream, fem_probl
   } else if (d->kind == FEM_MAXKSAT) {
     if ((st = host_sat(d, hs)) != FEM_OK) return st;
   } else {
-    if ((st = host_graph(d->kind, d->q, d, hg)) != FEM_OK) return st;
+    if ((st = host_graph(kind, d->q, d, hg)) != FEM_OK) return st;
   }
   std::vector<int32_t> nodew;
   int64_t nodew_sq = d->n;
@@ -461,7 +469,10 @@ fem_status fem_create_problem(const fem_problem_desc* d, void* stream, fem_probl
   }
   // 2. device side
   std::unique_ptr<fem_problem> p(new fem_problem());
-  p->kind = d->kind;
+  p->kind = kind;
+  p->coloring = d->kind == FEM_COLORING;
+  p->wtot_i = hg.wsum_i;
+  p->wtot_f = hg.wsum_f;
   p->n = d->n;
   p->q = d->q;
   FEM_CUDA(cudaGetDevice(&p->device));
@@ -581,7 +592,9 @@ fem_status fem_anneal(fem_problem_t p, const fem_anneal_params* a, void* stream)
       return fail(FEM_ERR_STATE, "a resumed call must keep replicas, n_steps, grad_mode and optimizer");
   }
   if (a->t_end == a->t_begin) return FEM_OK;
-  const std::vector<StepScalars> sc = make_step_scalars(*a, p->kind != FEM_BMINCUT);
+  fem_anneal_params a_eff = *a;
+  if (p->coloring) a_eff.lambda_max = 0.0;  // no balance term
+  const std::vector<StepScalars> sc = make_step_scalars(a_eff, p->kind != FEM_BMINCUT);
   auto run = [&](cudaStream_t st_) -> fem_status {
     if (p->dense) return dense_steps(p, sc, a->t_begin, st_);
     if (p->kind == FEM_MAXCUT) return maxcut_sparse_steps(p, *a, sc, st_);

@@ -48,6 +48,9 @@ struct Problem {
   float* cnorm = nullptr;      // MaxCut c_i = 1/sum|W_ij| (when !unit_w); bMinCut c^f
   float* cnorm2 = nullptr;     // bMinCut c^a
   int32_t* nodew = nullptr;    // bMinCut node weights V_i (NULL: all 1)
+  bool coloring = false;       // FEM_COLORING on the bMinCut data path (kind == FEM_BMINCUT)
+  int64_t wtot_i = 0;          // sum of the edge weights (integer weights)
+  double wtot_f = 0.0;         // the same in fp64
   int64_t nodew_sq = 0;        // sum_i V_i^2 (n when unweighted)
 
   // ---- clauses (Max-k-SAT)

@@ -24,7 +24,9 @@ FEM_OPT_ADAM, FEM_OPT_RMSPROP, FEM_OPT_SGD = 0, 1, 2
 FEM_GRAD_EXACT, FEM_GRAD_PAPER = 0, 1
 FEM_PREC_FP32, FEM_PREC_BF16, FEM_PREC_BF16X2, FEM_PREC_FP8 = 0, 1, 2, 3
 
-KINDS = {"maxcut": FEM_MAXCUT, "bmincut": FEM_BMINCUT, "sat": FEM_MAXKSAT}
+FEM_COLORING = 3
+KINDS = {"maxcut": FEM_MAXCUT, "bmincut": FEM_BMINCUT, "sat": FEM_MAXKSAT, "coloring": FEM_COLORING}
+Q_STATE_KINDS = ("bmincut", "coloring")
 SCHEDULES = {"exponential": FEM_SCHED_EXPONENTIAL, "inverse_proportional": FEM_SCHED_INVERSE_PROPORTIONAL}
 OPTIMIZERS = {"adam": FEM_OPT_ADAM, "rmsprop": FEM_OPT_RMSPROP, "sgd": FEM_OPT_SGD}
 GRAD_MODES = {"exact": FEM_GRAD_EXACT, "paper": FEM_GRAD_PAPER}
@@ -284,13 +286,13 @@ class Problem:
         return self
 
     def fields(self):
-        shape = (self.n, self.replicas) if self.kind != "bmincut" else (self.n, self.replicas, self.q)
+        shape = (self.n, self.replicas) if self.kind not in Q_STATE_KINDS else (self.n, self.replicas, self.q)
         out = np.empty(shape, np.float32)
         fem_read_fields(self.handle, out, self.stream)
         return out
 
     def _shape(self):
-        return (self.n, self.replicas) if self.kind != "bmincut" else (self.n, self.replicas, self.q)
+        return (self.n, self.replicas) if self.kind not in Q_STATE_KINDS else (self.n, self.replicas, self.q)
 
     def state(self):
         """(h, m, v) as float32 host arrays (a checkpoint, with info()['steps_done'])."""

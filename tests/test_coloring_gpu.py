@@ -1,0 +1,109 @@
+"""Graph colouring (q-state Potts energy of violated edges) on the bMinCut data path,
+against the FP64 oracle: softmax marginals within 1e-4 over the first 50 steps (exact
+mode; paper mode on agreeing replicas), violation counts bit-exact for the GPU's own
+states, a planted 3-colourable graph coloured far better than at random, and a
+colouring member of a batch equal to annealing it alone."""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2412_09285_b300 import instances as I
+
+pytestmark = pytest.mark.gpu
+
+TOL_P = 1e-4
+D_COND = 1e-6
+MAX_ILL = 5e-3
+CHECK = [1, 2, 5, 10, 20, 35, 50]
+
+
+@pytest.fixture(scope="module")
+def fem():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA device")
+    from paper_2412_09285_b300 import build
+    build.build()
+    from paper_2412_09285_b300 import fem as F
+    return F
+
+
+def _softmax(h):
+    e = np.exp(h - h.max(axis=-1, keepdims=True))
+    return e / e.sum(axis=-1, keepdims=True)
+
+
+def _planted(n, q, deg, seed):
+    """Random graph with no edge inside one of q planted colour classes (q-colourable)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    m = int(n * deg / 2)
+    cls = rng.integers(0, q, size=n)
+    i = rng.integers(0, n, size=4 * m)
+    j = rng.integers(0, n, size=4 * m)
+    keep = (cls[i] != cls[j])
+    a, b = np.minimum(i[keep], j[keep]), np.maximum(i[keep], j[keep])
+    key = np.unique(a.astype(np.int64) * n + b)[:m]
+    return I.Graph(n, (key // n).astype(np.int32), (key % n).astype(np.int32), np.ones(key.size))
+
+
+@pytest.mark.parametrize("mode", ["exact", "paper"])
+def test_coloring_marginals_first_50_steps(fem, mode):
+    g = I.rgg(800, 8.0, seed=101)
+    W = O.coupling_matrix(g.n, g.ei, g.ej, g.w)
+    h0 = I.initial_fields(800, 16, seed=102, q=3)
+    P = fem.Problem("coloring", graph=g, q=3)
+    got, t = {}, 0
+    for T in CHECK:
+        P.anneal(h_init=h0 if t == 0 else None, replicas=16, n_steps=1000, t_begin=t, t_end=T,
+                 grad_mode=mode, beta_max=20.0)
+        got[T] = P.fields()
+        t = T
+    tr = {t: None for t in CHECK}
+    cd = {t: None for t in CHECK}
+    O.anneal(("coloring", W), h0.astype(np.float64), 1000, t_end=50, mode=mode, beta_max=20.0, trace=tr, cond=cd)
+    agree = np.ones(16, bool)
+    if mode == "paper":
+        for T in CHECK:
+            agree &= np.all(np.argmax(got[T], axis=2) == np.argmax(tr[T], axis=2), axis=0)
+        assert agree.sum() >= 12, agree.sum()
+    for T in CHECK:
+        err = np.abs(_softmax(got[T][:, agree].astype(np.float64)) - _softmax(tr[T][:, agree]))
+        ok = np.broadcast_to((cd[T][:, agree] >= D_COND).all(axis=-1, keepdims=True), err.shape)
+        assert (~ok).mean() <= MAX_ILL
+        assert err[ok].max() <= TOL_P, (mode, T, float(err[ok].max()))
+
+
+def test_coloring_violations_bit_exact_and_planted_graph_coloured(fem):
+    g = _planted(3000, 3, 6.0, seed=103)
+    h0 = I.initial_fields(g.n, 32, seed=104, q=3)
+    P = fem.Problem("coloring", graph=g, q=3).anneal(h_init=h0, n_steps=1000, beta_max=20.0)
+    st = P.states()
+    E = O.coloring_energy(g.ei, g.ej, g.w, st)
+    res = P.best()
+    assert np.array_equal(res["energy_i64"], E)
+    assert res["best_replica"] == int(np.argmin(E))
+    print(f"\nplanted 3-colourable graph, n = 3000, {g.ei.size} edges: best replica violates "
+          f"{int(E.min())} edges (mean over replicas {E.mean():.1f})")
+    # a random colouring violates a third of the edges; a planted degree-6 instance is in
+    # the hard regime of 3-colouring, so the bar is relative
+    assert E.min() <= 0.02 * g.ei.size
+
+
+def test_coloring_member_in_a_batch_equals_alone(fem):
+    gs = [I.rgg(600, 8.0, seed=105 + k) for k in range(2)]
+    h0 = [I.initial_fields(600, 16, seed=107 + k, q=4) for k in range(2)]
+    kinds = ["coloring", "bmincut"]
+    alone = [fem.Problem(k, graph=g, q=4).anneal(h_init=h, n_steps=80, lambda_max=0.5).state()
+             for k, g, h in zip(kinds, gs, h0)]
+    probs = [fem.Problem(k, graph=g, q=4) for k, g in zip(kinds, gs)]
+    fem.Batch(probs).anneal(h_inits=h0, replicas=16, n_steps=80, lambda_max=0.5)
+    for p, ref in zip(probs, alone):
+        for x, y in zip(p.state(), ref):
+            assert np.array_equal(x, y)
+
+
+def test_coloring_rejects_node_weights(fem):
+    g = I.rgg(60, 6.0, seed=109)
+    with pytest.raises(fem.FemError) as e:
+        fem.Problem("coloring", graph=g, q=3, node_weight=np.ones(60))
+    assert e.value.status == fem.FEM_ERR_INVALID_ARG

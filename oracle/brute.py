@@ -11,7 +11,7 @@ from __future__ import annotations
 import numpy as np
 
 __all__ = [
-    "all_binary", "all_qary", "maxcut_bruteforce", "bmincut_bruteforce", "coloring_bruteforce",
+    "all_binary", "all_qary", "maxcut_bruteforce", "bmincut_bruteforce", "coloring_bruteforce", "qubo_bruteforce",
     "sat_bruteforce", "mf_free_energy_by_enumeration",
 ]
 
@@ -51,6 +51,13 @@ def coloring_bruteforce(n, ei, ej, w, q):
     """Minimum violated edge weight sum_E W_ij [sigma_i == sigma_j] over all q^n colourings."""
     X = all_qary(n, q)
     return (np.asarray(w)[None, :] * (X[:, ei] == X[:, ej])).sum(axis=1).min()
+
+
+def qubo_bruteforce(n, ei, ej, w, d):
+    """Minimum of sum_E 2 w sigma_i sigma_j + sum_i d_i sigma_i over all 2^n binary states."""
+    X = all_binary(n).astype(np.float64)
+    E = (2.0 * np.asarray(w)[None, :] * X[:, ei] * X[:, ej]).sum(axis=1) + X @ np.asarray(d, np.float64)
+    return E.min()
 
 
 def sat_bruteforce(n, ptr, lits):

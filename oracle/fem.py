@@ -42,6 +42,7 @@ __all__ = [
     "maxcut_free_energy", "maxcut_grad", "maxcut_normaliser",
     "bmincut_free_energy", "bmincut_grad", "bmincut_normalisers",
     "coloring_free_energy", "coloring_grad", "coloring_energy",
+    "qubo_free_energy", "qubo_grad", "qubo_states", "qubo_energy",
     "sat_arrays", "sat_free_energy", "sat_grad",
     "Adam", "RMSprop", "SGD", "make_optimizer", "anneal",
     "maxcut_states", "maxcut_cut_edges", "maxcut_cut_spin", "maxcut_cut_matrix",
@@ -241,6 +242,43 @@ def bmincut_grad(W, h, beta, lam, gamma=1.0, mode="paper", cf=None, ca=None, dis
 
 
 # ----------------------------------------------------------------------------
+# QUBO (SM, COPs that translate into QUBO formulations): binary sigma_i in {0, 1},
+#   E(sigma) = sum_{i != j} Q_ij sigma_i sigma_j + sum_i d_i sigma_i,
+# Q symmetric with zero diagonal and d the diagonal of the paper's Q (sigma_i^2 =
+# sigma_i for binary variables, so the diagonal is linear).  Single field
+# p_i = P(sigma_i = 1) = sigmoid(h_i).
+# ----------------------------------------------------------------------------
+
+def qubo_free_energy(Q, d, h, beta):
+    """F = sum_{i != j} Q_ij p_i p_j + sum_i d_i p_i + (1/beta) sum_i [p ln p + (1-p) ln(1-p)]
+    (U_MF is the exact expectation of E under the product distribution).  h: [N, R] -> [R]."""
+    p = sigmoid(h)
+    U = (p * np.asarray(Q @ p)).sum(axis=0) + (np.asarray(d, np.float64)[:, None] * p).sum(axis=0)
+    return U + (_xlogx(p) + _xlogx(1.0 - p)).sum(axis=0) / beta
+
+
+def qubo_grad(Q, d, h, beta, gamma=1.0):
+    """dF/dh_i = gamma p_i (1 - p_i) [2 sum_j Q_ij p_j + d_i + h_i / beta]
+    (Eq. gradients_wrt_h for one field: ln(p / (1 - p)) = h)."""
+    p = sigmoid(h)
+    return gamma * p * (1.0 - p) * (2.0 * np.asarray(Q @ p) + np.asarray(d, np.float64)[:, None] + h / beta)
+
+
+def qubo_states(h):
+    """sigma_i = 1 where h_i >= 0 (p >= 1/2) else 0.  h: [N, R] -> int8 [N, R]."""
+    return (np.asarray(h) >= 0).astype(np.int8)
+
+
+def qubo_energy(ei, ej, w, d, sigma):
+    """E = sum_{(i,j) in E} 2 Q_ij sigma_i sigma_j + sum_i d_i sigma_i per replica (each
+    off-diagonal pair listed once in (ei, ej, w))."""
+    w = _as_exact(w)
+    d = _as_exact(d)
+    s = sigma.astype(np.int64)
+    return (2 * w[:, None] * s[ei] * s[ej]).sum(axis=0) + (d[:, None] * s).sum(axis=0)
+
+
+# ----------------------------------------------------------------------------
 # Graph colouring (q-state Potts; SM, problems of multi-valued variables):
 #   E(sigma) = sum_{(i,j) in E} W_ij delta(sigma_i, sigma_j)   (violated edges)
 #   U_MF = sum_{(i,j) in E} W_ij sum_s P_i(s) P_j(s)
@@ -432,7 +470,8 @@ def anneal(problem, h0, n_step, *, t_begin=0, t_end=None, schedule="exponential"
            gamma=1.0, lambda_max=1.0, opt=None, trace=None, cond=None):
     """Run anneal steps t_begin .. t_end-1 from fields h0 (copied, float64).
 
-    problem: ("maxcut", W) | ("bmincut", W) | ("bmincut", W, V) | ("coloring", W) | ("sat", groups)
+    problem: ("maxcut", W) | ("bmincut", W) | ("bmincut", W, V) | ("coloring", W) | ("qubo", (Q, d))
+             | ("sat", groups)
     Returns (h, opt); pass ``opt`` back in to resume.  ``trace``, if a dict
     {t: None}, is filled with copies of h after step t (1-based count of steps done).
     ``cond``, if a dict {t: None}, is filled with the elementwise minimum over the
@@ -456,6 +495,8 @@ def anneal(problem, h0, n_step, *, t_begin=0, t_end=None, schedule="exponential"
             g = bmincut_grad(data, h, beta, lams[t], gamma=gamma, mode=mode, V=node_w)
         elif kind == "coloring":
             g = coloring_grad(data, h, beta, gamma=gamma, mode=mode)
+        elif kind == "qubo":
+            g = qubo_grad(data[0], data[1], h, beta, gamma=gamma)
         elif kind == "sat":
             g = sat_grad(data, h, beta, gamma=gamma)
         else:

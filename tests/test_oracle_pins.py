@@ -531,3 +531,65 @@ def test_coloring_oracle_reaches_a_proper_colouring():
     h, _ = O.anneal(("coloring", W), h0, 1000, mode="exact", beta_max=20.0)
     E = O.coloring_energy(ei, ej, w, O.bmincut_states(h))
     assert E.min() == 0
+
+
+# ---- QUBO (SM, COPs that translate into QUBO formulations)
+
+def _qubo(n, p, seed):
+    g = I.er_gnp(n, p, seed, "real")
+    Q = O.coupling_matrix(g.n, g.ei, g.ej, g.w)
+    d = _rng(seed + 1).normal(size=n)
+    return g, Q, d
+
+
+def test_qubo_free_energy_matches_enumeration():
+    g, Q, d = _qubo(6, 0.6, 51)
+    beta = 0.8
+    h = _rng(53).normal(size=(6, 2))
+    F = O.qubo_free_energy(Q, d, h, beta)
+    for r in range(2):
+        p = O.sigmoid(h[:, r])
+        marg = np.stack([1.0 - p, p], axis=1)           # states 0, 1
+
+        def E(X):
+            Xf = X.astype(np.float64)
+            return (2.0 * g.w[None, :] * Xf[:, g.ei] * Xf[:, g.ej]).sum(axis=1) + Xf @ d
+
+        ref = O.mf_free_energy_by_enumeration(marg, E, beta)
+        assert F[r] == pytest.approx(ref, rel=1e-12, abs=1e-12)
+
+
+def test_qubo_gradient_is_fd_of_F():
+    g, Q, d = _qubo(9, 0.5, 54)
+    h = _rng(56).normal(size=(9, 3))
+    ana = O.qubo_grad(Q, d, h, 0.7)
+    fd = _fd(lambda x: O.qubo_free_energy(Q, d, x, 0.7), h)
+    assert np.max(np.abs(ana - fd)) <= 1e-7 * max(1.0, np.max(np.abs(fd)))
+
+
+def test_maxcut_as_qubo_free_energy_identity():
+    """MaxCut as a QUBO: -cut = sum_E 2 w s_i s_j - sum_i (sum_j w_ij) s_i with s in {0, 1},
+    i.e. Q = W, d_i = -sum_j W_ij.  Then U_QUBO = -cut_MF (each edge once) while the
+    MaxCut free energy counts ordered pairs, so F_maxcut(h, beta) = 2 F_QUBO(h, 2 beta);
+    the sigmoid fields agree (p_i = P(sigma_i = +1) = P(s_i = 1))."""
+    g, W = _small_graph(10, 0.5, 57, "real")
+    d = -np.asarray(W.sum(axis=1)).ravel()
+    h = _rng(58).normal(size=(10, 3))
+    assert np.allclose(O.maxcut_free_energy(W, h, 0.9), 2.0 * O.qubo_free_energy(W, d, h, 1.8),
+                       rtol=1e-12, atol=1e-12)
+
+
+def test_qubo_oracle_reaches_the_maximum_independent_set():
+    """Maximum independent set as a QUBO (a prominent example listed in the SM):
+    E = -sum_i s_i + 2 sum_E s_i s_j (penalty 2 per violated edge); its minimum is minus
+    the largest independent set.  Brute force over 2^14 states and the oracle's best
+    replica (Adam, 1000 steps, beta 0.05 -> 20) agree."""
+    g = I.er_gnp(14, 0.3, 59, "unit")
+    w = np.ones(g.ei.size)                      # 2 w s_i s_j with w = 1: penalty 2 per edge
+    d = -np.ones(14)
+    best = O.qubo_bruteforce(14, g.ei, g.ej, w, d)
+    Q = O.coupling_matrix(14, g.ei, g.ej, w)
+    h0 = 0.001 * _rng(60).normal(size=(14, 32))
+    h, _ = O.anneal(("qubo", (Q, d)), h0, 1000, mode="exact", beta_max=20.0)
+    E = O.qubo_energy(g.ei, g.ej, w, d, O.qubo_states(h))
+    assert E.min() == best

@@ -57,7 +57,13 @@ typedef enum {
  * E = sum_{(i,j) in E} W_ij delta(sigma_i, sigma_j) (SM, problems of multi-valued
  * variables), on the bMinCut data path with the coupling's sign reversed and no
  * balance term (lambda_max is ignored); the read-out energy is E itself. */
-typedef enum { FEM_MAXCUT = 0, FEM_BMINCUT = 1, FEM_MAXKSAT = 2, FEM_COLORING = 3 } fem_kind;
+/* FEM_QUBO: binary sigma_i in {0, 1} with E = sum_{i != j} Q_ij sigma_i sigma_j +
+ * sum_i d_i sigma_i (SM, COPs that translate into QUBO formulations; the diagonal of
+ * Q is the linear term d because sigma_i^2 = sigma_i).  The graph lists each
+ * off-diagonal pair once with w = Q_ij; d comes from fem_problem_desc.linear.  One
+ * sigmoid field per variable, FEM_GRAD_EXACT only; the read-out energy is E and a
+ * variable's state is 1 where h >= 0. */
+typedef enum { FEM_MAXCUT = 0, FEM_BMINCUT = 1, FEM_MAXKSAT = 2, FEM_COLORING = 3, FEM_QUBO = 4 } fem_kind;
 
 /* Methods, "Different annealing schedules for the inverse temperature":
  *   exponential          beta(t) = exp(ln b_min + t (ln b_max - ln b_min)/(N_step - 1))
@@ -125,6 +131,7 @@ typedef struct fem_problem* fem_problem_t; /* opaque; owned by the library until
  *                where a coarsened node weighs the number of nodes it groups), and
  *                the read-out energy cut + lambda_max sum_s [n_s^2 - sum_{i in s} V_i^2]
  *                with n_s = sum_{i in s} V_i.  NULL: every V_i = 1.
+ *   linear       optional (QUBO only), n coefficients d_i of the linear term; NULL: 0.
  */
 typedef struct {
   int32_t kind;
@@ -139,6 +146,7 @@ typedef struct {
   const int64_t* clause_ptr;
   const int32_t* lits;
   const double* node_weight;
+  const double* linear;
 } fem_problem_desc;
 
 /* Anneal parameters.

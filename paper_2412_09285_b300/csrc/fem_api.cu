@@ -418,16 +418,19 @@ fem_status fem_create_problem(const fem_problem_desc* d, void* stream, fem_probl
   g_last_error.clear();
   if (!d || !out) return fail(FEM_ERR_INVALID_ARG, "desc and out must be non-NULL");
   *out = nullptr;
-  if (d->kind < FEM_MAXCUT || d->kind > FEM_COLORING) return fail(FEM_ERR_INVALID_ARG, "unknown kind %d", d->kind);
+  if (d->kind < FEM_MAXCUT || d->kind > FEM_QUBO) return fail(FEM_ERR_INVALID_ARG, "unknown kind %d", d->kind);
   if (d->n < 1) return fail(FEM_ERR_INVALID_ARG, "n must be >= 1");
-  if ((d->kind == FEM_MAXCUT || d->kind == FEM_MAXKSAT) && d->q != 2)
-    return fail(FEM_ERR_INVALID_ARG, "q must be 2 for MaxCut and Max-k-SAT");
+  if ((d->kind == FEM_MAXCUT || d->kind == FEM_MAXKSAT || d->kind == FEM_QUBO) && d->q != 2)
+    return fail(FEM_ERR_INVALID_ARG, "q must be 2 for MaxCut, Max-k-SAT and QUBO");
+  if (d->linear && d->kind != FEM_QUBO) return fail(FEM_ERR_INVALID_ARG, "linear applies to QUBO problems only");
+  if (d->kind == FEM_QUBO && (d->dense_J || d->node_weight))
+    return fail(FEM_ERR_INVALID_ARG, "QUBO takes a sparse graph of off-diagonal entries and optional linear terms");
   if ((d->kind == FEM_BMINCUT || d->kind == FEM_COLORING) && (d->q < 2 || d->q > 8))
     return fail(FEM_ERR_UNSUPPORTED, "bMinCut and colouring support 2 <= q <= 8");
   if (d->kind == FEM_COLORING && (d->dense_J || d->node_weight))
     return fail(FEM_ERR_INVALID_ARG, "colouring takes a sparse graph without node weights");
   // colouring runs on the bMinCut data path (same normalisers, counts and read-out)
-  const int32_t kind = d->kind == FEM_COLORING ? FEM_BMINCUT : d->kind;
+  const int32_t kind = d->kind == FEM_COLORING ? FEM_BMINCUT : (d->kind == FEM_QUBO ? FEM_MAXCUT : d->kind);
   cudaStream_t s = (cudaStream_t)stream;
   // 1. host-side validation and construction (no CUDA call yet)
   HostGraph hg;
@@ -448,6 +451,30 @@ fem_status fem_create_problem(const fem_problem_desc* d, void* stream, fem_probl
     if ((st = host_sat(d, hs)) != FEM_OK) return st;
   } else {
     if ((st = host_graph(kind, d->q, d, hg)) != FEM_OK) return st;
+  }
+  // QUBO: the gradient's per-node constant sum_j Q_ij + d_i and the linear terms
+  std::vector<float> qoff;
+  std::vector<double> qlin_f;
+  std::vector<int64_t> qlin_i;
+  bool qlin_int = true;
+  if (d->kind == FEM_QUBO) {
+    std::vector<double> rs(d->n, 0.0);
+    for (int64_t e = 0; e < d->n_edges; ++e) {
+      const double w = d->w ? d->w[e] : 1.0;
+      rs[d->ei[e]] += w;
+      rs[d->ej[e]] += w;
+    }
+    qoff.resize(d->n);
+    qlin_f.resize(d->n);
+    qlin_i.resize(d->n);
+    for (int32_t i = 0; i < d->n; ++i) {
+      const double li = d->linear ? d->linear[i] : 0.0;
+      if (!std::isfinite(li)) return fail(FEM_ERR_INVALID_ARG, "linear[%d] must be finite", i);
+      if (li != std::rint(li) || std::fabs(li) > 1e15) qlin_int = false;
+      qlin_f[i] = li;
+      qlin_i[i] = qlin_int ? (int64_t)li : 0;
+      qoff[i] = (float)(rs[i] + li);
+    }
   }
   std::vector<int32_t> nodew;
   int64_t nodew_sq = d->n;
@@ -471,6 +498,8 @@ fem_status fem_create_problem(const fem_problem_desc* d, void* stream, fem_probl
   std::unique_ptr<fem_problem> p(new fem_problem());
   p->kind = kind;
   p->coloring = d->kind == FEM_COLORING;
+  p->qubo = d->kind == FEM_QUBO;
+  p->qlin_int = qlin_int;
   p->wtot_i = hg.wsum_i;
   p->wtot_f = hg.wsum_f;
   p->n = d->n;
@@ -481,6 +510,9 @@ fem_status fem_create_problem(const fem_problem_desc* d, void* stream, fem_probl
   else st = d->kind == FEM_MAXKSAT ? upload_sat(p.get(), hs, s) : upload_graph(p.get(), hg, s);
   p->nodew_sq = nodew_sq;
   if (st == FEM_OK && !nodew.empty()) st = upload(p.get(), &p->nodew, nodew, s);
+  if (st == FEM_OK && p->qubo) st = upload(p.get(), &p->qoff, qoff, s);
+  if (st == FEM_OK && p->qubo) st = upload(p.get(), &p->qlin_f, qlin_f, s);
+  if (st == FEM_OK && p->qubo) st = upload(p.get(), &p->qlin_i, qlin_i, s);
   if (st == FEM_OK) st = dev_alloc_t(p.get(), &p->err, 1);
   if (st == FEM_OK) {
     const cudaError_t e1 = cudaMemsetAsync(p->err, 0, sizeof(int32_t), s);
@@ -522,8 +554,10 @@ fem_status fem_anneal(fem_problem_t p, const fem_anneal_params* a, void* stream)
     if (a->t_begin > 0 && a->precision != p->precision)
       return fail(FEM_ERR_STATE, "a resumed call must keep the precision");
   } else if (p->kind == FEM_MAXCUT && R % 32 != 0) {
-    return fail(FEM_ERR_UNSUPPORTED, "sparse MaxCut needs replicas %% 32 == 0");
+    return fail(FEM_ERR_UNSUPPORTED, "sparse MaxCut and QUBO need replicas %% 32 == 0");
   }
+  if (p->qubo && a->grad_mode != FEM_GRAD_EXACT)
+    return fail(FEM_ERR_UNSUPPORTED, "QUBO has the exact gradient only (the paper defines no discretised form)");
   if (p->kind == FEM_BMINCUT) {
     const int rpw = 32 / bmincut_bits(p->q);
     if (R % 16 != 0 || R % rpw != 0 || R > 1024)

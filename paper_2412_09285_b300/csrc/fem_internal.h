@@ -49,6 +49,11 @@ struct Problem {
   float* cnorm2 = nullptr;     // bMinCut c^a
   int32_t* nodew = nullptr;    // bMinCut node weights V_i (NULL: all 1)
   bool coloring = false;       // FEM_COLORING on the bMinCut data path (kind == FEM_BMINCUT)
+  bool qubo = false;           // FEM_QUBO on the MaxCut data path (kind == FEM_MAXCUT)
+  float* qoff = nullptr;       // QUBO: sum_j Q_ij + d_i per node (the gradient's constant part)
+  int64_t* qlin_i = nullptr;   // QUBO: d_i (integer coefficients)
+  double* qlin_f = nullptr;    // QUBO: d_i (fp64)
+  bool qlin_int = true;
   int64_t wtot_i = 0;          // sum of the edge weights (integer weights)
   double wtot_f = 0.0;         // the same in fp64
   int64_t nodew_sq = 0;        // sum_i V_i^2 (n when unweighted)

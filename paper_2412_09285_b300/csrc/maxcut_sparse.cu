@@ -31,6 +31,8 @@ struct MaxcutArgs {
   float* v;
   const uint32_t* words_in;
   uint32_t* words_out;
+  float ccoef;          // exact mode: coefficient of sum_j W_ij m_j (2 for MaxCut, 1 for QUBO)
+  const float* offset;  // exact mode: per-node constant of the field (QUBO), NULL for MaxCut
 };
 
 // One warp per (node, block of 32 replicas); lane = replica.  Neighbour column
@@ -99,7 +101,10 @@ __global__ void __launch_bounds__(256) k_maxcut_step(MaxcutArgs a, StepScalars s
           }
         }
       }
-      field = 2.f * facc;
+      // MaxCut: 2 sum_j W_ij m_j.  QUBO: with p = (1 + m)/2, 2 sum_j Q_ij p_j + d_i =
+      // sum_j Q_ij m_j + (sum_j Q_ij + d_i)
+      field = a.ccoef * facc;
+      if (a.offset) field += a.offset[i];
     }
     const float g = s.gq * (field + hi * s.inv_beta) * one_minus_m2(hi);
     opt_update<OPT>(hi, mi, vi, g, s);
@@ -309,11 +314,67 @@ __global__ void __launch_bounds__(256) k_maxcut_cut_partial(
 
 // Sum the partials of every replica in block order, set E_r = -cut_r, then the
 // argmin over replicas with the lowest index winning ties.  One block.
-// E_r = -cut_r for replica r = blockIdx.x (the argmin follows in k_argmin_replica).
+// QUBO energy partials: E_r = sum_{i<j} 2 Q_ij s_i s_j + sum_i d_i s_i with s = 1 where
+// h >= 0 (sign bit clear); same blocking and fixed summation order as the cut partials.
+template <bool UNIT, bool INTW>
+__global__ void __launch_bounds__(256) k_qubo_partial(
+    const int32_t* __restrict__ row_ptr, const uint32_t* __restrict__ col,
+    const float* __restrict__ w, const double* __restrict__ w64, const int64_t* __restrict__ lin_i,
+    const double* __restrict__ lin_f, const uint32_t* __restrict__ words, int32_t n, int32_t R, int32_t wpn,
+    int64_t* __restrict__ part_i, double* __restrict__ part_f) {
+  __shared__ int64_t si[8][32];
+  __shared__ double sf[8][32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int wb = blockIdx.y;
+  int64_t acc_i = 0;
+  double acc_f = 0.0;
+  for (int i = blockIdx.x * 8 + warp; i < n; i += gridDim.x * 8) {
+    const uint32_t bi = (words[(size_t)i * wpn + wb] >> lane) & 1u;
+    if (!bi) {
+      if (INTW) acc_i += lin_i[i];
+      else acc_f += lin_f[i];
+    }
+    const int beg = row_ptr[i], end = row_ptr[i + 1];
+    for (int k0 = beg; k0 < end; k0 += 32) {
+      const int k = k0 + lane;
+      uint32_t c = 0, word = 0;
+      if (k < end) {
+        c = col[k];
+        word = words[(size_t)(c & 0x7fffffffu) * wpn + wb];
+      }
+      const int cnt = min(32, end - k0);
+      for (int e = 0; e < cnt; ++e) {
+        const uint32_t ce = __shfl_sync(kFullMask, c, e);
+        const uint32_t bj = (__shfl_sync(kFullMask, word, e) >> lane) & 1u;
+        const uint32_t j = ce & 0x7fffffffu;
+        if ((int)j <= i || bi || bj) continue;
+        if (INTW) acc_i += 2 * (UNIT ? ((ce >> 31) ? -1 : 1) : (int64_t)w[k0 + e]);
+        else acc_f += 2.0 * w64[k0 + e];
+      }
+    }
+  }
+  si[warp][lane] = acc_i;
+  sf[warp][lane] = acc_f;
+  __syncthreads();
+  if (warp == 0) {
+    int64_t ti = 0;
+    double tf = 0.0;
+    for (int k = 0; k < 8; ++k) {
+      ti += si[k][lane];
+      tf += sf[k][lane];
+    }
+    const size_t o = (size_t)blockIdx.x * R + (size_t)wb * 32 + lane;
+    if (INTW) part_i[o] = ti;
+    else part_f[o] = tf;
+  }
+}
+
+// E_r = -cut_r (MaxCut, negate) or the QUBO energy for replica r = blockIdx.x (the
+// argmin follows in k_argmin_replica).
 template <bool INTW>
 __global__ void __launch_bounds__(kRedThreads) k_maxcut_finish(const int64_t* __restrict__ part_i,
                                                                const double* __restrict__ part_f,
-                                                               int32_t nblk, int32_t R,
+                                                               int32_t nblk, int32_t R, int32_t negate,
                                                                int64_t* __restrict__ e_i,
                                                                double* __restrict__ e_f) {
   __shared__ int64_t shi[kRedThreads];
@@ -322,35 +383,36 @@ __global__ void __launch_bounds__(kRedThreads) k_maxcut_finish(const int64_t* __
   if (INTW) {
     const int64_t t = column_sum<int64_t>(part_i, nblk, R, r, shi);
     if (threadIdx.x == 0) {
-      e_i[r] = -t;
-      e_f[r] = (double)(-t);
+      e_i[r] = negate ? -t : t;
+      e_f[r] = (double)(negate ? -t : t);
     }
   } else {
     const double t = column_sum<double>(part_f, nblk, R, r, shf);
     if (threadIdx.x == 0) {
       e_i[r] = 0;
-      e_f[r] = -t;
+      e_f[r] = negate ? -t : t;
     }
   }
 }
 
 // states[i] = +1 / -1 of replica r (from the sign words).
+// States from sign words: a set bit (h < 0) is `lo` (MaxCut -1, QUBO 0), a clear bit 1.
 __global__ void k_maxcut_states_one(const uint32_t* __restrict__ words, int32_t n, int32_t wpn,
-                                    const int32_t* __restrict__ best, int32_t* __restrict__ out) {
+                                    const int32_t* __restrict__ best, int32_t* __restrict__ out, int32_t lo) {
   const int r = best[0];
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-    out[i] = ((words[(size_t)i * wpn + (r >> 5)] >> (r & 31)) & 1u) ? -1 : 1;
+    out[i] = ((words[(size_t)i * wpn + (r >> 5)] >> (r & 31)) & 1u) ? lo : 1;
   }
 }
 
 __global__ void k_maxcut_states_all(const uint32_t* __restrict__ words, int32_t n, int32_t R,
-                                    int32_t wpn, int32_t* __restrict__ out) {
+                                    int32_t wpn, int32_t* __restrict__ out, int32_t lo) {
   const size_t total = (size_t)n * R;
   for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
        e += (size_t)gridDim.x * blockDim.x) {
     const size_t i = e / R;
     const int r = (int)(e - i * R);
-    out[e] = ((words[i * wpn + (r >> 5)] >> (r & 31)) & 1u) ? -1 : 1;
+    out[e] = ((words[i * wpn + (r >> 5)] >> (r & 31)) & 1u) ? lo : 1;
   }
 }
 
@@ -443,6 +505,8 @@ fem_status maxcut_sparse_steps(Problem* p, const fem_anneal_params& a,
   args.wpn = p->words_per_node;
   args.m = p->m;
   args.v = p->v;
+  args.ccoef = p->qubo ? 1.f : 2.f;
+  args.offset = p->qubo ? p->qoff : nullptr;
   for (size_t k = 0; k < sc.size(); ++k) {
     if (p->grad_mode == FEM_GRAD_PAPER) {
       args.h_in = p->h[0];
@@ -470,24 +534,38 @@ fem_status maxcut_readout(Problem* p, cudaStream_t s) {
   const int wpn = p->words_per_node;
   const dim3 grid(p->part_blocks, wpn);
   const uint32_t* words = p->words[p->cur];
-  if (p->int_w) {
+  const bool intw = p->int_w && (!p->qubo || p->qlin_int);
+  if (p->qubo) {
+    if (intw && p->unit_w)
+      k_qubo_partial<true, true><<<grid, 256, 0, s>>>(p->row_ptr, p->col, p->w, p->w64, p->qlin_i, p->qlin_f,
+                                                      words, p->n, p->R, wpn, p->part_i, p->part_f);
+    else if (intw)
+      k_qubo_partial<false, true><<<grid, 256, 0, s>>>(p->row_ptr, p->col, p->w, p->w64, p->qlin_i, p->qlin_f,
+                                                       words, p->n, p->R, wpn, p->part_i, p->part_f);
+    else
+      k_qubo_partial<false, false><<<grid, 256, 0, s>>>(p->row_ptr, p->col, p->w, p->w64, p->qlin_i, p->qlin_f,
+                                                        words, p->n, p->R, wpn, p->part_i, p->part_f);
+  } else if (intw) {
     if (p->unit_w)
       k_maxcut_cut_partial<true, true><<<grid, 256, 0, s>>>(p->row_ptr, p->col, p->w, p->w64, words,
                                                             p->n, p->R, wpn, p->part_i, p->part_f);
     else
       k_maxcut_cut_partial<false, true><<<grid, 256, 0, s>>>(p->row_ptr, p->col, p->w, p->w64, words,
                                                              p->n, p->R, wpn, p->part_i, p->part_f);
-    k_maxcut_finish<true><<<p->R, kRedThreads, 0, s>>>(p->part_i, p->part_f, p->part_blocks, p->R,
-                                                        p->energy_i, p->energy_f);
   } else {
     k_maxcut_cut_partial<false, false><<<grid, 256, 0, s>>>(p->row_ptr, p->col, p->w, p->w64, words,
                                                             p->n, p->R, wpn, p->part_i, p->part_f);
-    k_maxcut_finish<false><<<p->R, kRedThreads, 0, s>>>(p->part_i, p->part_f, p->part_blocks, p->R,
-                                                         p->energy_i, p->energy_f);
   }
+  const int negate = p->qubo ? 0 : 1;
+  if (intw)
+    k_maxcut_finish<true><<<p->R, kRedThreads, 0, s>>>(p->part_i, p->part_f, p->part_blocks, p->R, negate,
+                                                        p->energy_i, p->energy_f);
+  else
+    k_maxcut_finish<false><<<p->R, kRedThreads, 0, s>>>(p->part_i, p->part_f, p->part_blocks, p->R, negate,
+                                                         p->energy_i, p->energy_f);
   k_argmin_replica<<<1, 1024, 0, s>>>(p->energy_f, p->R, p->best);
   k_maxcut_states_one<<<(p->n + 255) / 256 < 1024 ? (p->n + 255) / 256 : 1024, 256, 0, s>>>(
-      words, p->n, wpn, p->best, p->states_dev);
+      words, p->n, wpn, p->best, p->states_dev, p->qubo ? 0 : -1);
   count_launches(4);
   FEM_CUDA(cudaGetLastError());
   return FEM_OK;
@@ -498,7 +576,7 @@ fem_status maxcut_states_all(Problem* p, int32_t* out_dev, cudaStream_t s) {
   size_t blocks = (total + 255) / 256;
   if (blocks > (size_t)p->sm_count * 16) blocks = (size_t)p->sm_count * 16;
   k_maxcut_states_all<<<(int)blocks, 256, 0, s>>>(p->words[p->cur], p->n, p->R, p->words_per_node,
-                                                  out_dev);
+                                                  out_dev, p->qubo ? 0 : -1);
   count_launches(1);
   FEM_CUDA(cudaGetLastError());
   return FEM_OK;

@@ -186,7 +186,7 @@ def _traffic_from_profile(name, kind):
     return int(m2.group(1)) if source_sha256(kind) == m1.group(1) else None
 
 
-def _roofline(wl, inst, step_ms, precision, persistent=False):
+def _roofline(wl, inst, step_ms, precision, persistent=False, grad_mode="paper"):
     """Algorithmic work of one step launch / its measured duration, against the peak."""
     peaks, src = _peaks()
     csrc = os.path.join(ROOT, "paper_2412_09285_b300", "csrc")
@@ -209,6 +209,17 @@ def _roofline(wl, inst, step_ms, precision, persistent=False):
                             if wl is WORKLOADS["batched"] else None),
                 "kernel": "k_batch_step<4, paper>", "algorithmic_bytes_per_launch": alg, "launch_ms": step_ms,
                 "peak_source": f"{src} hbm_gbs (copy), of {src}", "frac_of_8TBs": ach / 8000.0}
+    if wl["kind"] == "sparse" and grad_mode == "exact":
+        n, nnz = inst.n, 2 * inst.n_edges
+        # h, m, v read + written, m = tanh(h/2) read once (its gathers beyond that are
+        # traffic, not algorithm) and written once, CSR, sign words written
+        alg = 24 * n * R + 8 * n * R + 4 * nnz + 4 * (n + 1) + 4 * n * (R // 32)
+        ach = alg / (step_ms / 1e3) / 1e9
+        return {"bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": ach / peaks["hbm_gbs"], "traffic": None,
+                "kernel": "k_maxcut_step<exact, adam, unit>", "algorithmic_bytes_per_launch": alg,
+                "launch_ms": step_ms, "peak_source": f"{src} hbm_gbs (copy), of {src}",
+                "frac_of_8TBs": ach / 8000.0}
     if wl["kind"] == "sparse":
         n, nnz = inst.n, 2 * inst.n_edges
         # h, m, v read + written (24 B per node*replica), CSR col (4 B per directed entry),
@@ -418,8 +429,8 @@ def run_ours(args, wl):
         h0 = torch.from_numpy(h0_host).to(dev)
     stream = torch.cuda.current_stream()
     prob = _make_problem(fem, wl, inst, stream, args.dense_launch)
-    kw = dict(grad_mode="exact" if precision == "bf16x2" else "paper", optimizer="adam", lr=0.1,
-              precision=precision)
+    grad_mode = args.grad_mode or ("exact" if precision == "bf16x2" else "paper")
+    kw = dict(grad_mode=grad_mode, optimizer="adam", lr=0.1, precision=precision)
 
     window_launches = []
 
@@ -506,13 +517,15 @@ def run_ours(args, wl):
             "dtype": {"bf16": "bf16", "fp8": "e4m3", "bf16x2": "bf16x2", "fp32": "f32"}[precision]
             if wl["kind"] == "dense" else "f32",
             "data": "synthetic",
-            "config": {"workload": wl["name"], "n": inst.n, "units_per_replica": _units_per_replica(wl, inst),
+            "config": {"workload": wl["name"] if grad_mode == "paper" or wl["kind"] != "sparse"
+                       else wl["name"].replace("paper-mode gradient", "exact gradient"), "n": inst.n, "units_per_replica": _units_per_replica(wl, inst),
                        "replicas_per_gpu": R, "anneal_steps": n_steps, "precision": precision,
                        "parallelism": f"replica-sharded x{ws}",
                        "l2": ("inputs larger than L2" if wl["kind"] == "sparse" and inst.n > 100000
                               else "working set L2-resident (latency/compute-bound workload)")},
             "roofline": _roofline(wl, inst, step_ms, precision,
-                                  persistent=bool(window_launches) and window_launches[-1] == 1), "gpu_launches": int(launches), "e2e": e2e,
+                                  persistent=bool(window_launches) and window_launches[-1] == 1,
+                                  grad_mode=grad_mode), "gpu_launches": int(launches), "e2e": e2e,
             "clocks": clk.summary(),
             "best_energy": float(best["energy_f64"][best["best_replica"]])}
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
@@ -667,6 +680,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="sparse", choices=sorted(WORKLOADS))
     ap.add_argument("--precision", default="bf16", choices=["bf16", "fp8", "bf16x2", "fp32"])
+    ap.add_argument("--grad-mode", default=None, choices=["paper", "exact"],
+                    help="sparse workloads: the discretised (paper) or exact gradient (default paper)")
     ap.add_argument("--dense-launch", default="auto", choices=["auto", "per_step", "persistent"],
                     help="dense workload: persistent (state in tensor memory) or one kernel per step")
     ap.add_argument("--no-cpu-baseline", action="store_true")

@@ -346,6 +346,9 @@ static fem_status ensure_state(Problem* p, int32_t R, cudaStream_t s) {
                       : (p->kind == FEM_BMINCUT) ? R * bmincut_bits(p->q) / 32 : (R + 31) / 32;
   for (int b = 0; b < 2; ++b)
     if ((st = dev_alloc_t(p, &p->words[b], (size_t)p->n * p->words_per_node)) != FEM_OK) return st;
+  if (p->kind == FEM_MAXCUT)
+    for (int b = 0; b < 2; ++b)
+      if ((st = dev_alloc_t(p, &p->mag[b], per)) != FEM_OK) return st;
   if (p->kind == FEM_BMINCUT) {
     for (int b = 0; b < 3; ++b) {
       if ((st = dev_alloc_t(p, &p->cnt[b], (size_t)R * p->q)) != FEM_OK) return st;

@@ -31,6 +31,8 @@ struct MaxcutArgs {
   float* v;
   const uint32_t* words_in;
   uint32_t* words_out;
+  const float* mag_in;  // exact mode: m_j = tanh(h_j / 2) of the fields this step reads
+  float* mag_out;       // exact mode: m of the updated fields, for the next step
   float ccoef;          // exact mode: coefficient of sum_j W_ij m_j (2 for MaxCut, 1 for QUBO)
   const float* offset;  // exact mode: per-node constant of the field (QUBO), NULL for MaxCut
 };
@@ -92,8 +94,7 @@ __global__ void __launch_bounds__(256) k_maxcut_step(MaxcutArgs a, StepScalars s
         const int cnt = min(32, end - k0);
         for (int e = 0; e < cnt; ++e) {
           const uint32_t ce = __shfl_sync(kFullMask, c, e);
-          const float hj = a.h_in[(size_t)(ce & 0x7fffffffu) * a.R + (size_t)wb * 32 + lane];
-          const float mj = tanhf(0.5f * hj);
+          const float mj = a.mag_in[(size_t)(ce & 0x7fffffffu) * a.R + (size_t)wb * 32 + lane];
           if (UNIT) {
             facc += (ce >> 31) ? -mj : mj;
           } else {
@@ -111,6 +112,7 @@ __global__ void __launch_bounds__(256) k_maxcut_step(MaxcutArgs a, StepScalars s
     a.h_out[idx] = hi;
     a.m[idx] = mi;
     if (OPT != FEM_OPT_SGD) a.v[idx] = vi;
+    if (MODE == FEM_GRAD_EXACT) a.mag_out[idx] = tanhf(0.5f * hi);  // gathered by the next step
     const uint32_t ball = __ballot_sync(kFullMask, hi < 0.f);
     if (lane == 0) a.words_out[(size_t)i * a.wpn + wb] = ball;
   }
@@ -243,9 +245,11 @@ __global__ void __launch_bounds__(256, 5) k_maxcut_step_paper(MaxcutArgs a, Step
   }
 }
 
-// Sign words of the fields: bit r of word (i, b) is set when h[i][32b + r] < 0.
+// Sign words of the fields: bit r of word (i, b) is set when h[i][32b + r] < 0 (and,
+// when mag is non-NULL, m = tanh(h/2) for the exact-mode
+// gathers).
 __global__ void k_pack_sign_words(const float* __restrict__ h, int32_t n, int32_t R,
-                                  int32_t wpn, uint32_t* __restrict__ words) {
+                                  int32_t wpn, uint32_t* __restrict__ words, float* __restrict__ mag) {
   const int lane = threadIdx.x & 31;
   const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
   for (long long it = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -253,6 +257,7 @@ __global__ void k_pack_sign_words(const float* __restrict__ h, int32_t n, int32_
     const float x = h[it * 32 + lane];  // [n][R] with R = 32 wpn: item it covers elements it*32..
     const uint32_t b = __ballot_sync(kFullMask, x < 0.f);
     if (lane == 0) words[it] = b;
+    if (mag) mag[it * 32 + lane] = tanhf(0.5f * x);
   }
 }
 
@@ -482,8 +487,9 @@ int grid_for_warps(const Problem* p, long long warps) {
 
 fem_status maxcut_pack_words(Problem* p, int hbuf, int wbuf, cudaStream_t s) {
   const long long items = (long long)p->n * p->words_per_node;
-  k_pack_sign_words<<<grid_for_warps(p, items), 256, 0, s>>>(p->h[hbuf], p->n, p->R,
-                                                              p->words_per_node, p->words[wbuf]);
+  k_pack_sign_words<<<grid_for_warps(p, items), 256, 0, s>>>(
+      p->h[hbuf], p->n, p->R, p->words_per_node, p->words[wbuf],
+      p->grad_mode == FEM_GRAD_EXACT ? p->mag[wbuf] : nullptr);
   count_launches(1);
   FEM_CUDA(cudaGetLastError());
   return FEM_OK;
@@ -517,6 +523,8 @@ fem_status maxcut_sparse_steps(Problem* p, const fem_anneal_params& a,
     }
     args.words_in = p->words[p->cur];
     args.words_out = p->words[p->cur ^ 1];
+    args.mag_in = p->mag[p->cur];
+    args.mag_out = p->mag[p->cur ^ 1];
     fn(args, sc[k], p->sm_count, groups, s);
     p->cur ^= 1;
   }

@@ -12,6 +12,7 @@ import numpy as np
 
 __all__ = [
     "all_binary", "all_qary", "maxcut_bruteforce", "bmincut_bruteforce", "coloring_bruteforce", "qubo_bruteforce",
+    "pspin_bruteforce",
     "sat_bruteforce", "mf_free_energy_by_enumeration",
 ]
 
@@ -57,6 +58,17 @@ def qubo_bruteforce(n, ei, ej, w, d):
     """Minimum of sum_E 2 w sigma_i sigma_j + sum_i d_i sigma_i over all 2^n binary states."""
     X = all_binary(n).astype(np.float64)
     E = (2.0 * np.asarray(w)[None, :] * X[:, ei] * X[:, ej]).sum(axis=1) + X @ np.asarray(d, np.float64)
+    return E.min()
+
+
+def pspin_bruteforce(n, ptr, var, J, b):
+    """Minimum of sum_v J_v prod_{i in v} s_i + sum_i b_i s_i over all 2^n spin states."""
+    S = 2.0 * all_binary(n).astype(np.float64) - 1.0
+    E = S @ np.asarray(b, np.float64)
+    ptr = np.asarray(ptr)
+    var = np.asarray(var)
+    for t in range(ptr.shape[0] - 1):
+        E = E + J[t] * S[:, var[ptr[t]:ptr[t + 1]]].prod(axis=1)
     return E.min()
 
 

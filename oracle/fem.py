@@ -43,6 +43,7 @@ __all__ = [
     "bmincut_free_energy", "bmincut_grad", "bmincut_normalisers",
     "coloring_free_energy", "coloring_grad", "coloring_energy",
     "qubo_free_energy", "qubo_grad", "qubo_states", "qubo_energy",
+    "pspin_free_energy", "pspin_grad", "pspin_energy",
     "sat_arrays", "sat_free_energy", "sat_grad",
     "Adam", "RMSprop", "SGD", "make_optimizer", "anneal",
     "maxcut_states", "maxcut_cut_edges", "maxcut_cut_spin", "maxcut_cut_matrix",
@@ -471,7 +472,7 @@ def anneal(problem, h0, n_step, *, t_begin=0, t_end=None, schedule="exponential"
     """Run anneal steps t_begin .. t_end-1 from fields h0 (copied, float64).
 
     problem: ("maxcut", W) | ("bmincut", W) | ("bmincut", W, V) | ("coloring", W) | ("qubo", (Q, d))
-             | ("sat", groups)
+             | ("pspin", (ptr, var, J, b)) | ("sat", groups)
     Returns (h, opt); pass ``opt`` back in to resume.  ``trace``, if a dict
     {t: None}, is filled with copies of h after step t (1-based count of steps done).
     ``cond``, if a dict {t: None}, is filled with the elementwise minimum over the
@@ -497,6 +498,8 @@ def anneal(problem, h0, n_step, *, t_begin=0, t_end=None, schedule="exponential"
             g = coloring_grad(data, h, beta, gamma=gamma, mode=mode)
         elif kind == "qubo":
             g = qubo_grad(data[0], data[1], h, beta, gamma=gamma)
+        elif kind == "pspin":
+            g = pspin_grad(*data, h, beta, gamma=gamma)
         elif kind == "sat":
             g = sat_grad(data, h, beta, gamma=gamma)
         else:
@@ -509,6 +512,53 @@ def anneal(problem, h0, n_step, *, t_begin=0, t_end=None, schedule="exponential"
         if trace is not None and (t + 1) in trace:
             trace[t + 1] = h.copy()
     return h, opt
+
+
+# ----------------------------------------------------------------------------
+# Higher-order interactions (SM, problems with multi-variable interactions: p-spin
+# glasses and the quantum error-correction Hamiltonian): spins sigma_i in {-1, +1},
+#   E(sigma) = sum_v J_v prod_{i in v} sigma_i + sum_i b_i sigma_i,
+# <E> = sum_v J_v prod_{i in v} m_i + sum_i b_i m_i with m_i = tanh(h_i / 2) =
+# P_i(+1) - P_i(-1).  Terms are given as (ptr, var) lists of 0-based variables.
+# ----------------------------------------------------------------------------
+
+def _pspin_terms(ptr, var):
+    ptr = np.asarray(ptr, np.int64)
+    var = np.asarray(var, np.int64)
+    return [var[ptr[t]:ptr[t + 1]] for t in range(ptr.shape[0] - 1)]
+
+
+def pspin_free_energy(ptr, var, J, b, h, beta):
+    """F = <E> + (1/beta) sum_i [p ln p + (1-p) ln(1-p)], p = sigmoid(h).  h: [N, R] -> [R]."""
+    m = np.tanh(0.5 * np.asarray(h, np.float64))
+    U = (np.asarray(b, np.float64)[:, None] * m).sum(axis=0)
+    for Jt, vs in zip(np.asarray(J, np.float64), _pspin_terms(ptr, var)):
+        U = U + Jt * m[vs].prod(axis=0)
+    p = sigmoid(h)
+    return U + (_xlogx(p) + _xlogx(1.0 - p)).sum(axis=0) / beta
+
+
+def pspin_grad(ptr, var, J, b, h, beta, gamma=1.0):
+    """dF/dh_i = gamma (1 - m_i^2) / 4 [2 (sum_{v ni i} J_v prod_{k in v, k != i} m_k + b_i) + h_i / beta]
+    (dm/dh = (1 - m^2)/2 and the entropy term h/beta p(1-p) = h/beta (1 - m^2)/4)."""
+    m = np.tanh(0.5 * np.asarray(h, np.float64))
+    dE = np.repeat(np.asarray(b, np.float64)[:, None], h.shape[1], axis=1)
+    for Jt, vs in zip(np.asarray(J, np.float64), _pspin_terms(ptr, var)):
+        for a, i in enumerate(vs):
+            others = np.delete(vs, a)
+            dE[i] += Jt * (m[others].prod(axis=0) if others.size else 1.0)
+    return gamma * 0.25 * (1.0 - m * m) * (2.0 * dE + h / beta)
+
+
+def pspin_energy(ptr, var, J, b, sigma):
+    """E = sum_v J_v prod_{i in v} sigma_i + sum_i b_i sigma_i per replica, sigma in {-1, +1}."""
+    J = _as_exact(J)
+    b = _as_exact(b)
+    s = sigma.astype(np.int64)
+    E = (b[:, None] * s).sum(axis=0)
+    for Jt, vs in zip(J, _pspin_terms(ptr, var)):
+        E = E + Jt * s[vs].prod(axis=0)
+    return E
 
 
 # ----------------------------------------------------------------------------

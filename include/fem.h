@@ -63,7 +63,16 @@ typedef enum {
  * off-diagonal pair once with w = Q_ij; d comes from fem_problem_desc.linear.  One
  * sigmoid field per variable, FEM_GRAD_EXACT only; the read-out energy is E and a
  * variable's state is 1 where h >= 0. */
-typedef enum { FEM_MAXCUT = 0, FEM_BMINCUT = 1, FEM_MAXKSAT = 2, FEM_COLORING = 3, FEM_QUBO = 4 } fem_kind;
+/* FEM_PSPIN: spins sigma_i in {-1, +1} with multi-spin terms (p-spin glasses, the
+ * quantum error-correction Hamiltonian; SM, problems with multi-variable
+ * interactions): E = sum_v J_v prod_{i in v} sigma_i + sum_i b_i sigma_i.  Terms come
+ * in clause_ptr / lits (1 to 8 distinct variables each; a negated literal multiplies
+ * its term by -1), J_v in term_weight, b_i in linear (NULL: 0).  One sigmoid field per
+ * spin (m = tanh(h/2)), the exact gradient in both modes; the read-out energy is E and
+ * a spin's state is +1 where h >= 0, else -1. */
+typedef enum {
+  FEM_MAXCUT = 0, FEM_BMINCUT = 1, FEM_MAXKSAT = 2, FEM_COLORING = 3, FEM_QUBO = 4, FEM_PSPIN = 5
+} fem_kind;
 
 /* Methods, "Different annealing schedules for the inverse temperature":
  *   exponential          beta(t) = exp(ln b_min + t (ln b_max - ln b_min)/(N_step - 1))
@@ -131,7 +140,9 @@ typedef struct fem_problem* fem_problem_t; /* opaque; owned by the library until
  *                where a coarsened node weighs the number of nodes it groups), and
  *                the read-out energy cut + lambda_max sum_s [n_s^2 - sum_{i in s} V_i^2]
  *                with n_s = sum_{i in s} V_i.  NULL: every V_i = 1.
- *   linear       optional (QUBO only), n coefficients d_i of the linear term; NULL: 0.
+ *   linear       optional (QUBO and p-spin), n coefficients of the linear term (d_i,
+ *                b_i); NULL: 0.
+ *   term_weight  p-spin only (required there): n_clauses coefficients J_v of the terms.
  */
 typedef struct {
   int32_t kind;
@@ -147,6 +158,7 @@ typedef struct {
   const int32_t* lits;
   const double* node_weight;
   const double* linear;
+  const double* term_weight;
 } fem_problem_desc;
 
 /* Anneal parameters.

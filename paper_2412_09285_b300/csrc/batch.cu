@@ -45,6 +45,8 @@ struct BatchMember {
   const int32_t* occ_ptr;
   const int32_t* occ;
   const int2* oth;
+  const float* jw;   // p-spin members: term coefficients, NULL for Max-k-SAT
+  const float* lin;  // p-spin members: fields b_i
 };
 
 struct BatchItem {
@@ -113,6 +115,8 @@ __device__ void run_sat_item(const BatchMember& b, const BatchItem& it, const St
   a.occ_ptr = b.occ_ptr;
   a.occ = b.occ;
   a.oth = b.oth;
+  a.jw = b.jw;
+  a.lin = b.lin;
   a.n = b.n;
   a.R = b.R;
   a.opt = b.opt;
@@ -282,6 +286,8 @@ static fem_status batch_prepare(Batch* b, cudaStream_t s) {
     m.occ_ptr = p->occ_ptr;
     m.occ = p->occ;
     m.oth = reinterpret_cast<const int2*>(p->oth);
+    m.jw = p->pspin ? p->pj : nullptr;
+    m.lin = p->pspin ? p->qoff : nullptr;
     dm.push_back(m);
     if (p->kind == FEM_BMINCUT) {
       b->elems_bmc += (long long)p->n * p->R;

@@ -421,11 +421,15 @@ fem_status fem_create_problem(const fem_problem_desc* d, void* stream, fem_probl
   g_last_error.clear();
   if (!d || !out) return fail(FEM_ERR_INVALID_ARG, "desc and out must be non-NULL");
   *out = nullptr;
-  if (d->kind < FEM_MAXCUT || d->kind > FEM_QUBO) return fail(FEM_ERR_INVALID_ARG, "unknown kind %d", d->kind);
+  if (d->kind < FEM_MAXCUT || d->kind > FEM_PSPIN) return fail(FEM_ERR_INVALID_ARG, "unknown kind %d", d->kind);
   if (d->n < 1) return fail(FEM_ERR_INVALID_ARG, "n must be >= 1");
-  if ((d->kind == FEM_MAXCUT || d->kind == FEM_MAXKSAT || d->kind == FEM_QUBO) && d->q != 2)
-    return fail(FEM_ERR_INVALID_ARG, "q must be 2 for MaxCut, Max-k-SAT and QUBO");
-  if (d->linear && d->kind != FEM_QUBO) return fail(FEM_ERR_INVALID_ARG, "linear applies to QUBO problems only");
+  if ((d->kind == FEM_MAXCUT || d->kind == FEM_MAXKSAT || d->kind == FEM_QUBO || d->kind == FEM_PSPIN) && d->q != 2)
+    return fail(FEM_ERR_INVALID_ARG, "q must be 2 for MaxCut, Max-k-SAT, QUBO and p-spin");
+  if (d->linear && d->kind != FEM_QUBO && d->kind != FEM_PSPIN)
+    return fail(FEM_ERR_INVALID_ARG, "linear applies to QUBO and p-spin problems only");
+  if (d->term_weight && d->kind != FEM_PSPIN) return fail(FEM_ERR_INVALID_ARG, "term_weight applies to p-spin only");
+  if (d->kind == FEM_PSPIN && d->n_clauses > 0 && !d->term_weight)
+    return fail(FEM_ERR_INVALID_ARG, "p-spin needs term_weight");
   if (d->kind == FEM_QUBO && (d->dense_J || d->node_weight))
     return fail(FEM_ERR_INVALID_ARG, "QUBO takes a sparse graph of off-diagonal entries and optional linear terms");
   if ((d->kind == FEM_BMINCUT || d->kind == FEM_COLORING) && (d->q < 2 || d->q > 8))
@@ -433,7 +437,10 @@ fem_status fem_create_problem(const fem_problem_desc* d, void* stream, fem_probl
   if (d->kind == FEM_COLORING && (d->dense_J || d->node_weight))
     return fail(FEM_ERR_INVALID_ARG, "colouring takes a sparse graph without node weights");
   // colouring runs on the bMinCut data path (same normalisers, counts and read-out)
-  const int32_t kind = d->kind == FEM_COLORING ? FEM_BMINCUT : (d->kind == FEM_QUBO ? FEM_MAXCUT : d->kind);
+  const int32_t kind = d->kind == FEM_COLORING ? FEM_BMINCUT
+                       : d->kind == FEM_QUBO   ? FEM_MAXCUT
+                       : d->kind == FEM_PSPIN  ? FEM_MAXKSAT
+                                               : d->kind;
   cudaStream_t s = (cudaStream_t)stream;
   // 1. host-side validation and construction (no CUDA call yet)
   HostGraph hg;
@@ -450,7 +457,7 @@ fem_status fem_create_problem(const fem_problem_desc* d, void* stream, fem_probl
         if (i == j && x != 0.f) return fail(FEM_ERR_INVALID_ARG, "dense_J must have a zero diagonal");
         if (j > i && x != J[(size_t)j * d->n + i]) return fail(FEM_ERR_INVALID_ARG, "dense_J must be symmetric");
       }
-  } else if (d->kind == FEM_MAXKSAT) {
+  } else if (kind == FEM_MAXKSAT) {
     if ((st = host_sat(d, hs)) != FEM_OK) return st;
   } else {
     if ((st = host_graph(kind, d->q, d, hg)) != FEM_OK) return st;
@@ -479,6 +486,38 @@ fem_status fem_create_problem(const fem_problem_desc* d, void* stream, fem_probl
       qoff[i] = (float)(rs[i] + li);
     }
   }
+  // p-spin: term coefficients with the literals' negations folded in, and the fields
+  std::vector<float> pj_f32;
+  std::vector<double> pj_f64;
+  std::vector<int64_t> pj_i64;
+  bool pspin_int = true;
+  if (d->kind == FEM_PSPIN) {
+    const int64_t M = d->n_clauses;
+    pj_f32.resize(M);
+    pj_f64.resize(M);
+    pj_i64.resize(M);
+    for (int64_t c = 0; c < M; ++c) {
+      double J = d->term_weight[c];
+      if (!std::isfinite(J)) return fail(FEM_ERR_INVALID_ARG, "term_weight[%lld] must be finite", (long long)c);
+      for (int64_t k = d->clause_ptr[c]; k < d->clause_ptr[c + 1]; ++k)
+        if (d->lits[k] < 0) J = -J;
+      if (J != std::rint(J) || std::fabs(J) > 1099511627776.0) pspin_int = false;
+      pj_f32[c] = (float)J;
+      pj_f64[c] = J;
+      pj_i64[c] = pspin_int ? (int64_t)J : 0;
+    }
+    qoff.resize(d->n);
+    qlin_f.resize(d->n);
+    qlin_i.resize(d->n);
+    for (int32_t i = 0; i < d->n; ++i) {
+      const double b = d->linear ? d->linear[i] : 0.0;
+      if (!std::isfinite(b)) return fail(FEM_ERR_INVALID_ARG, "linear[%d] must be finite", i);
+      if (b != std::rint(b) || std::fabs(b) > 1099511627776.0) pspin_int = false;
+      qoff[i] = (float)b;
+      qlin_f[i] = b;
+      qlin_i[i] = pspin_int ? (int64_t)b : 0;
+    }
+  }
   std::vector<int32_t> nodew;
   int64_t nodew_sq = d->n;
   if (d->node_weight) {
@@ -503,6 +542,8 @@ fem_status fem_create_problem(const fem_problem_desc* d, void* stream, fem_probl
   p->coloring = d->kind == FEM_COLORING;
   p->qubo = d->kind == FEM_QUBO;
   p->qlin_int = qlin_int;
+  p->pspin = d->kind == FEM_PSPIN;
+  p->pspin_int = pspin_int;
   p->wtot_i = hg.wsum_i;
   p->wtot_f = hg.wsum_f;
   p->n = d->n;
@@ -510,12 +551,18 @@ fem_status fem_create_problem(const fem_problem_desc* d, void* stream, fem_probl
   FEM_CUDA(cudaGetDevice(&p->device));
   FEM_CUDA(cudaDeviceGetAttribute(&p->sm_count, cudaDevAttrMultiProcessorCount, p->device));
   if (d->kind == FEM_MAXCUT && d->dense_J) st = dense_upload(p.get(), d->dense_J, s);
-  else st = d->kind == FEM_MAXKSAT ? upload_sat(p.get(), hs, s) : upload_graph(p.get(), hg, s);
+  else st = kind == FEM_MAXKSAT ? upload_sat(p.get(), hs, s) : upload_graph(p.get(), hg, s);  // internal kind
   p->nodew_sq = nodew_sq;
   if (st == FEM_OK && !nodew.empty()) st = upload(p.get(), &p->nodew, nodew, s);
   if (st == FEM_OK && p->qubo) st = upload(p.get(), &p->qoff, qoff, s);
   if (st == FEM_OK && p->qubo) st = upload(p.get(), &p->qlin_f, qlin_f, s);
   if (st == FEM_OK && p->qubo) st = upload(p.get(), &p->qlin_i, qlin_i, s);
+  if (st == FEM_OK && p->pspin) st = upload(p.get(), &p->qoff, qoff, s);
+  if (st == FEM_OK && p->pspin) st = upload(p.get(), &p->qlin_f, qlin_f, s);
+  if (st == FEM_OK && p->pspin) st = upload(p.get(), &p->qlin_i, qlin_i, s);
+  if (st == FEM_OK && p->pspin && !pj_f32.empty()) st = upload(p.get(), &p->pj, pj_f32, s);
+  if (st == FEM_OK && p->pspin && !pj_f64.empty()) st = upload(p.get(), &p->pj_f, pj_f64, s);
+  if (st == FEM_OK && p->pspin && !pj_i64.empty()) st = upload(p.get(), &p->pj_i, pj_i64, s);
   if (st == FEM_OK) st = dev_alloc_t(p.get(), &p->err, 1);
   if (st == FEM_OK) {
     const cudaError_t e1 = cudaMemsetAsync(p->err, 0, sizeof(int32_t), s);
@@ -629,6 +676,11 @@ fem_status fem_anneal(fem_problem_t p, const fem_anneal_params* a, void* stream)
       return fail(FEM_ERR_STATE, "a resumed call must keep replicas, n_steps, grad_mode and optimizer");
   }
   if (a->t_end == a->t_begin) return FEM_OK;
+  // the device data every step kernel dereferences must exist (a guard against an
+  // inconsistent problem, which would otherwise reach a kernel as null pointers)
+  if (!p->dense && (p->kind == FEM_MAXKSAT ? (!p->occ_ptr || (p->n_clauses > 0 && (!p->cl_ptr || !p->occ)))
+                                           : (!p->row_ptr || (p->nnz > 0 && !p->col))))
+    return fail(FEM_ERR_STATE, "the problem's device data is incomplete");
   fem_anneal_params a_eff = *a;
   if (p->coloring) a_eff.lambda_max = 0.0;  // no balance term
   const std::vector<StepScalars> sc = make_step_scalars(a_eff, p->kind != FEM_BMINCUT);

@@ -50,10 +50,15 @@ struct Problem {
   int32_t* nodew = nullptr;    // bMinCut node weights V_i (NULL: all 1)
   bool coloring = false;       // FEM_COLORING on the bMinCut data path (kind == FEM_BMINCUT)
   bool qubo = false;           // FEM_QUBO on the MaxCut data path (kind == FEM_MAXCUT)
-  float* qoff = nullptr;       // QUBO: sum_j Q_ij + d_i per node (the gradient's constant part)
-  int64_t* qlin_i = nullptr;   // QUBO: d_i (integer coefficients)
-  double* qlin_f = nullptr;    // QUBO: d_i (fp64)
+  float* qoff = nullptr;       // per-node constant of the gradient: QUBO sum_j Q_ij + d_i, p-spin b_i
+  int64_t* qlin_i = nullptr;   // QUBO d_i / p-spin b_i, integer (read-out)
+  double* qlin_f = nullptr;    // the same, fp64
   bool qlin_int = true;
+  bool pspin = false;          // FEM_PSPIN on the Max-k-SAT data path (kind == FEM_MAXKSAT)
+  float* pj = nullptr;         // p-spin term coefficients J_v (negations folded in), fp32 for the steps
+  int64_t* pj_i = nullptr;     // the same, integer (read-out)
+  double* pj_f = nullptr;      // the same, fp64 (read-out)
+  bool pspin_int = true;       // every J_v and b_i is an integer
   int64_t wtot_i = 0;          // sum of the edge weights (integer weights)
   double wtot_f = 0.0;         // the same in fp64
   int64_t nodew_sq = 0;        // sum_i V_i^2 (n when unweighted)

@@ -35,10 +35,79 @@ __global__ void __launch_bounds__(256) k_sat_step(SatArgs a, StepScalars s) {
     sat_element(a, s, e);
 }
 
-__global__ void k_sat_marginals(const float* __restrict__ h, long long total, float* __restrict__ P) {
+// The gathered marginals of the fields: P = sigmoid(h) (Max-k-SAT) or m = tanh(h/2) (p-spin).
+__global__ void k_sat_marginals(const float* __restrict__ h, long long total, float* __restrict__ P, int32_t pspin) {
   for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
        e += (long long)gridDim.x * blockDim.x)
-    P[e] = sigmoidf_fast(h[e]);
+    P[e] = pspin ? tanhf(0.5f * h[e]) : sigmoidf_fast(h[e]);
+}
+
+// p-spin energy partials: per replica, sum over terms of J_v prod_{i in v} sigma_i plus
+// sum_i b_i sigma_i, sigma = +1 where h >= 0 else -1; block = 16 rows (terms, then
+// spins) x 16 replicas, each thread summing its rows in a fixed order.
+template <bool INTW>
+__global__ void __launch_bounds__(256) k_pspin_partial(const int32_t* __restrict__ cl_ptr,
+                                                       const int32_t* __restrict__ cl_lit, int64_t M,
+                                                       const int64_t* __restrict__ J_i, const double* __restrict__ J_f,
+                                                       const int64_t* __restrict__ b_i, const double* __restrict__ b_f,
+                                                       int32_t n, const float* __restrict__ h, int32_t R,
+                                                       int64_t* __restrict__ part_i, double* __restrict__ part_f) {
+  __shared__ int64_t si[256];
+  __shared__ double sf[256];
+  const int rw = threadIdx.x >> 4, rl = threadIdx.x & 15;
+  const int r = blockIdx.y * 16 + rl;
+  int64_t acc_i = 0;
+  double acc_f = 0.0;
+  if (r < R) {
+    for (long long c = (long long)blockIdx.x * 16 + rw; c < M; c += (long long)gridDim.x * 16) {
+      int sgn = 1;
+      for (int b = cl_ptr[c]; b < cl_ptr[c + 1]; ++b)
+        if (h[(size_t)(cl_lit[b] >> 1) * R + r] < 0.f) sgn = -sgn;
+      if (INTW) acc_i += sgn * J_i[c];
+      else acc_f += sgn * J_f[c];
+    }
+    for (long long i = (long long)blockIdx.x * 16 + rw; i < n; i += (long long)gridDim.x * 16) {
+      const int sgn = h[(size_t)i * R + r] >= 0.f ? 1 : -1;
+      if (INTW) acc_i += sgn * b_i[i];
+      else acc_f += sgn * b_f[i];
+    }
+  }
+  si[threadIdx.x] = acc_i;
+  sf[threadIdx.x] = acc_f;
+  __syncthreads();
+  if (rw == 0 && r < R) {
+    int64_t ti = 0;
+    double tf = 0.0;
+    for (int k = 0; k < 16; ++k) {
+      ti += si[k * 16 + rl];
+      tf += sf[k * 16 + rl];
+    }
+    if (INTW) part_i[(size_t)blockIdx.x * R + r] = ti;
+    else part_f[(size_t)blockIdx.x * R + r] = tf;
+  }
+}
+
+// p-spin energy of replica r = blockIdx.x from the partials (integer or fp64).
+__global__ void __launch_bounds__(kRedThreads) k_pspin_finish(const int64_t* __restrict__ part_i,
+                                                              const double* __restrict__ part_f, int32_t nblk,
+                                                              int32_t R, int32_t intw, int64_t* __restrict__ e_i,
+                                                              double* __restrict__ e_f) {
+  __shared__ int64_t shi[kRedThreads];
+  __shared__ double shf[kRedThreads];
+  const int r = blockIdx.x;
+  if (intw) {
+    const int64_t t = column_sum<int64_t>(part_i, nblk, R, r, shi);
+    if (threadIdx.x == 0) {
+      e_i[r] = t;
+      e_f[r] = (double)t;
+    }
+  } else {
+    const double t = column_sum<double>(part_f, nblk, R, r, shf);
+    if (threadIdx.x == 0) {
+      e_i[r] = 0;
+      e_f[r] = t;
+    }
+  }
 }
 
 // Per-block partial counts of unsatisfied clauses; a thread keeps one replica.
@@ -85,13 +154,14 @@ __global__ void __launch_bounds__(kRedThreads) k_sat_finish(const int64_t* __res
   }
 }
 
+// States: 1 where h >= 0, else `lo` (Max-k-SAT 0, p-spin -1).
 __global__ void k_sat_states(const float* __restrict__ h, int32_t n, int32_t R,
-                             const int32_t* __restrict__ best, int32_t* __restrict__ out, int32_t all) {
+                             const int32_t* __restrict__ best, int32_t* __restrict__ out, int32_t all, int32_t lo) {
   const size_t total = all ? (size_t)n * R : (size_t)n;
   for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
        e += (size_t)gridDim.x * blockDim.x) {
     const size_t idx = all ? e : e * R + best[0];
-    out[e] = h[idx] >= 0.f ? 1 : 0;
+    out[e] = h[idx] >= 0.f ? 1 : lo;
   }
 }
 
@@ -107,7 +177,7 @@ int grid_for(const Problem* p, long long threads, int per_sm) {
 // Marginals read by step t (buffer t%2) from the current fields.
 fem_status sat_marginals(Problem* p, int t, cudaStream_t st) {
   const long long total = (long long)p->n * p->R;
-  k_sat_marginals<<<grid_for(p, total, 8), 256, 0, st>>>(p->h[0], total, p->satP[t & 1]);
+  k_sat_marginals<<<grid_for(p, total, 8), 256, 0, st>>>(p->h[0], total, p->satP[t & 1], p->pspin ? 1 : 0);
   count_launches(1);
   FEM_CUDA(cudaGetLastError());
   return FEM_OK;
@@ -126,6 +196,8 @@ fem_status sat_steps(Problem* p, const std::vector<StepScalars>& sc, int t_begin
   a.occ_ptr = p->occ_ptr;
   a.occ = p->occ;
   a.oth = reinterpret_cast<const int2*>(p->oth);
+  a.jw = p->pspin ? p->pj : nullptr;
+  a.lin = p->pspin ? p->qoff : nullptr;
   a.n = p->n;
   a.R = p->R;
   a.opt = p->optimizer;
@@ -148,11 +220,22 @@ fem_status sat_readout(Problem* p, cudaStream_t st) {
   const int nb = (int)std::min<long long>(std::max<long long>(1, (p->n_clauses + 15) / 16),
                                           (long long)p->part_blocks);
   const dim3 grid(nb, (p->R + 15) / 16);
-  k_sat_unsat_partial<<<grid, 256, 0, st>>>(p->cl_ptr, p->cl_lit, p->n_clauses, p->h[0], p->R, p->part_i);
-  k_sat_finish<<<p->R, kRedThreads, 0, st>>>(p->part_i, nb, p->R, p->energy_i, p->energy_f);
+  if (p->pspin) {
+    if (p->pspin_int)
+      k_pspin_partial<true><<<grid, 256, 0, st>>>(p->cl_ptr, p->cl_lit, p->n_clauses, p->pj_i, p->pj_f, p->qlin_i,
+                                                  p->qlin_f, p->n, p->h[0], p->R, p->part_i, p->part_f);
+    else
+      k_pspin_partial<false><<<grid, 256, 0, st>>>(p->cl_ptr, p->cl_lit, p->n_clauses, p->pj_i, p->pj_f, p->qlin_i,
+                                                   p->qlin_f, p->n, p->h[0], p->R, p->part_i, p->part_f);
+    k_pspin_finish<<<p->R, kRedThreads, 0, st>>>(p->part_i, p->part_f, nb, p->R, p->pspin_int ? 1 : 0,
+                                                  p->energy_i, p->energy_f);
+  } else {
+    k_sat_unsat_partial<<<grid, 256, 0, st>>>(p->cl_ptr, p->cl_lit, p->n_clauses, p->h[0], p->R, p->part_i);
+    k_sat_finish<<<p->R, kRedThreads, 0, st>>>(p->part_i, nb, p->R, p->energy_i, p->energy_f);
+  }
   k_argmin_replica<<<1, 1024, 0, st>>>(p->energy_f, p->R, p->best);
   k_sat_states<<<(p->n + 255) / 256 < 1024 ? (p->n + 255) / 256 : 1024, 256, 0, st>>>(
-      p->h[0], p->n, p->R, p->best, p->states_dev, 0);
+      p->h[0], p->n, p->R, p->best, p->states_dev, 0, p->pspin ? -1 : 0);
   count_launches(4);
   FEM_CUDA(cudaGetLastError());
   return FEM_OK;
@@ -162,7 +245,7 @@ fem_status sat_states_all(Problem* p, int32_t* out, cudaStream_t st) {
   const size_t total = (size_t)p->n * p->R;
   size_t blocks = (total + 255) / 256;
   if (blocks > (size_t)p->sm_count * 16) blocks = (size_t)p->sm_count * 16;
-  k_sat_states<<<(int)blocks, 256, 0, st>>>(p->h[0], p->n, p->R, p->best, out, 1);
+  k_sat_states<<<(int)blocks, 256, 0, st>>>(p->h[0], p->n, p->R, p->best, out, 1, p->pspin ? -1 : 0);
   count_launches(1);
   FEM_CUDA(cudaGetLastError());
   return FEM_OK;

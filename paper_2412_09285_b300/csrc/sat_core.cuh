@@ -13,6 +13,8 @@ struct SatArgs {
   const int32_t* occ_ptr;  // [n+1]
   const int32_t* occ;      // [n_occ]: (clause << 3) | position
   const int2* oth;         // [n_occ] or NULL: 3-SAT, the other two literals (own negation in bit 31)
+  const float* jw;         // p-spin: term coefficients J_v (NULL: Max-k-SAT)
+  const float* lin;        // p-spin: fields b_i
   int32_t n, R, opt;
   float* h;
   float* m;
@@ -25,12 +27,16 @@ struct SatArgs {
 __device__ __forceinline__ float sigmoidf_fast(float x) { return __fdividef(1.f, 1.f + __expf(-x)); }
 
 // The update of element e = i*R + r (variable i, replica r) of one step.
+// p-spin (a.jw != NULL, SM multi-variable interactions): the marginal buffers hold
+// m = tanh(h/2), a term's factor for spin k is m_k, and
+//   g_i = gamma (1 - m_i^2)/4 [2 (sum_{v ni i} J_v prod_{k in v, k != i} m_k + b_i) + h_i/beta].
 __device__ __forceinline__ void sat_element(const SatArgs& a, const StepScalars& s, long long e) {
   {
     int i, r;
     split_element(e, a.R, i, r);
     float hi = a.h[e], mi = a.m[e];
     float vi = a.opt == FEM_OPT_SGD ? 0.f : a.v[e];
+    const bool pspin = a.jw != nullptr;
     float G = 0.f;
     const int ob = a.occ_ptr[i], oe = a.occ_ptr[i + 1];
     for (int o = ob; o < oe; ++o) {
@@ -46,16 +52,17 @@ __device__ __forceinline__ void sat_element(const SatArgs& a, const StepScalars&
           continue;
         }
         const float pk = a.P_in[(size_t)(lit >> 1) * a.R + r];
-        prod *= (lit & 1) ? pk : 1.f - pk;
+        prod *= pspin ? pk : ((lit & 1) ? pk : 1.f - pk);
       }
-      G = fmaf(sgn, prod, G);
+      G = fmaf(pspin ? a.jw[c] : sgn, prod, G);
     }
-    const float g = s.gq * (hi * s.inv_beta - G) * one_minus_m2_fast(hi);
+    const float g = pspin ? s.gq * fmaf(2.f, G + a.lin[i], hi * s.inv_beta) * one_minus_m2_fast(hi)
+                          : s.gq * (hi * s.inv_beta - G) * one_minus_m2_fast(hi);
     opt_update_fast_rt(a.opt, hi, mi, vi, g, s);
     a.h[e] = hi;
     a.m[e] = mi;
     if (a.opt != FEM_OPT_SGD) a.v[e] = vi;
-    a.P_out[e] = sigmoidf_fast(hi);
+    a.P_out[e] = pspin ? tanhf(0.5f * hi) : sigmoidf_fast(hi);
   }
 }
 
@@ -66,7 +73,9 @@ __device__ __forceinline__ void sat_element(const SatArgs& a, const StepScalars&
 // variable waits for a few memory round trips instead of four per occurrence.  The
 // products and the sum over occurrences run in the order of sat_element, so both
 // give the same bits.
-__device__ __forceinline__ bool sat_k3_shape(const SatArgs& a) { return a.oth && (a.R == 16 || a.R % 32 == 0); }
+__device__ __forceinline__ bool sat_k3_shape(const SatArgs& a) {
+  return a.oth && !a.jw && (a.R == 16 || a.R % 32 == 0);
+}
 
 __device__ __forceinline__ void sat_element_k3(const SatArgs& a, const StepScalars& s, long long e, bool act,
                                                int lane) {

@@ -24,9 +24,9 @@ FEM_OPT_ADAM, FEM_OPT_RMSPROP, FEM_OPT_SGD = 0, 1, 2
 FEM_GRAD_EXACT, FEM_GRAD_PAPER = 0, 1
 FEM_PREC_FP32, FEM_PREC_BF16, FEM_PREC_BF16X2, FEM_PREC_FP8 = 0, 1, 2, 3
 
-FEM_COLORING, FEM_QUBO = 3, 4
+FEM_COLORING, FEM_QUBO, FEM_PSPIN = 3, 4, 5
 KINDS = {"maxcut": FEM_MAXCUT, "bmincut": FEM_BMINCUT, "sat": FEM_MAXKSAT, "coloring": FEM_COLORING,
-         "qubo": FEM_QUBO}
+         "qubo": FEM_QUBO, "pspin": FEM_PSPIN}
 Q_STATE_KINDS = ("bmincut", "coloring")
 SCHEDULES = {"exponential": FEM_SCHED_EXPONENTIAL, "inverse_proportional": FEM_SCHED_INVERSE_PROPORTIONAL}
 OPTIMIZERS = {"adam": FEM_OPT_ADAM, "rmsprop": FEM_OPT_RMSPROP, "sgd": FEM_OPT_SGD}
@@ -40,7 +40,7 @@ class fem_problem_desc(C.Structure):
         ("n_edges", C.c_int64), ("ei", C.c_void_p), ("ej", C.c_void_p), ("w", C.c_void_p),
         ("dense_J", C.c_void_p),
         ("n_clauses", C.c_int64), ("clause_ptr", C.c_void_p), ("lits", C.c_void_p),
-        ("node_weight", C.c_void_p), ("linear", C.c_void_p),
+        ("node_weight", C.c_void_p), ("linear", C.c_void_p), ("term_weight", C.c_void_p),
     ]
 
 
@@ -243,7 +243,7 @@ class Problem:
     from ``instances``); h_init may also be a CUDA torch tensor."""
 
     def __init__(self, kind="maxcut", graph=None, clauses=None, dense=None, q=2, stream=None, node_weight=None,
-                 linear=None):
+                 linear=None, term_weight=None):
         self.kind = kind
         self.stream = stream
         d = fem_problem_desc()
@@ -257,6 +257,10 @@ class Problem:
             w = np.ascontiguousarray(graph.w, np.float64)
             self._keep += [ei, ej, w]
             d.n_edges, d.ei, d.ej, d.w = ei.shape[0], _ptr(ei), _ptr(ej), _ptr(w)
+        if term_weight is not None:
+            T = np.ascontiguousarray(term_weight, np.float64)
+            self._keep.append(T)
+            d.term_weight = _ptr(T)
         if linear is not None:
             L = np.ascontiguousarray(linear, np.float64)
             self._keep.append(L)

@@ -186,7 +186,7 @@ def _traffic_from_profile(name, kind):
     return int(m2.group(1)) if source_sha256(kind) == m1.group(1) else None
 
 
-def _roofline(wl, inst, step_ms, precision, persistent=False, grad_mode="paper"):
+def _roofline(wl, inst, step_ms, precision, dense_launch=None, grad_mode="paper"):
     """Algorithmic work of one step launch / its measured duration, against the peak."""
     peaks, src = _peaks()
     csrc = os.path.join(ROOT, "paper_2412_09285_b300", "csrc")
@@ -245,8 +245,11 @@ def _roofline(wl, inst, step_ms, precision, persistent=False, grad_mode="paper")
         bound = "tensor"
         psrc = (f"{src} bf16_tflops_sustained" + (" x 2 (nominal fp8/bf16 ratio)" if precision == "fp8" else "")
                 + f", of {src}")
-    if persistent:
-        # one cooperative launch runs the whole timed window; figures are per step
+    persistent = dense_launch in ("persistent", "persistent_single")
+    if dense_launch == "persistent":
+        # one launch of CTA pairs runs the whole timed window; figures are per step
+        kernel, prof = f"k_dense_anneal_tc<{precision}, pair>", f"dense_anneal_{precision}_pair_sk2000_R1024.md"
+    elif persistent:
         kernel, prof = f"k_dense_anneal_tc<{precision}>", f"dense_anneal_{precision}_sk2000_R1024.md"
     else:
         kernel = f"k_dense_step_{'fp32' if precision == 'fp32' else 'tc<' + precision + '>'}"
@@ -432,19 +435,15 @@ def run_ours(args, wl):
     grad_mode = args.grad_mode or ("exact" if precision == "bf16x2" else "paper")
     kw = dict(grad_mode=grad_mode, optimizer="adam", lr=0.1, precision=precision)
 
-    window_launches = []
-
     def one_anneal(k, events):
         """Fresh fields from the resident h0, then k steps, then the read-out.  Events
         bracket steps 1..k-1 so the per-launch step time excludes the initialisation."""
         prob.anneal(h_init=h0, replicas=R, n_steps=n_steps, t_begin=0, t_end=1, **kw)
         if k > 1:
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            l0 = fem.fem_kernel_launches()
             e0.record(stream)
             prob.anneal(replicas=R, n_steps=n_steps, t_begin=1, t_end=k, **kw)
             e1.record(stream)
-            window_launches.append(fem.fem_kernel_launches() - l0)
             events.append((e0, e1, k - 1))
         return prob.best()
 
@@ -524,7 +523,7 @@ def run_ours(args, wl):
                        "l2": ("inputs larger than L2" if wl["kind"] == "sparse" and inst.n > 100000
                               else "working set L2-resident (latency/compute-bound workload)")},
             "roofline": _roofline(wl, inst, step_ms, precision,
-                                  persistent=bool(window_launches) and window_launches[-1] == 1,
+                                  dense_launch=prob.dense_last_launch() if wl["kind"] == "dense" else None,
                                   grad_mode=grad_mode), "gpu_launches": int(launches), "e2e": e2e,
             "clocks": clk.summary(),
             "best_energy": float(best["energy_f64"][best["best_replica"]])}
@@ -682,8 +681,9 @@ def main():
     ap.add_argument("--precision", default="bf16", choices=["bf16", "fp8", "bf16x2", "fp32"])
     ap.add_argument("--grad-mode", default=None, choices=["paper", "exact"],
                     help="sparse workloads: the discretised (paper) or exact gradient (default paper)")
-    ap.add_argument("--dense-launch", default="auto", choices=["auto", "per_step", "persistent"],
-                    help="dense workload: persistent (state in tensor memory) or one kernel per step")
+    ap.add_argument("--dense-launch", default="auto", choices=["auto", "per_step", "persistent", "persistent_single"],
+                    help="dense workload: persistent (state in tensor memory; CTA pairs where the row tiles "
+                         "pair up, persistent_single without pairs) or one kernel per step")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ttt", action="store_true",
                     help="time to target cut of the dense, batched or warmstart workload against plain FP32 FEM")

@@ -99,18 +99,26 @@ typedef enum { FEM_GRAD_EXACT = 0, FEM_GRAD_PAPER = 1 } fem_grad_mode;
  *            the discretised +-1 marginals and integer couplings |J| <= 16 are exact). */
 typedef enum { FEM_PREC_FP32 = 0, FEM_PREC_BF16 = 1, FEM_PREC_BF16X2 = 2, FEM_PREC_FP8 = 3 } fem_precision;
 
-/* How a dense tensor-core anneal is launched (fem_set_dense_launch).  Both give
- * bit-identical fields; they differ only in where the optimizer state lives.
+/* How a dense tensor-core anneal is launched (fem_set_dense_launch).  All give
+ * bit-identical fields; they differ only in where the optimizer state lives and how
+ * the CTAs share the contraction.
  *   AUTO        PERSISTENT when the problem fits it, else PER_STEP (the default).
  *   PER_STEP    one kernel per step; h, m, v stay in global memory.
- *   PERSISTENT  one cooperative kernel per fem_anneal window: every CTA keeps its
- *               128 x 128 (rows x replicas) tile of h, m, v in tensor memory for the
- *               whole window and meets the other CTAs of its replica block at a
- *               barrier after each step.  Needs precision BF16, BF16X2 or FP8,
- *               R % 128 == 0 and (n_pad/128) * (R/128) <= the number of SMs, where
- *               n_pad = n rounded up to 128; fem_anneal returns FEM_ERR_UNSUPPORTED
- *               otherwise. */
-typedef enum { FEM_DENSE_AUTO = 0, FEM_DENSE_PER_STEP = 1, FEM_DENSE_PERSISTENT = 2 } fem_dense_launch;
+ *   PERSISTENT  one kernel per fem_anneal window: every CTA keeps its 128 x 128
+ *               (rows x replicas) tile of h, m, v in tensor memory for the whole
+ *               window and meets the other CTAs of its replica block at a barrier
+ *               after each step.  With an even number of row tiles, CTAs run in
+ *               pairs (clusters of 2) that issue 256-row MMAs together, each copying
+ *               half of the operand; otherwise one CTA per tile.  Needs precision BF16, BF16X2 or FP8, R % 128 == 0 and
+ *               (n_pad/128) * (R/128) co-resident CTAs (one per SM), where n_pad = n
+ *               rounded up to 128; fem_anneal returns FEM_ERR_UNSUPPORTED otherwise.
+ *   PERSISTENT_SINGLE  PERSISTENT without CTA pairs (one CTA per row tile). */
+typedef enum {
+  FEM_DENSE_AUTO = 0,
+  FEM_DENSE_PER_STEP = 1,
+  FEM_DENSE_PERSISTENT = 2,
+  FEM_DENSE_PERSISTENT_SINGLE = 3
+} fem_dense_launch;
 
 typedef struct fem_problem* fem_problem_t; /* opaque; owned by the library until fem_destroy */
 
@@ -326,17 +334,27 @@ fem_status fem_sync(fem_problem_t p, void* stream);
  * FEM_ERR_INVALID_ARG for other values or a problem without dense couplings. */
 fem_status fem_set_dense_launch(fem_problem_t p, int32_t mode);
 
+/* The kernel the last fem_anneal window of a dense problem ran on: FEM_DENSE_PER_STEP,
+ * FEM_DENSE_PERSISTENT (CTA pairs) or FEM_DENSE_PERSISTENT_SINGLE; 0 before the
+ * first window, and for problems without dense couplings. */
+fem_status fem_dense_last_launch(fem_problem_t p, int32_t* mode);
+
 /* Failure detection (no counterpart in the paper).
  *   fem_set_step_barrier_timeout: the limit, in ns, on the persistent dense kernel's
  *     per-step barrier between CTAs (default 2 s).  A CTA that waits longer records
  *     FEM_ERR_TIMEOUT in the problem's sticky error word, lets its own copies and MMAs
  *     land, frees its tensor memory and returns; the others give up in turn.  The error
  *     surfaces on the next fem_read_* / fem_sync call; an fem_anneal with t_begin == 0
- *     clears it.  0 gives up at the first check (tests use it to exercise the path).
+ *     clears it.
+ *   fem_inject_step_stall: the persistent dense kernel's CTAs of row tile `row_tile`
+ *     (rows 128 * row_tile ..) stop arriving at the step barrier, so the waits of the
+ *     other CTAs of their replica blocks run out (tests of the timeout path without a
+ *     GPU fault); -1 switches it off.  FEM_ERR_INVALID_ARG for row_tile < -1.
  *   fem_inject_allocation_failure: after `after` >= 0 further successful device
  *     allocations of problems, the next one fails with FEM_ERR_OOM (then the injection
  *     switches itself off); -1 disables it.  Process-wide, for tests. */
 fem_status fem_set_step_barrier_timeout(fem_problem_t p, int64_t ns);
+fem_status fem_inject_step_stall(fem_problem_t p, int32_t row_tile);
 void fem_inject_allocation_failure(int64_t after);
 
 /* Release every resource owned by p (NULL is ignored). */

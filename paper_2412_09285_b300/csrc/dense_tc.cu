@@ -103,6 +103,15 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* tm, in
       ::"r"(smem_u32(dst)), "l"(tm), "r"(x), "r"(y), "r"(smem_u32(bar))
       : "memory");
 }
+// CTA pair: a copy into this CTA's shared memory whose completion is counted on an
+// mbarrier of the pair's even CTA (`bar` is its shared::cluster address).
+__device__ __forceinline__ void tma_load_2d_pair(void* dst, const CUtensorMap* tm, int x, int y, uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes.cta_group::2 [%0], [%1, {%2, "
+      "%3}], [%4];" ::"r"(smem_u32(dst)),
+      "l"(tm), "r"(x), "r"(y), "r"(bar)
+      : "memory");
+}
 __device__ __forceinline__ void tmem_alloc(uint32_t* dst, uint32_t ncols) {
   asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(dst)), "r"(ncols)
                : "memory");
@@ -110,6 +119,31 @@ __device__ __forceinline__ void tmem_alloc(uint32_t* dst, uint32_t ncols) {
 }
 __device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
   asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+// CTA-pair forms: one warp of each CTA of the pair executes them; the allocation has
+// the same address in both CTAs.
+__device__ __forceinline__ void tmem_alloc_pair(uint32_t* dst, uint32_t ncols) {
+  asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(dst)), "r"(ncols)
+               : "memory");
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc_pair(uint32_t taddr, uint32_t ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+__device__ __forceinline__ uint32_t cluster_rank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+// Every thread of both CTAs of the pair; also orders their memory accesses.
+__device__ __forceinline__ void cluster_sync_all() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+// Address of the same shared variable in the CTA of the given rank of this cluster.
+__device__ __forceinline__ uint32_t cluster_addr(const void* p, uint32_t rank) {
+  uint32_t r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(smem_u32(p)), "r"(rank));
+  return r;
 }
 __device__ __forceinline__ void tc_fence_before() {
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -132,6 +166,31 @@ __device__ __forceinline__ void umma_f8(uint32_t d, uint64_t a, uint64_t b, uint
 __device__ __forceinline__ void umma_commit(uint64_t* bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
                : "memory");
+}
+// CTA pair (M = 256): A rows 0..127 come from this CTA's shared memory and rows
+// 128..255 from the same offsets in the other CTA's; B's N columns are split the same
+// way, and each CTA's tensor memory receives its own 128 rows of D.
+__device__ __forceinline__ void umma_f16_pair(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::2.kind::f16 [%0], %1, %2, %3, p;\n}\n"
+      ::"r"(d), "l"(a), "l"(b), "r"(idesc), "r"(acc)
+      : "memory");
+}
+__device__ __forceinline__ void umma_f8_pair(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::2.kind::f8f6f4 [%0], %1, %2, %3, p;\n}\n"
+      ::"r"(d), "l"(a), "l"(b), "r"(idesc), "r"(acc)
+      : "memory");
+}
+// Arrives on the barrier at this offset in both CTAs of the pair once the MMAs issued
+// so far have completed.
+__device__ __forceinline__ void umma_commit_pair(uint64_t* bar) {
+  const uint16_t both = 0x3;
+  asm volatile(
+      "tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(
+          smem_u32(bar)),
+      "h"(both)
+      : "memory");
 }
 // TMEM <-> registers, 32 lanes x 8 columns.  A load is issued without waiting; its
 // outputs are tied to tmem_wait_ld, which every reader calls first (it waits for all
@@ -168,9 +227,10 @@ __device__ __forceinline__ uint64_t desc_sw128(uint32_t saddr) {
 }
 
 // Instruction descriptor: fp32 accumulator, A and B of format `fmt` (kind::f16:
-// 1 = bf16; kind::f8f6f4: 0 = e4m3), both K-major, N = 128, M = 128.
-__host__ __device__ constexpr uint32_t make_idesc(uint32_t fmt) {
-  return (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(kTile >> 3) << 17) | ((uint32_t)(kTile >> 4) << 24);
+// 1 = bf16; kind::f8f6f4: 0 = e4m3), both K-major, N = 128, M = 128 (one CTA) or
+// 256 (a CTA pair).
+__host__ __device__ constexpr uint32_t make_idesc(uint32_t fmt, uint32_t m = kTile) {
+  return (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(kTile >> 3) << 17) | ((m >> 4) << 24);
 }
 
 __device__ __forceinline__ uint16_t bf16_bits(float x) {
@@ -400,17 +460,27 @@ __global__ void __launch_bounds__(kThreads, 1) k_dense_step_tc(const __grid_cons
 }
 
 // --------------------------------------------- persistent anneal (one launch)
-// The step above, run for a whole window of steps by one cooperative launch.  Each
-// CTA keeps its 128 x 128 tile of h, m and v in tensor memory for the whole window
-// (TMEM columns 128.., 256.., 384..; the accumulator uses 0..127), so the optimizer
-// state is read from global memory once at the start and written once at the end.
+// The step above, run for a whole window of steps by one launch.  Each CTA keeps its
+// 128 x 128 tile of h, m and v in tensor memory for the whole window (TMEM columns
+// 128.., 256.., 384..; the accumulator uses 0..127), so the optimizer state is read
+// from global memory once at the start and written once at the end.
+//
 // Per step the only data a CTA needs from other CTAs is the next operand M^T of its
 // replica block, written by the n_pad/128 CTAs that share blockIdx.y; those CTAs meet
 // at a counter barrier in global memory after each step (release/acquire at GPU
 // scope, plus a proxy fence because the operand is written with ordinary stores and
-// read by TMA).  All waits are bounded; a CTA that gives up records the timeout bit,
-// lets its copies and MMAs in flight land, frees its TMEM and leaves, and the CTAs
-// waiting for it give up in turn.
+// read by TMA).
+//
+// PAIR: two CTAs (a cluster of 2, row tiles 2p and 2p + 1) issue M = 256 MMAs
+// together.  Each loads its own 128 rows of J and half of the 128 replica columns of
+// M^T, so a CTA copies 1.5 instead of 2 bytes into shared memory per byte of J it
+// uses.  Both CTAs' copies of a stage complete on the even CTA's barrier, which
+// expects the bytes of both; the even CTA issues the MMAs, and its commits arrive on
+// the barriers of both CTAs.
+//
+// All waits are bounded; a CTA that gives up records the timeout bit, lets its copies
+// and MMAs in flight land, frees its TMEM and leaves, and the CTAs waiting for it give
+// up in turn.
 constexpr int kTmemCols = 4 * kTile;  // accumulator, h, m, v
 
 struct DenseAnnealArgs {
@@ -421,6 +491,7 @@ struct DenseAnnealArgs {
   int32_t t_begin, n_steps;
   int32_t* bar;              // one arrival counter per replica block (stride 32 ints), zero at launch
   unsigned long long bar_wait_ns;  // limit on the step barrier (the copy and MMA waits keep kWaitNs)
+  int32_t stall_tile;        // tests: the CTAs of this row tile never arrive at the barrier (-1: none)
 };
 
 __device__ __forceinline__ bool wait_counter(const int32_t* ctr, int32_t target, int32_t* err,
@@ -437,7 +508,15 @@ __device__ __forceinline__ bool wait_counter(const int32_t* ctr, int32_t target,
   }
 }
 
-template <int PREC>
+__host__ __device__ constexpr int anneal_stages(int prec, bool pair) {
+  return pair ? (prec == FEM_PREC_BF16X2 ? 6 : 8) : stages_for(prec);
+}
+__host__ __device__ constexpr uint32_t anneal_stage_bytes(int prec, bool pair) {
+  return (uint32_t)(kTile * kChunkBytes + (pair ? kTile / 2 : kTile) * kChunkBytes * (prec == FEM_PREC_BF16X2 ? 2 : 1));
+}
+constexpr int kMaxAnnealStages = 8;
+
+template <int PREC, bool PAIR>
 __global__ void __launch_bounds__(kThreads, 1) k_dense_anneal_tc(const __grid_constant__ CUtensorMap tmA,
                                                            const __grid_constant__ CUtensorMap tmB0,
                                                            const __grid_constant__ CUtensorMap tmB1,
@@ -448,16 +527,19 @@ __global__ void __launch_bounds__(kThreads, 1) k_dense_anneal_tc(const __grid_co
   constexpr int kElem = PREC == FEM_PREC_FP8 ? 1 : 2;
   constexpr int kChunkK = kChunkBytes / kElem;
   constexpr int kMmaK = PREC == FEM_PREC_FP8 ? 32 : 16;
-  constexpr uint32_t kTileBytes = kTile * kChunkBytes;
-  constexpr uint32_t kStageBytes = kTileBytes * (X2 ? 3 : 2);
-  constexpr uint32_t kIdesc = make_idesc(PREC == FEM_PREC_FP8 ? 0u : 1u);
-  constexpr int kStages = stages_for(PREC);
+  constexpr int kBRows = PAIR ? kTile / 2 : kTile;  // replica rows of M^T this CTA copies
+  constexpr uint32_t kATileBytes = kTile * kChunkBytes;
+  constexpr uint32_t kBTileBytes = kBRows * kChunkBytes;
+  constexpr uint32_t kStageBytes = anneal_stage_bytes(PREC, PAIR);
+  constexpr uint32_t kIdesc = make_idesc(PREC == FEM_PREC_FP8 ? 0u : 1u, PAIR ? 2 * kTile : kTile);
+  constexpr int kStages = anneal_stages(PREC, PAIR);
+  static_assert(kStageBytes % 1024 == 0 && kBTileBytes % 1024 == 0, "128B-swizzled tiles need 1 KB alignment");
   constexpr int kCols = 8;  // replica columns per TMEM load / store in the epilogue
 
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  __shared__ __align__(8) uint64_t full[kMaxStages];
-  __shared__ __align__(8) uint64_t empty[kMaxStages];
+  __shared__ __align__(8) uint64_t full[kMaxAnnealStages];
+  __shared__ __align__(8) uint64_t empty[kMaxAnnealStages];
   __shared__ __align__(8) uint64_t done;
   __shared__ uint32_t tmem_base_slot;
   __shared__ int32_t abort_flag;
@@ -466,6 +548,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_dense_anneal_tc(const __grid_co
 
   const DenseArgs& a = x.a;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint32_t rank = PAIR ? cluster_rank() : 0u;
+  const bool issuer = rank == 0;  // issues the MMAs (always, without PAIR)
   const int i0 = blockIdx.x * kTile, r0 = blockIdx.y * kTile;
   const int nchunks = a.n_pad / kChunkK;
 
@@ -479,7 +563,11 @@ __global__ void __launch_bounds__(kThreads, 1) k_dense_anneal_tc(const __grid_co
     if (x.n_steps > 0) s_sc = x.sc[0];
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  if (warp == 0) tmem_alloc(&tmem_base_slot, kTmemCols);
+  if (PAIR) cluster_sync_all();  // the other CTA's barriers exist before anything arrives on them
+  if (warp == 0) {
+    if (PAIR) tmem_alloc_pair(&tmem_base_slot, kTmemCols);
+    else tmem_alloc(&tmem_base_slot, kTmemCols);
+  }
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
@@ -527,13 +615,21 @@ __global__ void __launch_bounds__(kThreads, 1) k_dense_anneal_tc(const __grid_co
           break;
         }
         uint8_t* sa = smem + st * kStageBytes;
-        mbar_expect_tx(&full[st], kStageBytes);
-        tma_load_2d(sa, &tmA, kc * kChunkK, i0, &full[st]);
-        tma_load_2d(sa + kTileBytes, mb, kc * kChunkK, r0, &full[st]);
-        if (X2) tma_load_2d(sa + 2 * kTileBytes, mlo, kc * kChunkK, r0, &full[st]);
+        const int x0 = kc * kChunkK, rb = r0 + (int)rank * kBRows;
+        if (issuer) {
+          mbar_expect_tx(&full[st], PAIR ? 2 * kStageBytes : kStageBytes);  // a pair: both CTAs' copies
+          tma_load_2d(sa, &tmA, x0, i0, &full[st]);
+          tma_load_2d(sa + kATileBytes, mb, x0, rb, &full[st]);
+          if (X2) tma_load_2d(sa + kATileBytes + kBTileBytes, mlo, x0, rb, &full[st]);
+        } else {
+          const uint32_t bar = cluster_addr(&full[st], 0);
+          tma_load_2d_pair(sa, &tmA, x0, i0, bar);
+          tma_load_2d_pair(sa + kATileBytes, mb, x0, rb, bar);
+          if (X2) tma_load_2d_pair(sa + kATileBytes + kBTileBytes, mlo, x0, rb, bar);
+        }
         issued = g + 1;
       }
-    } else if (threadIdx.x == 32) {
+    } else if (threadIdx.x == 32 && issuer) {
       for (int kc = 0; kc < nchunks; ++kc) {
         const int g = k * nchunks + kc, st = g % kStages;
         if (!mbar_wait(&full[st], (g / kStages) & 1, a.err)) {
@@ -542,19 +638,28 @@ __global__ void __launch_bounds__(kThreads, 1) k_dense_anneal_tc(const __grid_co
         }
         tc_fence_after();
         const uint32_t sa = smem_u32(smem + st * kStageBytes);
-        const uint64_t da = desc_sw128(sa), db = desc_sw128(sa + kTileBytes);
-        const uint64_t dblo = desc_sw128(sa + 2 * kTileBytes);
+        const uint64_t da = desc_sw128(sa), db = desc_sw128(sa + kATileBytes);
+        const uint64_t dblo = desc_sw128(sa + kATileBytes + kBTileBytes);
 #pragma unroll
         for (int kk = 0; kk < kChunkK / kMmaK; ++kk) {
           const uint64_t adv = (uint64_t)((kk * kMmaK * kElem) >> 4);
           const uint32_t acc = (kc > 0 || kk > 0) ? 1u : 0u;
-          if (PREC == FEM_PREC_FP8) umma_f8(tmem, da + adv, db + adv, kIdesc, acc);
-          else umma_f16(tmem, da + adv, db + adv, kIdesc, acc);
-          if (X2) umma_f16(tmem, da + adv, dblo + adv, kIdesc, 1u);
+          if (PAIR) {
+            if (PREC == FEM_PREC_FP8) umma_f8_pair(tmem, da + adv, db + adv, kIdesc, acc);
+            else umma_f16_pair(tmem, da + adv, db + adv, kIdesc, acc);
+            if (X2) umma_f16_pair(tmem, da + adv, dblo + adv, kIdesc, 1u);
+          } else {
+            if (PREC == FEM_PREC_FP8) umma_f8(tmem, da + adv, db + adv, kIdesc, acc);
+            else umma_f16(tmem, da + adv, db + adv, kIdesc, acc);
+            if (X2) umma_f16(tmem, da + adv, dblo + adv, kIdesc, 1u);
+          }
         }
-        umma_commit(&empty[st]);
+        if (PAIR) umma_commit_pair(&empty[st]);
+        else umma_commit(&empty[st]);
       }
-      umma_commit(&done);  // also after a failed wait: done then tracks the MMAs issued
+      // also after a failed wait: done then tracks the MMAs issued
+      if (PAIR) umma_commit_pair(&done);
+      else umma_commit(&done);
     }
     __syncwarp();
 
@@ -612,7 +717,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_dense_anneal_tc(const __grid_co
     if (threadIdx.x == 0 && k + 1 < x.n_steps && !*abort_v) {
       int32_t* ctr = x.bar + blockIdx.y * 32;
       asm volatile("fence.proxy.async.global;" ::: "memory");
-      asm volatile("red.release.gpu.global.add.s32 [%0], 1;" ::"l"(ctr) : "memory");  // cumulative over bar.sync
+      if ((int)blockIdx.x != x.stall_tile)
+        asm volatile("red.release.gpu.global.add.s32 [%0], 1;" ::"l"(ctr) : "memory");  // cumulative over bar.sync
       if (!wait_counter(ctr, (k + 1) * (int32_t)gridDim.x, a.err, x.bar_wait_ns)) *abort_v = 1;
       asm volatile("fence.proxy.async.global;" ::: "memory");
     }
@@ -624,7 +730,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_dense_anneal_tc(const __grid_co
 
   if (*abort_v) {
     // let the stage loads still in flight land before the CTA's shared memory is released
-    if (threadIdx.x == 0)
+    // (a pair's odd CTA counts its copies on the even CTA's barriers, which wait for both)
+    if (threadIdx.x == 0 && issuer)
       for (int g = issued - kStages < 0 ? 0 : issued - kStages; g < issued; ++g)
         mbar_wait(&full[g % kStages], (g / kStages) & 1, a.err);
   } else {
@@ -650,10 +757,13 @@ __global__ void __launch_bounds__(kThreads, 1) k_dense_anneal_tc(const __grid_co
     }
   }
   tc_fence_before();
-  __syncthreads();
+  // neither CTA of a pair leaves while the other may still use its shared or tensor memory
+  if (PAIR) cluster_sync_all();
+  else __syncthreads();
   if (warp == 0) {
     tc_fence_after();
-    tmem_dealloc(tmem, kTmemCols);
+    if (PAIR) tmem_dealloc_pair(tmem, kTmemCols);
+    else tmem_dealloc(tmem, kTmemCols);
   }
 }
 
@@ -857,13 +967,13 @@ PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
   return fn;
 }
 
-// 2D K-major map: rows x n_pad elements, box = 128 rows x 128 bytes, 128B swizzle.
-fem_status make_map(CUtensorMap* m, const void* base, int rows, int n_pad, int elem_bytes) {
+// 2D K-major map: rows x n_pad elements, box = box_rows rows x 128 bytes, 128B swizzle.
+fem_status make_map(CUtensorMap* m, const void* base, int rows, int n_pad, int elem_bytes, int box_rows = kTile) {
   auto enc = get_encode();
   if (!enc) return fail(FEM_ERR_CUDA, "cuTensorMapEncodeTiled is not available");
   const cuuint64_t dims[2] = {(cuuint64_t)n_pad, (cuuint64_t)rows};
   const cuuint64_t strides[1] = {(cuuint64_t)n_pad * elem_bytes};
-  const cuuint32_t box[2] = {(cuuint32_t)(kChunkBytes / elem_bytes), (cuuint32_t)kTile};
+  const cuuint32_t box[2] = {(cuuint32_t)(kChunkBytes / elem_bytes), (cuuint32_t)box_rows};
   const cuuint32_t estr[2] = {1, 1};
   const CUresult r = enc(m, elem_bytes == 2 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_UINT8, 2,
                          const_cast<void*>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
@@ -893,34 +1003,83 @@ fem_status launch_tc(Problem* p, const DenseArgs& a, const StepScalars& s, int i
   return FEM_OK;
 }
 
-// Whether the persistent kernel can run this problem: tensor-core precision, whole
-// replica tiles, and every CTA co-resident (one per SM).
-template <int PREC>
+size_t anneal_smem_bytes(int prec, bool pair) {
+  return (size_t)anneal_stages(prec, pair) * anneal_stage_bytes(prec, pair) + 1024;
+}
+
+cudaLaunchConfig_t anneal_config(Problem* p, int prec, bool pair, cudaLaunchAttribute* attr, bool cooperative,
+                                 cudaStream_t st) {
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = dim3(p->n_pad / kTile, p->R / kTile);
+  cfg.blockDim = dim3(kThreads);
+  cfg.dynamicSmemBytes = anneal_smem_bytes(prec, pair);
+  cfg.stream = st;
+  int na = 0;
+  if (pair) {
+    attr[na].id = cudaLaunchAttributeClusterDimension;
+    attr[na].val.clusterDim.x = 2;
+    attr[na].val.clusterDim.y = 1;
+    attr[na].val.clusterDim.z = 1;
+    ++na;
+  }
+  if (cooperative) {
+    attr[na].id = cudaLaunchAttributeCooperative;
+    attr[na].val.cooperative = 1;
+    ++na;
+  }
+  cfg.attrs = attr;
+  cfg.numAttrs = na;
+  return cfg;
+}
+
+// Whether a persistent kernel can run this problem: tensor-core precision, whole
+// replica tiles, an even number of row tiles for CTA pairs, and every CTA co-resident
+// (one per SM; for pairs, as many co-resident clusters as the grid has).
+template <int PREC, bool PAIR>
 bool anneal_fits(Problem* p) {
+  if (p->R % kTile != 0 || p->R == 0) return false;
+  const int tiles = p->n_pad / kTile;
+  if (PAIR && tiles % 2 != 0) return false;
+  const long grid = (long)tiles * (p->R / kTile);
   static int per_sm = -1;
   if (per_sm < 0) {
-    if (cudaFuncSetAttribute(k_dense_anneal_tc<PREC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)tc_smem_bytes(PREC)) != cudaSuccess ||
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_dense_anneal_tc<PREC>, kThreads,
-                                                      tc_smem_bytes(PREC)) != cudaSuccess) {
+    if (cudaFuncSetAttribute(k_dense_anneal_tc<PREC, PAIR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)anneal_smem_bytes(PREC, PAIR)) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_dense_anneal_tc<PREC, PAIR>, kThreads,
+                                                      anneal_smem_bytes(PREC, PAIR)) != cudaSuccess) {
       cudaGetLastError();
       per_sm = 0;
     }
   }
-  const long grid = (long)(p->n_pad / kTile) * (p->R / kTile);
-  return p->R % kTile == 0 && per_sm > 0 && grid <= (long)per_sm * p->sm_count;
+  if (per_sm <= 0 || grid > (long)per_sm * p->sm_count) return false;
+  if (!PAIR) return true;
+  cudaLaunchAttribute attr[2];
+  cudaLaunchConfig_t cfg = anneal_config(p, PREC, true, attr, false, nullptr);
+  int clusters = 0;
+  if (cudaOccupancyMaxActiveClusters(&clusters, k_dense_anneal_tc<PREC, PAIR>, &cfg) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return (long)clusters * 2 >= grid;
 }
 
-bool anneal_fits_any(Problem* p) {
+// The persistent kernel a window runs on: 2 = CTA pairs, 1 = one CTA per tile, 0 = none.
+int anneal_kind(Problem* p) {
+  const bool single_only = p->dense_launch == FEM_DENSE_PERSISTENT_SINGLE;
   switch (p->precision) {
-    case FEM_PREC_BF16: return anneal_fits<FEM_PREC_BF16>(p);
-    case FEM_PREC_BF16X2: return anneal_fits<FEM_PREC_BF16X2>(p);
-    case FEM_PREC_FP8: return anneal_fits<FEM_PREC_FP8>(p);
-    default: return false;
+    case FEM_PREC_BF16:
+      return !single_only && anneal_fits<FEM_PREC_BF16, true>(p) ? 2 : anneal_fits<FEM_PREC_BF16, false>(p) ? 1 : 0;
+    case FEM_PREC_BF16X2:
+      return !single_only && anneal_fits<FEM_PREC_BF16X2, true>(p) ? 2
+             : anneal_fits<FEM_PREC_BF16X2, false>(p)              ? 1
+                                                                   : 0;
+    case FEM_PREC_FP8:
+      return !single_only && anneal_fits<FEM_PREC_FP8, true>(p) ? 2 : anneal_fits<FEM_PREC_FP8, false>(p) ? 1 : 0;
+    default: return 0;
   }
 }
 
-template <int PREC>
+template <int PREC, bool PAIR>
 fem_status launch_anneal_tc(Problem* p, const DenseArgs& a, int t_begin, int n_steps, cudaStream_t st) {
   DenseAnnealArgs x{};
   x.a = a;
@@ -933,22 +1092,33 @@ fem_status launch_anneal_tc(Problem* p, const DenseArgs& a, int t_begin, int n_s
   x.n_steps = n_steps;
   x.bar = p->dense_bar;
   x.bar_wait_ns = (unsigned long long)p->barrier_wait_ns;
-  const int groups = p->R / kTile;
-  FEM_CUDA(cudaMemsetAsync(p->dense_bar, 0, (size_t)groups * 32 * sizeof(int32_t), st));
+  x.stall_tile = p->stall_tile;
+  FEM_CUDA(cudaMemsetAsync(p->dense_bar, 0, (size_t)(p->R / kTile) * 32 * sizeof(int32_t), st));
   const bool x2 = PREC == FEM_PREC_BF16X2;
-  cudaLaunchConfig_t cfg{};
-  cfg.gridDim = dim3(p->n_pad / kTile, groups);
-  cfg.blockDim = dim3(kThreads);
-  cfg.dynamicSmemBytes = tc_smem_bytes(PREC);
-  cfg.stream = st;
-  cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributeCooperative;
-  attr[0].val.cooperative = 1;
-  cfg.attrs = attr;
-  cfg.numAttrs = 1;
-  FEM_CUDA(cudaLaunchKernelEx(&cfg, k_dense_anneal_tc<PREC>, PREC == FEM_PREC_FP8 ? p->tmap_a8 : p->tmap_a16,
-                              p->tmap_b[0], p->tmap_b[1], x2 ? p->tmap_blo[0] : p->tmap_b[0],
-                              x2 ? p->tmap_blo[1] : p->tmap_b[1], x));
+  const CUtensorMap* b = PAIR ? p->tmap_bh : p->tmap_b;
+  const CUtensorMap* blo = PAIR ? p->tmap_blo_h : p->tmap_blo;
+  const CUtensorMap& ta = PREC == FEM_PREC_FP8 ? p->tmap_a8 : p->tmap_a16;
+  // A cooperative launch guarantees that all CTAs are co-resident; where the driver
+  // refuses it for clusters, the occupancy check above stands in for it (and a CTA
+  // that is never scheduled alongside the others only makes them time out).
+  static int coop = 1;
+  cudaLaunchAttribute attr[2];
+  cudaError_t e = cudaErrorUnknown;
+  if (coop) {
+    cudaLaunchConfig_t cfg = anneal_config(p, PREC, PAIR, attr, true, st);
+    e = cudaLaunchKernelEx(&cfg, k_dense_anneal_tc<PREC, PAIR>, ta, b[0], b[1], x2 ? blo[0] : b[0], x2 ? blo[1] : b[1],
+                           x);
+    if (e != cudaSuccess && PAIR) {
+      cudaGetLastError();
+      coop = 0;
+    }
+  }
+  if (!coop) {
+    cudaLaunchConfig_t cfg = anneal_config(p, PREC, PAIR, attr, false, st);
+    e = cudaLaunchKernelEx(&cfg, k_dense_anneal_tc<PREC, PAIR>, ta, b[0], b[1], x2 ? blo[0] : b[0], x2 ? blo[1] : b[1],
+                           x);
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "persistent dense launch");
   return FEM_OK;
 }
 
@@ -1047,7 +1217,11 @@ fem_status dense_state(Problem* p, int R, int prec) {
       FEM_CUDA(cudaMemset(p->mt_lo[b], 0, per * 2));
     }
     if (prec != FEM_PREC_FP32 && (st = make_map(&p->tmap_b[b], p->mt[b], R, p->n_pad, eb)) != FEM_OK) return st;
+    if (prec != FEM_PREC_FP32 && (st = make_map(&p->tmap_bh[b], p->mt[b], R, p->n_pad, eb, kTile / 2)) != FEM_OK)
+      return st;
     if (prec == FEM_PREC_BF16X2 && (st = make_map(&p->tmap_blo[b], p->mt_lo[b], R, p->n_pad, 2)) != FEM_OK)
+      return st;
+    if (prec == FEM_PREC_BF16X2 && (st = make_map(&p->tmap_blo_h[b], p->mt_lo[b], R, p->n_pad, 2, kTile / 2)) != FEM_OK)
       return st;
   }
   p->part_blocks = p->n_pad / 32;
@@ -1121,7 +1295,7 @@ fem_status dense_operand(Problem* p, int t, cudaStream_t s) {
   return FEM_OK;
 }
 
-bool dense_persistent_ok(Problem* p) { return anneal_fits_any(p); }
+bool dense_persistent_ok(Problem* p) { return anneal_kind(p) > 0; }
 
 fem_status dense_steps(Problem* p, const std::vector<StepScalars>& sc, int t_begin, cudaStream_t s) {
   DenseArgs a{};
@@ -1137,36 +1311,47 @@ fem_status dense_steps(Problem* p, const std::vector<StepScalars>& sc, int t_beg
   a.cnorm = p->rowabs;
   a.err = p->err;
   // AUTO takes the persistent kernel for windows of two or more steps
-  const bool persistent = !sc.empty() && p->dense_launch != FEM_DENSE_PER_STEP &&
-                          (p->dense_launch == FEM_DENSE_PERSISTENT || sc.size() > 1) && anneal_fits_any(p);
-  if (p->dense_launch == FEM_DENSE_PERSISTENT && !persistent && !sc.empty())
+  const bool forced = p->dense_launch == FEM_DENSE_PERSISTENT || p->dense_launch == FEM_DENSE_PERSISTENT_SINGLE;
+  const int kind = sc.empty() || p->dense_launch == FEM_DENSE_PER_STEP || !(forced || sc.size() > 1)
+                       ? 0
+                       : anneal_kind(p);
+  if (forced && kind == 0 && !sc.empty())
     return fail(FEM_ERR_UNSUPPORTED, "persistent dense anneal needs a tensor-core precision, R %% 128 == 0 and "
                 "(n_pad/128)*(R/128) co-resident CTAs");
-  if (persistent) {
+  if (kind > 0) {
     fem_status st = upload_scalars(p, sc, s);
     if (st == FEM_OK) {
-      const int groups = p->R / kTile;
-      if (p->dense_bar_groups < groups) {  // first use, or more replica blocks than before
+      const int64_t flags = (int64_t)(p->R / kTile) * 32;  // one counter per replica block, 128 bytes apart
+      if (p->dense_bar_cap < flags) {  // first use, or more replica blocks than before
         if (p->dense_bar) {
           FEM_CUDA(cudaStreamSynchronize(s));
           cudaFree(p->dense_bar);
           p->allocs.erase(std::remove(p->allocs.begin(), p->allocs.end(), (void*)p->dense_bar), p->allocs.end());
           p->dense_bar = nullptr;
+          p->dense_bar_cap = 0;
         }
-        if ((st = dev_alloc_t(p, &p->dense_bar, (size_t)groups * 32)) != FEM_OK) return st;
-        p->dense_bar_groups = groups;
+        if ((st = dev_alloc_t(p, &p->dense_bar, (size_t)flags)) != FEM_OK) return st;
+        p->dense_bar_cap = flags;
       }
-      switch (p->precision) {
-        case FEM_PREC_BF16: st = launch_anneal_tc<FEM_PREC_BF16>(p, a, t_begin, (int)sc.size(), s); break;
-        case FEM_PREC_BF16X2: st = launch_anneal_tc<FEM_PREC_BF16X2>(p, a, t_begin, (int)sc.size(), s); break;
-        default: st = launch_anneal_tc<FEM_PREC_FP8>(p, a, t_begin, (int)sc.size(), s); break;
+    }
+    if (st == FEM_OK) {
+      const int n = (int)sc.size();
+      switch (p->precision * 2 + (kind == 2 ? 1 : 0)) {
+        case FEM_PREC_BF16 * 2: st = launch_anneal_tc<FEM_PREC_BF16, false>(p, a, t_begin, n, s); break;
+        case FEM_PREC_BF16 * 2 + 1: st = launch_anneal_tc<FEM_PREC_BF16, true>(p, a, t_begin, n, s); break;
+        case FEM_PREC_BF16X2 * 2: st = launch_anneal_tc<FEM_PREC_BF16X2, false>(p, a, t_begin, n, s); break;
+        case FEM_PREC_BF16X2 * 2 + 1: st = launch_anneal_tc<FEM_PREC_BF16X2, true>(p, a, t_begin, n, s); break;
+        case FEM_PREC_FP8 * 2: st = launch_anneal_tc<FEM_PREC_FP8, false>(p, a, t_begin, n, s); break;
+        default: st = launch_anneal_tc<FEM_PREC_FP8, true>(p, a, t_begin, n, s); break;
       }
     }
     if (st != FEM_OK) return st;
+    p->dense_last_launch = kind == 2 ? FEM_DENSE_PERSISTENT : FEM_DENSE_PERSISTENT_SINGLE;
     count_launches(1);
     FEM_CUDA(cudaGetLastError());
     return FEM_OK;
   }
+  if (!sc.empty()) p->dense_last_launch = FEM_DENSE_PER_STEP;
   for (size_t k = 0; k < sc.size(); ++k) {
     const int t = t_begin + (int)k, in = t & 1, out = (t + 1) & 1;
     a.mt_out = p->mt[out];

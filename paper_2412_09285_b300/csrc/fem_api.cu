@@ -771,11 +771,17 @@ fem_status fem_set_step_barrier_timeout(fem_problem_t p, int64_t ns) {
   return FEM_OK;
 }
 
+fem_status fem_inject_step_stall(fem_problem_t p, int32_t row_tile) {
+  if (!p || row_tile < -1) return fail(FEM_ERR_INVALID_ARG, "fem_inject_step_stall: problem and row_tile >= -1 required");
+  p->stall_tile = row_tile;
+  return FEM_OK;
+}
+
 void fem_inject_allocation_failure(int64_t after) { g_fail_alloc_after.store(after < 0 ? -1 : after); }
 
 fem_status fem_set_dense_launch(fem_problem_t p, int32_t mode) {
   if (!p || !p->dense) return fail(FEM_ERR_INVALID_ARG, "fem_set_dense_launch: not a dense problem");
-  if (mode < FEM_DENSE_AUTO || mode > FEM_DENSE_PERSISTENT)
+  if (mode < FEM_DENSE_AUTO || mode > FEM_DENSE_PERSISTENT_SINGLE)
     return fail(FEM_ERR_INVALID_ARG, "fem_set_dense_launch: mode %d", (int)mode);
   p->dense_launch = mode;
   return FEM_OK;
@@ -896,6 +902,12 @@ fem_status fem_problem_info(fem_problem_t p, int32_t* steps_done, int32_t* n, in
     else if (p->kind == FEM_MAXKSAT) *units_per_replica = p->n_occ;
     else *units_per_replica = p->n_edges;
   }
+  return FEM_OK;
+}
+
+fem_status fem_dense_last_launch(fem_problem_t p, int32_t* mode) {
+  if (!p || !mode) return fail(FEM_ERR_INVALID_ARG, "problem and mode must be non-NULL");
+  *mode = p->dense ? p->dense_last_launch : 0;
   return FEM_OK;
 }
 

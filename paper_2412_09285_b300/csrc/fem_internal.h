@@ -85,12 +85,15 @@ struct Problem {
   int32_t dense_R_alloc = 0, dense_prec_alloc = -1;
   void* mt_lo[2] = {nullptr, nullptr};  // exact mode, bf16 low parts
   CUtensorMap tmap_a16, tmap_a8, tmap_b[2], tmap_blo[2];
+  CUtensorMap tmap_bh[2], tmap_blo_h[2];  // the same operands in boxes of 64 replica rows (CTA pairs)
   int32_t dense_launch = 0;               // fem_dense_launch
+  int32_t dense_last_launch = 0;          // the fem_dense_launch kind the last window ran on
   int64_t barrier_wait_ns = 2000000000;   // persistent kernel: limit on its step barrier
+  int32_t stall_tile = -1;                // tests: row tile whose CTAs never arrive at the step barrier
   StepScalars* dense_sc = nullptr;        // persistent anneal: the window's step scalars
   int64_t dense_sc_cap = 0;
-  int32_t* dense_bar = nullptr;           // persistent anneal: per replica block arrival counters
-  int32_t dense_bar_groups = 0;
+  int32_t* dense_bar = nullptr;           // persistent anneal: per replica block arrival counters (stride 32)
+  int64_t dense_bar_cap = 0;              // ints allocated
 
   // ---- replica state
   int32_t R = 0, steps_done = 0, n_steps = 0;

@@ -78,7 +78,9 @@ def _load():
         "fem_problem_info": (S, [P, P, P, P, P, P]),
         "fem_sync": (S, [P, P]),
         "fem_set_dense_launch": (S, [P, C.c_int32]),
+        "fem_dense_last_launch": (S, [P, C.POINTER(C.c_int32)]),
         "fem_set_step_barrier_timeout": (S, [P, C.c_int64]),
+        "fem_inject_step_stall": (S, [P, C.c_int32]),
         "fem_inject_allocation_failure": (None, [C.c_int64]),
         "fem_destroy": (None, [P]),
         "fem_status_string": (C.c_char_p, [S]),
@@ -182,13 +184,25 @@ def fem_sync(handle, stream=None):
     _check(_lib.fem_sync(handle, _stream(stream)), "fem_sync")
 
 
+def fem_dense_last_launch(handle):
+    out = C.c_int32()
+    _check(_lib.fem_dense_last_launch(handle, C.byref(out)), "fem_dense_last_launch")
+    return out.value
+
+
 def fem_set_dense_launch(handle, mode):
-    """mode: 0 auto, 1 one kernel per step, 2 persistent (fem_dense_launch)."""
+    """mode: 0 auto, 1 one kernel per step, 2 persistent, 3 persistent without CTA
+    pairs (fem_dense_launch)."""
     _check(_lib.fem_set_dense_launch(handle, int(mode)), "fem_set_dense_launch")
 
 
 def fem_set_step_barrier_timeout(handle, ns):
     _check(_lib.fem_set_step_barrier_timeout(handle, int(ns)), "fem_set_step_barrier_timeout")
+
+
+def fem_inject_step_stall(handle, row_tile):
+    """The persistent dense kernel's CTAs of `row_tile` stop reporting ready (-1: off)."""
+    _check(_lib.fem_inject_step_stall(handle, int(row_tile)), "fem_inject_step_stall")
 
 
 def fem_inject_allocation_failure(after):
@@ -332,8 +346,13 @@ class Problem:
         return fem_problem_info(self.handle)
 
     def set_dense_launch(self, mode):
-        """'auto', 'per_step' or 'persistent' (dense problems)."""
-        fem_set_dense_launch(self.handle, {"auto": 0, "per_step": 1, "persistent": 2}[mode])
+        """'auto', 'per_step', 'persistent' or 'persistent_single' (dense problems)."""
+        fem_set_dense_launch(self.handle, {"auto": 0, "per_step": 1, "persistent": 2, "persistent_single": 3}[mode])
+
+    def dense_last_launch(self):
+        """The kernel the last window ran on: None, 'per_step', 'persistent' (CTA pairs)
+        or 'persistent_single'."""
+        return {0: None, 1: "per_step", 2: "persistent", 3: "persistent_single"}[fem_dense_last_launch(self.handle)]
 
     def sync(self):
         fem_sync(self.handle, self.stream)

@@ -191,36 +191,43 @@ def _run(fem, g, h0, launch, n_steps, windows, **kw):
     return P
 
 
+@pytest.mark.parametrize("n,launch,kind", [(300, "persistent", "persistent_single"),
+                                           (500, "persistent", "persistent"),
+                                           (500, "persistent_single", "persistent_single")])
 @pytest.mark.parametrize("prec,mode,opt", [
     ("bf16", "paper", "adam"), ("fp8", "paper", "adam"), ("bf16x2", "exact", "adam"), ("bf16", "exact", "adam"),
     ("bf16", "paper", "rmsprop"), ("fp8", "paper", "sgd")])
-def test_persistent_matches_per_step(fem, prec, mode, opt):
+def test_persistent_matches_per_step(fem, prec, mode, opt, n, launch, kind):
     """The persistent launch (state in tensor memory for the whole window, a barrier
     per step between the CTAs of a replica block) gives the per-step kernel's h, m, v
-    bit for bit: n = 300 (three row tiles, the last one ragged), two replica blocks,
-    and the window split [0, 37) + [37, 120) for the persistent run."""
-    g = I.sk_dense(300, seed=92)
-    h0 = I.initial_fields(300, 256, seed=93)
+    bit for bit, in exact mode too (all kernels accumulate the K chunks in order): n = 300 (three row tiles, the last one ragged: one CTA per tile), n = 500
+    (four row tiles: CTA pairs issuing 256-row MMAs, or single CTAs when asked), two
+    replica blocks, and the window split [0, 37) + [37, 120) for the persistent run."""
+    g = I.sk_dense(n, seed=92)
+    h0 = I.initial_fields(n, 256, seed=93)
     kw = dict(precision=prec, grad_mode=mode, optimizer=opt)
     if opt == "rmsprop":
         kw.update(lr=0.01)
     if opt == "sgd":
         kw.update(lr=0.05, momentum=0.9)
-    ref = _run(fem, g, h0, "per_step", 120, [120], **kw).state()
-    got = _run(fem, g, h0, "persistent", 120, [37, 120], **kw).state()
-    for a, b, name in zip(got, ref, "hmv"):
+    ref = _run(fem, g, h0, "per_step", 120, [120], **kw)
+    assert ref.dense_last_launch() == "per_step"
+    got = _run(fem, g, h0, launch, 120, [37, 120], **kw)
+    assert got.dense_last_launch() == kind
+    for a, b, name in zip(got.state(), ref.state(), "hmv"):
         assert np.array_equal(a, b), (name, int(np.sum(a != b)))
 
 
 def test_persistent_full_size(fem):
-    """n = 2000, R = 1024 (the dense SK workload, 128 co-resident CTAs): 60 persistent
-    steps equal 60 per-step launches bit for bit, in bf16 and e4m3."""
+    """n = 2000, R = 1024 (the dense SK workload, 128 co-resident CTAs in 64 pairs): 60
+    persistent steps equal 60 per-step launches bit for bit, in bf16 and e4m3."""
     g = I.sk_dense(2000, seed=94)
     h0 = I.initial_fields(2000, 1024, seed=95)
     for prec in ("bf16", "fp8"):
         ref = _run(fem, g, h0, "per_step", 1000, [60], precision=prec).state()
-        got = _run(fem, g, h0, "persistent", 1000, [60], precision=prec).state()
-        for a, b, name in zip(got, ref, "hmv"):
+        P = _run(fem, g, h0, "persistent", 1000, [60], precision=prec)
+        assert P.dense_last_launch() == "persistent"
+        for a, b, name in zip(P.state(), ref, "hmv"):
             assert np.array_equal(a, b), (prec, name, int(np.sum(a != b)))
 
 

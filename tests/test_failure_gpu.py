@@ -1,6 +1,7 @@
 """Failure detection without a GPU fault: a device allocation that fails (injected
-on the host) and the persistent dense kernel's step barrier running out of time (its
-limit set to zero).  Both surface as status codes, and the device stays usable."""
+on the host) and the persistent dense kernel's step barrier running out of time (a
+row tile whose CTAs never arrive, injected on the host).  Both surface as status
+codes, and the device stays usable."""
 import numpy as np
 import pytest
 
@@ -39,17 +40,26 @@ def test_injected_allocation_failure(fem):
     assert ref["energy_i64"].min() < 0
 
 
-def test_step_barrier_timeout_is_reported(fem):
-    g = I.sk_dense(300, seed=73)
-    h0 = I.initial_fields(300, 256, seed=74)
+@pytest.mark.parametrize("n,kind,tile", [(300, "persistent_single", 1), (500, "persistent", 0),
+                                         (500, "persistent", 3)])
+def test_step_barrier_timeout_is_reported(fem, n, kind, tile):
+    """The CTAs of one row tile never arrive at the step barrier (a counter that never
+    reaches its target, injected on the host); the CTAs waiting at it give up after
+    1 ms.  n = 300: three row tiles, one CTA each; n = 500: four, in CTA pairs (the
+    stalled CTA the even or the odd one of its pair)."""
+    g = I.sk_dense(n, seed=73)
+    h0 = I.initial_fields(n, 256, seed=74)
     P = fem.Problem("maxcut", dense=g.dense)
     P.set_dense_launch("persistent")
-    fem.fem_set_step_barrier_timeout(P.handle, 0)
+    fem.fem_set_step_barrier_timeout(P.handle, 1_000_000)
+    fem.fem_inject_step_stall(P.handle, tile)
     P.anneal(h_init=h0, n_steps=50, precision="bf16")
+    assert P.dense_last_launch() == kind
     with pytest.raises(fem.FemError) as e:
         P.best()
     assert e.value.status == fem.FEM_ERR_TIMEOUT
-    # a fresh start with the default limit clears the error and gives the normal result
+    # a fresh start without the stall clears the error and gives the normal result
+    fem.fem_inject_step_stall(P.handle, -1)
     fem.fem_set_step_barrier_timeout(P.handle, 2_000_000_000)
     got = P.anneal(h_init=h0, n_steps=50, precision="bf16").state()
     Q = fem.Problem("maxcut", dense=g.dense)
@@ -59,3 +69,5 @@ def test_step_barrier_timeout_is_reported(fem):
         assert np.array_equal(a, b)
     with pytest.raises(fem.FemError):
         fem.fem_set_step_barrier_timeout(P.handle, -1)
+    with pytest.raises(fem.FemError):
+        fem.fem_inject_step_stall(P.handle, -2)

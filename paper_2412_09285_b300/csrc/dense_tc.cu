@@ -543,7 +543,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_dense_anneal_tc(const __grid_co
   __shared__ __align__(8) uint64_t done;
   __shared__ uint32_t tmem_base_slot;
   __shared__ int32_t abort_flag;
-  __shared__ StepScalars s_sc;  // the current step's scalars (written by thread 0 between steps)
+  __shared__ StepScalars s_sc[2];  // step k's scalars in s_sc[k & 1] (thread 0 loads the next during step k)
   volatile int32_t* abort_v = &abort_flag;
 
   const DenseArgs& a = x.a;
@@ -560,7 +560,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_dense_anneal_tc(const __grid_co
     }
     mbar_init(&done, 1);
     abort_flag = 0;
-    if (x.n_steps > 0) s_sc = x.sc[0];
+    if (x.n_steps > 0) s_sc[0] = x.sc[0];
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (PAIR) cluster_sync_all();  // the other CTA's barriers exist before anything arrives on them
@@ -629,6 +629,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_dense_anneal_tc(const __grid_co
         }
         issued = g + 1;
       }
+      if (k + 1 < x.n_steps) s_sc[(k + 1) & 1] = x.sc[k + 1];  // read by step k + 1's epilogue
     } else if (threadIdx.x == 32 && issuer) {
       for (int kc = 0; kc < nchunks; ++kc) {
         const int g = k * nchunks + kc, st = g % kStages;
@@ -667,7 +668,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_dense_anneal_tc(const __grid_co
     tc_fence_after();
     if (!ok) *abort_v = 1;
     if (__all_sync(kFullMask, ok) && !*abort_v) {
-      const StepScalars s = s_sc;  // registers: the operand stores below are generic and could alias it
+      const StepScalars s = s_sc[k & 1];  // registers: the operand stores below are generic and could alias it
       void* mt_out = x.mt[(t + 1) & 1];
       void* mt_lo_out = x.mt_lo[(t + 1) & 1];
 #pragma unroll
@@ -722,7 +723,6 @@ __global__ void __launch_bounds__(kThreads, 1) k_dense_anneal_tc(const __grid_co
       if (!wait_counter(ctr, (k + 1) * (int32_t)gridDim.x, a.err, x.bar_wait_ns)) *abort_v = 1;
       asm volatile("fence.proxy.async.global;" ::: "memory");
     }
-    if (threadIdx.x == 0 && k + 1 < x.n_steps) s_sc = x.sc[k + 1];
     __syncthreads();
     tc_fence_after();
     if (*abort_v) break;

@@ -1098,26 +1098,14 @@ fem_status launch_anneal_tc(Problem* p, const DenseArgs& a, int t_begin, int n_s
   const CUtensorMap* b = PAIR ? p->tmap_bh : p->tmap_b;
   const CUtensorMap* blo = PAIR ? p->tmap_blo_h : p->tmap_blo;
   const CUtensorMap& ta = PREC == FEM_PREC_FP8 ? p->tmap_a8 : p->tmap_a16;
-  // A cooperative launch guarantees that all CTAs are co-resident; where the driver
-  // refuses it for clusters, the occupancy check above stands in for it (and a CTA
-  // that is never scheduled alongside the others only makes them time out).
-  static int coop = 1;
+  // One CTA per tile: a cooperative launch guarantees that all CTAs are co-resident.
+  // CTA pairs: a cluster launch, with co-residency from the cluster occupancy check in
+  // anneal_fits (a CTA that was never scheduled alongside the others would only make
+  // them time out at the step barrier).
   cudaLaunchAttribute attr[2];
-  cudaError_t e = cudaErrorUnknown;
-  if (coop) {
-    cudaLaunchConfig_t cfg = anneal_config(p, PREC, PAIR, attr, true, st);
-    e = cudaLaunchKernelEx(&cfg, k_dense_anneal_tc<PREC, PAIR>, ta, b[0], b[1], x2 ? blo[0] : b[0], x2 ? blo[1] : b[1],
-                           x);
-    if (e != cudaSuccess && PAIR) {
-      cudaGetLastError();
-      coop = 0;
-    }
-  }
-  if (!coop) {
-    cudaLaunchConfig_t cfg = anneal_config(p, PREC, PAIR, attr, false, st);
-    e = cudaLaunchKernelEx(&cfg, k_dense_anneal_tc<PREC, PAIR>, ta, b[0], b[1], x2 ? blo[0] : b[0], x2 ? blo[1] : b[1],
-                           x);
-  }
+  cudaLaunchConfig_t cfg = anneal_config(p, PREC, PAIR, attr, !PAIR, st);
+  const cudaError_t e = cudaLaunchKernelEx(&cfg, k_dense_anneal_tc<PREC, PAIR>, ta, b[0], b[1], x2 ? blo[0] : b[0],
+                                           x2 ? blo[1] : b[1], x);
   if (e != cudaSuccess) return cuda_fail(e, "persistent dense launch");
   return FEM_OK;
 }

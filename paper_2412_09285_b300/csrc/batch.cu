@@ -125,10 +125,8 @@ __device__ void run_sat_item(const BatchMember& b, const BatchItem& it, const St
   a.v = b.v;
   a.P_in = b.satP[t & 1];
   a.P_out = b.satP[(t + 1) & 1];
-  if (sat_k3_shape(a)) {
-    const int lane = threadIdx.x & 31;
-    for (long long base = it.e0 + (threadIdx.x & ~31); base < it.e1; base += blockDim.x)
-      sat_element_k3(a, s, base + lane, base + lane < it.e1, lane);
+  if (sat_k3_shape(a)) {  // four replicas per thread (e0 and e1 are multiples of R)
+    for (long long e = it.e0 + threadIdx.x * 4; e < it.e1; e += blockDim.x * 4) sat_element_k3<2>(a, s, e);
     return;
   }
   for (long long e = it.e0 + threadIdx.x; e < it.e1; e += blockDim.x) sat_element(a, s, e);

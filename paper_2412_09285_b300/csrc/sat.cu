@@ -23,11 +23,10 @@ namespace {
 
 __global__ void __launch_bounds__(256) k_sat_step(SatArgs a, StepScalars s) {
   const long long total = (long long)a.n * a.R;
-  if (sat_k3_shape(a)) {
-    const int lane = threadIdx.x & 31;
-    for (long long base = (long long)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < total;
-         base += (long long)gridDim.x * blockDim.x)
-      sat_element_k3(a, s, base + lane, base + lane < total, lane);
+  if (sat_k3_shape(a)) {  // four replicas per thread
+    for (long long e = ((long long)blockIdx.x * blockDim.x + threadIdx.x) * 4; e < total;
+         e += (long long)gridDim.x * blockDim.x * 4)
+      sat_element_k3<4>(a, s, e);
     return;
   }
   for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;

@@ -66,69 +66,76 @@ __device__ __forceinline__ void sat_element(const SatArgs& a, const StepScalars&
   }
 }
 
-// The same update for 3-SAT, a warp at a time (all 32 lanes call it together; lanes
-// with act == false contribute nothing).  The G = min(R, 32) lanes of a variable
-// (R == 16 or R % 32 == 0) load G occurrences' other-literal pairs at once, then
-// issue the marginal gathers of 8 occurrences before using any of them, so a
-// variable waits for a few memory round trips instead of four per occurrence.  The
-// products and the sum over occurrences run in the order of sat_element, so both
-// give the same bits.
-__device__ __forceinline__ bool sat_k3_shape(const SatArgs& a) {
-  return a.oth && !a.jw && (a.R == 16 || a.R % 32 == 0);
+// The same update for 3-SAT with four replicas per thread (R % 4 == 0): the thread of
+// element e (a multiple of 4) updates replicas r..r+3 of variable i with float4 loads
+// of the state and of both other literals' marginals, so the occurrence table, the
+// address arithmetic and the literal decoding are paid once per four replicas.  A
+// factor P or 1 - P is fma(+-1, P, 0 or 1), which rounds exactly as either; the
+// products and the sum over occurrences run in the order of sat_element, so both give
+// the same bits.  Occurrences are taken U at a time: their other-literal pairs, then
+// all 2U marginal gathers, then the arithmetic (U = 2 where registers are scarce).
+__device__ __forceinline__ bool sat_k3_shape(const SatArgs& a) { return a.oth && !a.jw && a.R % 4 == 0; }
+
+__device__ __forceinline__ float4 ld_f4(const float* p) { return *reinterpret_cast<const float4*>(p); }
+__device__ __forceinline__ void st_f4(float* p, const float4& x) { *reinterpret_cast<float4*>(p) = x; }
+
+__device__ __forceinline__ float sat_factor(int lit, float p) {
+  return fmaf((lit & 1) ? 1.f : -1.f, p, (lit & 1) ? 0.f : 1.f);  // negated literal: P, else 1 - P
 }
 
-__device__ __forceinline__ void sat_element_k3(const SatArgs& a, const StepScalars& s, long long e, bool act,
-                                               int lane) {
-  const int G = a.R >= 32 ? 32 : 16;
+template <int U>
+__device__ __forceinline__ void sat_element_k3(const SatArgs& a, const StepScalars& s, long long e) {
+  int i, r;
+  split_element(e, a.R, i, r);
   const bool sgd = a.opt == FEM_OPT_SGD;
-  int i = 0, r = 0, ob = 0, nocc = 0;
-  float hi = 0.f, mi = 0.f, vi = 0.f;
-  if (act) {
-    split_element(e, a.R, i, r);
-    hi = a.h[e];
-    mi = a.m[e];
-    vi = sgd ? 0.f : a.v[e];
-    ob = a.occ_ptr[i];
-    nocc = a.occ_ptr[i + 1] - ob;
-  }
-  int maxocc = nocc;
-  if (G == 16) maxocc = max(maxocc, __shfl_xor_sync(kFullMask, maxocc, 16));
-  const int sub = lane & (G - 1), gbase = lane & ~(G - 1);
-  float Gs = 0.f;
-  for (int j0 = 0; j0 < maxocc; j0 += G) {
-    int2 ot = make_int2(0, 0);
-    if (j0 + sub < nocc) ot = a.oth[ob + j0 + sub];
-    const int cnt = min(max(nocc - j0, 0), G), lim = min(maxocc - j0, G);
-    for (int jb = 0; jb < lim; jb += 8) {
-      int la[8], lb[8];
-      float pa[8], pb[8];
+  float4 h = ld_f4(a.h + e), m = ld_f4(a.m + e);
+  float4 v = sgd ? make_float4(0.f, 0.f, 0.f, 0.f) : ld_f4(a.v + e);
+  const int ob = a.occ_ptr[i], oe = a.occ_ptr[i + 1];
+  const float* P = a.P_in + r;
+  float G0 = 0.f, G1 = 0.f, G2 = 0.f, G3 = 0.f;
+  for (int o = ob; o < oe; o += U) {
+    int2 ot[U];
 #pragma unroll
-      for (int u = 0; u < 8; ++u) {
-        const int src = gbase + ((jb + u) & (G - 1));
-        la[u] = __shfl_sync(kFullMask, ot.x, src);
-        lb[u] = __shfl_sync(kFullMask, ot.y, src);
-        const bool v = jb + u < cnt;
-        pa[u] = v ? a.P_in[(size_t)(((uint32_t)la[u] & 0x7fffffffu) >> 1) * a.R + r] : 0.f;
-        pb[u] = v ? a.P_in[(size_t)((uint32_t)lb[u] >> 1) * a.R + r] : 0.f;
+    for (int u = 0; u < U; ++u) ot[u] = o + u < oe ? a.oth[o + u] : make_int2(0, 0);
+    float4 pa[U], pb[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      if (o + u < oe) {
+        pa[u] = ld_f4(P + (size_t)(((uint32_t)ot[u].x & 0x7fffffffu) >> 1) * a.R);
+        pb[u] = ld_f4(P + (size_t)((uint32_t)ot[u].y >> 1) * a.R);
       }
+    }
 #pragma unroll
-      for (int u = 0; u < 8; ++u) {
-        if (jb + u < cnt) {
-          const float ua = (la[u] & 1) ? pa[u] : 1.f - pa[u];
-          const float ub = (lb[u] & 1) ? pb[u] : 1.f - pb[u];
-          Gs = fmaf(la[u] < 0 ? -1.f : 1.f, ua * ub, Gs);
-        }
+    for (int u = 0; u < U; ++u) {
+      if (o + u < oe) {
+        const float sg = ot[u].x < 0 ? -1.f : 1.f;  // the own literal's negation
+        G0 = fmaf(sg, sat_factor(ot[u].x, pa[u].x) * sat_factor(ot[u].y, pb[u].x), G0);
+        G1 = fmaf(sg, sat_factor(ot[u].x, pa[u].y) * sat_factor(ot[u].y, pb[u].y), G1);
+        G2 = fmaf(sg, sat_factor(ot[u].x, pa[u].z) * sat_factor(ot[u].y, pb[u].z), G2);
+        G3 = fmaf(sg, sat_factor(ot[u].x, pa[u].w) * sat_factor(ot[u].y, pb[u].w), G3);
       }
     }
   }
-  if (act) {
-    const float g = s.gq * (hi * s.inv_beta - Gs) * one_minus_m2_fast(hi);
+  float* hv = &h.x;
+  float* mv = &m.x;
+  float* vv = &v.x;
+  const float Gs[4] = {G0, G1, G2, G3};
+  float4 pout;
+  float* pv = &pout.x;
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    float hi = hv[c], mi = mv[c], vi = vv[c];
+    const float g = s.gq * (hi * s.inv_beta - Gs[c]) * one_minus_m2_fast(hi);
     opt_update_fast_rt(a.opt, hi, mi, vi, g, s);
-    a.h[e] = hi;
-    a.m[e] = mi;
-    if (!sgd) a.v[e] = vi;
-    a.P_out[e] = sigmoidf_fast(hi);
+    hv[c] = hi;
+    mv[c] = mi;
+    vv[c] = vi;
+    pv[c] = sigmoidf_fast(hi);
   }
+  st_f4(a.h + e, h);
+  st_f4(a.m + e, m);
+  if (!sgd) st_f4(a.v + e, v);
+  st_f4(a.P_out + e, pout);
 }
 
 }  // namespace fem

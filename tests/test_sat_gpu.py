@@ -206,16 +206,16 @@ def test_wide_clause_unsupported(fem):
 
 
 @pytest.mark.parametrize("opt", ["adam", "rmsprop"])
-def test_three_sat_warp_path_matches_general_path(fem, opt):
-    """Uniform 3-SAT with R = 16 or R = 32 runs the warp-cooperative kernel (other-
-    literal table, occurrences fetched a group at a time); R = 48 runs the general
-    per-thread kernel.  Replicas are independent, so the first 16 / 32 replicas of the
-    R = 48 run must equal the narrow runs bit for bit."""
+def test_three_sat_four_replica_path_matches_general_path(fem, opt):
+    """Uniform 3-SAT with R % 4 == 0 runs the four-replicas-per-thread kernel (other-
+    literal table, float4 gathers, occurrences a few at a time); R = 50 runs the
+    general per-thread kernel.  Replicas are independent, so the first 4 / 16 / 32 / 48
+    replicas of the R = 50 run must equal the narrow runs bit for bit."""
     c = I.random_ksat(3000, 12600, 3, seed=51)
-    wide = I.initial_fields(c.n, 48, seed=52)
+    wide = I.initial_fields(c.n, 50, seed=52)
     kw = dict(optimizer=opt, lr=0.1 if opt == "adam" else 0.01)
     ref = fem.Problem("sat", clauses=c).anneal(h_init=wide, n_steps=200, **kw).state()
-    for R in (16, 32):
+    for R in (4, 16, 32, 48):
         got = fem.Problem("sat", clauses=c).anneal(h_init=np.ascontiguousarray(wide[:, :R]), n_steps=200,
                                                     **kw).state()
         for a, b, name in zip(got, ref, "hmv"):

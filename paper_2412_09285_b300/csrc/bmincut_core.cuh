@@ -227,12 +227,15 @@ __device__ __forceinline__ void bmincut_element(const BmcArgs& a, const StepScal
       if (MODE == FEM_GRAD_PAPER) nc[q] = act ? a.cnt_in[r * Q + q] - (own == q ? Vi : 0) : 0;
       else ps[q] = act ? a.ps_in[r * Q + q] : 0ull;
     }
-    float cen[Q];
+    // d(s, s') is antisymmetric bit for bit (each step is an exact difference, a product
+    // or an fma, all odd under negation in round-to-nearest), and d(s, s) = +0 leaves
+    // the sum unchanged (it starts at +0 and never becomes -0), so only the pairs s < s'
+    // are formed; the sums still run over s' in order.
+    float dm[Q][Q];
 #pragma unroll
     for (int q = 0; q < Q; ++q) {
-      float c = 0.f;
 #pragma unroll
-      for (int q2 = 0; q2 < Q; ++q2) {
+      for (int q2 = q + 1; q2 < Q; ++q2) {
         float d;
         // node weights (SM, node-weighted balance term): lambda c^a_i V_i [n(s) - V_i e_i(s)]
         // (paper) and 2 lambda V_i [sum_j V_j P_j(s) - V_i P_i(s)] (exact); V_i = 1 gives
@@ -245,9 +248,16 @@ __device__ __forceinline__ void bmincut_element(const BmcArgs& a, const StepScal
           const float dcol = (float)(long long)(ps[q] - ps[q2]) * kPsumInv;
           d = a.cw * (acc[q] - acc[q2]) + 2.f * lam * (float)Vi * (dcol - (float)Vi * (P[q] - P[q2]));
         }
-        d = fmaf(h[q] - h[q2], s.inv_beta, d);
-        c = fmaf(P[q2], d, c);
+        dm[q][q2] = fmaf(h[q] - h[q2], s.inv_beta, d);
       }
+    }
+    float cen[Q];
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+      float c = 0.f;
+#pragma unroll
+      for (int q2 = 0; q2 < Q; ++q2)
+        if (q2 != q) c = fmaf(P[q2], q < q2 ? dm[q][q2] : -dm[q2][q], c);
       cen[q] = c;
     }
     with_opt(a.opt, [&](auto O) {

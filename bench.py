@@ -2,9 +2,11 @@
 """Benchmark of the FEM per-step replica update on B300 (one JSON line on stdout).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                    [--workload sparse|small|dense] [--precision bf16|fp8|bf16x2|fp32]
+                    [--workload W] [--precision bf16|fp8|bf16x2|fp32] [--grad-mode paper|exact]
 
-Workloads (synthetic, seeded; the paper's data sets are not available):
+Workloads (synthetic, seeded; the paper's data sets are not available; the batched, warm-start
+and single-problem workloads bmincut, bmincut_weighted, coloring, qubo, sat and pspin are
+described in WORKLOADS below):
   sparse (default)  sparse MaxCut at scale: ER G(n, m), n = 2^20, m = 3n, +-1 weights,
                     R = 32, 2000-step exponential beta 0.05 -> 5, Adam lr 0.1, paper-mode
                     gradient.  Units: |E| undirected edges x replicas x steps.
@@ -75,6 +77,94 @@ WORKLOADS = {
                           ratio=4.2, R=16, n_steps=1000, graph_seed=5, h_seed=6, cpu_steps=2),
 }
 
+# One problem per kind of the widened rows (balanced MinCut with and without node weights,
+# colouring, QUBO, Max-3-SAT, higher-order p-spin terms), each at a size whose state is
+# larger than L2.  The CPU oracle baseline of these runs on an instance of the same
+# generator at 1/cpu_div of the size (a full oracle step at this size takes minutes).
+_SINGLE = dict(n=1 << 20, n_steps=1000, cpu_div=16, cpu_steps=4)
+_SCHED = "1000-step exponential beta 0.05->5, Adam lr 0.1"
+WORKLOADS.update({
+    "bmincut": dict(_SINGLE, kind="single", problem="bmincut", graph="rgg", deg=10.0, q=4, R=16, graph_seed=41,
+                    h_seed=42, name=f"balanced 4-way MinCut: random geometric graph n=2^20, mean degree 10, unit "
+                                    f"weights, lambda_max=1, R=16, {_SCHED}, paper-mode gradient"),
+    "bmincut_weighted": dict(_SINGLE, kind="single", problem="bmincut", graph="rgg", deg=10.0, q=4, R=16,
+                             node_weights=(1, 4), graph_seed=41, h_seed=42,
+                             name=f"node-weighted balanced 4-way MinCut: random geometric graph n=2^20, mean degree "
+                                  f"10, node weights uniform in 1..4, lambda_max=1, R=16, {_SCHED}, paper-mode "
+                                  f"gradient"),
+    "coloring": dict(_SINGLE, kind="single", problem="coloring", graph="rgg", deg=10.0, q=4, R=16, graph_seed=43,
+                     h_seed=44, name=f"4-colouring: random geometric graph n=2^20, mean degree 10, R=16, {_SCHED}, "
+                                     f"paper-mode gradient"),
+    "qubo": dict(_SINGLE, kind="single", problem="qubo", graph="er", m=3 << 20, R=32, linear=(-2, 2),
+                 grad_mode="exact", graph_seed=45, h_seed=46,
+                 name=f"QUBO: ER G(n,m) n=2^20, m=3n, couplings +-1, linear terms uniform in -2..2, R=32, "
+                      f"{_SCHED}, exact gradient"),
+    "sat": dict(_SINGLE, kind="single", problem="sat", ratio=4.2, k=3, R=16, graph_seed=47, h_seed=48,
+                name=f"random Max-3-SAT: n=2^20 variables, M=4.2n clauses, uniform literal signs, R=16, {_SCHED}"),
+    "pspin": dict(_SINGLE, kind="single", problem="pspin", ratio=4.2, k=3, R=16, linear=(-1, 1), graph_seed=49,
+                  cpu_div=32, cpu_steps=1,
+                  h_seed=50, name=f"3-spin interactions: n=2^20 spins, 4.2n random 3-spin terms, J=+-1, fields "
+                                  f"uniform in -1..1, R=16, {_SCHED}"),
+})
+
+
+class _SingleInstance:
+    """One problem of a widened row (graph or clause list plus node weights, linear
+    terms or term couplings), at 1/scale of the workload's size."""
+
+    def __init__(self, wl, scale=1):
+        from paper_2412_09285_b300 import instances as I
+        n, s = wl["n"] // scale, wl["graph_seed"]
+        rng = np.random.Generator(np.random.PCG64(s + 7))
+        self.problem, self.graph, self.clauses = wl["problem"], None, None
+        self.node_weight = self.linear = self.term_weight = None
+        if wl["problem"] in ("sat", "pspin"):
+            self.clauses = I.random_ksat(n, int(round(wl["ratio"] * n)), wl["k"], seed=s)
+            if wl["problem"] == "pspin":  # terms of distinct spins; the sign lives in J
+                self.clauses = I.Clauses(n, self.clauses.ptr, np.abs(self.clauses.lits))
+                self.term_weight = rng.choice([-1.0, 1.0], size=self.clauses.n_clauses)
+            self.n, self.units = n, int(self.clauses.ptr[-1])
+        else:
+            self.graph = (I.rgg(n, wl["deg"], seed=s) if wl["graph"] == "rgg"
+                          else I.er_gnm(n, wl["m"] // scale, seed=s, weights="pm1"))
+            self.n, self.units = n, self.graph.n_edges
+        if "node_weights" in wl:
+            lo, hi = wl["node_weights"]
+            self.node_weight = rng.integers(lo, hi + 1, size=n).astype(np.int32)
+        if "linear" in wl:
+            lo, hi = wl["linear"]
+            self.linear = rng.integers(lo, hi + 1, size=n).astype(np.float64)
+
+    def problem_obj(self, fem, wl, stream):
+        return fem.Problem(self.problem, graph=self.graph, clauses=self.clauses, q=wl.get("q", 2), stream=stream,
+                           node_weight=self.node_weight, linear=self.linear, term_weight=self.term_weight)
+
+    def oracle_problem(self):
+        import oracle as O
+        if self.clauses is not None:
+            c = self.clauses
+            if self.problem == "sat":
+                return ("sat", O.sat_arrays(c.ptr, c.lits))
+            return ("pspin", (c.ptr, np.abs(c.lits) - 1, self.term_weight, self.linear))
+        g = self.graph
+        W = O.coupling_matrix(g.n, g.ei, g.ej, g.w)
+        if self.problem == "qubo":
+            return ("qubo", (W, self.linear))
+        if self.problem == "bmincut" and self.node_weight is not None:
+            return ("bmincut", W, self.node_weight.astype(np.float64))
+        return (self.problem, W)
+
+    def host_bytes(self):
+        """Bytes of the problem description a user passes from host memory."""
+        b = 0
+        if self.graph is not None:
+            b += 8 * self.graph.n_edges + 4 * (self.n + 1)
+        if self.clauses is not None:
+            b += 8 * (self.clauses.n_clauses + 1) + 4 * int(self.clauses.ptr[-1])
+        for x in (self.node_weight, self.linear, self.term_weight):
+            b += 0 if x is None else x.nbytes
+        return b
+
 
 class _BatchInstance:
     """The members of the batched workload (graphs and clause lists)."""
@@ -136,6 +226,8 @@ def _instance(wl):
     from paper_2412_09285_b300 import instances as I
     if wl["kind"] == "batched":
         return _BatchInstance(wl)
+    if wl["kind"] == "single":
+        return _SingleInstance(wl)
     if wl["kind"] == "dense":
         return I.sk_dense(wl["n"], seed=wl["graph_seed"])
     if "m" in wl:
@@ -146,6 +238,8 @@ def _instance(wl):
 def _make_problem(fem, wl, inst, stream, dense_launch="auto"):
     if wl["kind"] == "batched":
         return _BatchRunner(fem, wl, inst, stream)
+    if wl["kind"] == "single":
+        return inst.problem_obj(fem, wl, stream)
     if wl["kind"] == "dense":
         P = fem.Problem("maxcut", dense=inst.dense, stream=stream)
         P.set_dense_launch(dense_launch)
@@ -208,6 +302,39 @@ def _roofline(wl, inst, step_ms, precision, dense_launch=None, grad_mode="paper"
                 "traffic": (_traffic_from_profile("batch_step_bmc256_sat64_R16.md", "batched")
                             if wl is WORKLOADS["batched"] else None),
                 "kernel": "k_batch_step<4, paper>", "algorithmic_bytes_per_launch": alg, "launch_ms": step_ms,
+                "peak_source": f"{src} hbm_gbs (copy), of {src}", "frac_of_8TBs": ach / 8000.0}
+    if wl["kind"] == "single":
+        n, R_, pr = inst.n, R, wl["problem"]
+        if pr in ("bmincut", "coloring"):
+            q, nnz = wl["q"], 2 * inst.graph.n_edges
+            bits = max(1, (q - 1).bit_length())
+            # h, m, v read + written, col, row_ptr, c^f and c^a, argmax words read once and
+            # written once (+ node weights)
+            alg = 24 * q * n * R_ + 4 * nnz + 4 * (n + 1) + 8 * n + 8 * n * max(1, R_ * bits // 32)
+            alg += 4 * n if inst.node_weight is not None else 0
+            kernel = f"k_bmincut_step<{q}, paper>"
+        elif pr == "qubo":
+            nnz = 2 * inst.graph.n_edges
+            # the exact-mode MaxCut step: h, m, v, the gathered marginals m = tanh(h/2) read
+            # once and written once, CSR, sign words, per-node offsets
+            alg = 24 * n * R_ + 8 * n * R_ + 4 * nnz + 4 * (n + 1) + 4 * n * (R_ // 32) + 4 * n
+            kernel = "k_maxcut_step<exact, adam, unit> (QUBO offsets)"
+        elif pr == "sat":
+            L = inst.units
+            # h, m, v, the marginals read once and written once, occurrence pointers and
+            # the other-literal table (8 B per occurrence)
+            alg = 24 * n * R_ + 8 * n * R_ + 4 * (n + 1) + 8 * L
+            kernel = "k_sat_step (four replicas per thread)"
+        else:
+            L, M = inst.units, inst.clauses.n_clauses
+            # h, m, v, the marginals, occurrences, clause pointers and literals, term
+            # couplings and fields, each read once
+            alg = 24 * n * R_ + 8 * n * R_ + 4 * (n + 1) + 8 * L + 8 * M + 4 * n
+            kernel = "k_sat_step (p-spin terms)"
+        ach = alg / (step_ms / 1e3) / 1e9
+        return {"bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": ach / peaks["hbm_gbs"], "traffic": None, "kernel": kernel,
+                "algorithmic_bytes_per_launch": alg, "launch_ms": step_ms,
                 "peak_source": f"{src} hbm_gbs (copy), of {src}", "frac_of_8TBs": ach / 8000.0}
     if wl["kind"] == "sparse" and grad_mode == "exact":
         n, nnz = inst.n, 2 * inst.n_edges
@@ -324,7 +451,7 @@ def _oracle_problem(wl, inst):
 
 
 def _units_per_replica(wl, inst):
-    if wl["kind"] == "batched":
+    if wl["kind"] in ("batched", "single"):
         return inst.units
     return inst.n * (inst.n - 1) // 2 if wl["kind"] == "dense" else inst.n_edges
 
@@ -353,6 +480,25 @@ def _oracle_batch_sample(wl, inst, replicas, steps, n_members=(8, 4)):
     return units, wall, cpu
 
 
+def _oracle_single_sample(wl, replicas, steps, warmup=0):
+    """Oracle steps warmup .. warmup+steps on the workload's generator at 1/cpu_div of its
+    size; returns (units, wall, cpu)."""
+    import oracle as O
+    from paper_2412_09285_b300 import instances as I
+    small = _SingleInstance(wl, scale=wl["cpu_div"])
+    qh = wl["q"] if wl["problem"] in ("bmincut", "coloring") else 1
+    h = I.initial_fields(small.n, replicas, seed=wl["h_seed"], q=qh).astype(np.float64)
+    mode = wl.get("grad_mode", "paper")
+    prob = small.oracle_problem()
+    opt = None
+    if warmup:
+        h, opt = O.anneal(prob, h, wl["n_steps"], t_end=warmup, mode=mode)
+    c0, t0 = time.process_time(), time.perf_counter()
+    O.anneal(prob, h, wl["n_steps"], t_begin=warmup, t_end=warmup + steps, mode=mode, opt=opt)
+    wall, cpu = time.perf_counter() - t0, time.process_time() - c0
+    return small.units * replicas * steps, wall, cpu
+
+
 def cpu_baseline(wl, inst):
     """The FP64 oracle as it stands, timed on this host on a bounded sample."""
     import oracle as O
@@ -363,6 +509,11 @@ def cpu_baseline(wl, inst):
         return {"value": units / wall, "unit": METRIC, "cores": max(1, round(cpu / wall)), "kind": "oracle",
                 "sample": f"first {steps} steps of the first 8 bMinCut and 4 SAT members, all {wl['R']} "
                           f"replicas; {wall:.1f} s wall"}
+    if wl["kind"] == "single":
+        units, wall, cpu = _oracle_single_sample(wl, wl["R"], steps)
+        return {"value": units / wall, "unit": METRIC, "cores": max(1, round(cpu / wall)), "kind": "oracle",
+                "sample": f"the same generator at n/{wl['cpu_div']} (n={wl['n'] // wl['cpu_div']}), first {steps} "
+                          f"steps, all {wl['R']} replicas; {wall:.1f} s wall"}
     prob = _oracle_problem(wl, inst)
     h0 = I.initial_fields(inst.n, wl["R"], seed=wl["h_seed"]).astype(np.float64)
     c0, t0 = time.process_time(), time.perf_counter()
@@ -380,10 +531,14 @@ def run_reference(args, wl):
         return
     import oracle as O
     from paper_2412_09285_b300 import instances as I
-    inst = _instance(wl)
+    inst = _instance(wl) if wl["kind"] != "single" else None
     if wl["kind"] == "batched":
         r_sample = 1
         units, wall, cpu = _oracle_batch_sample(wl, inst, r_sample, args.steps, n_members=(4, 2))
+        value = units / wall
+    elif wl["kind"] == "single":
+        r_sample = wl["R"]
+        units, wall, cpu = _oracle_single_sample(wl, r_sample, args.steps, warmup=args.warmup)
         value = units / wall
     else:
         prob = _oracle_problem(wl, inst)
@@ -403,7 +558,9 @@ def run_reference(args, wl):
             "data": "synthetic", "config": {"workload": wl["name"]},
             "cpu_baseline": {"value": value, "unit": METRIC, "cores": max(1, round(cpu / wall)),
                              "kind": "oracle",
-                             "sample": f"{r_sample} of {wl['R']} replicas per step, same instance"},
+                             "sample": (f"the same generator at n/{wl['cpu_div']}, all {wl['R']} replicas"
+                                        if wl["kind"] == "single"
+                                        else f"{r_sample} of {wl['R']} replicas per step, same instance")},
             "e2e": {"value": value, "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -428,11 +585,12 @@ def run_ours(args, wl):
         h0 = [torch.from_numpy(x).to(dev) for x in h0_host]
         Wm = max(Wm, 8)   # the first call also tunes the work-item size (two steps per candidate)
     else:
-        h0_host = I.initial_fields(inst.n, R, seed=wl["h_seed"] + 7919 * rank)
+        qh = wl["q"] if wl.get("problem") in ("bmincut", "coloring") else 1
+        h0_host = I.initial_fields(inst.n, R, seed=wl["h_seed"] + 7919 * rank, q=qh)
         h0 = torch.from_numpy(h0_host).to(dev)
     stream = torch.cuda.current_stream()
     prob = _make_problem(fem, wl, inst, stream, args.dense_launch)
-    grad_mode = args.grad_mode or ("exact" if precision == "bf16x2" else "paper")
+    grad_mode = args.grad_mode or wl.get("grad_mode") or ("exact" if precision == "bf16x2" else "paper")
     kw = dict(grad_mode=grad_mode, optimizer="adam", lr=0.1, precision=precision)
 
     def one_anneal(k, events):
@@ -501,6 +659,8 @@ def run_ours(args, wl):
     p2.close()
     if wl["kind"] == "dense":
         h2d = h0_bytes + 4 * inst.n * inst.n
+    elif wl["kind"] == "single":
+        h2d = h0_bytes + inst.host_bytes()
     elif wl["kind"] == "batched":
         h2d = h0_bytes + sum(4 * (g.n + 1) + 8 * g.n_edges for g in inst.graphs) \
             + sum(8 * (c.n_clauses + 1) + 8 * int(c.ptr[-1]) for c in inst.sats)
@@ -520,8 +680,9 @@ def run_ours(args, wl):
                        else wl["name"].replace("paper-mode gradient", "exact gradient"), "n": inst.n, "units_per_replica": _units_per_replica(wl, inst),
                        "replicas_per_gpu": R, "anneal_steps": n_steps, "precision": precision,
                        "parallelism": f"replica-sharded x{ws}",
-                       "l2": ("inputs larger than L2" if wl["kind"] == "sparse" and inst.n > 100000
-                              else "working set L2-resident (latency/compute-bound workload)")},
+                       "l2": ("working set L2-resident (latency/compute-bound workload)"
+                              if wl["kind"] == "dense" or (wl["kind"] == "sparse" and inst.n <= 100000)
+                              else "inputs larger than L2")},
             "roofline": _roofline(wl, inst, step_ms, precision,
                                   dense_launch=prob.dense_last_launch() if wl["kind"] == "dense" else None,
                                   grad_mode=grad_mode), "gpu_launches": int(launches), "e2e": e2e,

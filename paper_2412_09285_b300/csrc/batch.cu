@@ -46,6 +46,7 @@ struct BatchMember {
   const int32_t* occ;
   const int2* oth;
   const float* jw;   // p-spin members: term coefficients, NULL for Max-k-SAT
+  const float* jwo;  // p-spin members with 3-spin terms: J per occurrence
   const float* lin;  // p-spin members: fields b_i
 };
 
@@ -116,6 +117,7 @@ __device__ void run_sat_item(const BatchMember& b, const BatchItem& it, const St
   a.occ = b.occ;
   a.oth = b.oth;
   a.jw = b.jw;
+  a.jwo = b.jwo;
   a.lin = b.lin;
   a.n = b.n;
   a.R = b.R;
@@ -125,8 +127,11 @@ __device__ void run_sat_item(const BatchMember& b, const BatchItem& it, const St
   a.v = b.v;
   a.P_in = b.satP[t & 1];
   a.P_out = b.satP[(t + 1) & 1];
-  if (sat_k3_shape(a)) {  // four replicas per thread (e0 and e1 are multiples of R)
-    for (long long e = it.e0 + threadIdx.x * 4; e < it.e1; e += blockDim.x * 4) sat_element_k3<2>(a, s, e);
+  // four replicas per thread (e0 and e1 are multiples of R); p-spin members take the
+  // per-element path here, which gives the same bits, since its extra registers would
+  // spill in this kernel
+  if (sat_k3_shape(a) && !a.jw) {
+    for (long long e = it.e0 + threadIdx.x * 4; e < it.e1; e += blockDim.x * 4) sat_element_k3<2, false>(a, s, e);
     return;
   }
   for (long long e = it.e0 + threadIdx.x; e < it.e1; e += blockDim.x) sat_element(a, s, e);
@@ -285,6 +290,7 @@ static fem_status batch_prepare(Batch* b, cudaStream_t s) {
     m.occ = p->occ;
     m.oth = reinterpret_cast<const int2*>(p->oth);
     m.jw = p->pspin ? p->pj : nullptr;
+    m.jwo = p->pspin ? p->pjo : nullptr;
     m.lin = p->pspin ? p->qoff : nullptr;
     dm.push_back(m);
     if (p->kind == FEM_BMINCUT) {

@@ -561,6 +561,11 @@ fem_status fem_create_problem(const fem_problem_desc* d, void* stream, fem_probl
   if (st == FEM_OK && p->pspin) st = upload(p.get(), &p->qlin_f, qlin_f, s);
   if (st == FEM_OK && p->pspin) st = upload(p.get(), &p->qlin_i, qlin_i, s);
   if (st == FEM_OK && p->pspin && !pj_f32.empty()) st = upload(p.get(), &p->pj, pj_f32, s);
+  if (st == FEM_OK && p->pspin && !hs.oth.empty()) {  // 3-spin terms: the step reads J per occurrence
+    std::vector<float> pjo(hs.occ.size());
+    for (size_t o = 0; o < hs.occ.size(); ++o) pjo[o] = pj_f32[hs.occ[o] >> 3];
+    st = upload(p.get(), &p->pjo, pjo, s);
+  }
   if (st == FEM_OK && p->pspin && !pj_f64.empty()) st = upload(p.get(), &p->pj_f, pj_f64, s);
   if (st == FEM_OK && p->pspin && !pj_i64.empty()) st = upload(p.get(), &p->pj_i, pj_i64, s);
   if (st == FEM_OK) st = dev_alloc_t(p.get(), &p->err, 1);

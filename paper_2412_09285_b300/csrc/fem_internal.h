@@ -56,6 +56,7 @@ struct Problem {
   bool qlin_int = true;
   bool pspin = false;          // FEM_PSPIN on the Max-k-SAT data path (kind == FEM_MAXKSAT)
   float* pj = nullptr;         // p-spin term coefficients J_v (negations folded in), fp32 for the steps
+  float* pjo = nullptr;        // 3-spin terms only: J_v of each occurrence's term, in occurrence order
   int64_t* pj_i = nullptr;     // the same, integer (read-out)
   double* pj_f = nullptr;      // the same, fp64 (read-out)
   bool pspin_int = true;       // every J_v and b_i is an integer

@@ -21,18 +21,24 @@
 namespace fem {
 namespace {
 
+// PATH: 0 the per-element update (any clause widths, any R); 1 Max-3-SAT and 2 3-spin
+// terms with four replicas per thread (R % 4 == 0).  One kernel per path, so each is
+// compiled with only the registers it needs.
+template <int PATH>
 __global__ void __launch_bounds__(256) k_sat_step(SatArgs a, StepScalars s) {
   const long long total = (long long)a.n * a.R;
-  if (sat_k3_shape(a)) {  // four replicas per thread
+  if (PATH > 0) {
     for (long long e = ((long long)blockIdx.x * blockDim.x + threadIdx.x) * 4; e < total;
          e += (long long)gridDim.x * blockDim.x * 4)
-      sat_element_k3<4>(a, s, e);
+      sat_element_k3<4, PATH == 2>(a, s, e);
     return;
   }
   for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
        e += (long long)gridDim.x * blockDim.x)
     sat_element(a, s, e);
 }
+
+using SatStep = void (*)(SatArgs, StepScalars);
 
 // The gathered marginals of the fields: P = sigmoid(h) (Max-k-SAT) or m = tanh(h/2) (p-spin).
 __global__ void k_sat_marginals(const float* __restrict__ h, long long total, float* __restrict__ P, int32_t pspin) {
@@ -183,11 +189,13 @@ fem_status sat_marginals(Problem* p, int t, cudaStream_t st) {
 }
 
 fem_status sat_steps(Problem* p, const std::vector<StepScalars>& sc, int t_begin, cudaStream_t st) {
-  static int per_sm = 0;
-  if (per_sm == 0) {
+  static const SatStep kernels[3] = {k_sat_step<0>, k_sat_step<1>, k_sat_step<2>};
+  static int per_sm[3] = {0, 0, 0};
+  const int path = (p->oth && p->R % 4 == 0) ? (!p->pspin ? 1 : (p->pjo ? 2 : 0)) : 0;
+  if (per_sm[path] == 0) {
     int b = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_sat_step, 256, 0) != cudaSuccess || b < 1) b = 1;
-    per_sm = b;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kernels[path], 256, 0) != cudaSuccess || b < 1) b = 1;
+    per_sm[path] = b;
   }
   SatArgs a{};
   a.cl_ptr = p->cl_ptr;
@@ -196,6 +204,7 @@ fem_status sat_steps(Problem* p, const std::vector<StepScalars>& sc, int t_begin
   a.occ = p->occ;
   a.oth = reinterpret_cast<const int2*>(p->oth);
   a.jw = p->pspin ? p->pj : nullptr;
+  a.jwo = p->pspin ? p->pjo : nullptr;
   a.lin = p->pspin ? p->qoff : nullptr;
   a.n = p->n;
   a.R = p->R;
@@ -203,12 +212,12 @@ fem_status sat_steps(Problem* p, const std::vector<StepScalars>& sc, int t_begin
   a.h = p->h[0];
   a.m = p->m;
   a.v = p->v;
-  const int grid = grid_for(p, (long long)p->n * p->R, per_sm);
+  const int grid = grid_for(p, (long long)p->n * p->R, per_sm[path]);
   for (size_t k = 0; k < sc.size(); ++k) {
     const int t = t_begin + (int)k;
     a.P_in = p->satP[t & 1];
     a.P_out = p->satP[(t + 1) & 1];
-    k_sat_step<<<grid, 256, 0, st>>>(a, sc[k]);
+    kernels[path]<<<grid, 256, 0, st>>>(a, sc[k]);
   }
   count_launches((int64_t)sc.size());
   FEM_CUDA(cudaGetLastError());

@@ -14,6 +14,7 @@ struct SatArgs {
   const int32_t* occ;      // [n_occ]: (clause << 3) | position
   const int2* oth;         // [n_occ] or NULL: 3-SAT, the other two literals (own negation in bit 31)
   const float* jw;         // p-spin: term coefficients J_v (NULL: Max-k-SAT)
+  const float* jwo;        // p-spin with 3-spin terms: J_v of each occurrence's term (with oth)
   const float* lin;        // p-spin: fields b_i
   int32_t n, R, opt;
   float* h;
@@ -66,24 +67,30 @@ __device__ __forceinline__ void sat_element(const SatArgs& a, const StepScalars&
   }
 }
 
-// The same update for 3-SAT with four replicas per thread (R % 4 == 0): the thread of
-// element e (a multiple of 4) updates replicas r..r+3 of variable i with float4 loads
-// of the state and of both other literals' marginals, so the occurrence table, the
-// address arithmetic and the literal decoding are paid once per four replicas.  A
-// factor P or 1 - P is fma(+-1, P, 0 or 1), which rounds exactly as either; the
-// products and the sum over occurrences run in the order of sat_element, so both give
-// the same bits.  Occurrences are taken U at a time: their other-literal pairs, then
-// all 2U marginal gathers, then the arithmetic (U = 2 where registers are scarce).
-__device__ __forceinline__ bool sat_k3_shape(const SatArgs& a) { return a.oth && !a.jw && a.R % 4 == 0; }
+// The same update for 3-literal clauses or 3-spin terms with four replicas per thread
+// (R % 4 == 0): the thread of element e (a multiple of 4) updates replicas r..r+3 of
+// variable i with float4 loads of the state and of both other literals' marginals, so
+// the occurrence table, the address arithmetic and the literal decoding are paid once
+// per four replicas.  Max-3-SAT: a factor P or 1 - P is fma(+-1, P, 0 or 1), which
+// rounds exactly as either; p-spin (PSPIN): the factors are the mean spins m and each
+// occurrence carries its term's J.  The products and the sum over occurrences run in
+// the order of sat_element, so both give the same bits.  Occurrences are taken U at a
+// time: their other-literal pairs, then all 2U marginal gathers, then the arithmetic
+// (U = 2 where registers are scarce).
+__device__ __forceinline__ bool sat_k3_shape(const SatArgs& a) {
+  return a.oth && a.R % 4 == 0 && (!a.jw || a.jwo);
+}
 
 __device__ __forceinline__ float4 ld_f4(const float* p) { return *reinterpret_cast<const float4*>(p); }
 __device__ __forceinline__ void st_f4(float* p, const float4& x) { *reinterpret_cast<float4*>(p) = x; }
 
+template <bool PSPIN>
 __device__ __forceinline__ float sat_factor(int lit, float p) {
+  if (PSPIN) return p;
   return fmaf((lit & 1) ? 1.f : -1.f, p, (lit & 1) ? 0.f : 1.f);  // negated literal: P, else 1 - P
 }
 
-template <int U>
+template <int U, bool PSPIN>
 __device__ __forceinline__ void sat_element_k3(const SatArgs& a, const StepScalars& s, long long e) {
   int i, r;
   split_element(e, a.R, i, r);
@@ -95,8 +102,12 @@ __device__ __forceinline__ void sat_element_k3(const SatArgs& a, const StepScala
   float G0 = 0.f, G1 = 0.f, G2 = 0.f, G3 = 0.f;
   for (int o = ob; o < oe; o += U) {
     int2 ot[U];
+    float sg[U];
 #pragma unroll
-    for (int u = 0; u < U; ++u) ot[u] = o + u < oe ? a.oth[o + u] : make_int2(0, 0);
+    for (int u = 0; u < U; ++u) {
+      ot[u] = o + u < oe ? a.oth[o + u] : make_int2(0, 0);
+      if (PSPIN) sg[u] = o + u < oe ? a.jwo[o + u] : 0.f;
+    }
     float4 pa[U], pb[U];
 #pragma unroll
     for (int u = 0; u < U; ++u) {
@@ -108,11 +119,11 @@ __device__ __forceinline__ void sat_element_k3(const SatArgs& a, const StepScala
 #pragma unroll
     for (int u = 0; u < U; ++u) {
       if (o + u < oe) {
-        const float sg = ot[u].x < 0 ? -1.f : 1.f;  // the own literal's negation
-        G0 = fmaf(sg, sat_factor(ot[u].x, pa[u].x) * sat_factor(ot[u].y, pb[u].x), G0);
-        G1 = fmaf(sg, sat_factor(ot[u].x, pa[u].y) * sat_factor(ot[u].y, pb[u].y), G1);
-        G2 = fmaf(sg, sat_factor(ot[u].x, pa[u].z) * sat_factor(ot[u].y, pb[u].z), G2);
-        G3 = fmaf(sg, sat_factor(ot[u].x, pa[u].w) * sat_factor(ot[u].y, pb[u].w), G3);
+        if (!PSPIN) sg[u] = ot[u].x < 0 ? -1.f : 1.f;  // the own literal's negation
+        G0 = fmaf(sg[u], sat_factor<PSPIN>(ot[u].x, pa[u].x) * sat_factor<PSPIN>(ot[u].y, pb[u].x), G0);
+        G1 = fmaf(sg[u], sat_factor<PSPIN>(ot[u].x, pa[u].y) * sat_factor<PSPIN>(ot[u].y, pb[u].y), G1);
+        G2 = fmaf(sg[u], sat_factor<PSPIN>(ot[u].x, pa[u].z) * sat_factor<PSPIN>(ot[u].y, pb[u].z), G2);
+        G3 = fmaf(sg[u], sat_factor<PSPIN>(ot[u].x, pa[u].w) * sat_factor<PSPIN>(ot[u].y, pb[u].w), G3);
       }
     }
   }
@@ -120,17 +131,19 @@ __device__ __forceinline__ void sat_element_k3(const SatArgs& a, const StepScala
   float* mv = &m.x;
   float* vv = &v.x;
   const float Gs[4] = {G0, G1, G2, G3};
+  const float lin = PSPIN ? a.lin[i] : 0.f;
   float4 pout;
   float* pv = &pout.x;
 #pragma unroll
   for (int c = 0; c < 4; ++c) {
     float hi = hv[c], mi = mv[c], vi = vv[c];
-    const float g = s.gq * (hi * s.inv_beta - Gs[c]) * one_minus_m2_fast(hi);
+    const float g = PSPIN ? s.gq * fmaf(2.f, Gs[c] + lin, hi * s.inv_beta) * one_minus_m2_fast(hi)
+                          : s.gq * (hi * s.inv_beta - Gs[c]) * one_minus_m2_fast(hi);
     opt_update_fast_rt(a.opt, hi, mi, vi, g, s);
     hv[c] = hi;
     mv[c] = mi;
     vv[c] = vi;
-    pv[c] = sigmoidf_fast(hi);
+    pv[c] = PSPIN ? tanhf(0.5f * hi) : sigmoidf_fast(hi);
   }
   st_f4(a.h + e, h);
   st_f4(a.m + e, m);

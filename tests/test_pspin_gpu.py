@@ -101,3 +101,20 @@ def test_pspin_arguments(fem):
     with pytest.raises(fem.FemError) as e:
         fem.Problem("sat", clauses=cl, term_weight=J)
     assert e.value.status == fem.FEM_ERR_INVALID_ARG
+
+
+def test_three_spin_four_replica_path_matches_general_path(fem):
+    """3-spin terms with R % 4 == 0 take the four-replicas-per-thread kernel (other-spin
+    table, each occurrence carrying its term's coupling, negations folded in); R = 50
+    takes the per-element kernel.  Replicas are independent, so the first 4 / 16 / 48
+    replicas of the R = 50 run must equal the narrow runs bit for bit."""
+    cl, ptr, var, J, b = _instance(3000, 9000, 3, 3, seed=131)
+    lits = cl.lits.copy()
+    lits[::5] *= -1  # some negated spins (their sign goes into the term's coupling)
+    mk = lambda: fem.Problem("pspin", clauses=I.Clauses(3000, ptr, lits), term_weight=J, linear=b)
+    wide = I.initial_fields(3000, 50, seed=132)
+    ref = mk().anneal(h_init=wide, n_steps=200).state()
+    for R in (4, 16, 48):
+        got = mk().anneal(h_init=np.ascontiguousarray(wide[:, :R]), n_steps=200).state()
+        for x, y, name in zip(got, ref, "hmv"):
+            assert np.array_equal(x, y[:, :R]), (R, name, int(np.sum(x != y[:, :R])))

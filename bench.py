@@ -280,11 +280,11 @@ def _traffic_from_profile(name, kind):
     return int(m2.group(1)) if source_sha256(kind) == m1.group(1) else None
 
 
-def _roofline(wl, inst, step_ms, precision, dense_launch=None, grad_mode="paper"):
+def _roofline(wl, inst, step_ms, precision, dense_launch=None, grad_mode="paper", opt="adam"):
     """Algorithmic work of one step launch / its measured duration, against the peak."""
     peaks, src = _peaks()
-    csrc = os.path.join(ROOT, "paper_2412_09285_b300", "csrc")
     R = wl["R"]
+    sb = 16 if opt == "sgd" else 24  # state bytes per element: h and m (+ v) read and written
     if wl["kind"] == "batched":
         q = wl["q"]
         alg = 0
@@ -340,24 +340,24 @@ def _roofline(wl, inst, step_ms, precision, dense_launch=None, grad_mode="paper"
         n, nnz = inst.n, 2 * inst.n_edges
         # h, m, v read + written, m = tanh(h/2) read once (its gathers beyond that are
         # traffic, not algorithm) and written once, CSR, sign words written
-        alg = 24 * n * R + 8 * n * R + 4 * nnz + 4 * (n + 1) + 4 * n * (R // 32)
+        alg = sb * n * R + 8 * n * R + 4 * nnz + 4 * (n + 1) + 4 * n * (R // 32)
         ach = alg / (step_ms / 1e3) / 1e9
         return {"bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                 "frac": ach / peaks["hbm_gbs"], "traffic": None,
-                "kernel": "k_maxcut_step<exact, adam, unit>", "algorithmic_bytes_per_launch": alg,
+                "kernel": f"k_maxcut_step<exact, {opt}, unit>", "algorithmic_bytes_per_launch": alg,
                 "launch_ms": step_ms, "peak_source": f"{src} hbm_gbs (copy), of {src}",
                 "frac_of_8TBs": ach / 8000.0}
     if wl["kind"] == "sparse":
         n, nnz = inst.n, 2 * inst.n_edges
         # h, m, v read + written (24 B per node*replica), CSR col (4 B per directed entry),
         # row_ptr, the sign words read once and written once (4 B per node per 32 replicas)
-        alg = 24 * n * R + 4 * nnz + 4 * (n + 1) + 8 * n * (R // 32)
+        alg = sb * n * R + 4 * nnz + 4 * (n + 1) + 8 * n * (R // 32)
         ach = alg / (step_ms / 1e3) / 1e9
         return {"bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                 "frac": ach / peaks["hbm_gbs"],
                 "traffic": (_traffic_from_profile("maxcut_step_sparse_n1M_R32.md", "sparse")
-                            if wl is WORKLOADS["sparse"] else None),
-                "kernel": "k_maxcut_step_paper<adam, unit, 4>", "algorithmic_bytes_per_launch": alg,
+                            if wl is WORKLOADS["sparse"] and opt == "adam" else None),
+                "kernel": f"k_maxcut_step_paper<{opt}, unit, 4>", "algorithmic_bytes_per_launch": alg,
                 "launch_ms": step_ms, "peak_source": f"{src} hbm_gbs (copy), of {src}",
                 "frac_of_8TBs": ach / 8000.0}
     n = inst.n
@@ -591,7 +591,10 @@ def run_ours(args, wl):
     stream = torch.cuda.current_stream()
     prob = _make_problem(fem, wl, inst, stream, args.dense_launch)
     grad_mode = args.grad_mode or wl.get("grad_mode") or ("exact" if precision == "bf16x2" else "paper")
-    kw = dict(grad_mode=grad_mode, optimizer="adam", lr=0.1, precision=precision)
+    kw = dict(grad_mode=grad_mode, optimizer=args.optimizer, lr=args.lr or {"adam": 0.1, "rmsprop": 0.01, "sgd": 0.05}[
+        args.optimizer], precision=precision, schedule=args.schedule)
+    if args.optimizer == "sgd":
+        kw.update(momentum=0.9)
 
     def one_anneal(k, events):
         """Fresh fields from the resident h0, then k steps, then the read-out.  Events
@@ -679,13 +682,16 @@ def run_ours(args, wl):
             "config": {"workload": wl["name"] if grad_mode == "paper" or wl["kind"] != "sparse"
                        else wl["name"].replace("paper-mode gradient", "exact gradient"), "n": inst.n, "units_per_replica": _units_per_replica(wl, inst),
                        "replicas_per_gpu": R, "anneal_steps": n_steps, "precision": precision,
+                       "optimizer": f"{kw['optimizer']} lr {kw['lr']}" + (" momentum 0.9" if kw["optimizer"] == "sgd"
+                                                                           else ""),
+                       "schedule": kw["schedule"],
                        "parallelism": f"replica-sharded x{ws}",
                        "l2": ("working set L2-resident (latency/compute-bound workload)"
                               if wl["kind"] == "dense" or (wl["kind"] == "sparse" and inst.n <= 100000)
                               else "inputs larger than L2")},
             "roofline": _roofline(wl, inst, step_ms, precision,
                                   dense_launch=prob.dense_last_launch() if wl["kind"] == "dense" else None,
-                                  grad_mode=grad_mode), "gpu_launches": int(launches), "e2e": e2e,
+                                  grad_mode=grad_mode, opt=kw["optimizer"]), "gpu_launches": int(launches), "e2e": e2e,
             "clocks": clk.summary(),
             "best_energy": float(best["energy_f64"][best["best_replica"]])}
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
@@ -845,6 +851,10 @@ def main():
     ap.add_argument("--dense-launch", default="auto", choices=["auto", "per_step", "persistent", "persistent_single"],
                     help="dense workload: persistent (state in tensor memory; CTA pairs where the row tiles "
                          "pair up, persistent_single without pairs) or one kernel per step")
+    ap.add_argument("--optimizer", default="adam", choices=["adam", "rmsprop", "sgd"],
+                    help="the optimizer of the step (adam lr 0.1, rmsprop lr 0.01, sgd lr 0.05 momentum 0.9)")
+    ap.add_argument("--lr", type=float, default=None)
+    ap.add_argument("--schedule", default="exponential", choices=["exponential", "inverse_proportional"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ttt", action="store_true",
                     help="time to target cut of the dense, batched or warmstart workload against plain FP32 FEM")

@@ -247,13 +247,18 @@ def _make_problem(fem, wl, inst, stream, dense_launch="auto"):
     return fem.Problem("maxcut", graph=inst, stream=stream)
 
 
-# The source files each profiled kernel is compiled from (its .cu and the local
-# headers it includes); a summary's traffic figure counts only while they are unchanged.
+# The source files each profiled kernel is compiled from (its .cu and the local headers
+# with device code it includes; the host-side problem record is not part of it); a
+# summary's traffic figure counts only while they are unchanged.
 KERNEL_SOURCES = {
-    "sparse": ["maxcut_sparse.cu", "step_common.cuh", "fem_internal.h"],
-    "dense": ["dense_tc.cu", "step_common.cuh", "fem_internal.h"],
-    "batched": ["batch.cu", "bmincut_core.cuh", "sat_core.cuh", "step_common.cuh", "fem_internal.h"],
+    "sparse": ["maxcut_sparse.cu", "step_common.cuh", "step_scalars.h"],
+    "dense": ["dense_tc.cu", "step_common.cuh", "step_scalars.h"],
+    "batched": ["batch.cu", "bmincut_core.cuh", "sat_core.cuh", "step_common.cuh", "step_scalars.h"],
+    "bmincut": ["bmincut_sparse.cu", "bmincut_core.cuh", "step_common.cuh", "step_scalars.h"],
+    "sat": ["sat.cu", "sat_core.cuh", "step_common.cuh", "step_scalars.h"],
 }
+# the committed ncu summary of each single-problem workload whose traffic is reported
+_SINGLE_PROFILES = {"bmincut": ("bmincut_step_rgg1M_q4_R16.md", "bmincut"), "sat": ("sat_step_3sat1M_R16.md", "sat")}
 
 
 def source_sha256(kind):
@@ -332,8 +337,10 @@ def _roofline(wl, inst, step_ms, precision, dense_launch=None, grad_mode="paper"
             alg = 24 * n * R_ + 8 * n * R_ + 4 * (n + 1) + 8 * L + 8 * M + 4 * n
             kernel = "k_sat_step (p-spin terms)"
         ach = alg / (step_ms / 1e3) / 1e9
+        prof = next((v for k, v in _SINGLE_PROFILES.items() if WORKLOADS.get(k) is wl), None)
         return {"bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                "frac": ach / peaks["hbm_gbs"], "traffic": None, "kernel": kernel,
+                "frac": ach / peaks["hbm_gbs"], "traffic": _traffic_from_profile(*prof) if prof else None,
+                "kernel": kernel,
                 "algorithmic_bytes_per_launch": alg, "launch_ms": step_ms,
                 "peak_source": f"{src} hbm_gbs (copy), of {src}", "frac_of_8TBs": ach / 8000.0}
     if wl["kind"] == "sparse" and grad_mode == "exact":

@@ -260,6 +260,14 @@ typedef struct fem_batch* fem_batch_t;
 fem_status fem_batch_create(fem_problem_t const* probs, int32_t count, fem_batch_t* out);
 fem_status fem_batch_anneal(fem_batch_t b, const fem_anneal_params* prm, const float* const* h_init,
                             void* stream);
+
+/* One-shot form of the three batch calls: fem_batch_create, fem_batch_anneal and
+ * fem_batch_destroy for `count` problems.  The work list and the step-loop graph are
+ * built for this call and released at its end, so it synchronises `stream`; the
+ * work-item size chosen by timing stays cached per problem shape across calls.
+ * Results equal those of the batch object (and of annealing each member alone). */
+fem_status fem_anneal_batch(fem_problem_t const* probs, int32_t count, const fem_anneal_params* prm,
+                            const float* const* h_init, void* stream);
 void fem_batch_destroy(fem_batch_t b);
 
 /* Warm-start network (not from the paper: a learned initialisation of the local

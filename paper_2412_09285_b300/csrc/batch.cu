@@ -492,4 +492,17 @@ fem_status fem_batch_anneal(fem_batch_t b, const fem_anneal_params* a, const flo
   return FEM_OK;
 }
 
+fem_status fem_anneal_batch(fem_problem_t const* probs, int32_t count, const fem_anneal_params* prm,
+                            const float* const* h_init, void* stream) {
+  fem_batch_t b = nullptr;
+  fem_status st = fem_batch_create(probs, count, &b);
+  if (st != FEM_OK) return st;
+  st = fem_batch_anneal(b, prm, h_init, stream);
+  // the work list and the graph must outlive the work queued on the stream
+  const cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+  if (st == FEM_OK && e != cudaSuccess) st = cuda_fail(e, "fem_anneal_batch");
+  fem_batch_destroy(b);
+  return st;
+}
+
 }  // extern "C"

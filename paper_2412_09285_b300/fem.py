@@ -81,6 +81,7 @@ def _load():
         "fem_dense_last_launch": (S, [P, C.POINTER(C.c_int32)]),
         "fem_set_step_barrier_timeout": (S, [P, C.c_int64]),
         "fem_inject_step_stall": (S, [P, C.c_int32]),
+        "fem_anneal_batch": (S, [P, C.c_int32, C.POINTER(fem_anneal_params), P, P]),
         "fem_inject_allocation_failure": (None, [C.c_int64]),
         "fem_destroy": (None, [P]),
         "fem_status_string": (C.c_char_p, [S]),
@@ -384,6 +385,24 @@ def fem_batch_anneal(batch, params, h_inits=None, stream=None):
         ptrs = (C.c_void_p * len(h_inits))(*[_ptr(h) for h in h_inits])
     _check(_lib.fem_batch_anneal(batch, C.byref(params), C.cast(ptrs, C.c_void_p) if ptrs else None,
                                  _stream(stream)), "fem_batch_anneal")
+
+
+def anneal_batch(problems, h_inits, replicas=None, n_steps=1000, t_begin=0, t_end=None, stream=None, **kw):
+    """One call for several problems (fem_anneal_batch): the batch is built for the
+    call and released after it; synchronises the stream."""
+    on_device = all(getattr(h, "is_cuda", False) for h in h_inits) if h_inits is not None else False
+    if h_inits is not None and not on_device:
+        h_inits = [np.ascontiguousarray(h, np.float32) for h in h_inits]
+    if replicas is None:
+        replicas = h_inits[0].shape[1]
+    for p in problems:
+        p.replicas = int(replicas)
+    params = make_params(replicas, n_steps, t_begin, t_end, None, **kw)
+    params.h_init_is_device = int(on_device)
+    handles = (C.c_void_p * len(problems))(*[p.handle for p in problems])
+    ptrs = (C.c_void_p * len(h_inits))(*[_ptr(h) for h in h_inits]) if h_inits is not None else None
+    _check(_lib.fem_anneal_batch(C.cast(handles, C.c_void_p), len(problems), C.byref(params),
+                                 C.cast(ptrs, C.c_void_p) if ptrs else None, _stream(stream)), "fem_anneal_batch")
 
 
 def fem_batch_destroy(batch):

@@ -90,3 +90,19 @@ def test_batch_rejects_unsupported_members(fem):
     with pytest.raises(fem.FemError) as e:
         fem.Batch([fem.Problem("bmincut", graph=rg, q=4), fem.Problem("bmincut", graph=rg, q=3)])
     assert e.value.status == fem.FEM_ERR_UNSUPPORTED
+
+
+def test_one_shot_batch_call_equals_batch_object(fem):
+    """fem_anneal_batch (the batch built for one call and released after it) gives the
+    batch object's results bit for bit, in two windows as in one."""
+    graphs, sats = _members(fem, 140)
+    R = 16
+    h0 = ([I.initial_fields(g.n, R, seed=240 + k, q=4) for k, g in enumerate(graphs)]
+          + [I.initial_fields(c.n, R, seed=340 + k) for k, c in enumerate(sats)])
+    ref = _make(fem, graphs, sats)
+    fem.Batch(ref).anneal(h_inits=h0, replicas=R, n_steps=200)
+    got = _make(fem, graphs, sats)
+    fem.anneal_batch(got, h0, replicas=R, n_steps=200, t_end=70)
+    fem.anneal_batch(got, None, replicas=R, n_steps=200, t_begin=70)
+    for a, b in zip(got, ref):
+        assert np.array_equal(a.fields(), b.fields())

@@ -711,3 +711,37 @@ def test_paper_cnf_repeated_variable_reading():
     c = mk(sets)
     states = table[:, :4].T.astype(np.int8)
     assert np.array_equal(O.sat_unsat(c.ptr, c.lits, states), table[:, 4])
+
+
+def test_single_field_is_the_two_state_softmax():
+    """The single-field form (P_i(+1) = sigmoid(h_i)) is the two-state softmax with
+    fields (h_i, 0) (Eq. gradients_wrt_h for q = 2; MaxCut's energy is bMinCut's cut term
+    with W -> -W and no balance term): equal free energies, and the single-field
+    gradient equals dF/dh(+1) = -dF/dh(-1) of the softmax form."""
+    g, W = _small_graph(9, 0.5, 21, "real")
+    h = _rng(22).normal(size=(9, 3))
+    H = np.stack([h, np.zeros_like(h)], axis=2)
+    beta = 0.8
+    assert np.allclose(O.maxcut_free_energy(W, h, beta), O.bmincut_free_energy(-W, H, beta, 0.0),
+                       rtol=1e-12, atol=1e-12)
+    gm = O.maxcut_grad(W, h, beta, mode="exact")
+    gb = O.bmincut_grad(-W, H, beta, 0.0, mode="exact")
+    assert np.allclose(gm, gb[:, :, 0], rtol=1e-10, atol=1e-13)
+    assert np.allclose(gm, -gb[:, :, 1], rtol=1e-10, atol=1e-13)
+
+
+def test_pure_entropy_fields_relax_to_zero():
+    """With no couplings the free energy is -S/beta, minimised by P = 1/2 (h = 0): the
+    gradient has the sign of h and vanishes at h = 0, and small gradient-descent steps
+    at fixed beta shrink every |h| monotonically."""
+    g, W = _small_graph(6, 0.5, 23, "unit")
+    W = 0.0 * W
+    h = _rng(24).normal(size=(6, 4))
+    gr = O.maxcut_grad(W, h, 1.0, mode="exact")
+    assert np.all(np.sign(gr) == np.sign(h))
+    assert np.all(O.maxcut_grad(W, np.zeros_like(h), 1.0, mode="exact") == 0.0)
+    tr = {t: None for t in range(1, 41)}
+    O.anneal(("maxcut", W), h, 40, beta_min=1.0, beta_max=1.0, optimizer="sgd", opt_kw=dict(lr=0.5),
+             mode="exact", trace=tr)
+    mags = np.stack([np.abs(h)] + [np.abs(tr[t]) for t in range(1, 41)])
+    assert np.all(np.diff(mags, axis=0) <= 0.0) and np.all(mags[-1] < mags[0])

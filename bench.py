@@ -258,7 +258,8 @@ KERNEL_SOURCES = {
     "sat": ["sat.cu", "sat_core.cuh", "step_common.cuh", "step_scalars.h"],
 }
 # the committed ncu summary of each single-problem workload whose traffic is reported
-_SINGLE_PROFILES = {"bmincut": ("bmincut_step_rgg1M_q4_R16.md", "bmincut"), "sat": ("sat_step_3sat1M_R16.md", "sat")}
+_SINGLE_PROFILES = {"bmincut": ("bmincut_step_rgg1M_q4_R16.md", "bmincut"), "sat": ("sat_step_3sat1M_R16.md", "sat"),
+                    "pspin": ("pspin_step_3spin1M_R16.md", "sat")}
 
 
 def source_sha256(kind):

@@ -424,13 +424,14 @@ __global__ void k_maxcut_states_all(const uint32_t* __restrict__ words, int32_t 
 constexpr int kNodesPerWarp = 4;
 
 // Persistent grid: exactly the resident blocks (occupancy x SMs), never more
-// than the work needs, so the grid-stride loop runs in a single wave.
-template <typename K>
-int resident_grid(K kernel, int sm_count, long long warps_needed) {
-  static int per_sm = 0;  // one cache per kernel instantiation
+// than the work needs, so the grid-stride loop runs in a single wave.  The
+// occupancy is queried once per kernel (K is the kernel itself, not its type).
+template <auto K>
+int resident_grid(int sm_count, long long warps_needed) {
+  static int per_sm = 0;
   if (per_sm == 0) {
     int b = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kernel, 256, 0) != cudaSuccess || b < 1) b = 1;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, K, 256, 0) != cudaSuccess || b < 1) b = 1;
     per_sm = b;
   }
   long long blocks = (warps_needed + 7) / 8;
@@ -446,17 +447,18 @@ constexpr long long kSmallGraphWarps = 4096;
 template <int MODE, int OPT, bool UNIT>
 void launch_step(const MaxcutArgs& a, const StepScalars& s, int sm_count, long long warps,
                  cudaStream_t st) {
+  const long long per_node = (long long)a.n * a.wpn;
   if (MODE == FEM_GRAD_PAPER) {
     if (warps < kSmallGraphWarps) {
-      auto k = k_maxcut_step_paper<OPT, UNIT, 1>;
-      k<<<resident_grid(k, sm_count, (long long)a.n * a.wpn), 256, 0, st>>>(a, s);
+      constexpr auto k = k_maxcut_step_paper<OPT, UNIT, 1>;
+      k<<<resident_grid<k>(sm_count, per_node), 256, 0, st>>>(a, s);
     } else {
-      auto k = k_maxcut_step_paper<OPT, UNIT, kNodesPerWarp>;
-      k<<<resident_grid(k, sm_count, warps), 256, 0, st>>>(a, s);
+      constexpr auto k = k_maxcut_step_paper<OPT, UNIT, kNodesPerWarp>;
+      k<<<resident_grid<k>(sm_count, warps), 256, 0, st>>>(a, s);
     }
   } else {
-    auto k = k_maxcut_step<FEM_GRAD_EXACT, OPT, UNIT>;
-    k<<<resident_grid(k, sm_count, warps), 256, 0, st>>>(a, s);
+    constexpr auto k = k_maxcut_step<FEM_GRAD_EXACT, OPT, UNIT>;
+    k<<<resident_grid<k>(sm_count, per_node), 256, 0, st>>>(a, s);
   }
 }
 
@@ -498,9 +500,7 @@ fem_status maxcut_pack_words(Problem* p, int hbuf, int wbuf, cudaStream_t s) {
 fem_status maxcut_sparse_steps(Problem* p, const fem_anneal_params& a,
                                const std::vector<StepScalars>& sc, cudaStream_t s) {
   const StepFn fn = pick_step(p->grad_mode, p->optimizer, p->unit_w);
-  const long long groups = p->grad_mode == FEM_GRAD_PAPER
-                               ? (long long)((p->n + kNodesPerWarp - 1) / kNodesPerWarp) * p->words_per_node
-                               : (long long)p->n * p->words_per_node;
+  const long long groups = (long long)((p->n + kNodesPerWarp - 1) / kNodesPerWarp) * p->words_per_node;
   MaxcutArgs args{};
   args.row_ptr = p->row_ptr;
   args.col = p->col;

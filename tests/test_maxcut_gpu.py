@@ -280,6 +280,31 @@ def test_error_paths(fem):
     P.sync()
 
 
+def _with_hubs(g, hubs, width, seed):
+    """g plus `hubs` nodes each joined to `width` random others with +-1 weights."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    have = {(a, b): x for a, b, x in zip(g.ei.tolist(), g.ej.tolist(), g.w.tolist())}
+    for h in rng.choice(g.n, hubs, replace=False).tolist():
+        for j in rng.choice(g.n, width, replace=False).tolist():
+            if j != h:
+                have.setdefault((min(h, j), max(h, j)), float(rng.choice([-1.0, 1.0])))
+    e = sorted(have)
+    return I.Graph(g.n, [a for a, _ in e], [b for _, b in e], [have[k] for k in e])
+
+
+@pytest.mark.parametrize("R", [32, 64])
+def test_exact_mode_grouped_nodes_with_hubs(fem, R):
+    """Exact mode at mid size (n = 20000, mean degree 6) with 40 hubs of degree ~100,
+    whose neighbour lists span several 32-entry chunks; R = 64 gives two replica words
+    per node."""
+    g = _with_hubs(I.er_gnm(20000, 60000, seed=31, weights="pm1"), 40, 100, seed=32)
+    h0 = I.initial_fields(g.n, R, seed=33)
+    _, got = _gpu_trace(fem, g, h0, [1, 10, 50], 1000, grad_mode="exact")
+    ref, cd = _oracle_trace(g, h0, [1, 10, 50], 1000, "exact", lr=0.1)
+    for t in (1, 10, 50):
+        _check_marginals(got[t], ref[t], cd[t], (R, t))
+
+
 def test_full_size_sparse_steps_match_oracle(fem):
     """N = 2^20, mean degree 6, +-1 weights, R = 32 (the sparse-at-scale
     workload) in the launch configuration the benchmark times: every element

@@ -307,7 +307,8 @@ def _roofline(wl, inst, step_ms, precision, dense_launch=None, grad_mode="paper"
                 "frac": ach / peaks["hbm_gbs"],
                 "traffic": (_traffic_from_profile("batch_step_bmc256_sat64_R16.md", "batched")
                             if wl is WORKLOADS["batched"] else None),
-                "kernel": "k_batch_step<4, paper>", "algorithmic_bytes_per_launch": alg, "launch_ms": step_ms,
+                "kernel": "k_batch_bmincut<4, paper> + k_batch_sat (the two launches of one step)",
+                "algorithmic_bytes_per_launch": alg, "launch_ms": step_ms,
                 "peak_source": f"{src} hbm_gbs (copy), of {src}", "frac_of_8TBs": ach / 8000.0}
     if wl["kind"] == "single":
         n, R_, pr = inst.n, R, wl["problem"]

@@ -243,8 +243,9 @@ fem_status fem_read_best(fem_problem_t p, int32_t* best_replica, int32_t* states
                          int64_t* energy_i64, double* energy_f64, void* stream);
 
 /* Batches: many sparse bMinCut and Max-k-SAT problems advanced together (the
- * batched, heterogeneous form of the per-step update).  One kernel launch per step
- * walks a work list of (member, node range) items across all members, the step loop
+ * batched, heterogeneous form of the per-step update).  Two kernel launches per step
+ * (one for the q-state members, one for the clause-shaped members) walk a work list of
+ * (member, node range) items across all members, the step loop
  * is captured in a CUDA graph and replayed, and the work-item size is chosen by
  * timing candidates on the first steps of the first call (cached per problem shape;
  * every candidate gives bit-identical results).  Each member keeps its own state:

@@ -1,13 +1,16 @@
-// Batched anneal: many bMinCut and Max-k-SAT problems advanced together, one
-// persistent launch per step over a work list, the step loop captured in a CUDA
-// graph, and the work-item size chosen by timing (a small autotuner).
+// Batched anneal: many bMinCut and Max-k-SAT problems advanced together, two
+// persistent launches per step over a work list (one for the q-state members, one
+// for the clause-shaped members, so that each kernel gets the registers of its own
+// element code), the step loop captured in a CUDA graph, and the work-item size
+// chosen by timing (a small autotuner).
 //
 // Every member keeps its own state buffers; the batch only adds a device table of
-// per-member descriptors and a list of work items (member, element range).  A block
-// takes items in a grid-stride loop; a bMinCut item accumulates its group counts in
-// shared memory and adds them to its member's counts once, so the per-member
-// results are bit-identical to running the members one by one (integer counts and
-// fixed-point sums do not depend on the order of the additions).
+// per-member descriptors and a list of work items (member, element range), the
+// q-state members' items first.  A block takes items in a grid-stride loop; a
+// bMinCut item accumulates its group counts in shared memory and adds them to its
+// member's counts once, so the per-member results are bit-identical to running
+// the members one by one (integer counts and fixed-point sums do not depend on the
+// order of the additions).
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -58,35 +61,41 @@ struct BatchItem {
 
 namespace {
 
+// The element code reads its arguments from a block-shared copy, written by thread 0
+// per item: values the compiler would otherwise hold in registers for the whole item
+// (and spill) are re-read from shared memory where they are used.
 template <int Q, int MODE>
 __device__ void run_bmincut_item(const BatchMember& b, const BatchItem& it, const StepScalars& s, int t,
-                                 int32_t* scnt, unsigned long long* sps) {
-  BmcArgs a{};
-  a.row_ptr = b.row_ptr;
-  a.col = b.col;
-  a.w = b.w;
-  a.cf = b.cf;
-  a.ca = b.ca;
-  a.nodew = b.nodew;
-  a.cw = b.cw;
-  a.lam_scale = b.lam_scale;
-  a.n = b.n;
-  a.R = b.R;
-  a.wpn = b.wpn;
-  a.opt = b.opt;
-  a.h_in = MODE == FEM_GRAD_PAPER ? b.h0 : ((t & 1) ? b.h1 : b.h0);
-  a.h_out = MODE == FEM_GRAD_PAPER ? b.h0 : ((t & 1) ? b.h0 : b.h1);
-  a.m = b.m;
-  a.v = b.v;
-  a.words_in = b.words[t & 1];
-  a.words_out = b.words[(t + 1) & 1];
-  a.cnt_in = b.cnt[t % 3];
-  a.cnt_out = b.cnt[(t + 1) % 3];
-  a.cnt_zero = b.cnt[(t + 2) % 3];
-  a.ps_in = b.psum[t % 3];
-  a.ps_out = b.psum[(t + 1) % 3];
-  a.ps_zero = b.psum[(t + 2) % 3];
-  const int RQ = b.R * Q;
+                                 int32_t* scnt, unsigned long long* sps, BmcArgs& a) {
+  if (threadIdx.x == 0) {
+    a = BmcArgs{};
+    a.row_ptr = b.row_ptr;
+    a.col = b.col;
+    a.w = b.w;
+    a.cf = b.cf;
+    a.ca = b.ca;
+    a.nodew = b.nodew;
+    a.cw = b.cw;
+    a.lam_scale = b.lam_scale;
+    a.n = b.n;
+    a.R = b.R;
+    a.wpn = b.wpn;
+    a.opt = b.opt;
+    a.h_in = MODE == FEM_GRAD_PAPER ? b.h0 : ((t & 1) ? b.h1 : b.h0);
+    a.h_out = MODE == FEM_GRAD_PAPER ? b.h0 : ((t & 1) ? b.h0 : b.h1);
+    a.m = b.m;
+    a.v = b.v;
+    a.words_in = b.words[t & 1];
+    a.words_out = b.words[(t + 1) & 1];
+    a.cnt_in = b.cnt[t % 3];
+    a.cnt_out = b.cnt[(t + 1) % 3];
+    a.cnt_zero = b.cnt[(t + 2) % 3];
+    a.ps_in = b.psum[t % 3];
+    a.ps_out = b.psum[(t + 1) % 3];
+    a.ps_zero = b.psum[(t + 2) % 3];
+  }
+  __syncthreads();
+  const int RQ = a.R * Q;
   for (int x = threadIdx.x; x < RQ; x += blockDim.x) {
     scnt[x] = 0;
     if (MODE == FEM_GRAD_EXACT) sps[x] = 0ull;
@@ -109,66 +118,78 @@ __device__ void run_bmincut_item(const BatchMember& b, const BatchItem& it, cons
   __syncthreads();
 }
 
-__device__ void run_sat_item(const BatchMember& b, const BatchItem& it, const StepScalars& s, int t) {
-  SatArgs a{};
-  a.cl_ptr = b.cl_ptr;
-  a.cl_lit = b.cl_lit;
-  a.occ_ptr = b.occ_ptr;
-  a.occ = b.occ;
-  a.oth = b.oth;
-  a.jw = b.jw;
-  a.jwo = b.jwo;
-  a.lin = b.lin;
-  a.n = b.n;
-  a.R = b.R;
-  a.opt = b.opt;
-  a.h = b.h0;
-  a.m = b.m;
-  a.v = b.v;
-  a.P_in = b.satP[t & 1];
-  a.P_out = b.satP[(t + 1) & 1];
-  // four replicas per thread (e0 and e1 are multiples of R); p-spin members take the
-  // per-element path here, which gives the same bits, since its extra registers would
-  // spill in this kernel
+__device__ void run_sat_item(const BatchMember& b, const BatchItem& it, const StepScalars& s, int t, SatArgs& a) {
+  if (threadIdx.x == 0) {
+    a = SatArgs{};
+    a.cl_ptr = b.cl_ptr;
+    a.cl_lit = b.cl_lit;
+    a.occ_ptr = b.occ_ptr;
+    a.occ = b.occ;
+    a.oth = b.oth;
+    a.jw = b.jw;
+    a.jwo = b.jwo;
+    a.lin = b.lin;
+    a.n = b.n;
+    a.R = b.R;
+    a.opt = b.opt;
+    a.h = b.h0;
+    a.m = b.m;
+    a.v = b.v;
+    a.P_in = b.satP[t & 1];
+    a.P_out = b.satP[(t + 1) & 1];
+  }
+  __syncthreads();
+  // four replicas per thread (e0 and e1 are multiples of R), two occurrences at a time;
+  // p-spin members take the per-element path, which gives the same bits, since the
+  // four-replica p-spin code would spill in this kernel
   if (sat_k3_shape(a) && !a.jw) {
     for (long long e = it.e0 + threadIdx.x * 4; e < it.e1; e += blockDim.x * 4) sat_element_k3<2, false>(a, s, e);
-    return;
+  } else {
+    for (long long e = it.e0 + threadIdx.x; e < it.e1; e += blockDim.x) sat_element(a, s, e);
   }
-  for (long long e = it.e0 + threadIdx.x; e < it.e1; e += blockDim.x) sat_element(a, s, e);
+  __syncthreads();  // the next item's arguments overwrite a
 }
 
-// One launch per step for every member: blocks walk the work list.  Q and MODE are
-// shared by all bMinCut members of a batch.
-// s_q carries the q-state gradient scale (gamma), s_1 the single-field one (gamma/4).
+// The q-state members' step: blocks walk their items (the first n_items of the list).
+// Q and MODE are shared by all of them; s carries the q-state gradient scale (gamma).
 template <int Q, int MODE>
-__global__ void __launch_bounds__(256, 4) k_batch_step(const BatchMember* __restrict__ members,
-                                                    const BatchItem* __restrict__ items, int32_t n_items,
-                                                    int32_t max_rq, StepScalars s_q, StepScalars s_1,
-                                                    int32_t t) {
+__global__ void __launch_bounds__(256, 4) k_batch_bmincut(const BatchMember* __restrict__ members,
+                                                       const BatchItem* __restrict__ items, int32_t n_items,
+                                                       int32_t max_rq, StepScalars s, int32_t t) {
   extern __shared__ unsigned long long smem_b[];
   unsigned long long* sps = smem_b;
   int32_t* scnt = reinterpret_cast<int32_t*>(smem_b + (MODE == FEM_GRAD_EXACT ? max_rq : 0));
+  __shared__ BmcArgs args;
   for (int k = blockIdx.x; k < n_items; k += gridDim.x) {
     const BatchItem it = items[k];
-    const BatchMember& b = members[it.member];
-    if (b.kind == FEM_BMINCUT) run_bmincut_item<Q, MODE>(b, it, s_q, t, scnt, sps);
-    else run_sat_item(b, it, s_1, t);
+    run_bmincut_item<Q, MODE>(members[it.member], it, s, t, scnt, sps, args);
   }
 }
 
-using BatchKernel = void (*)(const BatchMember*, const BatchItem*, int32_t, int32_t, StepScalars, StepScalars,
-                            int32_t);
+// The clause-shaped members' step (Max-k-SAT and p-spin); s carries the single-field
+// gradient scale (gamma/4).
+__global__ void __launch_bounds__(256, 4) k_batch_sat(const BatchMember* __restrict__ members,
+                                                   const BatchItem* __restrict__ items, int32_t n_items,
+                                                   StepScalars s, int32_t t) {
+  __shared__ SatArgs args;
+  for (int k = blockIdx.x; k < n_items; k += gridDim.x) {
+    const BatchItem it = items[k];
+    run_sat_item(members[it.member], it, s, t, args);
+  }
+}
+
+using BatchKernel = void (*)(const BatchMember*, const BatchItem*, int32_t, int32_t, StepScalars, int32_t);
 
 template <int MODE>
 BatchKernel pick_q(int q) {
   switch (q) {
-    case 2: return k_batch_step<2, MODE>;
-    case 3: return k_batch_step<3, MODE>;
-    case 4: return k_batch_step<4, MODE>;
-    case 5: return k_batch_step<5, MODE>;
-    case 6: return k_batch_step<6, MODE>;
-    case 7: return k_batch_step<7, MODE>;
-    default: return k_batch_step<8, MODE>;
+    case 2: return k_batch_bmincut<2, MODE>;
+    case 3: return k_batch_bmincut<3, MODE>;
+    case 4: return k_batch_bmincut<4, MODE>;
+    case 5: return k_batch_bmincut<5, MODE>;
+    case 6: return k_batch_bmincut<6, MODE>;
+    case 7: return k_batch_bmincut<7, MODE>;
+    default: return k_batch_bmincut<8, MODE>;
   }
 }
 
@@ -184,8 +205,8 @@ struct Batch {
   int R = 0, q = 4, mode = FEM_GRAD_PAPER, opt = FEM_OPT_ADAM;
   long long elems_bmc = 0, elems_sat = 0;
   BatchMember* d_members = nullptr;
-  BatchItem* d_items = nullptr;
-  int n_items = 0, nodes_per_item = 0, max_rq = 0;
+  BatchItem* d_items = nullptr;  // the q-state members' items, then the clause-shaped ones
+  int n_bmc = 0, n_sat = 0, nodes_per_item = 0, max_rq = 0;
   bool ready = false;
   std::vector<const void*> sig;  // member state pointers the descriptors were built from
   cudaStream_t capture_stream = nullptr;
@@ -210,25 +231,32 @@ static fem_status batch_free_plan(Batch* b) {
   b->allocs.clear();
   b->d_members = nullptr;
   b->d_items = nullptr;
-  b->n_items = 0;
+  b->n_bmc = b->n_sat = 0;
   b->nodes_per_item = 0;
   b->ready = false;
   return FEM_OK;
 }
 
 // Work items: every member's nodes in runs of `npi` nodes (npi even, so that
-// e0 = node0 * R is a multiple of 32 for R % 16 == 0).
+// e0 = node0 * R is a multiple of 32 for R % 16 == 0), the q-state members' items
+// first.
 static fem_status batch_build_items(Batch* b, int npi, std::vector<BatchItem>& items) {
   items.clear();
-  for (size_t k = 0; k < b->members.size(); ++k) {
-    const Problem* p = b->members[k];
-    bool first = true;
-    for (long long i0 = 0; i0 < p->n; i0 += npi) {
-      const long long i1 = std::min<long long>(p->n, i0 + npi);
-      items.push_back(BatchItem{(int32_t)k, first ? 1 : 0, i0 * p->R, i1 * p->R});
-      first = false;
+  b->n_bmc = 0;
+  for (int pass = 0; pass < 2; ++pass) {
+    for (size_t k = 0; k < b->members.size(); ++k) {
+      const Problem* p = b->members[k];
+      if ((p->kind == FEM_BMINCUT) != (pass == 0)) continue;
+      bool first = true;
+      for (long long i0 = 0; i0 < p->n; i0 += npi) {
+        const long long i1 = std::min<long long>(p->n, i0 + npi);
+        items.push_back(BatchItem{(int32_t)k, first ? 1 : 0, i0 * p->R, i1 * p->R});
+        first = false;
+      }
     }
+    if (pass == 0) b->n_bmc = (int)items.size();
   }
+  b->n_sat = (int)items.size() - b->n_bmc;
   return FEM_OK;
 }
 
@@ -245,7 +273,6 @@ static fem_status batch_upload_items(Batch* b, int npi, cudaStream_t s) {
   b->d_items = (BatchItem*)p;
   FEM_CUDA(cudaMemcpyAsync(b->d_items, items.data(), items.size() * sizeof(BatchItem), cudaMemcpyHostToDevice, s));
   FEM_CUDA(cudaStreamSynchronize(s));
-  b->n_items = (int)items.size();
   b->nodes_per_item = npi;
   return FEM_OK;
 }
@@ -313,17 +340,31 @@ static size_t batch_smem(const Batch* b) {
   return (size_t)b->max_rq * (b->mode == FEM_GRAD_EXACT ? 12 : 4);
 }
 
-static fem_status batch_launch(Batch* b, BatchKernel k, int grid, const StepScalars& sq, const StepScalars& s1,
-                               int t, cudaStream_t s) {
-  k<<<grid, 256, batch_smem(b), s>>>(b->d_members, b->d_items, b->n_items, b->max_rq, sq, s1, t);
-  return FEM_OK;
+// Resident blocks of a grid-stride launch over n items (at least one block).
+template <typename K>
+static int batch_grid(const Batch* b, K k, size_t smem, int n) {
+  int per_sm = 1;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, 256, smem) != cudaSuccess || per_sm < 1)
+    per_sm = 1;
+  return std::max(1, std::min(n, per_sm * b->sm_count));
 }
 
-static int batch_grid(Batch* b, BatchKernel k) {
-  int per_sm = 1;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, 256, batch_smem(b)) != cudaSuccess || per_sm < 1)
-    per_sm = 1;
-  return std::max(1, std::min(b->n_items, per_sm * b->sm_count));
+// One step: the q-state members' launch, then the clause-shaped members' launch.
+// Returns the number of launches.
+static int batch_launch(Batch* b, BatchKernel k, const StepScalars& sq, const StepScalars& s1, int t,
+                        cudaStream_t s) {
+  int n = 0;
+  if (b->n_bmc > 0) {
+    k<<<batch_grid(b, k, batch_smem(b), b->n_bmc), 256, batch_smem(b), s>>>(b->d_members, b->d_items, b->n_bmc,
+                                                                              b->max_rq, sq, t);
+    ++n;
+  }
+  if (b->n_sat > 0) {
+    k_batch_sat<<<batch_grid(b, k_batch_sat, 0, b->n_sat), 256, 0, s>>>(b->d_members, b->d_items + b->n_bmc,
+                                                                         b->n_sat, s1, t);
+    ++n;
+  }
+  return n;
 }
 
 }  // namespace fem
@@ -418,6 +459,7 @@ fem_status fem_batch_anneal(fem_batch_t b, const fem_anneal_params* a, const flo
   if (npi == 0) {
     const int cands[3] = {64, 256, 1024};
     float best_ms = 1e30f;
+    int64_t launches = 0;
     cudaEvent_t e0, e1;
     FEM_CUDA(cudaEventCreate(&e0));
     FEM_CUDA(cudaEventCreate(&e1));
@@ -425,12 +467,11 @@ fem_status fem_batch_anneal(fem_batch_t b, const fem_anneal_params* a, const flo
       if (done + 2 > sc.size()) break;
       fem_status st = batch_upload_items(b, c, s);
       if (st != FEM_OK) return st;
-      const int grid = batch_grid(b, k);
-      batch_launch(b, k, grid, sc[done], sc1[done], t, s);  // a warm step, not timed
+      launches += batch_launch(b, k, sc[done], sc1[done], t, s);  // a warm step, not timed
       ++t;
       ++done;
       FEM_CUDA(cudaEventRecord(e0, s));
-      batch_launch(b, k, grid, sc[done], sc1[done], t, s);
+      launches += batch_launch(b, k, sc[done], sc1[done], t, s);
       FEM_CUDA(cudaEventRecord(e1, s));
       FEM_CUDA(cudaEventSynchronize(e1));
       ++t;
@@ -447,14 +488,13 @@ fem_status fem_batch_anneal(fem_batch_t b, const fem_anneal_params* a, const flo
     if (npi == 0) npi = 256;
     std::lock_guard<std::mutex> lock(g_tune_mutex);
     g_tune_cache[key] = npi;
-    count_launches((int64_t)done);
+    count_launches(launches);
   }
   if (b->nodes_per_item != npi) {
     fem_status st = batch_upload_items(b, npi, s);
     if (st != FEM_OK) return st;
     batch_drop_graphs(b);
   }
-  const int grid = batch_grid(b, k);
   // ---- the remaining steps as one CUDA graph (captured on a private stream, replayed
   // on the caller's stream; cached for the same first step, item size and scalars)
   if (done < sc.size()) {
@@ -473,7 +513,7 @@ fem_status fem_batch_anneal(fem_batch_t b, const fem_anneal_params* a, const flo
       }
       if (!b->capture_stream) FEM_CUDA(cudaStreamCreateWithFlags(&b->capture_stream, cudaStreamNonBlocking));
       FEM_CUDA(cudaStreamBeginCapture(b->capture_stream, cudaStreamCaptureModeThreadLocal));
-      for (size_t j = 0; j < sq.size(); ++j) batch_launch(b, k, grid, sq[j], s1[j], t0 + (int)j, b->capture_stream);
+      for (size_t j = 0; j < sq.size(); ++j) batch_launch(b, k, sq[j], s1[j], t0 + (int)j, b->capture_stream);
       cudaGraph_t g = nullptr;
       const cudaError_t ec = cudaStreamEndCapture(b->capture_stream, &g);
       if (ec != cudaSuccess) return cuda_fail(ec, "batch graph capture");
@@ -485,7 +525,7 @@ fem_status fem_batch_anneal(fem_batch_t b, const fem_anneal_params* a, const flo
       hit = &b->graphs.back();
     }
     FEM_CUDA(cudaGraphLaunch(hit->exec, s));
-    count_launches((int64_t)sq.size());
+    count_launches((int64_t)sq.size() * ((b->n_bmc > 0) + (b->n_sat > 0)));
   }
   FEM_CUDA(cudaGetLastError());
   for (Problem* p : b->members) p->steps_done = a->t_end;

@@ -56,8 +56,9 @@ WORKLOADS = {
     "batched": dict(kind="batched", name="batched heterogeneous: 256 bMinCut (random geometric graphs, n "
                                         "log-uniform 1k-64k, mean degree 10, unit weights, q=4, lambda_max=1) + "
                                         "64 random Max-3-SAT (n log-uniform 5k-50k, M=4.2n), R=16 each, 1000-step "
-                                        "exponential beta 0.05->5, Adam lr 0.1, paper-mode gradient, one launch "
-                                        "per step, CUDA-graph step loop, autotuned work items",
+                                        "exponential beta 0.05->5, Adam lr 0.1, paper-mode gradient, two launches "
+                                        "per step (bMinCut and SAT members), CUDA-graph step loop, autotuned "
+                                        "work items",
                     n_bmc=256, bmc_lo=1000, bmc_hi=64000, deg=10.0, q=4, n_sat=64, sat_lo=5000, sat_hi=50000,
                     ratio=4.2, R=16, n_steps=1000, graph_seed=5, h_seed=6, cpu_steps=2),
     # learned warm start (time to target only): ER graphs, n log-uniform 20k-200k, mean

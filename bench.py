@@ -316,11 +316,17 @@ def _roofline(wl, inst, step_ms, precision, dense_launch=None, grad_mode="paper"
         if pr in ("bmincut", "coloring"):
             q, nnz = wl["q"], 2 * inst.graph.n_edges
             bits = max(1, (q - 1).bit_length())
-            # h, m, v read + written, col, row_ptr, c^f and c^a, argmax words read once and
-            # written once (+ node weights)
-            alg = 24 * q * n * R_ + 4 * nnz + 4 * (n + 1) + 8 * n + 8 * n * max(1, R_ * bits // 32)
+            wpn = max(1, R_ * bits // 32)
+            if grad_mode == "paper":
+                # h, m, v read + written, col, row_ptr, c^f and c^a, argmax words read once
+                # and written once (+ node weights)
+                alg = 24 * q * n * R_ + 4 * nnz + 4 * (n + 1) + 8 * n + 8 * n * wpn
+            else:
+                # h, m, v read + written, the gathered centred marginals read once and
+                # written once, col, row_ptr, argmax words written (+ node weights)
+                alg = 24 * q * n * R_ + 8 * q * n * R_ + 4 * nnz + 4 * (n + 1) + 4 * n * wpn
             alg += 4 * n if inst.node_weight is not None else 0
-            kernel = f"k_bmincut_step<{q}, paper>"
+            kernel = f"k_bmincut_step<{q}, {grad_mode}>"
         elif pr == "qubo":
             nnz = 2 * inst.graph.n_edges
             # the exact-mode MaxCut step: h, m, v, the gathered marginals m = tanh(h/2) read
@@ -341,6 +347,8 @@ def _roofline(wl, inst, step_ms, precision, dense_launch=None, grad_mode="paper"
             kernel = "k_sat_step (p-spin terms)"
         ach = alg / (step_ms / 1e3) / 1e9
         prof = next((v for k, v in _SINGLE_PROFILES.items() if WORKLOADS.get(k) is wl), None)
+        if grad_mode != (wl.get("grad_mode") or "paper"):
+            prof = None  # the committed captures are of the workload's own gradient mode
         return {"bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                 "frac": ach / peaks["hbm_gbs"], "traffic": _traffic_from_profile(*prof) if prof else None,
                 "kernel": kernel,

@@ -39,6 +39,7 @@ struct BatchMember {
   float* h1;
   float* m;
   float* v;
+  float* dq[2];  // exact mode: the centred marginals the neighbour terms gather
   uint32_t* words[2];
   int32_t* cnt[3];
   unsigned long long* psum[3];
@@ -83,6 +84,8 @@ __device__ void run_bmincut_item(const BatchMember& b, const BatchItem& it, cons
     a.opt = b.opt;
     a.h_in = MODE == FEM_GRAD_PAPER ? b.h0 : ((t & 1) ? b.h1 : b.h0);
     a.h_out = MODE == FEM_GRAD_PAPER ? b.h0 : ((t & 1) ? b.h0 : b.h1);
+    a.d_in = MODE == FEM_GRAD_PAPER ? nullptr : b.dq[t & 1];
+    a.d_out = MODE == FEM_GRAD_PAPER ? nullptr : b.dq[(t + 1) & 1];
     a.m = b.m;
     a.v = b.v;
     a.words_in = b.words[t & 1];
@@ -153,7 +156,7 @@ __device__ void run_sat_item(const BatchMember& b, const BatchItem& it, const St
 // The q-state members' step: blocks walk their items (the first n_items of the list).
 // Q and MODE are shared by all of them; s carries the q-state gradient scale (gamma).
 template <int Q, int MODE>
-__global__ void __launch_bounds__(256, 4) k_batch_bmincut(const BatchMember* __restrict__ members,
+__global__ void __launch_bounds__(256, Q >= 7 ? 3 : 4) k_batch_bmincut(const BatchMember* __restrict__ members,
                                                        const BatchItem* __restrict__ items, int32_t n_items,
                                                        int32_t max_rq, StepScalars s, int32_t t) {
   extern __shared__ unsigned long long smem_b[];
@@ -306,6 +309,7 @@ static fem_status batch_prepare(Batch* b, cudaStream_t s) {
     for (int k = 0; k < 2; ++k) {
       m.words[k] = p->words[k];
       m.satP[k] = p->satP[k];
+      m.dq[k] = p->kind == FEM_BMINCUT ? p->mag[k] : nullptr;
     }
     for (int k = 0; k < 3; ++k) {
       m.cnt[k] = p->cnt[k];
@@ -321,6 +325,8 @@ static fem_status batch_prepare(Batch* b, cudaStream_t s) {
     m.lin = p->pspin ? p->qoff : nullptr;
     dm.push_back(m);
     if (p->kind == FEM_BMINCUT) {
+      if (p->grad_mode == FEM_GRAD_EXACT && (!p->mag[0] || !p->mag[1]))
+        return fail(FEM_ERR_STATE, "exact-mode buffers of a member are not allocated");
       b->elems_bmc += (long long)p->n * p->R;
       b->max_rq = std::max(b->max_rq, p->R * p->q);
     } else {
@@ -429,7 +435,8 @@ fem_status fem_batch_anneal(fem_batch_t b, const fem_anneal_params* a, const flo
   for (const Problem* p : b->members)
     for (const void* x : {(const void*)p->h[0], (const void*)p->h[1], (const void*)p->m, (const void*)p->v,
                           (const void*)p->words[0], (const void*)p->words[1], (const void*)p->cnt[0],
-                          (const void*)p->psum[0], (const void*)p->satP[0], (const void*)p->satP[1]})
+                          (const void*)p->psum[0], (const void*)p->satP[0], (const void*)p->satP[1],
+                          (const void*)p->mag[0], (const void*)p->mag[1]})
       sig.push_back(x);
   const bool changed = !b->ready || b->R != R || b->mode != a->grad_mode || b->opt != a->optimizer || sig != b->sig;
   if (changed) {

@@ -31,6 +31,8 @@ struct BmcArgs {
   float* h_out;
   float* m;
   float* v;
+  const float* d_in;  // exact mode: q (P_j(s) - 1/q) of the fields h_in, [n][R][q]
+  float* d_out;       // exact mode: the same of the updated fields, gathered by the next step
   const uint32_t* words_in;
   uint32_t* words_out;
   const int32_t* cnt_in;
@@ -59,6 +61,27 @@ __device__ __forceinline__ void softmax_q(const float (&h)[Q], float (&P)[Q], fl
     P[s] = ex[s] * invZ;
     lnP[s] = h[s] - mx - lz;
   }
+}
+
+// q (P(s) - 1/q) of the softmax of h.  With u(s) = expm1(h(s) - max h) and
+// Z = sum_s exp(h(s) - max h) = q + sum_s u(s), it equals (q u(s) - sum_s' u(s')) / Z.
+// u is accurate relative to |h(s) - max h|, so near a uniform P, where those gaps are
+// as small as the differences h(s) - h(s'), the result keeps full relative accuracy
+// (P - 1/q formed in fp32 would not); q expm1 per element instead of q^2.
+template <int Q>
+__device__ __forceinline__ void centred_q(const float (&h)[Q], float (&d)[Q]) {
+  float mx = h[0];
+#pragma unroll
+  for (int q = 1; q < Q; ++q) mx = fmaxf(mx, h[q]);
+  float u[Q], su = 0.f;
+#pragma unroll
+  for (int q = 0; q < Q; ++q) {
+    u[q] = expm1f(h[q] - mx);
+    su += u[q];
+  }
+  const float invZ = __fdividef(1.f, (float)Q + su);  // Z in [1, q]
+#pragma unroll
+  for (int q = 0; q < Q; ++q) d[q] = fmaf((float)Q, u[q], -su) * invZ;
 }
 
 template <int Q>
@@ -193,22 +216,15 @@ __device__ __forceinline__ void bmincut_element(const BmcArgs& a, const StepScal
         }
       } else {
         // accumulate sum_j W_ij (P_j(s) - 1/q): the constant drops out of every
-        // difference below.  The deviation is evaluated as
-        // (1/q) sum_s' P_j(s') expm1(h_j(s) - h_j(s')), which keeps full relative
-        // accuracy when P_j is near uniform (P_j - 1/q in fp32 would not).
+        // difference below.  Each neighbour's q (P_j(s) - 1/q) (centred_q) was written
+        // by the step that produced h_j, once per node rather than once per edge.
         for (int k = beg; k < end; ++k) {
           const uint32_t j = a.col[k] & 0x7fffffffu;
           const float wk = a.w ? a.w[k] : 1.f;
-          float hj[Q], Pj[Q], lj[Q];
-          load_q<Q>(a.h_in + ((size_t)j * a.R + r) * Q, hj);
-          softmax_q<Q>(hj, Pj, lj);
+          float dj[Q];
+          load_q<Q>(a.d_in + ((size_t)j * a.R + r) * Q, dj);
 #pragma unroll
-          for (int q = 0; q < Q; ++q) {
-            float dq = 0.f;
-#pragma unroll
-            for (int q2 = 0; q2 < Q; ++q2) dq = fmaf(Pj[q2], expm1f(hj[q] - hj[q2]), dq);
-            acc[q] = fmaf(wk, dq * (1.f / Q), acc[q]);
-          }
+          for (int q = 0; q < Q; ++q) acc[q] = fmaf(wk, dj[q] * (1.f / Q), acc[q]);
         }
       }
     }
@@ -271,11 +287,13 @@ __device__ __forceinline__ void bmincut_element(const BmcArgs& a, const StepScal
       if (a.opt != FEM_OPT_SGD) store_q<Q>(a.v + idx, vv);
       atomicAdd(&scnt[r * Q + sn], Vi);
       if (MODE == FEM_GRAD_EXACT) {
-        float Pn[Q], ln[Q];
+        float Pn[Q], ln[Q], dn[Q];
         softmax_q<Q>(h, Pn, ln);
 #pragma unroll
         for (int q = 0; q < Q; ++q)
           atomicAdd(&sps[r * Q + q], __float2ull_rn(Pn[q] * kPsumScale) * (unsigned long long)Vi);
+        centred_q<Q>(h, dn);
+        store_q<Q>(a.d_out + idx, dn);
       }
     }
     uint32_t word = act ? ((uint32_t)sn << sh) : 0u;

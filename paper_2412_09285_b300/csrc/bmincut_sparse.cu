@@ -29,7 +29,7 @@ namespace {
 // One thread per (node, replica); a warp covers 32 consecutive (node, replica)
 // pairs, so R % RPW == 0 keeps every packed word inside one group of lanes.
 template <int Q, int MODE>
-__global__ void __launch_bounds__(256, 4) k_bmincut_step(BmcArgs a, StepScalars s) {
+__global__ void __launch_bounds__(256, Q >= 7 ? 3 : 4) k_bmincut_step(BmcArgs a, StepScalars s) {
   extern __shared__ unsigned long long smem_u64[];
   const int RQ = a.R * Q;
   unsigned long long* sps = smem_u64;                                // [R*Q] exact mode
@@ -68,7 +68,8 @@ __global__ void __launch_bounds__(256) k_bmincut_derive(const float* __restrict_
                                                         int32_t wpn, const int32_t* __restrict__ nodew,
                                                         uint32_t* __restrict__ words,
                                                         int32_t* __restrict__ cnt,
-                                                        unsigned long long* __restrict__ ps) {
+                                                        unsigned long long* __restrict__ ps,
+                                                        float* __restrict__ d) {
   constexpr int B = QBits<Q>::B, RPW = QBits<Q>::RPW;
   extern __shared__ unsigned long long smem_d[];
   const int RQ = R * Q;
@@ -100,6 +101,11 @@ __global__ void __launch_bounds__(256) k_bmincut_derive(const float* __restrict_
 #pragma unroll
       for (int q = 0; q < Q; ++q)
         atomicAdd(&sps[r * Q + q], __float2ull_rn(P[q] * kPsumScale) * (unsigned long long)Vi);
+      if (d) {  // exact mode: what the neighbours' terms gather at this step
+        float c[Q];
+        centred_q<Q>(x, c);
+        store_q<Q>(d + ((size_t)i * R + r) * Q, c);
+      }
     }
     uint32_t word = act ? ((uint32_t)sn << ((r % RPW) * B)) : 0u;
 #pragma unroll
@@ -256,6 +262,7 @@ fem_status steps_q(Problem* p, const std::vector<StepScalars>& sc, int t_begin, 
   a.m = p->m;
   a.v = p->v;
   const bool exact = p->grad_mode == FEM_GRAD_EXACT;
+  if (exact && (!p->mag[0] || !p->mag[1])) return fail(FEM_ERR_STATE, "exact-mode buffers are not allocated");
   const size_t smem = (size_t)p->R * Q * (exact ? 12 : 4);
   auto kern = exact ? k_bmincut_step<Q, FEM_GRAD_EXACT> : k_bmincut_step<Q, FEM_GRAD_PAPER>;
   if (smem > 48 * 1024) FEM_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
@@ -272,6 +279,8 @@ fem_status steps_q(Problem* p, const std::vector<StepScalars>& sc, int t_begin, 
     a.ps_in = p->psum[t % 3];
     a.ps_out = p->psum[(t + 1) % 3];
     a.ps_zero = p->psum[(t + 2) % 3];
+    a.d_in = exact ? p->mag[t & 1] : nullptr;
+    a.d_out = exact ? p->mag[(t + 1) & 1] : nullptr;
     kern<<<grid, 256, smem, st>>>(a, sc[k]);
   }
   count_launches((int64_t)sc.size());
@@ -283,6 +292,8 @@ fem_status steps_q(Problem* p, const std::vector<StepScalars>& sc, int t_begin, 
 // column sums in buffer t%3; buffer (t+1)%3, which step t accumulates into, is zeroed.
 template <int Q>
 fem_status derive_q(Problem* p, int t, cudaStream_t st) {
+  if (p->grad_mode == FEM_GRAD_EXACT && !p->mag[t & 1])
+    return fail(FEM_ERR_STATE, "exact-mode buffers are not allocated");
   const size_t rq = (size_t)p->R * Q;
   const float* h = p->grad_mode == FEM_GRAD_PAPER ? p->h[0] : p->h[t & 1];
   for (int b : {t % 3, (t + 1) % 3}) {
@@ -294,7 +305,8 @@ fem_status derive_q(Problem* p, int t, cudaStream_t st) {
     FEM_CUDA(cudaFuncSetAttribute(k_bmincut_derive<Q>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   const int grid = resident_grid(k_bmincut_derive<Q>, p->sm_count, (long long)p->n * p->R, smem);
   k_bmincut_derive<Q><<<grid, 256, smem, st>>>(h, p->n, p->R, p->words_per_node, p->nodew, p->words[t & 1],
-                                              p->cnt[t % 3], p->psum[t % 3]);
+                                              p->cnt[t % 3], p->psum[t % 3],
+                                              p->grad_mode == FEM_GRAD_EXACT ? p->mag[t & 1] : nullptr);
   count_launches(1);
   FEM_CUDA(cudaGetLastError());
   return FEM_OK;

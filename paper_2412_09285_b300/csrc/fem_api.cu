@@ -333,9 +333,17 @@ static void drop_step_graphs(Problem* p) {
   p->step_graphs.clear();
 }
 
-static fem_status ensure_state(Problem* p, int32_t R, cudaStream_t s) {
+static fem_status ensure_state(Problem* p, int32_t R, int32_t grad_mode, cudaStream_t s) {
   const size_t per = (size_t)p->n * R * (p->kind == FEM_BMINCUT ? p->q : 1);
-  if (p->R == R && p->h[0]) return FEM_OK;
+  if (p->R == R && p->h[0]) {
+    // bMinCut exact mode gathers its neighbours' centred marginals (first use)
+    if (p->kind == FEM_BMINCUT && grad_mode == FEM_GRAD_EXACT && !p->mag[0])
+      for (int b = 0; b < 2; ++b) {
+        const fem_status st = dev_alloc_t(p, &p->mag[b], per);
+        if (st != FEM_OK) return st;
+      }
+    return FEM_OK;
+  }
   drop_step_graphs(p);  // the graphs name the buffers being replaced
   fem_status st;
   for (int b = 0; b < 2; ++b)
@@ -346,9 +354,13 @@ static fem_status ensure_state(Problem* p, int32_t R, cudaStream_t s) {
                       : (p->kind == FEM_BMINCUT) ? R * bmincut_bits(p->q) / 32 : (R + 31) / 32;
   for (int b = 0; b < 2; ++b)
     if ((st = dev_alloc_t(p, &p->words[b], (size_t)p->n * p->words_per_node)) != FEM_OK) return st;
-  if (p->kind == FEM_MAXCUT)
-    for (int b = 0; b < 2; ++b)
+  if (p->kind == FEM_MAXCUT || (p->kind == FEM_BMINCUT && grad_mode == FEM_GRAD_EXACT)) {
+    for (int b = 0; b < 2; ++b) {
       if ((st = dev_alloc_t(p, &p->mag[b], per)) != FEM_OK) return st;
+    }
+  } else {
+    p->mag[0] = p->mag[1] = nullptr;  // sized for the old R
+  }
   if (p->kind == FEM_BMINCUT) {
     for (int b = 0; b < 3; ++b) {
       if ((st = dev_alloc_t(p, &p->cnt[b], (size_t)R * p->q)) != FEM_OK) return st;
@@ -650,7 +662,7 @@ fem_status fem_anneal(fem_problem_t p, const fem_anneal_params* a, void* stream)
     p->initialised = true;
   } else if (a->t_begin == 0) {
     if (!a->h_init) return fail(FEM_ERR_INVALID_ARG, "h_init is required when t_begin == 0");
-    fem_status st = ensure_state(p, R, s);
+    fem_status st = ensure_state(p, R, a->grad_mode, s);
     if (st != FEM_OK) return st;
     const size_t per = (size_t)p->n * R * (p->kind == FEM_BMINCUT ? p->q : 1);
     FEM_CUDA(cudaMemcpyAsync(p->h[0], a->h_init, per * sizeof(float),

@@ -98,7 +98,9 @@ struct Problem {
   float* m = nullptr;
   float* v = nullptr;
   uint32_t* words[2] = {nullptr, nullptr};
-  float* mag[2] = {nullptr, nullptr};  // sparse MaxCut / QUBO exact mode: m = tanh(h/2), ping-pong
+  // exact mode, what a neighbour term gathers, ping-pong: sparse MaxCut / QUBO m = tanh(h/2)
+  // ([n][R]); bMinCut and colouring q (P(s) - 1/q) ([n][R][q], allocated on first use)
+  float* mag[2] = {nullptr, nullptr};
   int32_t words_per_node = 0;
   void* mt[2] = {nullptr, nullptr};    // dense: discretised marginals for the tensor cores
   int32_t* cnt[3] = {nullptr, nullptr, nullptr};  // bMinCut group counts n_r(s), [R][q], rotating

@@ -219,6 +219,22 @@ def test_resume_and_checkpoint_bit_identical(fem, mode):
     assert np.array_equal(a.fields(), d.fields())
 
 
+def test_gradient_mode_and_replica_count_switches_on_one_problem(fem):
+    """One problem annealed in paper mode, then exact mode (its exact-mode buffers are
+    allocated on first use), then exact mode with more replicas (every buffer
+    reallocated), then paper mode again: each result equals a fresh problem's."""
+    q = 4
+    g = I.rgg(900, 9.0, seed=40)
+    runs = [("paper", 16), ("exact", 16), ("exact", 32), ("paper", 32)]
+    p = fem.Problem("bmincut", graph=g, q=q)
+    for mode, R in runs:
+        h0 = I.initial_fields(900, R, seed=41 + R, q=q)
+        p.anneal(h_init=h0, n_steps=120, grad_mode=mode)
+        fresh = fem.Problem("bmincut", graph=g, q=q).anneal(h_init=h0, n_steps=120, grad_mode=mode)
+        assert np.array_equal(p.fields(), fresh.fields()), (mode, R)
+        assert np.array_equal(p.best()["energy_i64"], fresh.best()["energy_i64"]), (mode, R)
+
+
 def test_bmincut_reaches_bruteforce_optimum(fem):
     g = I.rgg(9, 4.0, seed=45)
     q, lam = 3, 1.0

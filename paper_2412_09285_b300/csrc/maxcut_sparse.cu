@@ -37,10 +37,13 @@ struct MaxcutArgs {
   const float* offset;  // exact mode: per-node constant of the field (QUBO), NULL for MaxCut
 };
 
-// One warp per (node, block of 32 replicas); lane = replica.  Neighbour column
-// indices are loaded 32 at a time (one coalesced load), each lane gathers the
-// sign word of "its" neighbour, and the words are then broadcast by shuffles.
-template <int MODE, int OPT, bool UNIT>
+// Exact-mode step: one warp per (node, block of 32 replicas); lane = replica.
+// Neighbour column indices are loaded 32 at a time (one coalesced load) and
+// broadcast by shuffles; each lane gathers its replica's m_j of every neighbour (a
+// 128-byte line per neighbour and warp).  The kernel is bound by those gathers,
+// most of which miss L2 at n = 2^20 (m is 128 MiB); grouping nodes per warp,
+// eviction hints and replica blocking were all slower.
+template <int OPT, bool UNIT>
 __global__ void __launch_bounds__(256) k_maxcut_step(MaxcutArgs a, StepScalars s) {
   const int lane = threadIdx.x & 31;
   const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
@@ -54,65 +57,36 @@ __global__ void __launch_bounds__(256) k_maxcut_step(MaxcutArgs a, StepScalars s
     float mi = a.m[idx];
     float vi = (OPT == FEM_OPT_SGD) ? 0.f : a.v[idx];
     const int beg = a.row_ptr[i], end = a.row_ptr[i + 1];
-    float field;
-    if (MODE == FEM_GRAD_PAPER) {
-      int iacc = 0;
-      float facc = 0.f;
-      for (int k0 = beg; k0 < end; k0 += 32) {
-        const int k = k0 + lane;
-        uint32_t c = 0, word = 0;
-        float wk = 0.f;
-        if (k < end) {
-          c = a.col[k];
-          word = a.words_in[(size_t)(c & 0x7fffffffu) * a.wpn + wb];
-          if (!UNIT) wk = a.w[k];
-        }
-        const int cnt = min(32, end - k0);
-        for (int e = 0; e < cnt; ++e) {
-          const uint32_t bit = (__shfl_sync(kFullMask, word, e) >> lane) & 1u;
-          if (UNIT) {
-            const uint32_t ce = __shfl_sync(kFullMask, c, e);
-            iacc += ((ce >> 31) ^ bit) ? -1 : 1;
-          } else {
-            const float wv = __shfl_sync(kFullMask, wk, e);
-            facc += bit ? -wv : wv;
-          }
+    float facc = 0.f;
+    for (int k0 = beg; k0 < end; k0 += 32) {
+      const int k = k0 + lane;
+      uint32_t c = 0;
+      float wk = 0.f;
+      if (k < end) {
+        c = a.col[k];
+        if (!UNIT) wk = a.w[k];
+      }
+      const int cnt = min(32, end - k0);
+      for (int e = 0; e < cnt; ++e) {
+        const uint32_t ce = __shfl_sync(kFullMask, c, e);
+        const float mj = a.mag_in[(size_t)(ce & 0x7fffffffu) * a.R + (size_t)wb * 32 + lane];
+        if (UNIT) {
+          facc += (ce >> 31) ? -mj : mj;
+        } else {
+          facc = fmaf(__shfl_sync(kFullMask, wk, e), mj, facc);
         }
       }
-      const float cn = UNIT ? (end > beg ? 1.f / (float)(end - beg) : 0.f) : a.cnorm[i];
-      field = cn * (UNIT ? (float)iacc : facc);
-    } else {
-      float facc = 0.f;
-      for (int k0 = beg; k0 < end; k0 += 32) {
-        const int k = k0 + lane;
-        uint32_t c = 0;
-        float wk = 0.f;
-        if (k < end) {
-          c = a.col[k];
-          if (!UNIT) wk = a.w[k];
-        }
-        const int cnt = min(32, end - k0);
-        for (int e = 0; e < cnt; ++e) {
-          const uint32_t ce = __shfl_sync(kFullMask, c, e);
-          const float mj = a.mag_in[(size_t)(ce & 0x7fffffffu) * a.R + (size_t)wb * 32 + lane];
-          if (UNIT) {
-            facc += (ce >> 31) ? -mj : mj;
-          } else {
-            facc = fmaf(__shfl_sync(kFullMask, wk, e), mj, facc);
-          }
-        }
-      }
-      // MaxCut: 2 sum_j W_ij m_j.  QUBO: with p = (1 + m)/2, 2 sum_j Q_ij p_j + d_i =
-      // sum_j Q_ij m_j + (sum_j Q_ij + d_i)
-      field = a.ccoef * facc;
-      if (a.offset) field += a.offset[i];
     }
+    // MaxCut: 2 sum_j W_ij m_j.  QUBO: with p = (1 + m)/2, 2 sum_j Q_ij p_j + d_i =
+    // sum_j Q_ij m_j + (sum_j Q_ij + d_i)
+    float field = a.ccoef * facc;
+    if (a.offset) field += a.offset[i];
     const float g = s.gq * (field + hi * s.inv_beta) * one_minus_m2(hi);
     opt_update<OPT>(hi, mi, vi, g, s);
     a.h_out[idx] = hi;
     a.m[idx] = mi;
     if (OPT != FEM_OPT_SGD) a.v[idx] = vi;
-    if (MODE == FEM_GRAD_EXACT) a.mag_out[idx] = tanhf(0.5f * hi);  // gathered by the next step
+    a.mag_out[idx] = tanhf(0.5f * hi);  // gathered by the next step
     const uint32_t ball = __ballot_sync(kFullMask, hi < 0.f);
     if (lane == 0) a.words_out[(size_t)i * a.wpn + wb] = ball;
   }
@@ -457,7 +431,7 @@ void launch_step(const MaxcutArgs& a, const StepScalars& s, int sm_count, long l
       k<<<resident_grid<k>(sm_count, warps), 256, 0, st>>>(a, s);
     }
   } else {
-    constexpr auto k = k_maxcut_step<FEM_GRAD_EXACT, OPT, UNIT>;
+    constexpr auto k = k_maxcut_step<OPT, UNIT>;
     k<<<resident_grid<k>(sm_count, per_node), 256, 0, st>>>(a, s);
   }
 }

@@ -225,7 +225,13 @@ fem_status fem_create_problem(const fem_problem_desc* desc, void* stream, fem_pr
 
 /* Run anneal steps [t_begin, t_end) of FEM (Results "Free-Energy Machine"): per step,
  * beta(t) (and lambda(t)), the coupling contraction, the gradient of F with respect
- * to the fields, and one optimizer step on all R replicas.  Asynchronous. */
+ * to the fields, and one optimizer step on all R replicas.  Asynchronous.  A fresh
+ * start (t_begin == 0) allocates the replica state on first use and whenever R
+ * changes: fields, optimizer moments and derived buffers, about 16-24 bytes per
+ * field and replica (q fields per node for bMinCut; an exact-mode bMinCut anneal
+ * adds two more fp32 copies of the field array).  Returns FEM_ERR_OOM if an
+ * allocation fails, FEM_ERR_STATE for a resume whose t_begin, R, n_steps, gradient
+ * mode or optimizer differ from the run being resumed. */
 fem_status fem_anneal(fem_problem_t p, const fem_anneal_params* prm, void* stream);
 
 /* Read out (Results, argmax and argmin equations): each replica's state is the

@@ -97,14 +97,22 @@ __device__ __forceinline__ int argmax_q(const float (&h)[Q]) {
   return best;
 }
 
+// A node-replica's q fields are contiguous ([n][R][q]), so q = 8 and q = 4 start on
+// 16-byte boundaries and q = 6 and q = 2 on 8-byte ones.
 template <int Q>
 __device__ __forceinline__ void load_q(const float* p, float (&x)[Q]) {
-  if (Q == 4) {
-    const float4 t = *reinterpret_cast<const float4*>(p);
-    x[0] = t.x; x[1] = t.y; x[2] = t.z; x[3] = t.w;
-  } else if (Q == 2) {
-    const float2 t = *reinterpret_cast<const float2*>(p);
-    x[0] = t.x; x[1] = t.y;
+  if constexpr (Q % 4 == 0) {
+#pragma unroll
+    for (int s = 0; s < Q; s += 4) {
+      const float4 t = *reinterpret_cast<const float4*>(p + s);
+      x[s] = t.x; x[s + 1] = t.y; x[s + 2] = t.z; x[s + 3] = t.w;
+    }
+  } else if constexpr (Q % 2 == 0) {
+#pragma unroll
+    for (int s = 0; s < Q; s += 2) {
+      const float2 t = *reinterpret_cast<const float2*>(p + s);
+      x[s] = t.x; x[s + 1] = t.y;
+    }
   } else {
 #pragma unroll
     for (int s = 0; s < Q; ++s) x[s] = p[s];
@@ -113,10 +121,13 @@ __device__ __forceinline__ void load_q(const float* p, float (&x)[Q]) {
 
 template <int Q>
 __device__ __forceinline__ void store_q(float* p, const float (&x)[Q]) {
-  if (Q == 4) {
-    *reinterpret_cast<float4*>(p) = make_float4(x[0], x[1], x[2], x[3]);
-  } else if (Q == 2) {
-    *reinterpret_cast<float2*>(p) = make_float2(x[0], x[1]);
+  if constexpr (Q % 4 == 0) {
+#pragma unroll
+    for (int s = 0; s < Q; s += 4)
+      *reinterpret_cast<float4*>(p + s) = make_float4(x[s], x[s + 1], x[s + 2], x[s + 3]);
+  } else if constexpr (Q % 2 == 0) {
+#pragma unroll
+    for (int s = 0; s < Q; s += 2) *reinterpret_cast<float2*>(p + s) = make_float2(x[s], x[s + 1]);
   } else {
 #pragma unroll
     for (int s = 0; s < Q; ++s) p[s] = x[s];
@@ -152,6 +163,9 @@ __device__ __forceinline__ void bmincut_element(const BmcArgs& a, const StepScal
     // words at once, a warp bit-transpose turns them into bit planes, and popcounts
     // give the per-state counts (warp-uniform condition; every lane takes part).
     const bool planes = MODE == FEM_GRAD_PAPER && B <= 2 && !a.w && a.R * B == 32;
+    // q = 5..8 (4 bits per replica) with R = 16: two packed words per node, one bit-plane
+    // pass per word
+    const bool planes4 = MODE == FEM_GRAD_PAPER && B == 4 && !a.w && a.R == 16;
     if (act) {
       load_q<Q>(a.h_in + idx, h);
       load_q<Q>(a.m + idx, mm);
@@ -191,6 +205,39 @@ __device__ __forceinline__ void bmincut_element(const BmcArgs& a, const StepScal
       }
 #pragma unroll
       for (int q = 0; q < Q; ++q) acc[q] = (float)c[q < 4 ? q : 0];
+    } else if (MODE == FEM_GRAD_PAPER && B == 4 && planes4) {
+      // Lanes 0-15 and 16-31 are two nodes; lane sub holds replica sub, whose state sits
+      // in bits 4(sub % 8) .. of word sub / 8.  Each pass loads one word of up to 16
+      // neighbours per node, transposes, and the lanes whose replicas live in that word
+      // count their neighbours per state from three bit planes (states < 8).
+      const int deg = end - beg, sub = lane & 15;
+      const int maxdeg = max(deg, __shfl_xor_sync(kFullMask, deg, 16));
+      const int myw = sub >> 3, base = (sub & 7) * 4;
+      uint32_t c8[Q];
+#pragma unroll
+      for (int q = 0; q < Q; ++q) c8[q] = 0u;
+      for (int k0 = 0; k0 < maxdeg; k0 += 16) {
+        const int kk = k0 + sub;
+        const bool have = kk < deg;
+        const uint32_t j = have ? (a.col[beg + kk] & 0x7fffffffu) : 0u;
+        const int nv = min(max(deg - k0, 0), 16);
+        const uint32_t vm = (nv >= 16 ? 0xffffu : ((1u << nv) - 1u)) << (lane & 16);
+#pragma unroll
+        for (int w = 0; w < 2; ++w) {
+          const uint32_t word = have ? a.words_in[(size_t)j * 2 + w] : 0u;
+          const uint32_t t = warp_transpose32(word, lane);  // lane b: bit e = bit b of lane e's word
+          const uint32_t p0 = __shfl_sync(kFullMask, t, base);
+          const uint32_t p1 = __shfl_sync(kFullMask, t, base + 1);
+          const uint32_t p2 = __shfl_sync(kFullMask, t, base + 2);
+          if (myw == w) {
+#pragma unroll
+            for (int q = 0; q < Q; ++q)
+              c8[q] += __popc(((q & 1) ? p0 : ~p0) & ((q & 2) ? p1 : ~p1) & ((q & 4) ? p2 : ~p2) & vm);
+          }
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < Q; ++q) acc[q] = (float)c8[q];
     } else if (act) {
       if (MODE == FEM_GRAD_PAPER) {
         if (!a.w && end - beg < (Q <= 4 ? 65536 : 256)) {

@@ -92,7 +92,7 @@ def _agree(got, ref, checkpoints):
     return a
 
 
-@pytest.mark.parametrize("q", [4, 2, 3])
+@pytest.mark.parametrize("q", [4, 2, 3, 5, 6, 8])
 def test_exact_mode_marginals_first_50_steps(fem, q):
     g = I.rgg(1000, 10.0, seed=21)
     R = 32 if q == 2 else 16
@@ -112,6 +112,27 @@ def test_paper_mode_marginals_first_50_steps(fem, q, lam):
     assert agree.sum() >= R - 2, agree.sum()
     for t in CHECK:
         _check(got[t], ref[t], cd[t], (q, t), agree)
+
+
+@pytest.mark.parametrize("q", [5, 6, 8])
+def test_paper_mode_two_word_states(fem, q):
+    """q = 5..8 at R = 16: four bits per replica, two packed words per node, neighbour
+    counts from the bit planes of each word; q = 6 and 8 move their fields as float2 /
+    float4.  Marginals against the oracle over 50 steps, then int64 energies of the
+    GPU's own states after an anneal."""
+    g = I.rgg(1200, 10.0, seed=25)
+    R = 16
+    h0 = I.initial_fields(1200, R, seed=26, q=q)
+    _, got, ref, cd = _traces(fem, g, h0, q, CHECK, 1000, "paper", lr=0.1, lambda_max=0.2)
+    agree = _agree(got, ref, CHECK)
+    assert agree.sum() >= R - 2, agree.sum()
+    for t in CHECK:
+        _check(got[t], ref[t], cd[t], (q, t), agree)
+    P = fem.Problem("bmincut", graph=g, q=q).anneal(h_init=h0, n_steps=300, lambda_max=1.0)
+    st = P.states()
+    assert np.array_equal(st, np.argmax(P.fields(), axis=2))
+    E, _, _ = O.bmincut_objective(g.ei, g.ej, g.w, st, q, 1.0)
+    assert np.array_equal(P.best()["energy_i64"], E)
 
 
 def _opt_state(opt):

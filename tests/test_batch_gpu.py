@@ -1,4 +1,4 @@
-"""Batched anneal (bMinCut + Max-k-SAT members in one launch per step, CUDA-graph
+"""Batched anneal (bMinCut + Max-k-SAT members, two launches per step, CUDA-graph
 step loop, autotuned work items) against the same members annealed one by one.
 
 Every member's arithmetic is the single-problem kernel's and the shared counts are
@@ -33,21 +33,21 @@ def _members(fem, seed):
     return graphs, sats
 
 
-def _make(fem, graphs, sats):
-    return ([fem.Problem("bmincut", graph=g, q=4) for g in graphs]
+def _make(fem, graphs, sats, q=4):
+    return ([fem.Problem("bmincut", graph=g, q=q) for g in graphs]
             + [fem.Problem("sat", clauses=c) for c in sats])
 
 
-@pytest.mark.parametrize("mode", ["paper", "exact"])
-def test_batch_bit_identical_to_members_alone(fem, mode):
+@pytest.mark.parametrize("mode,q", [("paper", 4), ("exact", 4), ("paper", 8), ("exact", 8)])
+def test_batch_bit_identical_to_members_alone(fem, mode, q):
     graphs, sats = _members(fem, 100)
     R = 16
-    h0 = ([I.initial_fields(g.n, R, seed=200 + k, q=4) for k, g in enumerate(graphs)]
+    h0 = ([I.initial_fields(g.n, R, seed=200 + k, q=q) for k, g in enumerate(graphs)]
           + [I.initial_fields(c.n, R, seed=300 + k) for k, c in enumerate(sats)])
-    solo = _make(fem, graphs, sats)
+    solo = _make(fem, graphs, sats, q)
     for p, h in zip(solo, h0):
         p.anneal(h_init=h, n_steps=300, grad_mode=mode)
-    probs = _make(fem, graphs, sats)
+    probs = _make(fem, graphs, sats, q)
     b = fem.Batch(probs)
     b.anneal(h_inits=h0, replicas=R, n_steps=300, grad_mode=mode)
     for a, s in zip(probs, solo):
@@ -56,7 +56,7 @@ def test_batch_bit_identical_to_members_alone(fem, mode):
         assert np.array_equal(ra["energy_i64"], rs["energy_i64"]) and ra["best_replica"] == rs["best_replica"]
     # and the batched read-out is the oracle's objective for the batched states
     for a, g in zip(probs[:len(graphs)], graphs):
-        E, _, _ = O.bmincut_objective(g.ei, g.ej, g.w, a.states(), 4, 1.0)
+        E, _, _ = O.bmincut_objective(g.ei, g.ej, g.w, a.states(), q, 1.0)
         assert np.array_equal(a.best()["energy_i64"], E)
     for a, c in zip(probs[len(graphs):], sats):
         assert np.array_equal(a.best()["energy_i64"], O.sat_unsat(c.ptr, c.lits, a.states().astype(np.int8)))

@@ -260,7 +260,8 @@ KERNEL_SOURCES = {
 }
 # the committed ncu summary of each single-problem workload whose traffic is reported
 _SINGLE_PROFILES = {"bmincut": ("bmincut_step_rgg1M_q4_R16.md", "bmincut"), "sat": ("sat_step_3sat1M_R16.md", "sat"),
-                    "pspin": ("pspin_step_3spin1M_R16.md", "sat")}
+                    "pspin": ("pspin_step_3spin1M_R16.md", "sat"),
+                    "qubo": ("maxcut_step_exact_n1M_R32.md", "sparse", "qubo_traffic_bytes_per_launch")}
 
 
 def source_sha256(kind):
@@ -273,7 +274,7 @@ def source_sha256(kind):
     return h.hexdigest()
 
 
-def _traffic_from_profile(name, kind):
+def _traffic_from_profile(name, kind, key="traffic_bytes_per_launch"):
     """DRAM bytes per launch from a committed ncu summary, if the kernel's sources are
     unchanged since the capture (else None)."""
     try:
@@ -281,7 +282,7 @@ def _traffic_from_profile(name, kind):
     except OSError:
         return None
     m1 = re.search(r"source_sha256:\s*([0-9a-f]{64})", txt)
-    m2 = re.search(r"traffic_bytes_per_launch:\s*([0-9]+)", txt)
+    m2 = re.search(r"(?m)^" + key + r":\s*([0-9]+)", txt)
     if not (m1 and m2):
         return None
     return int(m2.group(1)) if source_sha256(kind) == m1.group(1) else None
@@ -361,7 +362,9 @@ def _roofline(wl, inst, step_ms, precision, dense_launch=None, grad_mode="paper"
         alg = sb * n * R + 8 * n * R + 4 * nnz + 4 * (n + 1) + 4 * n * (R // 32)
         ach = alg / (step_ms / 1e3) / 1e9
         return {"bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                "frac": ach / peaks["hbm_gbs"], "traffic": None,
+                "frac": ach / peaks["hbm_gbs"],
+                "traffic": (_traffic_from_profile("maxcut_step_exact_n1M_R32.md", "sparse")
+                            if wl is WORKLOADS["sparse"] and opt == "adam" else None),
                 "kernel": f"k_maxcut_step<exact, {opt}, unit>", "algorithmic_bytes_per_launch": alg,
                 "launch_ms": step_ms, "peak_source": f"{src} hbm_gbs (copy), of {src}",
                 "frac_of_8TBs": ach / 8000.0}

@@ -227,7 +227,8 @@ fem_status fem_create_problem(const fem_problem_desc* desc, void* stream, fem_pr
  * beta(t) (and lambda(t)), the coupling contraction, the gradient of F with respect
  * to the fields, and one optimizer step on all R replicas.  Asynchronous.  A fresh
  * start (t_begin == 0) allocates the replica state on first use and whenever R
- * changes: fields, optimizer moments and derived buffers, about 16-24 bytes per
+ * changes (the buffers of the previous R are freed first, which waits for the
+ * device): fields, optimizer moments and derived buffers, about 16-24 bytes per
  * field and replica (q fields per node for bMinCut; an exact-mode bMinCut anneal
  * adds two more fp32 copies of the field array).  Returns FEM_ERR_OOM if an
  * allocation fails, FEM_ERR_STATE for a resume whose t_begin, R, n_steps, gradient

@@ -345,6 +345,34 @@ static fem_status ensure_state(Problem* p, int32_t R, int32_t grad_mode, cudaStr
     return FEM_OK;
   }
   drop_step_graphs(p);  // the graphs name the buffers being replaced
+  // the buffers sized for the previous R are released first (cudaFree waits for the
+  // device, so no queued work still uses them)
+  auto release = [p](auto*& ptr) {
+    if (!ptr) return;
+    cudaFree(ptr);
+    p->allocs.erase(std::remove(p->allocs.begin(), p->allocs.end(), (void*)ptr), p->allocs.end());
+    ptr = nullptr;
+  };
+  for (int b = 0; b < 2; ++b) {
+    release(p->h[b]);
+    release(p->words[b]);
+    release(p->mag[b]);
+    release(p->satP[b]);
+  }
+  release(p->m);
+  release(p->v);
+  for (int b = 0; b < 3; ++b) {
+    release(p->cnt[b]);
+    release(p->psum[b]);
+  }
+  release(p->part_i);
+  release(p->part_f);
+  release(p->part_cnt);
+  release(p->energy_i);
+  release(p->energy_f);
+  release(p->best);
+  release(p->states_dev);
+  p->R = 0;  // no state until every buffer below is in place
   fem_status st;
   for (int b = 0; b < 2; ++b)
     if ((st = dev_alloc_t(p, &p->h[b], per)) != FEM_OK) return st;
@@ -358,8 +386,6 @@ static fem_status ensure_state(Problem* p, int32_t R, int32_t grad_mode, cudaStr
     for (int b = 0; b < 2; ++b) {
       if ((st = dev_alloc_t(p, &p->mag[b], per)) != FEM_OK) return st;
     }
-  } else {
-    p->mag[0] = p->mag[1] = nullptr;  // sized for the old R
   }
   if (p->kind == FEM_BMINCUT) {
     for (int b = 0; b < 3; ++b) {

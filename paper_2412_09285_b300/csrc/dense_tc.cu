@@ -1188,6 +1188,29 @@ fem_status dense_upload(Problem* p, const float* J, cudaStream_t s) {
 // State for R replicas: h, m, v [R][n_pad] and two operand buffers per part.
 fem_status dense_state(Problem* p, int R, int prec) {
   const size_t per = (size_t)R * p->n_pad;
+  // the buffers of the previous replica count or precision are released first
+  // (cudaFree waits for the device, so no queued work still uses them)
+  auto release = [p](auto*& ptr) {
+    if (!ptr) return;
+    cudaFree(ptr);
+    p->allocs.erase(std::remove(p->allocs.begin(), p->allocs.end(), (void*)ptr), p->allocs.end());
+    ptr = nullptr;
+  };
+  for (int b = 0; b < 2; ++b) {
+    release(p->h[b]);
+    release(p->mt[b]);
+    release(p->mt_lo[b]);
+  }
+  release(p->m);
+  release(p->v);
+  release(p->part_i);
+  release(p->part_f);
+  release(p->energy_i);
+  release(p->energy_f);
+  release(p->best);
+  release(p->states_dev);
+  p->dense_R_alloc = 0;  // no state until every buffer below is in place
+  p->R = 0;
   fem_status st;
   for (int b = 0; b < 2; ++b)
     if ((st = dev_alloc_t(p, &p->h[b], per)) != FEM_OK) return st;

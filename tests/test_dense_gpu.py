@@ -239,3 +239,19 @@ def test_persistent_unsupported(fem):
     assert e.value.status == fem.FEM_ERR_UNSUPPORTED
     with pytest.raises(fem.FemError):
         fem.Problem("maxcut", graph=I.er_gnm(50, 100, seed=1)).set_dense_launch("persistent")
+
+
+def test_precision_and_replica_count_switches_on_one_problem(fem):
+    """One dense problem annealed at bf16 with 128 replicas, then fp8 with 256, then
+    bf16 hi+lo exact mode with 128 (each switch frees and reallocates the state):
+    every result equals a fresh problem's bit for bit."""
+    g = I.sk_dense(300, seed=61)
+    runs = [("bf16", 128, "paper"), ("fp8", 256, "paper"), ("bf16x2", 128, "exact")]
+    p = fem.Problem("maxcut", dense=g.dense)
+    for prec, R, mode in runs:
+        h0 = I.initial_fields(300, R, seed=62 + R)
+        p.anneal(h_init=h0, n_steps=100, grad_mode=mode, precision=prec)
+        fresh = fem.Problem("maxcut", dense=g.dense).anneal(h_init=h0, n_steps=100, grad_mode=mode,
+                                                             precision=prec)
+        assert np.array_equal(p.fields(), fresh.fields()), (prec, R)
+        assert np.array_equal(p.best()["energy_i64"], fresh.best()["energy_i64"]), (prec, R)

@@ -88,6 +88,9 @@ WORKLOADS.update({
     "bmincut": dict(_SINGLE, kind="single", problem="bmincut", graph="rgg", deg=10.0, q=4, R=16, graph_seed=41,
                     h_seed=42, name=f"balanced 4-way MinCut: random geometric graph n=2^20, mean degree 10, unit "
                                     f"weights, lambda_max=1, R=16, {_SCHED}, paper-mode gradient"),
+    "bmincut_q8": dict(_SINGLE, kind="single", problem="bmincut", graph="rgg", deg=10.0, q=8, R=16, graph_seed=41,
+                       h_seed=42, name=f"balanced 8-way MinCut: random geometric graph n=2^20, mean degree 10, unit "
+                                       f"weights, lambda_max=1, R=16, {_SCHED}, paper-mode gradient"),
     "bmincut_weighted": dict(_SINGLE, kind="single", problem="bmincut", graph="rgg", deg=10.0, q=4, R=16,
                              node_weights=(1, 4), graph_seed=41, h_seed=42,
                              name=f"node-weighted balanced 4-way MinCut: random geometric graph n=2^20, mean degree "

@@ -84,6 +84,21 @@ __device__ __forceinline__ bool sat_k3_shape(const SatArgs& a) {
 __device__ __forceinline__ float4 ld_f4(const float* p) { return *reinterpret_cast<const float4*>(p); }
 __device__ __forceinline__ void st_f4(float* p, const float4& x) { *reinterpret_cast<float4*>(p) = x; }
 
+// The streaming state (h, m, v: read once and written once per step) with the
+// evict-first cache hint when STREAM, so that it displaces less of the gathered mean
+// spins in L2; measured faster for the 3-spin step and slower for Max-3-SAT, which
+// keeps plain accesses.
+template <bool STREAM>
+__device__ __forceinline__ float4 ld_state(const float* p) {
+  if constexpr (STREAM) return __ldcs(reinterpret_cast<const float4*>(p));
+  else return ld_f4(p);
+}
+template <bool STREAM>
+__device__ __forceinline__ void st_state(float* p, const float4& x) {
+  if constexpr (STREAM) __stcs(reinterpret_cast<float4*>(p), x);
+  else st_f4(p, x);
+}
+
 template <bool PSPIN>
 __device__ __forceinline__ float sat_factor(int lit, float p) {
   if (PSPIN) return p;
@@ -95,8 +110,8 @@ __device__ __forceinline__ void sat_element_k3(const SatArgs& a, const StepScala
   int i, r;
   split_element(e, a.R, i, r);
   const bool sgd = a.opt == FEM_OPT_SGD;
-  float4 h = ld_f4(a.h + e), m = ld_f4(a.m + e);
-  float4 v = sgd ? make_float4(0.f, 0.f, 0.f, 0.f) : ld_f4(a.v + e);
+  float4 h = ld_state<PSPIN>(a.h + e), m = ld_state<PSPIN>(a.m + e);
+  float4 v = sgd ? make_float4(0.f, 0.f, 0.f, 0.f) : ld_state<PSPIN>(a.v + e);
   const int ob = a.occ_ptr[i], oe = a.occ_ptr[i + 1];
   const float* P = a.P_in + r;
   float G0 = 0.f, G1 = 0.f, G2 = 0.f, G3 = 0.f;
@@ -145,9 +160,9 @@ __device__ __forceinline__ void sat_element_k3(const SatArgs& a, const StepScala
     vv[c] = vi;
     pv[c] = PSPIN ? tanhf(0.5f * hi) : sigmoidf_fast(hi);
   }
-  st_f4(a.h + e, h);
-  st_f4(a.m + e, m);
-  if (!sgd) st_f4(a.v + e, v);
+  st_state<PSPIN>(a.h + e, h);
+  st_state<PSPIN>(a.m + e, m);
+  if (!sgd) st_state<PSPIN>(a.v + e, v);
   st_f4(a.P_out + e, pout);
 }
 

@@ -10,16 +10,14 @@ import numpy as np
 import pytest
 
 import oracle as O
+import parity
 from paper_2412_09285_b300 import instances as I
 
 pytestmark = pytest.mark.gpu
 
-TOL_P = 1e-4
-# An Adam step moves by lr * (gradient rounding error) / D, D = sqrt(v) + eps.  The kernel
-# evaluates every difference of the centred gradient without cancellation (integer counts,
-# fixed-point column sums, expm1 deviations), so the error is ~1e-9 and D >= 1e-6 suffices.
-D_COND = {"exact": 1e-6, "paper": 1e-6}
-MAX_ILL = 5e-3
+# The kernel evaluates every difference of the centred gradient without cancellation
+# (integer counts, fixed-point column sums, expm1 deviations), so its gradient error is
+# ~1e-9; conditioning and the one-step check of excluded elements: tests/parity.py.
 CHECK = [1, 2, 5, 10, 20, 35, 50]
 
 
@@ -34,26 +32,9 @@ def fem():
     return F
 
 
-def _softmax(h):
-    z = h - h.max(axis=-1, keepdims=True)
-    e = np.exp(z)
-    return e / e.sum(axis=-1, keepdims=True)
-
-
-def _check(got, ref, cond, where, agree=None, mode="paper"):
-    P_got = _softmax(got.astype(np.float64))
-    P_ref = _softmax(ref)
-    pool = np.ones(got.shape, bool) if agree is None else np.broadcast_to(agree[None, :, None], got.shape)
-    # an element is well-conditioned when all q denominators of its (node, replica) are
-    okr = (cond >= D_COND[mode]).all(axis=-1, keepdims=True)
-    ok = pool & np.broadcast_to(okr, got.shape)
-    ill = pool & ~ok
-    assert ill.sum() <= MAX_ILL * max(1, pool.sum()), (where, "ill share", ill.mean())
-    err = np.abs(P_got - P_ref)
-    if ok.any():
-        assert err[ok].max() <= TOL_P, (where, float(err[ok].max()))
-    if ill.any():
-        assert err[ill].max() <= 0.05, (where, "ill", float(err[ill].max()))
+def _check(got, ref, cond, where, agree=None, mode="paper", forced=None, prev=None, prev_state=None):
+    return parity.compare(got, ref, cond, where, marg=parity.softmax, agree=agree, forced=forced,
+                          prev=prev, prev_state=prev_state)
 
 
 def _okw(kw):
@@ -67,22 +48,27 @@ def _sched(kw):
                 lambda_max=kw.get("lambda_max", 1.0))
 
 
-def _traces(fem, g, h0, q, checkpoints, n_steps, mode, V=None, **kw):
+def _problem(g, V=None):
     W = O.coupling_matrix(g.n, g.ei, g.ej, g.w)
+    return ("bmincut", W) if V is None else ("bmincut", W, V)
+
+
+def _forced(P, g, n_steps, mode, V=None, **kw):
+    """One step on both sides from a given fp32 state (parity.one_step)."""
+    run = {k: v for k, v in kw.items() if k != "optimizer"}
+    return parity.one_step(P, _problem(g, V), n_steps, optimizer=kw.get("optimizer", "adam"),
+                           opt_kw=_okw(kw), mode=mode, sched=_sched(kw), grad_mode=mode, **run)
+
+
+def _traces(fem, g, h0, q, checkpoints, n_steps, mode, V=None, **kw):
     P = fem.Problem("bmincut", graph=g, q=q, node_weight=V)
-    got, t = {}, 0
-    for T in checkpoints:
-        P.anneal(h_init=h0 if t == 0 else None, replicas=h0.shape[1], n_steps=n_steps, t_begin=t,
-                 t_end=T, grad_mode=mode, **kw)
-        got[T] = P.fields()
-        t = T
+    got, st = parity.gpu_windows(P, h0, checkpoints, n_steps, grad_mode=mode, **kw)
     tr = {t: None for t in checkpoints}
     cd = {t: None for t in checkpoints}
-    O.anneal(("bmincut", W) if V is None else ("bmincut", W, V), h0.astype(np.float64), n_steps,
-             t_end=max(checkpoints),
+    O.anneal(_problem(g, V), h0.astype(np.float64), n_steps, t_end=max(checkpoints),
              optimizer=kw.get("optimizer", "adam"), opt_kw=_okw(kw), mode=mode, trace=tr, cond=cd,
              **_sched(kw))
-    return P, got, tr, cd
+    return P, got, tr, cd, st
 
 
 def _agree(got, ref, checkpoints):
@@ -97,9 +83,9 @@ def test_exact_mode_marginals_first_50_steps(fem, q):
     g = I.rgg(1000, 10.0, seed=21)
     R = 32 if q == 2 else 16
     h0 = I.initial_fields(1000, R, seed=22, q=q)
-    _, got, ref, cd = _traces(fem, g, h0, q, CHECK, 1000, "exact", lr=0.1)
-    for t in CHECK:
-        _check(got[t], ref[t], cd[t], (q, t), mode="exact")
+    P, got, ref, cd, st = _traces(fem, g, h0, q, CHECK, 1000, "exact", lr=0.1)
+    parity.compare_trajectory(got, ref, cd, CHECK, q, marg=parity.softmax, state=st,
+                              forced=_forced(P, g, 1000, "exact", lr=0.1))
 
 
 @pytest.mark.parametrize("q,lam", [(4, 1.0), (4, 0.05), (8, 0.2)])
@@ -107,11 +93,11 @@ def test_paper_mode_marginals_first_50_steps(fem, q, lam):
     g = I.rgg(1200, 10.0, seed=23)
     R = 16 if q <= 4 else 32
     h0 = I.initial_fields(1200, R, seed=24, q=q)
-    _, got, ref, cd = _traces(fem, g, h0, q, CHECK, 1000, "paper", lr=0.1, lambda_max=lam)
+    P, got, ref, cd, st = _traces(fem, g, h0, q, CHECK, 1000, "paper", lr=0.1, lambda_max=lam)
     agree = _agree(got, ref, CHECK)
     assert agree.sum() >= R - 2, agree.sum()
-    for t in CHECK:
-        _check(got[t], ref[t], cd[t], (q, t), agree)
+    parity.compare_trajectory(got, ref, cd, CHECK, (q, lam), marg=parity.softmax, agree=agree, state=st,
+                              forced=_forced(P, g, 1000, "paper", lr=0.1, lambda_max=lam))
 
 
 @pytest.mark.parametrize("q", [5, 6, 8])
@@ -123,33 +109,16 @@ def test_paper_mode_two_word_states(fem, q):
     g = I.rgg(1200, 10.0, seed=25)
     R = 16
     h0 = I.initial_fields(1200, R, seed=26, q=q)
-    _, got, ref, cd = _traces(fem, g, h0, q, CHECK, 1000, "paper", lr=0.1, lambda_max=0.2)
+    P, got, ref, cd, st = _traces(fem, g, h0, q, CHECK, 1000, "paper", lr=0.1, lambda_max=0.2)
     agree = _agree(got, ref, CHECK)
     assert agree.sum() >= R - 2, agree.sum()
-    for t in CHECK:
-        _check(got[t], ref[t], cd[t], (q, t), agree)
+    parity.compare_trajectory(got, ref, cd, CHECK, q, marg=parity.softmax, agree=agree, state=st,
+                              forced=_forced(P, g, 1000, "paper", lr=0.1, lambda_max=0.2))
     P = fem.Problem("bmincut", graph=g, q=q).anneal(h_init=h0, n_steps=300, lambda_max=1.0)
     st = P.states()
     assert np.array_equal(st, np.argmax(P.fields(), axis=2))
     E, _, _ = O.bmincut_objective(g.ei, g.ej, g.w, st, q, 1.0)
     assert np.array_equal(P.best()["energy_i64"], E)
-
-
-def _opt_state(opt):
-    if isinstance(opt, O.Adam):
-        return opt.m, opt.v
-    if isinstance(opt, O.RMSprop):
-        return opt.buf, opt.v
-    return opt.buf, np.zeros_like(opt.buf)
-
-
-def _set_opt_state(opt, m, v):
-    if isinstance(opt, O.Adam):
-        opt.m, opt.v = m, v
-    elif isinstance(opt, O.RMSprop):
-        opt.buf, opt.v = m, v
-    else:
-        opt.buf = m
 
 
 @pytest.mark.parametrize("mode", ["exact", "paper"])
@@ -174,10 +143,10 @@ def test_teacher_forced_windows(fem, opt, kw, mode):
         if t0 > t:
             h, o = O.anneal(("bmincut", W), h, n_steps, t_begin=t, t_end=t0, optimizer=opt, opt=o,
                             mode=mode, **_sched(kw))
-        m, v = _opt_state(o)
+        m, v = parity.opt_state(o)
         h32, m32, v32 = (x.astype(np.float32) for x in (h, m, v))
         h = h32.astype(np.float64)
-        _set_opt_state(o, m32.astype(np.float64), v32.astype(np.float64))
+        parity.set_opt_state(o, m32.astype(np.float64), v32.astype(np.float64))
         cd = {t0 + 3: None}
         h, o = O.anneal(("bmincut", W), h, n_steps, t_begin=t0, t_end=t0 + 3, optimizer=opt, opt=o,
                         mode=mode, cond=cd, **_sched(kw))
@@ -191,7 +160,9 @@ def test_teacher_forced_windows(fem, opt, kw, mode):
         agree = (np.all(np.argmax(got, 2) == np.argmax(h, 2), axis=0) if mode == "paper" else None)
         if agree is not None:
             assert agree.sum() >= 14, (t0, agree.sum())
-        _check(got, h, cd[t0 + 3], (opt, mode, t0), agree, mode=mode)
+        _check(got, h, cd[t0 + 3], (opt, mode, t0), agree, mode=mode,
+               forced=_forced(P, g, n_steps, mode, optimizer=opt, **kw), prev=t0,
+               prev_state=(h32, m32, v32))
         t = t0 + 3
 
 
@@ -289,12 +260,12 @@ def test_weighted_marginals_first_50_steps(fem, mode):
     g = I.rgg(800, 10.0, seed=81)
     V = _node_weights(800, 82)
     h0 = I.initial_fields(800, 16, seed=83, q=4)
-    _, got, ref, cd = _traces(fem, g, h0, 4, CHECK, 1000, mode, V=V, lr=0.1, lambda_max=0.05)
+    P, got, ref, cd, st = _traces(fem, g, h0, 4, CHECK, 1000, mode, V=V, lr=0.1, lambda_max=0.05)
     agree = _agree(got, ref, CHECK) if mode == "paper" else None
     if agree is not None:
         assert agree.sum() >= 12, agree.sum()
-    for t in CHECK:
-        _check(got[t], ref[t], cd[t], (mode, t), agree=agree, mode=mode)
+    parity.compare_trajectory(got, ref, cd, CHECK, mode, marg=parity.softmax, agree=agree, state=st,
+                              forced=_forced(P, g, 1000, mode, V=V, lr=0.1, lambda_max=0.05))
 
 
 def test_weighted_objectives_bit_exact_and_unit_weights_change_nothing(fem):

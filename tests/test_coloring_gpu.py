@@ -7,13 +7,11 @@ import numpy as np
 import pytest
 
 import oracle as O
+import parity
 from paper_2412_09285_b300 import instances as I
 
 pytestmark = pytest.mark.gpu
 
-TOL_P = 1e-4
-D_COND = 1e-6
-MAX_ILL = 5e-3
 CHECK = [1, 2, 5, 10, 20, 35, 50]
 
 
@@ -26,11 +24,6 @@ def fem():
     build.build()
     from paper_2412_09285_b300 import fem as F
     return F
-
-
-def _softmax(h):
-    e = np.exp(h - h.max(axis=-1, keepdims=True))
-    return e / e.sum(axis=-1, keepdims=True)
 
 
 def _planted(n, q, deg, seed):
@@ -52,12 +45,7 @@ def test_coloring_marginals_first_50_steps(fem, mode):
     W = O.coupling_matrix(g.n, g.ei, g.ej, g.w)
     h0 = I.initial_fields(800, 16, seed=102, q=3)
     P = fem.Problem("coloring", graph=g, q=3)
-    got, t = {}, 0
-    for T in CHECK:
-        P.anneal(h_init=h0 if t == 0 else None, replicas=16, n_steps=1000, t_begin=t, t_end=T,
-                 grad_mode=mode, beta_max=20.0)
-        got[T] = P.fields()
-        t = T
+    got, st = parity.gpu_windows(P, h0, CHECK, 1000, grad_mode=mode, beta_max=20.0)
     tr = {t: None for t in CHECK}
     cd = {t: None for t in CHECK}
     O.anneal(("coloring", W), h0.astype(np.float64), 1000, t_end=50, mode=mode, beta_max=20.0, trace=tr, cond=cd)
@@ -66,11 +54,10 @@ def test_coloring_marginals_first_50_steps(fem, mode):
         for T in CHECK:
             agree &= np.all(np.argmax(got[T], axis=2) == np.argmax(tr[T], axis=2), axis=0)
         assert agree.sum() >= 12, agree.sum()
-    for T in CHECK:
-        err = np.abs(_softmax(got[T][:, agree].astype(np.float64)) - _softmax(tr[T][:, agree]))
-        ok = np.broadcast_to((cd[T][:, agree] >= D_COND).all(axis=-1, keepdims=True), err.shape)
-        assert (~ok).mean() <= MAX_ILL
-        assert err[ok].max() <= TOL_P, (mode, T, float(err[ok].max()))
+    forced = parity.one_step(P, ("coloring", W), 1000, mode=mode, sched=dict(beta_max=20.0),
+                             grad_mode=mode, beta_max=20.0)
+    parity.compare_trajectory(got, tr, cd, CHECK, mode, marg=parity.softmax,
+                              agree=agree if mode == "paper" else None, forced=forced, state=st)
 
 
 def test_coloring_violations_bit_exact_and_planted_graph_coloured(fem):

@@ -7,13 +7,11 @@ import numpy as np
 import pytest
 
 import oracle as O
+import parity
 from paper_2412_09285_b300 import instances as I
 
 pytestmark = pytest.mark.gpu
 
-TOL_P = 1e-4
-D_COND = 1e-6
-MAX_ILL = 5e-3
 CHECK = [1, 2, 5, 10, 20, 35, 50]
 
 
@@ -45,19 +43,12 @@ def test_pspin_marginals_first_50_steps(fem):
     cl, ptr, var, J, b = _instance(2000, 6000, 1, 4, seed=121)
     h0 = I.initial_fields(2000, 32, seed=122)
     P = fem.Problem("pspin", clauses=cl, term_weight=J, linear=b)
-    got, t = {}, 0
-    for T in CHECK:
-        P.anneal(h_init=h0 if t == 0 else None, replicas=32, n_steps=1000, t_begin=t, t_end=T)
-        got[T] = P.fields()
-        t = T
+    got, st = parity.gpu_windows(P, h0, CHECK, 1000)
     tr = {t: None for t in CHECK}
     cd = {t: None for t in CHECK}
     O.anneal(("pspin", (ptr, var, J, b)), h0.astype(np.float64), 1000, t_end=50, mode="exact", trace=tr, cond=cd)
-    for T in CHECK:
-        err = np.abs(O.sigmoid(got[T].astype(np.float64)) - O.sigmoid(tr[T]))
-        ok = cd[T] >= D_COND
-        assert (~ok).mean() <= MAX_ILL
-        assert err[ok].max() <= TOL_P, (T, float(err[ok].max()))
+    parity.compare_trajectory(got, tr, cd, CHECK, "pspin", state=st,
+                              forced=parity.one_step(P, ("pspin", (ptr, var, J, b)), 1000))
 
 
 def test_pspin_energies_bit_exact_and_negation_folding(fem):

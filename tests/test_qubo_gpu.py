@@ -5,13 +5,11 @@ import numpy as np
 import pytest
 
 import oracle as O
+import parity
 from paper_2412_09285_b300 import instances as I
 
 pytestmark = pytest.mark.gpu
 
-TOL_P = 1e-4
-D_COND = 1e-6
-MAX_ILL = 5e-3
 CHECK = [1, 2, 5, 10, 20, 35, 50]
 
 
@@ -32,19 +30,12 @@ def test_qubo_marginals_first_50_steps(fem):
     Q = O.coupling_matrix(g.n, g.ei, g.ej, g.w)
     h0 = I.initial_fields(600, 32, seed=113)
     P = fem.Problem("qubo", graph=g, linear=d)
-    got, t = {}, 0
-    for T in CHECK:
-        P.anneal(h_init=h0 if t == 0 else None, replicas=32, n_steps=1000, t_begin=t, t_end=T, grad_mode="exact")
-        got[T] = P.fields()
-        t = T
+    got, st = parity.gpu_windows(P, h0, CHECK, 1000, grad_mode="exact")
     tr = {t: None for t in CHECK}
     cd = {t: None for t in CHECK}
     O.anneal(("qubo", (Q, d)), h0.astype(np.float64), 1000, t_end=50, mode="exact", trace=tr, cond=cd)
-    for T in CHECK:
-        err = np.abs(O.sigmoid(got[T].astype(np.float64)) - O.sigmoid(tr[T]))
-        ok = cd[T] >= D_COND
-        assert (~ok).mean() <= MAX_ILL
-        assert err[ok].max() <= TOL_P, (T, float(err[ok].max()))
+    parity.compare_trajectory(got, tr, cd, CHECK, "qubo", state=st,
+                              forced=parity.one_step(P, ("qubo", (Q, d)), 1000, grad_mode="exact"))
 
 
 def test_mis_qubo_energies_bit_exact(fem):

@@ -8,13 +8,11 @@ import numpy as np
 import pytest
 
 import oracle as O
+import parity
 from paper_2412_09285_b300 import instances as I
 
 pytestmark = pytest.mark.gpu
 
-TOL_P = 1e-4
-D_COND = 1e-6
-MAX_ILL = 5e-3
 CHECK = [1, 2, 5, 10, 20, 35, 50]
 
 
@@ -29,14 +27,15 @@ def fem():
     return F
 
 
-def _check(got, ref, cond, where):
-    err = np.abs(O.sigmoid(got.astype(np.float64)) - O.sigmoid(ref))
-    ok = cond >= D_COND
-    assert (~ok).mean() <= MAX_ILL, (where, "ill share", (~ok).mean())
-    if ok.any():
-        assert err[ok].max() <= TOL_P, (where, float(err[ok].max()))
-    if (~ok).any():
-        assert err[~ok].max() <= 0.05, (where, "ill", float(err[~ok].max()))
+def _check(got, ref, cond, where, forced=None, prev=None, prev_state=None):
+    return parity.compare(got, ref, cond, where, forced=forced, prev=prev, prev_state=prev_state)
+
+
+def _forced(P, groups, n_steps, **kw):
+    """One step on both sides from a given fp32 state (parity.one_step)."""
+    run = {k: v for k, v in kw.items() if k != "optimizer"}
+    return parity.one_step(P, ("sat", groups), n_steps, optimizer=kw.get("optimizer", "adam"),
+                           opt_kw=_okw(kw), sched=_sched(kw), **run)
 
 
 def _okw(kw):
@@ -67,34 +66,12 @@ def test_marginals_first_50_steps(fem, kind):
     groups = O.sat_arrays(cl.ptr, cl.lits)
     h0 = I.initial_fields(cl.n, 16, seed=53)
     P = fem.Problem("sat", clauses=cl)
-    got, t = {}, 0
-    for T in CHECK:
-        P.anneal(h_init=h0 if t == 0 else None, replicas=16, n_steps=1000, t_begin=t, t_end=T)
-        got[T] = P.fields()
-        t = T
+    got, st = parity.gpu_windows(P, h0, CHECK, 1000)
     tr = {t: None for t in CHECK}
     cd = {t: None for t in CHECK}
     O.anneal(("sat", groups), h0.astype(np.float64), 1000, t_end=50, opt_kw=dict(lr=0.1), trace=tr,
              cond=cd)
-    for t in CHECK:
-        _check(got[t], tr[t], cd[t], t)
-
-
-def _opt_state(opt):
-    if isinstance(opt, O.Adam):
-        return opt.m, opt.v
-    if isinstance(opt, O.RMSprop):
-        return opt.buf, opt.v
-    return opt.buf, np.zeros_like(opt.buf)
-
-
-def _set_opt_state(opt, m, v):
-    if isinstance(opt, O.Adam):
-        opt.m, opt.v = m, v
-    elif isinstance(opt, O.RMSprop):
-        opt.buf, opt.v = m, v
-    else:
-        opt.buf = m
+    parity.compare_trajectory(got, tr, cd, CHECK, kind, state=st, forced=_forced(P, groups, 1000, lr=0.1))
 
 
 @pytest.mark.parametrize("opt,kw", [
@@ -117,10 +94,10 @@ def test_teacher_forced_windows(fem, opt, kw):
         if t0 > t:
             h, o = O.anneal(("sat", groups), h, n_steps, t_begin=t, t_end=t0, optimizer=opt, opt=o,
                             **_sched(kw))
-        m, v = _opt_state(o)
+        m, v = parity.opt_state(o)
         h32, m32, v32 = (x.astype(np.float32) for x in (h, m, v))
         h = h32.astype(np.float64)
-        _set_opt_state(o, m32.astype(np.float64), v32.astype(np.float64))
+        parity.set_opt_state(o, m32.astype(np.float64), v32.astype(np.float64))
         cd = {t0 + 3: None}
         h, o = O.anneal(("sat", groups), h, n_steps, t_begin=t0, t_end=t0 + 3, optimizer=opt, opt=o,
                         cond=cd, **_sched(kw))
@@ -129,7 +106,8 @@ def test_teacher_forced_windows(fem, opt, kw):
         else:
             P.set_state(h32, m32, v32, steps_done=t0)
             P.anneal(n_steps=n_steps, t_begin=t0, t_end=t0 + 3, optimizer=opt, replicas=32, **kw)
-        _check(P.fields(), h, cd[t0 + 3], (opt, t0))
+        _check(P.fields(), h, cd[t0 + 3], (opt, t0), forced=_forced(P, groups, n_steps, optimizer=opt, **kw),
+               prev=t0, prev_state=(h32, m32, v32))
         t = t0 + 3
 
 

@@ -24,6 +24,10 @@ constexpr int kNoallocMaxDevices = 64;
 // Partial cuts, [block][replica].  Every call overwrites the rows it reads, so
 // nothing has to be cleared between calls; calls that overlap on the GPU race.
 __device__ __align__(256) int64_t g_noalloc_partials[kNoallocBlocks * kNoallocMaxReplicas];
+// Set by the first kernel when the CSR names a row range or a column outside the
+// graph (the access is skipped); read and cleared by the second kernel, so it is
+// zero again when the next call starts.
+__device__ int32_t g_noalloc_bad;
 
 std::mutex g_noalloc_mutex;
 int64_t* g_noalloc_addr[kNoallocMaxDevices] = {};
@@ -56,16 +60,29 @@ __global__ void __launch_bounds__(256) k_noalloc_cut_partial(const int32_t* __re
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int wb = blockIdx.y;
   int64_t acc = 0;
+  const int nnz = row_ptr[n];
   for (int i = blockIdx.x * 8 + warp; i < n; i += gridDim.x * 8) {
     const uint32_t bi = (words[(size_t)i * wpn + wb] >> lane) & 1u;
-    for (int k0 = row_ptr[i]; k0 < row_ptr[i + 1]; k0 += 32) {
+    const int beg = row_ptr[i], end = row_ptr[i + 1];
+    if (beg < 0 || end < beg || end > nnz) {   // a row outside col[0, row_ptr[n])
+      if (lane == 0) g_noalloc_bad = 1;
+      continue;
+    }
+    for (int k0 = beg; k0 < end; k0 += 32) {
       const int k = k0 + lane;
       uint32_t c = 0, wd = 0;
-      if (k < row_ptr[i + 1]) {
+      bool bad = false;
+      if (k < end) {
         c = col[k];
-        wd = words[(size_t)(c & 0x7fffffffu) * wpn + wb];
+        const uint32_t j = c & 0x7fffffffu;
+        if (j < (uint32_t)n) wd = words[(size_t)j * wpn + wb];
+        else bad = true;
       }
-      const int cnt = min(32, row_ptr[i + 1] - k0);
+      if (__any_sync(kFullMask, bad)) {       // a column outside the graph: skip the row
+        if (lane == 0) g_noalloc_bad = 1;
+        break;
+      }
+      const int cnt = min(32, end - k0);
       for (int e = 0; e < cnt; ++e) {
         const uint32_t ce = __shfl_sync(kFullMask, c, e);
         const uint32_t bj = (__shfl_sync(kFullMask, wd, e) >> lane) & 1u;
@@ -83,7 +100,7 @@ __global__ void __launch_bounds__(256) k_noalloc_cut_partial(const int32_t* __re
 }
 
 // E_r = -cut_r summed over the partial rows in order, then the argmin over
-// replicas (lowest index on ties).
+// replicas (lowest index on ties); best = -1 when the CSR was malformed.
 __global__ void __launch_bounds__(1024) k_noalloc_finish(const int64_t* __restrict__ part, int32_t nblk,
                                                          int32_t R, int64_t* __restrict__ energy,
                                                          int32_t* __restrict__ best) {
@@ -114,7 +131,10 @@ __global__ void __launch_bounds__(1024) k_noalloc_finish(const int64_t* __restri
     }
     __syncthreads();
   }
-  if (threadIdx.x == 0) best[0] = si[0];
+  if (threadIdx.x == 0) {
+    best[0] = g_noalloc_bad ? -1 : si[0];
+    g_noalloc_bad = 0;
+  }
 }
 
 }  // namespace

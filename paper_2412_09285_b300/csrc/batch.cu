@@ -211,7 +211,7 @@ struct Batch {
   BatchItem* d_items = nullptr;  // the q-state members' items, then the clause-shaped ones
   int n_bmc = 0, n_sat = 0, nodes_per_item = 0, max_rq = 0;
   bool ready = false;
-  std::vector<const void*> sig;  // member state pointers the descriptors were built from
+  std::vector<uint64_t> sig;     // members' allocation generations the descriptors were built from
   cudaStream_t capture_stream = nullptr;
   // captured step loops, keyed by (first step, item size, the steps' scalars)
   struct Graph {
@@ -429,15 +429,11 @@ fem_status fem_batch_anneal(fem_batch_t b, const fem_anneal_params* a, const flo
   }
   if (a->t_end == a->t_begin) return FEM_OK;
   const int R = a->replicas;
-  // the descriptors hold member state pointers: rebuild them when any has changed
-  // (a fresh start may reallocate a member's buffers)
-  std::vector<const void*> sig;
-  for (const Problem* p : b->members)
-    for (const void* x : {(const void*)p->h[0], (const void*)p->h[1], (const void*)p->m, (const void*)p->v,
-                          (const void*)p->words[0], (const void*)p->words[1], (const void*)p->cnt[0],
-                          (const void*)p->psum[0], (const void*)p->satP[0], (const void*)p->satP[1],
-                          (const void*)p->mag[0], (const void*)p->mag[1]})
-      sig.push_back(x);
+  // the descriptors hold member device pointers: rebuild them when any member has
+  // allocated since (a fresh start or a new replica count or mode reallocates buffers,
+  // and a new buffer may reuse a freed address, so pointers alone cannot tell)
+  std::vector<uint64_t> sig;
+  for (const Problem* p : b->members) sig.push_back(p->alloc_gen);
   const bool changed = !b->ready || b->R != R || b->mode != a->grad_mode || b->opt != a->optimizer || sig != b->sig;
   if (changed) {
     b->sig = sig;

@@ -122,6 +122,8 @@ struct Problem {
 
   int32_t* err = nullptr;      // sticky device error word
   std::vector<void*> allocs;   // every cudaMalloc, freed by fem_destroy
+  uint64_t alloc_gen = 0;      // bumped by every allocation: holders of device pointers
+                               // (batch descriptors) rebuild when it changes
 };
 
 // ---- error reporting (thread-local last error)
@@ -161,7 +163,7 @@ fem_status bmincut_states_all(Problem* p, int32_t* out, cudaStream_t s);
 // ---- dense MaxCut on the tensor cores (dense_tc.cu)
 int dense_pad(int n);
 fem_status dense_upload(Problem* p, const float* J, cudaStream_t s);
-fem_status dense_state(Problem* p, int R, int prec);
+fem_status dense_state(Problem* p, int R, int prec, cudaStream_t s);
 fem_status dense_set_fields(Problem* p, const float* h_nr, bool on_device, cudaStream_t s);
 fem_status dense_get(Problem* p, const float* src_rn, float* dst_nr_host, cudaStream_t s);
 fem_status dense_put(Problem* p, float* dst_rn, const float* src_nr_host, cudaStream_t s);

@@ -382,6 +382,17 @@ const char* fem_status_string(fem_status s);
 /* One-line description of the last failure on the calling thread ("" if none). */
 const char* fem_last_error(void);
 
+/* The schedule values step t of the anneal described by `a` uses: beta_t (the
+ * exponential or inverse-proportional schedule from beta_min to beta_max over
+ * a->n_steps steps; Methods, "Different annealing schedules") and the balance
+ * weight lambda_t = lambda_max * t / (n_steps - 1) (SM, bMinCut demonstration).
+ * Only a->schedule, beta_min, beta_max, lambda_max and n_steps are read.  A caller
+ * that starts an anneal part-way along a schedule (a warm start) takes its beta from
+ * here.  Host-only and synchronous.  FEM_ERR_INVALID_ARG unless 0 <= t < n_steps,
+ * both betas are finite and > 0 and the schedule is known.  Either output may be
+ * NULL. */
+fem_status fem_schedule_value(const fem_anneal_params* a, int32_t t, double* beta, double* lambda);
+
 /* Number of CUDA kernels this library has launched in the process so far (all
  * handles, all threads).  Lets a caller count the device work behind a call. */
 int64_t fem_kernel_launches(void);
@@ -401,10 +412,15 @@ int64_t fem_kernel_launches(void);
  *   energy[replicas]  out: E_r = -cut_r (int64); best_replica[1] out: argmin E,
  *        lowest index on ties.
  * replicas must be a multiple of 32 and at most 1024 (FEM_ERR_UNSUPPORTED beyond).
- * Asynchronous on `stream`.  The first call on a device looks up the scratch address
- * (a CUDA runtime query), so make that first call before any stream capture.  Calls
- * share the scratch array: calls that overlap on the GPU (different streams, no
- * ordering between them) race and give wrong results. */
+ * Asynchronous on `stream`, so the CSR cannot be validated on the host: the kernel
+ * checks that every row lies in [0, row_ptr[n]) and every column is below n, skips
+ * anything outside (no access beyond those bounds) and then writes best_replica = -1;
+ * the energies of such a call are meaningless.  col must hold row_ptr[n] entries.
+ * The first call on a device looks up the scratch address (a CUDA runtime query),
+ * so make that first call before any stream capture; the address is cached for the
+ * life of the process and is invalid after cudaDeviceReset.  Calls share the scratch
+ * array: calls that overlap on the GPU (different streams, no ordering between them)
+ * race and give wrong results. */
 fem_status fem_maxcut_energies_noalloc(const int32_t* row_ptr, const uint32_t* col, int32_t n,
                                        const uint32_t* words, int32_t replicas, int64_t* energy,
                                        int32_t* best_replica, void* stream);

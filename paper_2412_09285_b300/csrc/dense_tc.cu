@@ -768,55 +768,95 @@ __global__ void __launch_bounds__(kThreads, 1) k_dense_anneal_tc(const __grid_co
 }
 
 // ------------------------------------------- CUDA-core fp32 step (the plain FEM)
-// 64 x 64 output tile per 256-thread block, 4 x 4 per thread, K tiles of 16 in
-// shared memory; the same epilogue as the tensor-core kernel.
+// S = J M^T on the CUDA cores: a 128 x 128 output tile (rows i x replicas r) per
+// 256-thread block, 8 x 8 per thread as two 4 x 4 quadrants 64 apart (so the
+// epilogue's float4 accesses of h, m, v along i coalesce across the 16 threads of a
+// row), K in tiles of 8 staged k-major in shared memory and double-buffered: the next
+// tile's global loads are in flight while the current one is multiplied.  The same
+// epilogue as the tensor-core kernels, in fp32 with IEEE operations.
+constexpr int kF32Tile = 128, kF32K = 8;
+
 __global__ void __launch_bounds__(256) k_dense_step_fp32(const float* __restrict__ J, const float* __restrict__ M,
                                                          DenseArgs a, StepScalars s) {
-  __shared__ float sJ[16][64 + 4];
-  __shared__ float sM[16][64 + 4];
-  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-  const int i0 = blockIdx.x * 64, r0 = blockIdx.y * 64;
-  float acc[4][4] = {};
-  for (int k0 = 0; k0 < a.n_pad; k0 += 16) {
-    for (int e = threadIdx.x; e < 16 * 64; e += 256) {
-      const int kk = e & 15, rr = e >> 4;
-      sJ[kk][rr] = J[(size_t)(i0 + rr) * a.n_pad + k0 + kk];
-      sM[kk][rr] = (r0 + rr < a.R) ? M[(size_t)(r0 + rr) * a.n_pad + k0 + kk] : 0.f;
+  __shared__ __align__(16) float sJ[2][kF32K][kF32Tile];
+  __shared__ __align__(16) float sM[2][kF32K][kF32Tile];
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  const int i0 = blockIdx.x * kF32Tile, r0 = blockIdx.y * kF32Tile;
+  // global -> shared: thread t moves 4 consecutive k of row t / 2 of each operand tile
+  const int lrow = tid >> 1, lk = (tid & 1) * 4;
+  const float* gJ = J + (size_t)(i0 + lrow) * a.n_pad + lk;
+  const bool mrow = r0 + lrow < a.R;
+  const float* gM = M + (size_t)(mrow ? r0 + lrow : 0) * a.n_pad + lk;
+  float4 nj = *reinterpret_cast<const float4*>(gJ);
+  float4 nm = mrow ? *reinterpret_cast<const float4*>(gM) : make_float4(0.f, 0.f, 0.f, 0.f);
+  auto stash = [&](int b) {
+    sJ[b][lk + 0][lrow] = nj.x; sJ[b][lk + 1][lrow] = nj.y; sJ[b][lk + 2][lrow] = nj.z; sJ[b][lk + 3][lrow] = nj.w;
+    sM[b][lk + 0][lrow] = nm.x; sM[b][lk + 1][lrow] = nm.y; sM[b][lk + 2][lrow] = nm.z; sM[b][lk + 3][lrow] = nm.w;
+  };
+  stash(0);
+  __syncthreads();
+  float acc[8][8];
+#pragma unroll
+  for (int p = 0; p < 8; ++p)
+#pragma unroll
+    for (int q = 0; q < 8; ++q) acc[p][q] = 0.f;
+  const int ntiles = a.n_pad / kF32K;
+  for (int kt = 0; kt < ntiles; ++kt) {
+    const int b = kt & 1;
+    if (kt + 1 < ntiles) {
+      nj = *reinterpret_cast<const float4*>(gJ + (kt + 1) * kF32K);
+      nm = mrow ? *reinterpret_cast<const float4*>(gM + (kt + 1) * kF32K) : make_float4(0.f, 0.f, 0.f, 0.f);
     }
-    __syncthreads();
 #pragma unroll
-    for (int kk = 0; kk < 16; ++kk) {
-      float x[4], y[4];
+    for (int kk = 0; kk < kF32K; ++kk) {
+      const float4 x0 = *reinterpret_cast<const float4*>(&sJ[b][kk][tx * 4]);
+      const float4 x1 = *reinterpret_cast<const float4*>(&sJ[b][kk][64 + tx * 4]);
+      const float4 y0 = *reinterpret_cast<const float4*>(&sM[b][kk][ty * 4]);
+      const float4 y1 = *reinterpret_cast<const float4*>(&sM[b][kk][64 + ty * 4]);
+      const float x[8] = {x0.x, x0.y, x0.z, x0.w, x1.x, x1.y, x1.z, x1.w};
+      const float y[8] = {y0.x, y0.y, y0.z, y0.w, y1.x, y1.y, y1.z, y1.w};
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        x[q] = sJ[kk][tx + 16 * q];
-        y[q] = sM[kk][ty + 16 * q];
-      }
+      for (int p = 0; p < 8; ++p)
 #pragma unroll
-      for (int p = 0; p < 4; ++p)
-#pragma unroll
-        for (int q = 0; q < 4; ++q) acc[p][q] = fmaf(x[p], y[q], acc[p][q]);
+        for (int q = 0; q < 8; ++q) acc[p][q] = fmaf(x[p], y[q], acc[p][q]);
     }
+    if (kt + 1 < ntiles) stash(b ^ 1);
     __syncthreads();
   }
   float* mt = reinterpret_cast<float*>(a.mt_out);
 #pragma unroll
-  for (int p = 0; p < 4; ++p) {
-    const int i = i0 + tx + 16 * p;
-    if (i >= a.n) continue;
-    const float cn = a.mode == FEM_GRAD_PAPER ? a.cnorm[i] : 2.f;
+  for (int q = 0; q < 8; ++q) {
+    const int r = r0 + (q < 4 ? ty * 4 + q : 64 + ty * 4 + q - 4);
+    if (r >= a.R) continue;
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const int r = r0 + ty + 16 * q;
-      if (r >= a.R) continue;
-      const size_t idx = (size_t)r * a.n_pad + i;
-      float hv = a.h[idx], mv = a.m[idx], vv = a.opt == FEM_OPT_SGD ? 0.f : a.v[idx];
-      const float g = s.gq * (cn * acc[p][q] + hv * s.inv_beta) * one_minus_m2(hv);
-      opt_update_rt(a.opt, hv, mv, vv, g, s);
-      a.h[idx] = hv;
-      a.m[idx] = mv;
-      if (a.opt != FEM_OPT_SGD) a.v[idx] = vv;
-      mt[idx] = a.mode == FEM_GRAD_PAPER ? (hv < 0.f ? -1.f : 1.f) : tanhf(0.5f * hv);
+    for (int half = 0; half < 2; ++half) {
+      const int ib = i0 + half * 64 + tx * 4;   // 4 consecutive rows
+      if (ib >= a.n) continue;
+      const size_t idx = (size_t)r * a.n_pad + ib;
+      float4 hv = *reinterpret_cast<const float4*>(a.h + idx);
+      float4 mv = *reinterpret_cast<const float4*>(a.m + idx);
+      float4 vv = a.opt == FEM_OPT_SGD ? make_float4(0.f, 0.f, 0.f, 0.f) : *reinterpret_cast<const float4*>(a.v + idx);
+      float4 ov;
+      float* hp = &hv.x;
+      float* mp = &mv.x;
+      float* vp = &vv.x;
+      float* op = &ov.x;
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const int i = ib + e;
+        if (i >= a.n) {   // padding rows keep their (zero) state and operand
+          op[e] = 0.f;
+          continue;
+        }
+        const float cn = a.mode == FEM_GRAD_PAPER ? a.cnorm[i] : 2.f;
+        const float g = s.gq * (cn * acc[half * 4 + e][q] + hp[e] * s.inv_beta) * one_minus_m2(hp[e]);
+        opt_update_rt(a.opt, hp[e], mp[e], vp[e], g, s);
+        op[e] = a.mode == FEM_GRAD_PAPER ? (hp[e] < 0.f ? -1.f : 1.f) : tanhf(0.5f * hp[e]);
+      }
+      *reinterpret_cast<float4*>(a.h + idx) = hv;
+      *reinterpret_cast<float4*>(a.m + idx) = mv;
+      if (a.opt != FEM_OPT_SGD) *reinterpret_cast<float4*>(a.v + idx) = vv;
+      *reinterpret_cast<float4*>(mt + idx) = ov;
     }
   }
 }
@@ -1186,7 +1226,7 @@ fem_status dense_upload(Problem* p, const float* J, cudaStream_t s) {
 }
 
 // State for R replicas: h, m, v [R][n_pad] and two operand buffers per part.
-fem_status dense_state(Problem* p, int R, int prec) {
+fem_status dense_state(Problem* p, int R, int prec, cudaStream_t s) {
   const size_t per = (size_t)R * p->n_pad;
   // the buffers of the previous replica count or precision are released first
   // (cudaFree waits for the device, so no queued work still uses them)
@@ -1221,11 +1261,12 @@ fem_status dense_state(Problem* p, int R, int prec) {
     p->mt_lo[b] = nullptr;
     if ((st = dev_alloc(p, &p->mt[b], per * eb)) != FEM_OK) return st;
     // the K padding (columns n..n_pad-1) is never written by a step: it must hold zeros,
-    // not arbitrary bits (0 x NaN would reach the accumulator)
-    FEM_CUDA(cudaMemset(p->mt[b], 0, per * eb));
+    // not arbitrary bits (0 x NaN would reach the accumulator); cleared on the anneal's
+    // stream, so the first contraction is ordered after it
+    FEM_CUDA(cudaMemsetAsync(p->mt[b], 0, per * eb, s));
     if (prec == FEM_PREC_BF16X2) {
       if ((st = dev_alloc(p, &p->mt_lo[b], per * 2)) != FEM_OK) return st;
-      FEM_CUDA(cudaMemset(p->mt_lo[b], 0, per * 2));
+      FEM_CUDA(cudaMemsetAsync(p->mt_lo[b], 0, per * 2, s));
     }
     if (prec != FEM_PREC_FP32 && (st = make_map(&p->tmap_b[b], p->mt[b], R, p->n_pad, eb)) != FEM_OK) return st;
     if (prec != FEM_PREC_FP32 && (st = make_map(&p->tmap_bh[b], p->mt[b], R, p->n_pad, eb, kTile / 2)) != FEM_OK)
@@ -1370,7 +1411,7 @@ fem_status dense_steps(Problem* p, const std::vector<StepScalars>& sc, int t_beg
     fem_status st = FEM_OK;
     switch (p->precision) {
       case FEM_PREC_FP32: {
-        const dim3 grid(p->n_pad / 64, (p->R + 63) / 64);
+        const dim3 grid(p->n_pad / kF32Tile, (p->R + kF32Tile - 1) / kF32Tile);
         k_dense_step_fp32<<<grid, 256, 0, s>>>(p->J32, reinterpret_cast<const float*>(p->mt[in]), a, sc[k]);
         break;
       }

@@ -57,6 +57,7 @@ fem_status dev_alloc(Problem* p, void** ptr, size_t bytes) {
     return fail(FEM_ERR_OOM, "cudaMalloc of %zu bytes failed: %s", bytes, cudaGetErrorString(e));
   }
   p->allocs.push_back(*ptr);
+  ++p->alloc_gen;
   return FEM_OK;
 }
 
@@ -75,12 +76,14 @@ static fem_status upload(Problem* p, T** dst, const std::vector<T>& src, cudaStr
 // ---------------------------------------------------------------------------
 static double beta_at(const fem_anneal_params& a, int t) {
   if (a.n_steps == 1) return a.beta_min;
-  const double x = (double)t / (double)(a.n_steps - 1);
   if (a.schedule == FEM_SCHED_EXPONENTIAL)
     return std::exp((std::log(a.beta_max) - std::log(a.beta_min)) / (a.n_steps - 1) * t +
                     std::log(a.beta_min));
-  (void)x;
   return 1.0 / ((1.0 / a.beta_max - 1.0 / a.beta_min) / (a.n_steps - 1) * t + 1.0 / a.beta_min);
+}
+
+static double lambda_at(const fem_anneal_params& a, int t) {
+  return a.n_steps == 1 ? 0.0 : a.lambda_max * (double)t / (double)(a.n_steps - 1);
 }
 
 std::vector<StepScalars> make_step_scalars(const fem_anneal_params& a, int32_t single_field) {
@@ -90,7 +93,7 @@ std::vector<StepScalars> make_step_scalars(const fem_anneal_params& a, int32_t s
     StepScalars s;
     std::memset(&s, 0, sizeof(s));
     const double beta = beta_at(a, t);
-    const double lam = a.n_steps == 1 ? 0.0 : a.lambda_max * (double)t / (double)(a.n_steps - 1);
+    const double lam = lambda_at(a, t);
     s.inv_beta = (float)(1.0 / beta);
     s.lambda = (float)lam;
     s.gq = (float)(single_field ? a.gamma_grad / 4.0 : a.gamma_grad);
@@ -126,7 +129,7 @@ std::vector<StepScalars> make_step_scalars(const fem_anneal_params& a, int32_t s
 }
 
 // Declared in the kernel files.
-fem_status maxcut_pack_words(Problem* p, int hbuf, int wbuf, cudaStream_t s);
+fem_status maxcut_pack_words(Problem* p, int hbuf, int wbuf, cudaStream_t s, const float* src = nullptr);
 const float* maxcut_current_fields(const Problem* p);
 fem_status maxcut_states_all(Problem* p, int32_t* out_dev, cudaStream_t s);
 
@@ -668,7 +671,7 @@ fem_status fem_anneal(fem_problem_t p, const fem_anneal_params* a, void* stream)
     if (!a->h_init) return fail(FEM_ERR_INVALID_ARG, "h_init is required when t_begin == 0");
     fem_status st = FEM_OK;
     if (p->dense_R_alloc != R || p->dense_prec_alloc != a->precision) {
-      if ((st = dense_state(p, R, a->precision)) != FEM_OK) return st;
+      if ((st = dense_state(p, R, a->precision, s)) != FEM_OK) return st;
     }
     p->R = R;
     p->cur = 0;
@@ -691,8 +694,11 @@ fem_status fem_anneal(fem_problem_t p, const fem_anneal_params* a, void* stream)
     fem_status st = ensure_state(p, R, a->grad_mode, s);
     if (st != FEM_OK) return st;
     const size_t per = (size_t)p->n * R * (p->kind == FEM_BMINCUT ? p->q : 1);
-    FEM_CUDA(cudaMemcpyAsync(p->h[0], a->h_init, per * sizeof(float),
-                             a->h_init_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
+    // MaxCut fields on the device are copied by the sign-word pass below
+    const bool fused_copy = p->kind == FEM_MAXCUT && a->h_init_is_device;
+    if (!fused_copy)
+      FEM_CUDA(cudaMemcpyAsync(p->h[0], a->h_init, per * sizeof(float),
+                               a->h_init_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
     FEM_CUDA(cudaMemsetAsync(p->m, 0, per * sizeof(float), s));
     FEM_CUDA(cudaMemsetAsync(p->v, 0, per * sizeof(float), s));
     p->cur = 0;
@@ -703,7 +709,7 @@ fem_status fem_anneal(fem_problem_t p, const fem_anneal_params* a, void* stream)
     p->precision = a->precision;
     p->lambda_max = a->lambda_max;
     if (p->kind == FEM_MAXCUT) {
-      if ((st = maxcut_pack_words(p, 0, 0, s)) != FEM_OK) return st;
+      if ((st = maxcut_pack_words(p, 0, 0, s, fused_copy ? a->h_init : nullptr)) != FEM_OK) return st;
     } else if (p->kind == FEM_BMINCUT) {
       if ((st = bmincut_derive(p, 0, s)) != FEM_OK) return st;
     } else {
@@ -806,6 +812,19 @@ fem_status fem_read_best(fem_problem_t p, int32_t* best_replica, int32_t* states
   if (energy_i64) FEM_CUDA(cudaMemcpyAsync(energy_i64, p->energy_i, (size_t)p->R * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
   if (energy_f64) FEM_CUDA(cudaMemcpyAsync(energy_f64, p->energy_f, (size_t)p->R * sizeof(double), cudaMemcpyDeviceToHost, s));
   return check_sticky(p, s);
+}
+
+fem_status fem_schedule_value(const fem_anneal_params* a, int32_t t, double* beta, double* lambda) {
+  g_last_error.clear();
+  if (!a) return fail(FEM_ERR_INVALID_ARG, "params must be non-NULL");
+  if (a->n_steps < 1 || t < 0 || t >= a->n_steps) return fail(FEM_ERR_INVALID_ARG, "need 0 <= t < n_steps");
+  if (!(a->beta_min > 0) || !(a->beta_max > 0) || !std::isfinite(a->beta_min) || !std::isfinite(a->beta_max))
+    return fail(FEM_ERR_INVALID_ARG, "beta_min and beta_max must be finite and > 0");
+  if (a->schedule != FEM_SCHED_EXPONENTIAL && a->schedule != FEM_SCHED_INVERSE_PROPORTIONAL)
+    return fail(FEM_ERR_INVALID_ARG, "unknown schedule %d", a->schedule);
+  if (beta) *beta = beta_at(*a, t);
+  if (lambda) *lambda = lambda_at(*a, t);
+  return FEM_OK;
 }
 
 fem_status fem_set_step_barrier_timeout(fem_problem_t p, int64_t ns) {

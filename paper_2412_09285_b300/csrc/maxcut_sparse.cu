@@ -220,10 +220,12 @@ __global__ void __launch_bounds__(256, 5) k_maxcut_step_paper(MaxcutArgs a, Step
 }
 
 // Sign words of the fields: bit r of word (i, b) is set when h[i][32b + r] < 0 (and,
-// when mag is non-NULL, m = tanh(h/2) for the exact-mode
-// gathers).
+// when mag is non-NULL, m = tanh(h/2) for the exact-mode gathers).  With copy
+// non-NULL the fields are also written there: a fresh start reads the caller's
+// initial fields once, instead of a device copy followed by this pass.
 __global__ void k_pack_sign_words(const float* __restrict__ h, int32_t n, int32_t R,
-                                  int32_t wpn, uint32_t* __restrict__ words, float* __restrict__ mag) {
+                                  int32_t wpn, uint32_t* __restrict__ words, float* __restrict__ mag,
+                                  float* __restrict__ copy) {
   const int lane = threadIdx.x & 31;
   const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
   for (long long it = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -232,6 +234,7 @@ __global__ void k_pack_sign_words(const float* __restrict__ h, int32_t n, int32_
     const uint32_t b = __ballot_sync(kFullMask, x < 0.f);
     if (lane == 0) words[it] = b;
     if (mag) mag[it * 32 + lane] = tanhf(0.5f * x);
+    if (copy) copy[it * 32 + lane] = x;
   }
 }
 
@@ -288,6 +291,72 @@ __global__ void __launch_bounds__(256) k_maxcut_cut_partial(
     const size_t o = (size_t)blockIdx.x * R + (size_t)wb * 32 + lane;
     if (INTW) part_i[o] = ti;
     else part_f[o] = tf;
+  }
+}
+
+// Unit-weight partial objectives, NPW consecutive nodes per warp.  The group's CSR
+// entries are read 32 at a time (one coalesced load); lane e forms the 32-replica word
+// of entry e's edge term from the two endpoints' sign words - MaxCut: the states
+// differ (XOR); QUBO: both variables are 1 (neither bit set) - and a 32 x 32 warp bit
+// transpose gives lane r, for every entry, replica r's bit.  One popcount under the
+// mask of entries with W = +1 minus one under W = -1 then adds a chunk's edges to
+// replica r's count (each undirected edge once: the entry with j > i).  The sums are
+// integers, so the grouping does not change the result.  The row pointers of the next
+// group are fetched while the current one is counted.
+template <bool QUBO, int NPW>
+__global__ void __launch_bounds__(256) k_maxcut_cut_grouped(
+    const int32_t* __restrict__ row_ptr, const uint32_t* __restrict__ col, const int64_t* __restrict__ lin_i,
+    const uint32_t* __restrict__ words, int32_t n, int32_t R, int32_t wpn, int64_t* __restrict__ part_i) {
+  __shared__ int64_t si[8][32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int wb = blockIdx.y;
+  const int ngroups = (n + NPW - 1) / NPW;
+  const int stride = gridDim.x * 8;
+  int64_t acc = 0;
+  int g = blockIdx.x * 8 + warp;
+  int rp = (g < ngroups && lane <= NPW) ? __ldg(row_ptr + min(g * NPW + lane, n)) : 0;
+  for (; g < ngroups; g += stride) {
+    const int i0 = g * NPW;
+    const uint32_t own = (lane < NPW && i0 + lane < n) ? __ldg(words + (size_t)(i0 + lane) * wpn + wb) : 0u;
+    int rb[NPW + 1];
+#pragma unroll
+    for (int k = 0; k <= NPW; ++k) rb[k] = __shfl_sync(kFullMask, rp, k);
+    const int gn = g + stride;
+    rp = (gn < ngroups && lane <= NPW) ? __ldg(row_ptr + min(gn * NPW + lane, n)) : 0;
+    for (int c0 = rb[0]; c0 < rb[NPW]; c0 += 32) {
+      const int e = c0 + lane;
+      const bool valid = e < rb[NPW];
+      int k = 0;
+#pragma unroll
+      for (int kk = 1; kk < NPW; ++kk) k += (e >= rb[kk]) ? 1 : 0;
+      const uint32_t wi = __shfl_sync(kFullMask, own, k);
+      uint32_t c = 0, wj = 0;
+      if (valid) {
+        c = __ldg(col + e);
+        wj = __ldg(words + (size_t)(c & 0x7fffffffu) * wpn + wb);
+      }
+      const bool take = valid && (int)(c & 0x7fffffffu) > i0 + k;
+      const uint32_t pm = __ballot_sync(kFullMask, take && !(c >> 31));
+      const uint32_t nm = __ballot_sync(kFullMask, take && (c >> 31));
+      const uint32_t x = QUBO ? ~(wi | wj) : (wi ^ wj);
+      const uint32_t tr = warp_transpose32(x, lane);
+      const int d = __popc(tr & pm) - __popc(tr & nm);
+      acc += QUBO ? 2 * d : d;
+    }
+    if (QUBO) {   // the linear terms of the group's variables that are 1
+#pragma unroll
+      for (int k = 0; k < NPW; ++k) {
+        const uint32_t wk = __shfl_sync(kFullMask, own, k);
+        if (i0 + k < n && !((wk >> lane) & 1u)) acc += __ldg(lin_i + i0 + k);
+      }
+    }
+  }
+  si[warp][lane] = acc;
+  __syncthreads();
+  if (warp == 0) {
+    int64_t t = 0;
+    for (int k = 0; k < 8; ++k) t += si[k][lane];
+    part_i[(size_t)blockIdx.x * R + (size_t)wb * 32 + lane] = t;
   }
 }
 
@@ -461,11 +530,11 @@ int grid_for_warps(const Problem* p, long long warps) {
 
 }  // namespace
 
-fem_status maxcut_pack_words(Problem* p, int hbuf, int wbuf, cudaStream_t s) {
+fem_status maxcut_pack_words(Problem* p, int hbuf, int wbuf, cudaStream_t s, const float* src) {
   const long long items = (long long)p->n * p->words_per_node;
   k_pack_sign_words<<<grid_for_warps(p, items), 256, 0, s>>>(
-      p->h[hbuf], p->n, p->R, p->words_per_node, p->words[wbuf],
-      p->grad_mode == FEM_GRAD_EXACT ? p->mag[wbuf] : nullptr);
+      src ? src : p->h[hbuf], p->n, p->R, p->words_per_node, p->words[wbuf],
+      p->grad_mode == FEM_GRAD_EXACT ? p->mag[wbuf] : nullptr, src ? p->h[hbuf] : nullptr);
   count_launches(1);
   FEM_CUDA(cudaGetLastError());
   return FEM_OK;
@@ -517,23 +586,23 @@ fem_status maxcut_readout(Problem* p, cudaStream_t s) {
   const dim3 grid(p->part_blocks, wpn);
   const uint32_t* words = p->words[p->cur];
   const bool intw = p->int_w && (!p->qubo || p->qlin_int);
-  if (p->qubo) {
-    if (intw && p->unit_w)
-      k_qubo_partial<true, true><<<grid, 256, 0, s>>>(p->row_ptr, p->col, p->w, p->w64, p->qlin_i, p->qlin_f,
-                                                      words, p->n, p->R, wpn, p->part_i, p->part_f);
-    else if (intw)
+  if (intw && p->unit_w) {   // the common case: grouped nodes and bit-sliced counts
+    if (p->qubo)
+      k_maxcut_cut_grouped<true, kNodesPerWarp><<<grid, 256, 0, s>>>(p->row_ptr, p->col, p->qlin_i, words, p->n,
+                                                                     p->R, wpn, p->part_i);
+    else
+      k_maxcut_cut_grouped<false, kNodesPerWarp><<<grid, 256, 0, s>>>(p->row_ptr, p->col, p->qlin_i, words, p->n,
+                                                                      p->R, wpn, p->part_i);
+  } else if (p->qubo) {
+    if (intw)
       k_qubo_partial<false, true><<<grid, 256, 0, s>>>(p->row_ptr, p->col, p->w, p->w64, p->qlin_i, p->qlin_f,
                                                        words, p->n, p->R, wpn, p->part_i, p->part_f);
     else
       k_qubo_partial<false, false><<<grid, 256, 0, s>>>(p->row_ptr, p->col, p->w, p->w64, p->qlin_i, p->qlin_f,
                                                         words, p->n, p->R, wpn, p->part_i, p->part_f);
   } else if (intw) {
-    if (p->unit_w)
-      k_maxcut_cut_partial<true, true><<<grid, 256, 0, s>>>(p->row_ptr, p->col, p->w, p->w64, words,
-                                                            p->n, p->R, wpn, p->part_i, p->part_f);
-    else
-      k_maxcut_cut_partial<false, true><<<grid, 256, 0, s>>>(p->row_ptr, p->col, p->w, p->w64, words,
-                                                             p->n, p->R, wpn, p->part_i, p->part_f);
+    k_maxcut_cut_partial<false, true><<<grid, 256, 0, s>>>(p->row_ptr, p->col, p->w, p->w64, words,
+                                                           p->n, p->R, wpn, p->part_i, p->part_f);
   } else {
     k_maxcut_cut_partial<false, false><<<grid, 256, 0, s>>>(p->row_ptr, p->col, p->w, p->w64, words,
                                                             p->n, p->R, wpn, p->part_i, p->part_f);

@@ -87,6 +87,7 @@ def _load():
         "fem_status_string": (C.c_char_p, [S]),
         "fem_last_error": (C.c_char_p, []),
         "fem_kernel_launches": (C.c_int64, []),
+        "fem_schedule_value": (S, [C.POINTER(fem_anneal_params), C.c_int32, P, P]),
         "fem_batch_create": (S, [P, C.c_int32, C.POINTER(P)]),
         "fem_batch_anneal": (S, [P, C.POINTER(fem_anneal_params), P, P]),
         "fem_batch_destroy": (None, [P]),
@@ -215,6 +216,15 @@ def fem_destroy(handle):
     _lib.fem_destroy(handle)
 
 
+def fem_schedule_value(t, n_steps, **kw):
+    """(beta_t, lambda_t) of step t of an anneal of n_steps steps with the schedule
+    settings in kw (the library's own schedule)."""
+    p = make_params(1, n_steps, **kw)
+    beta, lam = C.c_double(), C.c_double()
+    _check(_lib.fem_schedule_value(C.byref(p), int(t), C.byref(beta), C.byref(lam)), "fem_schedule_value")
+    return beta.value, lam.value
+
+
 def fem_kernel_launches() -> int:
     return int(_lib.fem_kernel_launches())
 
@@ -335,9 +345,11 @@ class Problem:
         fem_read_states(self.handle, out, self.stream)
         return out
 
-    def best(self):
+    def best(self, states=True):
+        """Best replica, every replica's energy and (unless states=False) the best
+        replica's states copied to the host."""
         br = np.zeros(1, np.int32)
-        st = np.empty(self.n, np.int32)
+        st = np.empty(self.n, np.int32) if states else None
         ei = np.empty(self.replicas, np.int64)
         ef = np.empty(self.replicas, np.float64)
         fem_read_best(self.handle, br, st, ei, ef, self.stream)

@@ -19,7 +19,6 @@ Every computation runs in the library's kernels; torch only holds device buffers
 from __future__ import annotations
 
 import ctypes as C
-import math
 
 import numpy as np
 
@@ -76,10 +75,8 @@ class Mpnn:
 
 
 def beta_at(t, n_steps, beta_min=0.05, beta_max=5.0):
-    """The exponential schedule's beta at step t (Methods, annealing schedules)."""
-    if n_steps == 1:
-        return beta_min
-    return math.exp((math.log(beta_max) - math.log(beta_min)) / (n_steps - 1) * t + math.log(beta_min))
+    """The exponential schedule's beta at step t, from the library (fem_schedule_value)."""
+    return F.fem_schedule_value(t, n_steps, beta_min=beta_min, beta_max=beta_max)[0]
 
 
 def fem_fields_at(problem, h0, n_steps, t_end, out, **kw):

@@ -54,8 +54,9 @@ def softmax(h):
 
 
 def _where(where):
-    test = os.environ.get("PYTEST_CURRENT_TEST", "").split(" ")[0].split("::")[-1]
-    return f"{test} {where}"
+    node = os.environ.get("PYTEST_CURRENT_TEST", "").split(" ")[0]
+    path, _, test = node.partition("::")
+    return f"{os.path.basename(path)[:-3]}::{test} {where}"
 
 
 def opt_state(opt):

@@ -91,3 +91,19 @@ def test_null_arguments_rejected(lib):
     assert so.fem_anneal(None, None, None) == lib.FEM_ERR_INVALID_ARG
     assert so.fem_read_best(None, None, None, None, None, None) == lib.FEM_ERR_INVALID_ARG
     so.fem_destroy(None)  # no-op
+
+
+@pytest.mark.parametrize("schedule,bmin,bmax,n", [("exponential", 0.05, 5.0, 2000),
+                                                  ("inverse_proportional", 1 / 1.16, 1 / 6e-5, 1000),
+                                                  ("exponential", 0.3, 0.3, 1)])
+def test_schedule_value_is_the_oracle_schedule(lib, schedule, bmin, bmax, n):
+    """fem_schedule_value (host-only) gives the beta and lambda schedule the oracle uses."""
+    import oracle as O
+    ref_b = O.beta_schedule(schedule, bmin, bmax, n)
+    ref_l = O.lambda_ramp(0.7, n)
+    for t in sorted({0, min(1, n - 1), n // 3, n - 1}):
+        b, lam = lib.fem_schedule_value(t, n, schedule=schedule, beta_min=bmin, beta_max=bmax, lambda_max=0.7)
+        assert b == pytest.approx(ref_b[t], rel=1e-13) and lam == pytest.approx(ref_l[t], rel=1e-13, abs=1e-15)
+    with pytest.raises(lib.FemError) as e:
+        lib.fem_schedule_value(n, n)
+    assert e.value.status == lib.FEM_ERR_INVALID_ARG

@@ -397,6 +397,16 @@ fem_status fem_schedule_value(const fem_anneal_params* a, int32_t t, double* bet
  * handles, all threads).  Lets a caller count the device work behind a call. */
 int64_t fem_kernel_launches(void);
 
+/* Where fem_create_problem builds a sparse graph's CSR: graphs with at least
+ * min_edges undirected edges on the device of the call (degrees, a prefix sum, a
+ * scatter of (column, edge) keys and a per-row sort), smaller ones on the host; a
+ * negative value keeps every build on the host.  Both give the same arrays bit for
+ * bit; validation (indices, self-loops, weights) always runs on the host first, and a
+ * duplicate edge is reported as FEM_ERR_INVALID_ARG by either builder.  Process-wide;
+ * the default is 65536.  Clause lists and dense couplings are always built on the
+ * host. */
+void fem_set_device_graph_build(int64_t min_edges);
+
 /* MaxCut energies of caller-provided sign words, without allocating.
  * The paper has no counterpart: this is a library service for callers that cannot
  * call cudaMalloc - for example code whose device memory is owned by a pool manager,

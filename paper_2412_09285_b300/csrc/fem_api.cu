@@ -129,6 +129,8 @@ std::vector<StepScalars> make_step_scalars(const fem_anneal_params& a, int32_t s
 }
 
 // Declared in the kernel files.
+fem_status device_graph_build(Problem* p, int32_t kind, int32_t q, const fem_problem_desc* d, bool unit, bool integer,
+                              cudaStream_t s);
 fem_status maxcut_pack_words(Problem* p, int hbuf, int wbuf, cudaStream_t s, const float* src = nullptr);
 const float* maxcut_current_fields(const Problem* p);
 fem_status maxcut_states_all(Problem* p, int32_t* out_dev, cudaStream_t s);
@@ -156,14 +158,20 @@ struct HostGraph {
   std::vector<double> w64;
 };
 
-static fem_status host_graph(int32_t kind, int32_t q, const fem_problem_desc* d, HostGraph& g) {
+// Graphs with at least this many edges build their CSR on the device
+// (fem_set_device_graph_build); below it the host builder is quicker than the launches.
+static std::atomic<int64_t> g_device_build_min_edges{1 << 16};
+
+// Validation, weight flags and sums always run on the host (one linear pass, before
+// any device work); with build == false the CSR is left to device_graph_build.
+static fem_status host_graph(int32_t kind, int32_t q, const fem_problem_desc* d, HostGraph& g, bool build = true) {
   const int32_t n = d->n;
   const int64_t E = d->n_edges;
   if (E < 0) return fail(FEM_ERR_INVALID_ARG, "n_edges < 0");
   if (E > 0 && (!d->ei || !d->ej)) return fail(FEM_ERR_INVALID_ARG, "ei/ej must be non-NULL");
   if (2 * E >= (int64_t)INT32_MAX) return fail(FEM_ERR_UNSUPPORTED, "2|E| must be < 2^31");
   bool unit = true, integer = true;
-  std::vector<int32_t> deg(n + 1, 0);
+  std::vector<int32_t> deg(build ? (size_t)n + 1 : 0, 0);
   for (int64_t e = 0; e < E; ++e) {
     const int32_t i = d->ei[e], j = d->ej[e];
     if (i < 0 || i >= n || j < 0 || j >= n)
@@ -178,9 +186,15 @@ static fem_status host_graph(int32_t kind, int32_t q, const fem_problem_desc* d,
     if (w != std::rint(w) || std::fabs(w) > 16777216.0) integer = false;
     g.wsum_f += w;
     if (integer) g.wsum_i += (int64_t)w;
-    deg[i]++;
-    deg[j]++;
+    if (build) {
+      deg[i]++;
+      deg[j]++;
+    }
   }
+  g.n_edges = E;
+  g.unit = unit;
+  g.integer = integer;
+  if (!build) return FEM_OK;
   std::vector<int32_t>& row_ptr = g.row_ptr;
   row_ptr.assign(n + 1, 0);
   for (int32_t i = 0; i < n; ++i) row_ptr[i + 1] = row_ptr[i] + deg[i];
@@ -487,6 +501,9 @@ fem_status fem_create_problem(const fem_problem_desc* d, void* stream, fem_probl
   HostGraph hg;
   HostSat hs;
   fem_status st = FEM_OK;
+  const int64_t dev_min = g_device_build_min_edges.load();
+  const bool device_build = !(d->kind == FEM_MAXCUT && d->dense_J) && kind != FEM_MAXKSAT && dev_min >= 0 &&
+                            d->n_edges >= dev_min && d->n_edges > 0;
   if (d->kind == FEM_MAXCUT && d->dense_J) {
     // symmetric, zero diagonal, integers with |J_ij| <= 127 (exact in bf16 and int8)
     const float* J = d->dense_J;
@@ -501,7 +518,7 @@ fem_status fem_create_problem(const fem_problem_desc* d, void* stream, fem_probl
   } else if (kind == FEM_MAXKSAT) {
     if ((st = host_sat(d, hs)) != FEM_OK) return st;
   } else {
-    if ((st = host_graph(kind, d->q, d, hg)) != FEM_OK) return st;
+    if ((st = host_graph(kind, d->q, d, hg, !device_build)) != FEM_OK) return st;
   }
   // QUBO: the gradient's per-node constant sum_j Q_ij + d_i and the linear terms
   std::vector<float> qoff;
@@ -592,7 +609,9 @@ fem_status fem_create_problem(const fem_problem_desc* d, void* stream, fem_probl
   FEM_CUDA(cudaGetDevice(&p->device));
   FEM_CUDA(cudaDeviceGetAttribute(&p->sm_count, cudaDevAttrMultiProcessorCount, p->device));
   if (d->kind == FEM_MAXCUT && d->dense_J) st = dense_upload(p.get(), d->dense_J, s);
-  else st = kind == FEM_MAXKSAT ? upload_sat(p.get(), hs, s) : upload_graph(p.get(), hg, s);  // internal kind
+  else if (kind == FEM_MAXKSAT) st = upload_sat(p.get(), hs, s);  // internal kind
+  else if (device_build) st = device_graph_build(p.get(), kind, d->q, d, hg.unit, hg.integer, s);
+  else st = upload_graph(p.get(), hg, s);
   p->nodew_sq = nodew_sq;
   if (st == FEM_OK && !nodew.empty()) st = upload(p.get(), &p->nodew, nodew, s);
   if (st == FEM_OK && p->qubo) st = upload(p.get(), &p->qoff, qoff, s);
@@ -838,6 +857,8 @@ fem_status fem_inject_step_stall(fem_problem_t p, int32_t row_tile) {
   p->stall_tile = row_tile;
   return FEM_OK;
 }
+
+void fem_set_device_graph_build(int64_t min_edges) { g_device_build_min_edges.store(min_edges); }
 
 void fem_inject_allocation_failure(int64_t after) { g_fail_alloc_after.store(after < 0 ? -1 : after); }
 

@@ -1,0 +1,340 @@
+// Device construction of a sparse problem's CSR (fem_create_problem for large edge
+// lists).  The host has already validated every edge (indices in range, no
+// self-loops, finite nonzero weights) and computed the weight flags and sums in one
+// linear pass; what costs time on the host - placing 2|E| directed entries and
+// sorting every row - runs here:
+//   1. degrees (atomic counts), 2. an exclusive scan to the row pointers,
+//   3. a scatter of (column << 32 | edge) keys into the rows,
+//   4. a sort of every row by column (one warp per row up to 32 entries, one block
+//      per row up to 4096, the host for the rare longer rows),
+//   5. one pass per row that rejects a repeated column (a duplicate edge) and writes
+//      the packed columns (the +-1 weight in bit 31 when every |w| = 1), the fp32 and
+//      fp64 weights and the row normalisations c_i (MaxCut: 1 / sum_j |W_ij|;
+//      bMinCut: c^f = q / sum_j W_ij, c^a = q / sqrt(sum_j W_ij)).
+// The columns of a row end up in increasing order and every row sum is taken in that
+// order in fp64, exactly as in the host builder, so both give the same arrays bit
+// for bit.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "fem_internal.h"
+
+namespace fem {
+namespace {
+
+constexpr unsigned kMask = 0xffffffffu;
+constexpr int kScanThreads = 256, kScanItems = 8, kScanTile = kScanThreads * kScanItems;
+constexpr int kBlockSortMax = 4096;  // longest row sorted by one block in shared memory
+
+__global__ void k_degrees(const int32_t* __restrict__ ei, const int32_t* __restrict__ ej, int64_t E,
+                          int32_t* __restrict__ deg) {
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < E; e += (long long)gridDim.x * blockDim.x) {
+    atomicAdd(deg + ei[e], 1);
+    atomicAdd(deg + ej[e], 1);
+  }
+}
+
+// Inclusive block scan of one value per thread (256 threads); returns the inclusive
+// prefix and writes the block total to *total.
+__device__ __forceinline__ int32_t block_scan(int32_t x, int32_t* warp_tot, int32_t* total) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int off = 1; off < 32; off <<= 1) {
+    const int32_t y = __shfl_up_sync(kMask, x, off);
+    if (lane >= off) x += y;
+  }
+  if (lane == 31) warp_tot[warp] = x;
+  __syncthreads();
+  if (warp == 0) {
+    int32_t t = lane < kScanThreads / 32 ? warp_tot[lane] : 0;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+      const int32_t y = __shfl_up_sync(kMask, t, off);
+      if (lane >= off) t += y;
+    }
+    if (lane < kScanThreads / 32) warp_tot[lane] = t;
+  }
+  __syncthreads();
+  const int32_t res = x + (warp > 0 ? warp_tot[warp - 1] : 0);
+  if (threadIdx.x == kScanThreads - 1) *total = res;
+  __syncthreads();
+  return res;
+}
+
+// out[i + 1] = sum of in[tile start .. i] for the tile of i; the tile's total to sums[tile].
+__global__ void __launch_bounds__(kScanThreads) k_scan_tiles(const int32_t* __restrict__ in, int32_t n,
+                                                            int32_t* __restrict__ out, int32_t* __restrict__ sums) {
+  __shared__ int32_t warp_tot[kScanThreads / 32];
+  __shared__ int32_t total;
+  const long long base = (long long)blockIdx.x * kScanTile + (long long)threadIdx.x * kScanItems;
+  int32_t v[kScanItems];
+  int32_t run = 0;
+#pragma unroll
+  for (int k = 0; k < kScanItems; ++k) {
+    const long long i = base + k;
+    run += i < n ? in[i] : 0;
+    v[k] = run;
+  }
+  const int32_t incl = block_scan(run, warp_tot, &total);
+  const int32_t before = incl - run;
+#pragma unroll
+  for (int k = 0; k < kScanItems; ++k) {
+    const long long i = base + k;
+    if (i < n) out[i + 1] = v[k] + before;
+  }
+  if (threadIdx.x == 0) sums[blockIdx.x] = total;
+}
+
+// Exclusive scan of the tile totals in place, by one block, 256 at a time with a carry.
+__global__ void __launch_bounds__(kScanThreads) k_scan_sums(int32_t* __restrict__ sums, int32_t nb) {
+  __shared__ int32_t warp_tot[kScanThreads / 32];
+  __shared__ int32_t total;
+  int32_t carry = 0;
+  for (int c0 = 0; c0 < nb; c0 += kScanThreads) {
+    const int i = c0 + threadIdx.x;
+    const int32_t x = i < nb ? sums[i] : 0;
+    const int32_t incl = block_scan(x, warp_tot, &total);
+    if (i < nb) sums[i] = incl - x + carry;
+    carry += total;
+    __syncthreads();
+  }
+}
+
+__global__ void k_scan_add(int32_t* __restrict__ out, int32_t n, const int32_t* __restrict__ sums) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    out[i + 1] += sums[i / kScanTile];
+}
+
+// Each undirected edge e = (i, j) becomes the key (j << 32 | e) in row i and
+// (i << 32 | e) in row j, at a slot taken from the row's cursor.
+__global__ void k_scatter(const int32_t* __restrict__ ei, const int32_t* __restrict__ ej, int64_t E,
+                          int32_t* __restrict__ cursor, unsigned long long* __restrict__ key) {
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < E; e += (long long)gridDim.x * blockDim.x) {
+    const uint32_t i = (uint32_t)ei[e], j = (uint32_t)ej[e];
+    key[atomicAdd(cursor + i, 1)] = ((unsigned long long)j << 32) | (uint32_t)e;
+    key[atomicAdd(cursor + j, 1)] = ((unsigned long long)i << 32) | (uint32_t)e;
+  }
+}
+
+// Rows of up to 32 entries: one warp per row, a bitonic sort across the lanes.  Longer
+// rows are listed for the block sort.
+__global__ void k_sort_rows_warp(const int32_t* __restrict__ row_ptr, int32_t n, unsigned long long* __restrict__ key,
+                                 int32_t* __restrict__ big, int32_t* __restrict__ nbig) {
+  const int lane = threadIdx.x & 31;
+  const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+  for (long long row = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; row < n; row += nwarps) {
+    const int beg = row_ptr[row], len = row_ptr[row + 1] - beg;
+    if (len <= 1) continue;
+    if (len > 32) {
+      if (lane == 0) big[atomicAdd(nbig, 1)] = (int32_t)row;
+      continue;
+    }
+    unsigned long long x = lane < len ? key[beg + lane] : ~0ull;
+#pragma unroll
+    for (int size = 2; size <= 32; size <<= 1) {
+#pragma unroll
+      for (int stride = size >> 1; stride > 0; stride >>= 1) {
+        const unsigned long long y = __shfl_xor_sync(kMask, x, stride);
+        const bool keep_min = ((lane & stride) == 0) == ((lane & size) == 0);
+        x = keep_min ? (x < y ? x : y) : (x < y ? y : x);
+      }
+    }
+    if (lane < len) key[beg + lane] = x;
+  }
+}
+
+// Rows of 33 .. kBlockSortMax entries: one block per row, a bitonic sort in shared
+// memory over the next power of two.  Longer rows are listed for the host.
+__global__ void __launch_bounds__(512) k_sort_rows_block(const int32_t* __restrict__ row_ptr,
+                                                         unsigned long long* __restrict__ key,
+                                                         const int32_t* __restrict__ big, const int32_t* __restrict__ nbig,
+                                                         int32_t* __restrict__ giant, int32_t* __restrict__ ngiant) {
+  __shared__ unsigned long long sk[kBlockSortMax];
+  const int nb = *nbig;
+  for (int b = blockIdx.x; b < nb; b += gridDim.x) {
+    const int row = big[b];
+    const int beg = row_ptr[row], len = row_ptr[row + 1] - beg;
+    if (len > kBlockSortMax) {
+      if (threadIdx.x == 0) giant[atomicAdd(ngiant, 1)] = row;
+      continue;
+    }
+    int P = 64;
+    while (P < len) P <<= 1;
+    for (int k = threadIdx.x; k < P; k += blockDim.x) sk[k] = k < len ? key[beg + k] : ~0ull;
+    __syncthreads();
+    for (int size = 2; size <= P; size <<= 1) {
+      for (int stride = size >> 1; stride > 0; stride >>= 1) {
+        for (int k = threadIdx.x; k < P; k += blockDim.x) {
+          const int partner = k ^ stride;
+          if (partner > k) {
+            const bool asc = (k & size) == 0;
+            const unsigned long long a = sk[k], c = sk[partner];
+            if ((a > c) == asc) {
+              sk[k] = c;
+              sk[partner] = a;
+            }
+          }
+        }
+        __syncthreads();
+      }
+    }
+    for (int k = threadIdx.x; k < len; k += blockDim.x) key[beg + k] = sk[k];
+    __syncthreads();
+  }
+}
+
+// One thread per row: duplicate check, packed columns, weights, row normalisations.
+// dup[0] is set (and dup[1], dup[2] name the pair) when a row repeats a column.
+__global__ void k_finish_rows(const int32_t* __restrict__ row_ptr, const unsigned long long* __restrict__ key,
+                              int32_t n, const double* __restrict__ w, int32_t unit, int32_t integer, int32_t kind,
+                              int32_t q, uint32_t* __restrict__ col, float* __restrict__ wf, double* __restrict__ w64,
+                              float* __restrict__ cnorm, float* __restrict__ cnorm2, int32_t* __restrict__ dup) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    double rsum = 0.0, rabs = 0.0;
+    uint32_t prev = 0xffffffffu;
+    for (int k = row_ptr[i]; k < row_ptr[i + 1]; ++k) {
+      const unsigned long long kk = key[k];
+      const uint32_t j = (uint32_t)(kk >> 32);
+      const double wt = w ? w[(uint32_t)kk] : 1.0;
+      if (j == prev && atomicCAS(dup, 0, 1) == 0) {
+        dup[1] = (int32_t)i;
+        dup[2] = (int32_t)j;
+      }
+      prev = j;
+      col[k] = j | ((unit && wt < 0.0) ? 0x80000000u : 0u);
+      if (!unit) wf[k] = (float)wt;
+      if (!integer) w64[k] = wt;
+      rsum += wt;
+      rabs += fabs(wt);
+    }
+    if (kind == FEM_MAXCUT) {
+      if (!unit) cnorm[i] = rabs > 0.0 ? (float)(1.0 / rabs) : 0.f;
+    } else {
+      cnorm[i] = rsum > 0.0 ? (float)((double)q / rsum) : 0.f;
+      cnorm2[i] = rsum > 0.0 ? (float)((double)q / sqrt(rsum)) : 0.f;
+    }
+  }
+}
+
+int grid_for(long long work, int sm_count, int threads = 256) {
+  long long b = (work + threads - 1) / threads;
+  const long long cap = (long long)sm_count * 8;
+  if (b > cap) b = cap;
+  return (int)(b < 1 ? 1 : b);
+}
+
+}  // namespace
+
+fem_status device_graph_build(Problem* p, int32_t kind, int32_t q, const fem_problem_desc* d, bool unit, bool integer,
+                              cudaStream_t s) {
+  const int32_t n = d->n;
+  const int64_t E = d->n_edges, nnz = 2 * E;
+  p->n_edges = E;
+  p->nnz = nnz;
+  p->unit_w = unit;
+  p->int_w = integer;
+  fem_status st;
+  if ((st = dev_alloc_t(p, &p->row_ptr, (size_t)n + 1)) != FEM_OK) return st;
+  if ((st = dev_alloc_t(p, &p->col, (size_t)nnz)) != FEM_OK) return st;
+  if (!unit && (st = dev_alloc_t(p, &p->w, (size_t)nnz)) != FEM_OK) return st;
+  if (!integer && (st = dev_alloc_t(p, &p->w64, (size_t)nnz)) != FEM_OK) return st;
+  const bool need_c = kind != FEM_MAXCUT || !unit;
+  if (need_c && (st = dev_alloc_t(p, &p->cnorm, (size_t)n)) != FEM_OK) return st;
+  if (kind != FEM_MAXCUT && (st = dev_alloc_t(p, &p->cnorm2, (size_t)n)) != FEM_OK) return st;
+
+  // scratch of the build, stream-ordered and released at the end
+  const int ntiles = (int)((n + kScanTile - 1) / kScanTile);
+  int32_t *ei = nullptr, *ej = nullptr, *deg = nullptr, *sums = nullptr, *cursor = nullptr, *big = nullptr,
+          *counters = nullptr;
+  double* w = nullptr;
+  unsigned long long* key = nullptr;
+  std::vector<void*> tmp;
+  auto talloc = [&](void** ptr, size_t bytes) -> fem_status {
+    const cudaError_t e = cudaMallocAsync(ptr, bytes < 16 ? 16 : bytes, s);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      *ptr = nullptr;
+      return fail(FEM_ERR_OOM, "device graph build: %zu bytes of scratch", bytes);
+    }
+    tmp.push_back(*ptr);
+    return FEM_OK;
+  };
+  auto release = [&]() {
+    for (void* x : tmp) cudaFreeAsync(x, s);
+    tmp.clear();
+  };
+  st = FEM_OK;
+  if (st == FEM_OK) st = talloc((void**)&ei, sizeof(int32_t) * (size_t)E);
+  if (st == FEM_OK) st = talloc((void**)&ej, sizeof(int32_t) * (size_t)E);
+  if (st == FEM_OK && d->w) st = talloc((void**)&w, sizeof(double) * (size_t)E);
+  if (st == FEM_OK) st = talloc((void**)&deg, sizeof(int32_t) * (size_t)n);
+  if (st == FEM_OK) st = talloc((void**)&sums, sizeof(int32_t) * (size_t)ntiles);
+  if (st == FEM_OK) st = talloc((void**)&cursor, sizeof(int32_t) * (size_t)n);
+  if (st == FEM_OK) st = talloc((void**)&big, sizeof(int32_t) * (size_t)n);
+  if (st == FEM_OK) st = talloc((void**)&counters, sizeof(int32_t) * 8);  // nbig, ngiant, dup[3]
+  if (st == FEM_OK) st = talloc((void**)&key, sizeof(unsigned long long) * (size_t)nnz);
+  if (st != FEM_OK) {
+    release();
+    return st;
+  }
+  int32_t* giant = cursor;  // the cursors are spent once the keys are placed
+  cudaError_t e = cudaSuccess;
+  auto step = [&](cudaError_t x) {
+    if (e == cudaSuccess) e = x;
+  };
+  step(cudaMemcpyAsync(ei, d->ei, sizeof(int32_t) * (size_t)E, cudaMemcpyHostToDevice, s));
+  step(cudaMemcpyAsync(ej, d->ej, sizeof(int32_t) * (size_t)E, cudaMemcpyHostToDevice, s));
+  if (d->w) step(cudaMemcpyAsync(w, d->w, sizeof(double) * (size_t)E, cudaMemcpyHostToDevice, s));
+  step(cudaMemsetAsync(deg, 0, sizeof(int32_t) * (size_t)n, s));
+  step(cudaMemsetAsync(counters, 0, sizeof(int32_t) * 8, s));
+  step(cudaMemsetAsync(p->row_ptr, 0, sizeof(int32_t), s));
+  if (e == cudaSuccess) {
+    const int sm = p->sm_count;
+    k_degrees<<<grid_for(E, sm), 256, 0, s>>>(ei, ej, E, deg);
+    k_scan_tiles<<<ntiles, kScanThreads, 0, s>>>(deg, n, p->row_ptr, sums);
+    k_scan_sums<<<1, kScanThreads, 0, s>>>(sums, ntiles);
+    k_scan_add<<<grid_for(n, sm), 256, 0, s>>>(p->row_ptr, n, sums);
+    step(cudaMemcpyAsync(cursor, p->row_ptr, sizeof(int32_t) * (size_t)n, cudaMemcpyDeviceToDevice, s));
+    k_scatter<<<grid_for(E, sm), 256, 0, s>>>(ei, ej, E, cursor, key);
+    k_sort_rows_warp<<<grid_for((long long)n * 32, sm), 256, 0, s>>>(p->row_ptr, n, key, big, counters);
+    k_sort_rows_block<<<sm * 2, 512, 0, s>>>(p->row_ptr, key, big, counters, giant, counters + 1);
+    count_launches(7);
+    step(cudaGetLastError());
+  }
+  // rows longer than the block sort handles (rare hubs) are sorted on the host
+  int32_t ngiant = 0;
+  if (e == cudaSuccess) step(cudaMemcpyAsync(&ngiant, counters + 1, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+  if (e == cudaSuccess) step(cudaStreamSynchronize(s));
+  if (e == cudaSuccess && ngiant > 0) {
+    std::vector<int32_t> rows(ngiant);
+    step(cudaMemcpy(rows.data(), giant, sizeof(int32_t) * (size_t)ngiant, cudaMemcpyDeviceToHost));
+    std::vector<unsigned long long> seg;
+    for (int32_t r : rows) {
+      if (e != cudaSuccess) break;
+      int32_t be[2];
+      step(cudaMemcpy(be, p->row_ptr + r, sizeof(be), cudaMemcpyDeviceToHost));
+      seg.resize((size_t)(be[1] - be[0]));
+      step(cudaMemcpy(seg.data(), key + be[0], seg.size() * sizeof(unsigned long long), cudaMemcpyDeviceToHost));
+      std::sort(seg.begin(), seg.end());
+      step(cudaMemcpy(key + be[0], seg.data(), seg.size() * sizeof(unsigned long long), cudaMemcpyHostToDevice));
+    }
+  }
+  int32_t dup[3] = {0, 0, 0};
+  if (e == cudaSuccess) {
+    k_finish_rows<<<grid_for(n, p->sm_count), 256, 0, s>>>(p->row_ptr, key, n, w, unit ? 1 : 0, integer ? 1 : 0, kind, q,
+                                                           p->col, p->w, p->w64, p->cnorm, p->cnorm2, counters + 2);
+    count_launches(1);
+    step(cudaGetLastError());
+    if (e == cudaSuccess) step(cudaMemcpyAsync(dup, counters + 2, sizeof(dup), cudaMemcpyDeviceToHost, s));
+  }
+  release();
+  if (e == cudaSuccess) step(cudaStreamSynchronize(s));
+  if (e != cudaSuccess) return cuda_fail(e, "device graph build");
+  if (dup[0]) return fail(FEM_ERR_INVALID_ARG, "duplicate edge (%d, %d)", dup[1], dup[2]);
+  return FEM_OK;
+}
+
+}  // namespace fem

@@ -83,6 +83,7 @@ def _load():
         "fem_inject_step_stall": (S, [P, C.c_int32]),
         "fem_anneal_batch": (S, [P, C.c_int32, C.POINTER(fem_anneal_params), P, P]),
         "fem_inject_allocation_failure": (None, [C.c_int64]),
+        "fem_set_device_graph_build": (None, [C.c_int64]),
         "fem_destroy": (None, [P]),
         "fem_status_string": (C.c_char_p, [S]),
         "fem_last_error": (C.c_char_p, []),
@@ -205,6 +206,11 @@ def fem_set_step_barrier_timeout(handle, ns):
 def fem_inject_step_stall(handle, row_tile):
     """The persistent dense kernel's CTAs of `row_tile` stop reporting ready (-1: off)."""
     _check(_lib.fem_inject_step_stall(handle, int(row_tile)), "fem_inject_step_stall")
+
+
+def fem_set_device_graph_build(min_edges):
+    """Graphs with at least min_edges edges build their CSR on the device (< 0: never)."""
+    _lib.fem_set_device_graph_build(int(min_edges))
 
 
 def fem_inject_allocation_failure(after):

@@ -70,6 +70,18 @@ WORKLOADS = {
                                              "0.05->5, Adam lr 0.1, paper-mode gradient",
                       n_lo=20000, n_hi=200000, deg=8.0, R=32, n_steps=2000, n_train=64, n_held=16, epochs=3,
                       lr=3e-3, rms=0.1, train_seed=31, held_seed=32, h_seed=33),
+    # the learned warm start at the full configuration: 2000 training and 100 held-out graphs
+    "warmstart_full": dict(kind="warmstart", name="learned warm start, full configuration: MaxCut on ER graphs, n "
+                                                  "log-uniform 20k-200k, mean degree 8, +-1 weights, R=32, 2000-step "
+                                                  "exponential beta 0.05->5, Adam lr 0.1, paper-mode gradient; 2000 "
+                                                  "training and 100 held-out graphs",
+                           n_lo=20000, n_hi=200000, deg=8.0, R=32, n_steps=2000, n_train=2000, n_held=100, epochs=2,
+                           lr=3e-3, rms=0.1, train_seed=31, held_seed=32, h_seed=33),
+    # the warm-start network's inference (fem_mpnn_predict) on the largest graph of the range
+    "mpnn": dict(kind="mpnn", name="warm-start network inference: 3 message-passing layers of width 64 (bf16 weights, "
+                                   "fp32 activations) and a 4-tap head on ER n=200000, mean degree 8, +-1 weights, "
+                                   "R=32 replicas of initial fields, rescaled to rms 0.1",
+                 n=200000, m=800000, R=32, graph_seed=34, h_seed=35, n_steps=1),
     # the batched workload at 1/8 scale (same size distributions): the case profiled in detail
     "batched_small": dict(kind="batched", name="batched heterogeneous at 1/8 scale: 32 bMinCut (random geometric "
                                               "graphs, n log-uniform 1k-64k, mean degree 10, unit weights, q=4) + 8 "
@@ -445,7 +457,7 @@ class ClockSampler:
     """nvidia-smi clocks / throttle reasons sampled during the timed region."""
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
-         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap,utilization.gpu")
 
     def __init__(self, index):
         self.index = index
@@ -473,22 +485,30 @@ class ClockSampler:
         return False
 
     def summary(self):
-        sm, mx, reasons = [], None, set()
+        """Median SM clock over the samples taken while the GPU was busy (utilisation
+        >= 50%; all samples if none was), the maximum clock, and every throttle reason
+        seen in any sample."""
+        sm, busy, mx, reasons = [], [], None, set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         for line in (self.out or "").strip().splitlines():
             f = [x.strip() for x in line.split(",")]
-            if len(f) < 9:
+            if len(f) < 10:
                 continue
             try:
-                sm.append(float(f[1]))
+                clk = float(f[1])
                 mx = float(f[2])
+                util = float(f[9])
             except ValueError:
                 continue
+            sm.append(clk)
+            if util >= 50.0:
+                busy.append(clk)
             for k, nm in enumerate(names):
                 if f[5 + k].lower().startswith("active"):
                     reasons.add(nm)
-        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
-                "reasons": sorted(reasons), "samples": len(sm)}
+        pick = busy or sm
+        return {"sm_mhz": statistics.median(pick) if pick else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm), "samples_busy": len(busy)}
 
 
 def _dist():
@@ -826,6 +846,10 @@ def run_ttt(args, wl):
     line = {"metric": "time-to-target-cut", "unit": "ms", "higher_is_better": False, "n_gpus": 1,
             "data": "synthetic", "config": {"workload": wl["name"], "target": "plain FP32 FEM best cut at the full "
                                             "budget, within 0.1%"}}
+    pool = None
+    if wl["kind"] == "warmstart" and wl["n_train"] + wl["n_held"] > 200:
+        import multiprocessing as mp   # graph generation on every host core (spawned processes)
+        pool = mp.get_context("spawn").Pool(_host_cores())
     clk = ClockSampler(0)
     clk.__enter__()
     if wl["kind"] == "dense":
@@ -890,10 +914,8 @@ def run_ttt(args, wl):
     else:
         from paper_2412_09285_b300 import warmstart as ws
         R, rms = wl["R"], wl["rms"]
-        t_gen, (train, held) = _timed(lambda: (ws.make_graphs(wl["n_train"], wl["n_lo"], wl["n_hi"], wl["deg"],
-                                                              seed=wl["train_seed"]),
-                                               ws.make_graphs(wl["n_held"], wl["n_lo"], wl["n_hi"], wl["deg"],
-                                                              seed=wl["held_seed"])))
+        gen = lambda cnt, seed: ws.make_graphs(cnt, wl["n_lo"], wl["n_hi"], wl["deg"], seed=seed, pool=pool)
+        t_gen, (train, held) = _timed(lambda: (gen(wl["n_train"], wl["train_seed"]), gen(wl["n_held"], wl["held_seed"])))
         net = ws.Mpnn(seed=1)
         t_train, losses = _timed(lambda: ws.train(net, train, wl["epochs"], R, N, lr=wl["lr"], seed=wl["h_seed"]))
         budgets = [N // 8, N // 4, N // 2, N]
@@ -931,11 +953,78 @@ def run_ttt(args, wl):
                          "train_s": t_train / 1e3, "generate_s": t_gen / 1e3, "held_out": len(held)}
         line["value"] = line["time_to_target"]["warm"]["fast_ms_mean_over_reached"]
     clk.__exit__(None, None, None)
+    if pool is not None:
+        pool.close()
     line["clocks"] = clk.summary()
     line["e2e"] = {"note": "every time is the wall time of the user calls (fem_anneal + fem_read_best) with "
                            + ("initial fields from pinned host memory and the best states read to the host"
                               if wl["kind"] != "warmstart" else "fields on the device and the best energy to the host")}
     print(json.dumps(line))
+
+
+def mpnn_algorithmic_bytes(n, nnz, R, width=64, feats=4, taps=4):
+    """Bytes of one fem_mpnn_predict when every array is read or written once: the CSR
+    (once per propagation), the features, three layers (propagation + dense update),
+    the head, the taps of P^k z and the output with its rescaling."""
+    csr = 4 * (n + 1) + 4 * nnz
+    b = csr + 4 * n * feats                                   # features
+    for din in (feats, width, width):
+        b += csr + 4 * n * din + 4 * n * din                  # a = P x: read x, write a
+        b += 4 * n * din * 2 + 4 * n * width                  # x' = tanh(x A + a B + b)
+    b += 4 * n * width + 4 * n * taps                         # head
+    b += 8 * n * R                                            # u_0 = z
+    b += (taps - 1) * (csr + 8 * n * R)                       # u_k = P u_(k-1)
+    b += 4 * n * taps + taps * 4 * n * R + 4 * n * R          # y = sum_k theta_k u_k
+    b += 3 * 4 * n * R                                        # rms rescaling
+    return b
+
+
+def run_mpnn(args, wl):
+    """Inference time of the warm-start network, against the HBM roofline of its
+    algorithmic bytes (one JSON line)."""
+    import torch
+    from paper_2412_09285_b300 import fem
+    from paper_2412_09285_b300 import instances as I
+    from paper_2412_09285_b300 import warmstart as ws
+    dev = torch.device("cuda")
+    g = I.er_gnm(wl["n"], wl["m"], seed=wl["graph_seed"], weights="pm1")
+    R = wl["R"]
+    P = fem.Problem("maxcut", graph=g)
+    net = ws.Mpnn(seed=1)
+    z = torch.from_numpy(I.initial_fields(g.n, R, seed=wl["h_seed"]) * np.float32(1000.0)).to(dev)
+    y = torch.empty_like(z)
+    stream = torch.cuda.current_stream()
+    K = args.steps or 50
+    for _ in range(max(3, args.warmup)):
+        net.predict(P, z, R, y, rms=0.1)
+    torch.cuda.synchronize()
+    l0 = fem.fem_kernel_launches()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(0) as clk:
+        e0.record(stream)
+        for _ in range(K):
+            net.predict(P, z, R, y, rms=0.1)
+        e1.record(stream)
+        torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / K
+    launches = fem.fem_kernel_launches() - l0
+    peaks, src = _peaks()
+    alg = mpnn_algorithmic_bytes(g.n, 2 * g.n_edges, R)
+    ach = alg / (ms / 1e3) / 1e9
+    flops = 2 * g.n * (4 * 64 * 2 + 64 * 64 * 2 * 2) + 2 * g.n * 64 * 4
+    line = {"metric": "mpnn-predict edge*replica/s", "value": g.n_edges * R / (ms / 1e3),
+            "unit": "edge*replica/s", "n_gpus": 1, "steps": K, "warmup": max(3, args.warmup), "ms_per_step": ms,
+            "higher_is_better": True, "dtype": "bf16 weights, f32 activations", "data": "synthetic",
+            "config": {"workload": wl["name"], "n": g.n, "edges": g.n_edges, "replicas": R},
+            "roofline": {"bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                         "frac": ach / peaks["hbm_gbs"], "traffic": None, "kernel": "fem_mpnn_predict (all launches)",
+                         "algorithmic_bytes_per_call": alg, "dense_flops_per_call": flops,
+                         "peak_source": f"{src} hbm_gbs (copy), of {src}",
+                         "note": "the layer products are n x 64 x 64 (about 7 GFLOP per call at n = 2e5, "
+                                 "90 us at the CUDA cores' FP32 FMA peak, 4 us on the tensor cores) against "
+                                 "about 1.1 GB of memory passes (170 us at the copy peak): memory-bound"},
+            "gpu_launches": int(launches), "launches_per_call": launches / K, "clocks": clk.summary()}
+    print(json.dumps(line), flush=True)
 
 
 def main():
@@ -962,6 +1051,9 @@ def main():
     wl = WORKLOADS[args.workload]
     if args.ttt or wl["kind"] == "warmstart":
         run_ttt(args, wl)
+        return
+    if wl["kind"] == "mpnn":
+        run_mpnn(args, wl)
         return
     if args.steps is None:
         args.steps = wl["n_steps"]

@@ -297,7 +297,11 @@ void fem_batch_destroy(fem_batch_t b);
  *   rms (fem_mpnn_predict): 0 returns y as is; rms > 0 rescales every replica's
  *   column to root-mean-square rms, y_ir * rms / sqrt(mean_i y_ir^2) (the network
  *   fixes the direction of the warm start, the caller its magnitude; an all-zero
- *   column stays zero).  FEM_ERR_INVALID_ARG for rms < 0 or NaN. */
+ *   column stays zero).  FEM_ERR_INVALID_ARG for rms < 0 or NaN.
+ * A network keeps a device workspace for its activations, grown to the largest call
+ * so far (a call that needs more allocates the rest stream-ordered and the workspace
+ * is grown when it ends, a step that waits for the device); calls on one network must
+ * not overlap on the GPU. */
 typedef struct fem_mpnn* fem_mpnn_t;
 int32_t fem_mpnn_num_params(void);
 fem_status fem_mpnn_create(const float* params_host, fem_mpnn_t* out);

@@ -265,13 +265,36 @@ __device__ __forceinline__ void bmincut_element(const BmcArgs& a, const StepScal
         // accumulate sum_j W_ij (P_j(s) - 1/q): the constant drops out of every
         // difference below.  Each neighbour's q (P_j(s) - 1/q) (centred_q) was written
         // by the step that produced h_j, once per node rather than once per edge.
-        for (int k = beg; k < end; ++k) {
-          const uint32_t j = a.col[k] & 0x7fffffffu;
-          const float wk = a.w ? a.w[k] : 1.f;
-          float dj[Q];
-          load_q<Q>(a.d_in + ((size_t)j * a.R + r) * Q, dj);
+        // G neighbours at a time: their column loads, then their gathers, then the sums
+        // in neighbour order (the same arithmetic as one at a time), so a thread waits
+        // for two memory round trips per G neighbours instead of two per neighbour
+        constexpr int G = Q <= 4 ? 4 : 2;
+        for (int k0 = beg; k0 < end; k0 += G) {
+          uint32_t jj[G];
+          float wkk[G];
 #pragma unroll
-          for (int q = 0; q < Q; ++q) acc[q] = fmaf(wk, dj[q] * (1.f / Q), acc[q]);
+          for (int u = 0; u < G; ++u) {
+            const bool ok = k0 + u < end;
+            jj[u] = ok ? (a.col[k0 + u] & 0x7fffffffu) : 0u;
+            wkk[u] = ok && a.w ? a.w[k0 + u] : 1.f;
+          }
+          float dj[G][Q];
+#pragma unroll
+          for (int u = 0; u < G; ++u) {
+            if (k0 + u < end) {
+              load_q<Q>(a.d_in + ((size_t)jj[u] * a.R + r) * Q, dj[u]);
+            } else {
+#pragma unroll
+              for (int q = 0; q < Q; ++q) dj[u][q] = 0.f;
+            }
+          }
+#pragma unroll
+          for (int u = 0; u < G; ++u) {
+            if (k0 + u < end) {
+#pragma unroll
+              for (int q = 0; q < Q; ++q) acc[q] = fmaf(wkk[u], dj[u][q] * (1.f / Q), acc[q]);
+            }
+          }
         }
       }
     }

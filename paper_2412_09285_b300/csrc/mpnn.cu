@@ -62,44 +62,86 @@ __global__ void k_feats(Graph g, float mean_deg, float* __restrict__ x0) {
 }
 
 // out = P X (transpose = 0) or P^T X = W D^-1 X (transpose = 1); X is [n][F].
-// One warp per node; lanes stride over the F features.
-__global__ void k_spmm(Graph g, const float* __restrict__ X, int F, int transpose, float* __restrict__ out) {
+// One warp per node; a lane holds two features (f and f + 32) of a 64-feature chunk.
+// The node's column indices are loaded 32 at a time (one coalesced load) and eight
+// neighbours' rows are gathered before any is added, so a warp waits for one memory
+// round trip per eight neighbours; the sums keep the neighbour order.
+constexpr int kSpmmGather = 8;
+
+template <bool TRANSPOSE>
+__global__ void __launch_bounds__(256) k_spmm(Graph g, const float* __restrict__ X, int F,
+                                              float* __restrict__ out) {
+  constexpr bool transpose = TRANSPOSE;
   const int lane = threadIdx.x & 31;
   for (int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < g.n; i += (gridDim.x * blockDim.x) >> 5) {
     const int b = g.row_ptr[i], e = g.row_ptr[i + 1];
-    for (int f0 = 0; f0 < F; f0 += 32) {
-      const int f = f0 + lane;
-      float acc = 0.f;
-      if (f < F) {
-        for (int k = b; k < e; ++k) {
-          const uint32_t c = g.col[k];
-          const int j = (int)(c & 0x7fffffffu);
-          float x = X[(size_t)j * F + f];
+    for (int f0 = 0; f0 < F; f0 += 64) {
+      const int fa = f0 + lane, fb = f0 + 32 + lane;
+      float acc_a = 0.f, acc_b = 0.f;
+      for (int k0 = b; k0 < e; k0 += 32) {
+        const int kk = k0 + lane;
+        uint32_t c = 0;
+        float wk = 0.f, dk = 1.f;
+        if (kk < e) {
+          c = g.col[kk];
+          wk = edge_w(g, kk, c);
           if (transpose) {
-            const int dj = g.row_ptr[j + 1] - g.row_ptr[j];
-            x = dj > 0 ? x / (float)dj : 0.f;
+            const int j = (int)(c & 0x7fffffffu);
+            dk = (float)(g.row_ptr[j + 1] - g.row_ptr[j]);
           }
-          acc = fmaf(edge_w(g, k, c), x, acc);
         }
-        if (!transpose) acc = (e > b) ? acc / (float)(e - b) : 0.f;
-        out[(size_t)i * F + f] = acc;
+        const int cnt = min(32, e - k0);
+        for (int u0 = 0; u0 < cnt; u0 += kSpmmGather) {
+          float xa[kSpmmGather], xb[kSpmmGather];
+#pragma unroll
+          for (int u = 0; u < kSpmmGather; ++u) {
+            const int j = (int)(__shfl_sync(kFullMask, c, u0 + u) & 0x7fffffffu);
+            const bool ok = u0 + u < cnt;
+            xa[u] = ok && fa < F ? X[(size_t)j * F + fa] : 0.f;
+            xb[u] = ok && fb < F ? X[(size_t)j * F + fb] : 0.f;
+          }
+#pragma unroll
+          for (int u = 0; u < kSpmmGather; ++u) {
+            if (u0 + u < cnt) {
+              const float w = __shfl_sync(kFullMask, wk, u0 + u);
+              float x1 = xa[u], x2 = xb[u];
+              if (transpose) {
+                const float dj = __shfl_sync(kFullMask, dk, u0 + u);
+                x1 = dj > 0.f ? x1 / dj : 0.f;
+                x2 = dj > 0.f ? x2 / dj : 0.f;
+              }
+              acc_a = fmaf(w, x1, acc_a);
+              acc_b = fmaf(w, x2, acc_b);
+            }
+          }
+        }
       }
+      if (!transpose) {
+        acc_a = (e > b) ? acc_a / (float)(e - b) : 0.f;
+        acc_b = (e > b) ? acc_b / (float)(e - b) : 0.f;
+      }
+      if (fa < F) out[(size_t)i * F + fa] = acc_a;
+      if (fb < F) out[(size_t)i * F + fb] = acc_b;
     }
   }
 }
 
-// x_out = tanh(x_in A + a B + b): 32 nodes per block, thread = (output o, 8 nodes).
+// x_out = tanh(x_in A + a B + b): 32 nodes per block; thread = (4 consecutive outputs,
+// 2 nodes 16 apart), so every shared-memory load of the weights (float4) and of the
+// inputs (broadcast) feeds 4 or 8 multiply-adds.
 __global__ void __launch_bounds__(256) k_layer_fwd(const float* __restrict__ x_in, const float* __restrict__ a,
                                                    int n, int din, const __nv_bfloat16* __restrict__ wts, int l,
                                                    float* __restrict__ x_out) {
-  __shared__ float sA[kH * kH], sB[kH * kH];
+  __shared__ __align__(16) float sA[kH * kH], sB[kH * kH];
   __shared__ float sx[32][kH], sa[32][kH];
   for (int t = threadIdx.x; t < din * kH; t += blockDim.x) {
     sA[t] = __bfloat162float(wts[off_A(l) + t]);
     sB[t] = __bfloat162float(wts[off_B(l) + t]);
   }
-  const int o = threadIdx.x & (kH - 1), ng = threadIdx.x >> 6;
-  const float bo = __bfloat162float(wts[off_b(l) + o]);
+  const int o4 = (threadIdx.x & 15) * 4, ng = threadIdx.x >> 4;
+  float bo[4];
+#pragma unroll
+  for (int c = 0; c < 4; ++c) bo[c] = __bfloat162float(wts[off_b(l) + o4 + c]);
   for (int i0 = blockIdx.x * 32; i0 < n; i0 += gridDim.x * 32) {
     __syncthreads();
     for (int t = threadIdx.x; t < 32 * din; t += blockDim.x) {
@@ -108,10 +150,33 @@ __global__ void __launch_bounds__(256) k_layer_fwd(const float* __restrict__ x_i
       sa[r][p] = i < n ? a[(size_t)i * din + p] : 0.f;
     }
     __syncthreads();
-    for (int r = ng; r < 32; r += 4) {
-      float acc = bo;
-      for (int p = 0; p < din; ++p) acc = fmaf(sx[r][p], sA[p * kH + o], fmaf(sa[r][p], sB[p * kH + o], acc));
-      if (i0 + r < n) x_out[(size_t)(i0 + r) * kH + o] = tanhf(acc);
+    float acc[2][4];
+#pragma unroll
+    for (int h = 0; h < 2; ++h)
+#pragma unroll
+      for (int c = 0; c < 4; ++c) acc[h][c] = bo[c];
+    for (int p = 0; p < din; ++p) {
+      const float4 wa = *reinterpret_cast<const float4*>(&sA[p * kH + o4]);
+      const float4 wb = *reinterpret_cast<const float4*>(&sB[p * kH + o4]);
+      const float wav[4] = {wa.x, wa.y, wa.z, wa.w}, wbv[4] = {wb.x, wb.y, wb.z, wb.w};
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const float xv = sx[ng + 16 * h][p], av = sa[ng + 16 * h][p];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) acc[h][c] = fmaf(xv, wav[c], fmaf(av, wbv[c], acc[h][c]));
+      }
+    }
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int i = i0 + ng + 16 * h;
+      if (i < n) {
+        float4 y;
+        y.x = tanhf(acc[h][0]);
+        y.y = tanhf(acc[h][1]);
+        y.z = tanhf(acc[h][2]);
+        y.w = tanhf(acc[h][3]);
+        *reinterpret_cast<float4*>(&x_out[(size_t)i * kH + o4]) = y;
+      }
     }
   }
 }
@@ -345,6 +410,11 @@ struct Mpnn {
   __nv_bfloat16* wb = nullptr;
   int64_t steps = 0;
   int sm_count = 148;
+  // workspace of a call's activations, grown to the largest call so far (a call that
+  // needs more takes stream-ordered allocations for the rest, and the next call finds
+  // the workspace grown); calls on one network must not overlap on the GPU
+  uint8_t* arena = nullptr;
+  size_t arena_cap = 0;
 };
 
 namespace {
@@ -362,18 +432,40 @@ struct Pass {
   float *theta = nullptr, *u = nullptr, *dtheta = nullptr, *loss_node = nullptr;
   // backward scratch
   float *dx = nullptr, *dx_in = nullptr, *da = nullptr, *tmp = nullptr, *part = nullptr;
+  Mpnn* net = nullptr;
+  size_t used = 0;  // bytes of the network's workspace handed out in this call
   std::vector<void*> mine;
 };
 
 fem_status pass_alloc(Pass& ps, void** p, size_t bytes, cudaStream_t s) {
-  FEM_CUDA(cudaMallocAsync(p, bytes, s));
-  ps.mine.push_back(*p);
+  const size_t need = (bytes + 255) & ~(size_t)255;
+  if (ps.net && ps.used + need <= ps.net->arena_cap) {
+    *p = ps.net->arena + ps.used;
+  } else {
+    FEM_CUDA(cudaMallocAsync(p, bytes, s));
+    ps.mine.push_back(*p);
+  }
+  ps.used += need;
   return FEM_OK;
 }
 
 void pass_free(Pass& ps, cudaStream_t s) {
   for (void* p : ps.mine) cudaFreeAsync(p, s);
   ps.mine.clear();
+  // grow the workspace to this call's size for the next call (cudaFree waits for the
+  // device, so no queued kernel still reads the old one)
+  if (ps.net && ps.used > ps.net->arena_cap) {
+    if (ps.net->arena) cudaFree(ps.net->arena);
+    ps.net->arena = nullptr;
+    ps.net->arena_cap = 0;
+    void* p = nullptr;
+    if (cudaMalloc(&p, ps.used) == cudaSuccess) {
+      ps.net->arena = (uint8_t*)p;
+      ps.net->arena_cap = ps.used;
+    } else {
+      cudaGetLastError();  // without a workspace the next call allocates again
+    }
+  }
 }
 
 // Forward pass; with m_t also the loss terms and dL/dtheta.
@@ -395,13 +487,13 @@ fem_status forward(const Mpnn* net, const Problem* pr, const float* z, int R, co
   k_feats<<<blocks_for(n, sm), 256, 0, s>>>(g, mean_deg > 0.f ? mean_deg : 1.f, ps.x[0]);
   for (int l = 1; l <= 3; ++l) {
     const int din = l == 1 ? kF0 : kH;
-    k_spmm<<<wb_nodes, 256, 0, s>>>(g, ps.x[l - 1], din, 0, ps.a[l]);
+    k_spmm<false><<<wb_nodes, 256, 0, s>>>(g, ps.x[l - 1], din, ps.a[l]);
     k_layer_fwd<<<blocks_for((size_t)n * 8, sm), 256, 0, s>>>(ps.x[l - 1], ps.a[l], n, din, net->wb, l, ps.x[l]);
   }
   k_head<<<blocks_for((size_t)n * kTaps, sm), 256, 0, s>>>(ps.x[3], n, net->wb, ps.theta);
   FEM_CUDA(cudaMemcpyAsync(ps.u, z, (size_t)n * R * 4, cudaMemcpyDeviceToDevice, s));
   for (int k = 1; k < kTaps; ++k)
-    k_spmm<<<wb_nodes, 256, 0, s>>>(g, ps.u + (size_t)(k - 1) * n * R, R, 0, ps.u + (size_t)k * n * R);
+    k_spmm<false><<<wb_nodes, 256, 0, s>>>(g, ps.u + (size_t)(k - 1) * n * R, R, ps.u + (size_t)k * n * R);
   if (m_t) {
     if ((st = pass_alloc(ps, (void**)&ps.dtheta, (size_t)n * kTaps * 4, s)) != FEM_OK) return st;
     if ((st = pass_alloc(ps, (void**)&ps.loss_node, (size_t)n * 4, s)) != FEM_OK) return st;
@@ -445,7 +537,7 @@ fem_status backward(Mpnn* net, const Problem* pr, Pass& ps, cudaStream_t s) {
     launches += 7;
     if (l > 1) {
       k_layer_bwd_dx<<<blocks_for((size_t)n * 8, sm), 256, 0, s>>>(ps.dx, n, din, net->wb, l, ps.dx_in, ps.da);
-      k_spmm<<<blocks_for((size_t)n * 32, sm), 256, 0, s>>>(g, ps.da, din, 1, ps.tmp);
+      k_spmm<true><<<blocks_for((size_t)n * 32, sm), 256, 0, s>>>(g, ps.da, din, ps.tmp);
       k_add<<<blocks_for((size_t)n * din, sm), 256, 0, s>>>(ps.dx_in, ps.tmp, (size_t)n * din);
       std::swap(ps.dx, ps.dx_in);
       launches += 3;
@@ -514,6 +606,7 @@ void fem_mpnn_destroy(fem_mpnn_t net) {
   cudaFree(net->v);
   cudaFree(net->g);
   cudaFree(net->wb);
+  cudaFree(net->arena);
   delete net;
 }
 
@@ -538,6 +631,7 @@ fem_status fem_mpnn_predict(fem_mpnn_t net, fem_problem_t g, const float* z, int
   if (!(rms >= 0.f)) return fail(FEM_ERR_INVALID_ARG, "rms must be >= 0");
   cudaStream_t s = (cudaStream_t)stream;
   Pass ps;
+  ps.net = net;
   st = forward(net, g, z, R, nullptr, y, ps, s);
   if (st == FEM_OK && rms > 0.f) {
     const int n = g->n, nblk = (n + kRmsRows - 1) / kRmsRows;
@@ -564,6 +658,7 @@ fem_status fem_mpnn_grad(fem_mpnn_t net, fem_problem_t g, const float* z, const 
   if (!m_t) return fail(FEM_ERR_INVALID_ARG, "h_target must be non-NULL");
   cudaStream_t s = (cudaStream_t)stream;
   Pass ps;
+  ps.net = net;
   st = forward(net, g, z, R, m_t, nullptr, ps, s);
   if (st == FEM_OK) st = backward(net, g, ps, s);
   if (st == FEM_OK) st = read_loss(ps, g->n, R, loss, s);

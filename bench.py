@@ -757,10 +757,15 @@ def run_ours(args, wl):
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     p2 = _make_problem(fem, wl, inst_pinned, stream, args.dense_launch)
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
     p2.anneal(h_init=h0_pinned, replicas=R, n_steps=n_steps, t_end=e2e_steps, **kw)
+    torch.cuda.synchronize()
+    t2 = time.perf_counter()
     p2.best()
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t0
+    phases = {"create": (t1 - t0) * 1e3, "anneal_with_h_init": (t2 - t1) * 1e3, "read_best": (t0 + e2e_s - t2) * 1e3}
     p2.close()
     if wl["kind"] == "dense":
         h2d = h0_bytes + 4 * inst.n * inst.n
@@ -774,6 +779,7 @@ def run_ours(args, wl):
     d2h = 4 * inst.n + 16 * R + 4
     e2e = {"value": units_per_step * e2e_steps / e2e_s, "unit": METRIC,
            "h2d_bytes_per_step": int(round(h2d / e2e_steps)), "d2h_bytes_per_step": int(round(d2h / e2e_steps)),
+           "phases_ms": {k: round(v, 3) for k, v in phases.items()},
            "note": f"one full user call sequence per {e2e_steps} steps: fem_create_problem from pinned host arrays "
                    "(validation on the host, the CSR built on the device for graphs of >= 65536 edges), h_init "
                    "from pinned host memory, anneal, fem_read_best (best states and energies) to host"}

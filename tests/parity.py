@@ -92,26 +92,22 @@ def gpu_windows(P, h0, checkpoints, n_steps, **run_kw):
     return got, state
 
 
-def one_step(P, problem, n_steps, optimizer="adam", opt_kw=None, mode="exact", sched=None,
-             **run_kw):
-    """A function (T, (h, m, v)) -> (GPU fields, oracle fields) after one step from that
-    fp32 state, on both sides."""
+def one_step_from(gpu_step, problem, n_steps, optimizer="adam", opt_kw=None, mode="exact", sched=None):
+    """A function (T, (h, m, v)) -> (GPU fields, oracle fields, extra) after one step from
+    that fp32 state on both sides; gpu_step(T, h, m, v) runs the GPU step and returns the
+    fields and first moment it leaves.  extra["cond"] holds the oracle's optimizer
+    denominators of the step; for Adam, extra also holds the applied gradients."""
     sched = dict(sched or {})
 
     def step(T, state):
         h, m, v = (np.ascontiguousarray(x, dtype=np.float32) for x in state)
-        if T == 0:    # a step count of 0 is a fresh start: fields from h_init, zero state
-            P.anneal(h_init=h, n_steps=n_steps, t_end=1, optimizer=optimizer, **run_kw)
-        else:
-            P.set_state(h, m, v, steps_done=T)
-            P.anneal(n_steps=n_steps, t_begin=T, t_end=T + 1, optimizer=optimizer, replicas=h.shape[1],
-                     **run_kw)
-        got, m_got, _ = P.state()
+        got, m_got = gpu_step(T, h, m, v)
         o = O.make_optimizer(optimizer, h.shape, **(opt_kw or dict(lr=0.1)))
         set_opt_state(o, m.astype(np.float64), v.astype(np.float64))
+        cd = {T + 1: None}
         ref, o = O.anneal(problem, h.astype(np.float64), n_steps, t_begin=T, t_end=T + 1,
-                          optimizer=optimizer, opt=o, mode=mode, **sched)
-        extra = None
+                          optimizer=optimizer, opt=o, mode=mode, cond=cd, **sched)
+        extra = dict(cond=cd[T + 1])   # the oracle's denominators of this step
         if optimizer == "adam":
             b1 = o.b1
             g_got = (m_got.astype(np.float64) - b1 * m.astype(np.float64)) / (1.0 - b1)
@@ -126,10 +122,28 @@ def one_step(P, problem, n_steps, optimizer="adam", opt_kw=None, mode="exact", s
                 return hh
             # the fp32 rounding of the moments the gradient is read back from
             g_rb = 2.0 ** -23 * (b1 * np.abs(m.astype(np.float64)) + np.abs(m_got.astype(np.float64))) / (1.0 - b1)
-            extra = dict(g_got=g_got, g_ref=g_ref, g_readback=g_rb, replay=replay)
+            extra.update(g_got=g_got, g_ref=g_ref, g_readback=g_rb, replay=replay)
         return got, ref, extra
 
     return step
+
+
+def one_step(P, problem, n_steps, optimizer="adam", opt_kw=None, mode="exact", sched=None,
+             **run_kw):
+    """one_step_from with the GPU step of problem P: its state written with
+    fem_write_state (T > 0) or a fresh start (T = 0), then one anneal step."""
+
+    def gpu_step(T, h, m, v):
+        if T == 0:    # a step count of 0 is a fresh start: fields from h_init, zero state
+            P.anneal(h_init=h, n_steps=n_steps, t_end=1, optimizer=optimizer, **run_kw)
+        else:
+            P.set_state(h, m, v, steps_done=T)
+            P.anneal(n_steps=n_steps, t_begin=T, t_end=T + 1, optimizer=optimizer, replicas=h.shape[1],
+                     **run_kw)
+        got, m_got, _ = P.state()
+        return got, m_got
+
+    return one_step_from(gpu_step, problem, n_steps, optimizer, opt_kw, mode, sched)
 
 
 def compare(got, ref, cond, where, marg=sigmoid, agree=None, forced=None, prev=None, prev_state=None):
@@ -169,7 +183,7 @@ def compare(got, ref, cond, where, marg=sigmoid, agree=None, forced=None, prev=N
             if qstate:   # a q-state element's fields share one conditioning record
                 over = np.broadcast_to(over.any(axis=-1, keepdims=True), got.shape)
             assert not (over & ~ill).any(), (where, "over TOL_P in one step and not excluded")
-            assert extra is not None, (where, "gradient read-back needs an Adam step")
+            assert "g_got" in extra, (where, "gradient read-back needs an Adam step")
             gg, gr = extra["g_got"][over], extra["g_ref"][over]
             dg = float((np.abs(gg - gr) - (G_TOL_ABS + G_TOL_REL * np.abs(gr) + extra["g_readback"][over])).max())
             e_rep = float(np.abs(marg(extra["replay"](extra["g_got"]))[over] - marg(g1)[over]).max())

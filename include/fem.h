@@ -405,10 +405,12 @@ int64_t fem_kernel_launches(void);
  * min_edges undirected edges on the device of the call (degrees, a prefix sum, a
  * scatter of (column, edge) keys and a per-row sort), smaller ones on the host; a
  * negative value keeps every build on the host.  Both give the same arrays bit for
- * bit; validation (indices, self-loops, weights) always runs on the host first, and a
- * duplicate edge is reported as FEM_ERR_INVALID_ARG by either builder.  Process-wide;
- * the default is 65536.  Clause lists and dense couplings are always built on the
- * host. */
+ * bit.  The device builder validates the copied edge list on the device (indices,
+ * self-loops, weights; chunk sums of the weights added in the same order as on the
+ * host) before anything indexes with it, the host builder on the host threads; either
+ * reports the lowest invalid edge, or a duplicate edge, as FEM_ERR_INVALID_ARG with the
+ * same message.  Process-wide; the default is 65536.  Clause lists and dense couplings
+ * are always built on the host. */
 void fem_set_device_graph_build(int64_t min_edges);
 
 /* MaxCut energies of caller-provided sign words, without allocating.

@@ -10,6 +10,7 @@
 #include <cstring>
 #include <memory>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "fem_internal.h"
@@ -129,8 +130,9 @@ std::vector<StepScalars> make_step_scalars(const fem_anneal_params& a, int32_t s
 }
 
 // Declared in the kernel files.
-fem_status device_graph_build(Problem* p, int32_t kind, int32_t q, const fem_problem_desc* d, bool unit, bool integer,
-                              cudaStream_t s);
+// Validates the edge list on the device (setting unit_w, int_w and the weight sums of
+// p) and builds the CSR there.
+fem_status device_graph_build(Problem* p, int32_t kind, int32_t q, const fem_problem_desc* d, cudaStream_t s);
 fem_status maxcut_pack_words(Problem* p, int hbuf, int wbuf, cudaStream_t s, const float* src = nullptr);
 const float* maxcut_current_fields(const Problem* p);
 fem_status maxcut_states_all(Problem* p, int32_t* out_dev, cudaStream_t s);
@@ -162,39 +164,123 @@ struct HostGraph {
 // (fem_set_device_graph_build); below it the host builder is quicker than the launches.
 static std::atomic<int64_t> g_device_build_min_edges{1 << 16};
 
-// Validation, weight flags and sums always run on the host (one linear pass, before
-// any device work); with build == false the CSR is left to device_graph_build.
+// One unit of the host edge scan: the first invalid edge, the weight flags and the
+// integer sum; the fp64 sums of its chunks go to csum.
+struct EdgeScan {
+  int64_t bad = -1;  // lowest invalid edge of the unit, or -1
+  bool unit = true, integer = true;
+  int64_t wsum_i = 0;
+};
+
+constexpr int64_t kScanUnit = 256 * kWeightChunk;  // edges per unit of work of a host thread
+
+// Edges e0 .. e1-1 (e0 a multiple of kWeightChunk).  The flags and sums stay in
+// registers until the end (the records of neighbouring threads share cache lines).
+static void scan_edges(int32_t kind, const fem_problem_desc* d, int64_t e0, int64_t e1, EdgeScan& out,
+                       double* csum) {
+  const uint32_t n = (uint32_t)d->n;
+  const bool pos_only = kind == FEM_BMINCUT;
+  int64_t si = 0;
+  bool unit = true, integer = true;
+  int64_t bad = -1;
+  for (int64_t c0 = e0; c0 < e1 && bad < 0; c0 += kWeightChunk) {
+    const int64_t c1 = std::min(e1, c0 + kWeightChunk);
+    double sf = 0.0;
+    for (int64_t e = c0; e < c1; ++e) {
+      const int32_t i = d->ei[e], j = d->ej[e];
+      const double w = d->w ? d->w[e] : 1.0;
+      const double a = std::fabs(w);
+      // in range, no self-loop, finite (NaN fails the comparison) and nonzero
+      if (!((uint32_t)i < n && (uint32_t)j < n && i != j && a <= 1.7976931348623157e308 && w != 0.0 &&
+            (!pos_only || w > 0.0))) {
+        bad = e;
+        break;
+      }
+      unit = unit && a == 1.0;
+      const bool small = a <= 16777216.0;
+      const int64_t wi = (int64_t)(small ? w : 0.0);
+      integer = integer && small && (double)wi == w;
+      sf += w;
+      si += wi;
+    }
+    csum[c0 / kWeightChunk] = sf;
+  }
+  EdgeScan r;
+  r.bad = bad;
+  r.unit = unit;
+  r.integer = integer;
+  r.wsum_i = si;
+  out = r;
+}
+
+fem_status edge_error(const fem_problem_desc* d, int32_t kind, int64_t e) {
+  const int32_t i = d->ei[e], j = d->ej[e], n = d->n;
+  const double w = d->w ? d->w[e] : 1.0;
+  if (i < 0 || i >= n || j < 0 || j >= n)
+    return fail(FEM_ERR_INVALID_ARG, "edge %lld: endpoint out of range [0, %d)", (long long)e, n);
+  if (i == j) return fail(FEM_ERR_INVALID_ARG, "edge %lld: self-loop at %d", (long long)e, i);
+  if (!std::isfinite(w) || w == 0.0)
+    return fail(FEM_ERR_INVALID_ARG, "edge %lld: weight must be finite and nonzero", (long long)e);
+  (void)kind;  // the remaining check: bMinCut weights are positive
+  return fail(FEM_ERR_INVALID_ARG, "edge %lld: bMinCut weights must be positive", (long long)e);
+}
+
+// The checks every edge list gets before it is read.
+static fem_status edge_list_basics(const fem_problem_desc* d) {
+  if (d->n_edges < 0) return fail(FEM_ERR_INVALID_ARG, "n_edges < 0");
+  if (d->n_edges > 0 && (!d->ei || !d->ej)) return fail(FEM_ERR_INVALID_ARG, "ei/ej must be non-NULL");
+  if (2 * d->n_edges >= (int64_t)INT32_MAX) return fail(FEM_ERR_UNSUPPORTED, "2|E| must be < 2^31");
+  return FEM_OK;
+}
+
+// Validation, weight flags and sums on the host, before any device work, over
+// several host threads for long lists; with build, the CSR too (the device builder
+// takes large lists and validates them itself).  The error names the lowest invalid edge.
 static fem_status host_graph(int32_t kind, int32_t q, const fem_problem_desc* d, HostGraph& g, bool build = true) {
   const int32_t n = d->n;
   const int64_t E = d->n_edges;
-  if (E < 0) return fail(FEM_ERR_INVALID_ARG, "n_edges < 0");
-  if (E > 0 && (!d->ei || !d->ej)) return fail(FEM_ERR_INVALID_ARG, "ei/ej must be non-NULL");
-  if (2 * E >= (int64_t)INT32_MAX) return fail(FEM_ERR_UNSUPPORTED, "2|E| must be < 2^31");
-  bool unit = true, integer = true;
-  std::vector<int32_t> deg(build ? (size_t)n + 1 : 0, 0);
-  for (int64_t e = 0; e < E; ++e) {
-    const int32_t i = d->ei[e], j = d->ej[e];
-    if (i < 0 || i >= n || j < 0 || j >= n)
-      return fail(FEM_ERR_INVALID_ARG, "edge %lld: endpoint out of range [0, %d)", (long long)e, n);
-    if (i == j) return fail(FEM_ERR_INVALID_ARG, "edge %lld: self-loop at %d", (long long)e, i);
-    const double w = d->w ? d->w[e] : 1.0;
-    if (!std::isfinite(w) || w == 0.0)
-      return fail(FEM_ERR_INVALID_ARG, "edge %lld: weight must be finite and nonzero", (long long)e);
-    if (kind == FEM_BMINCUT && w < 0.0)
-      return fail(FEM_ERR_INVALID_ARG, "edge %lld: bMinCut weights must be positive", (long long)e);
-    if (std::fabs(w) != 1.0) unit = false;
-    if (w != std::rint(w) || std::fabs(w) > 16777216.0) integer = false;
-    g.wsum_f += w;
-    if (integer) g.wsum_i += (int64_t)w;
-    if (build) {
-      deg[i]++;
-      deg[j]++;
+  fem_status st0 = edge_list_basics(d);
+  if (st0 != FEM_OK) return st0;
+  const int64_t nunits = (E + kScanUnit - 1) / kScanUnit;
+  std::vector<EdgeScan> part((size_t)nunits);
+  std::vector<double> csum((size_t)((E + kWeightChunk - 1) / kWeightChunk), 0.0);
+  auto run = [&](int64_t u) {
+    scan_edges(kind, d, u * kScanUnit, std::min(E, (u + 1) * kScanUnit), part[u], csum.data());
+  };
+  const int64_t hw = std::max<int64_t>(1, (int64_t)std::thread::hardware_concurrency());
+  const int nth = (int)std::min<int64_t>({nunits, hw, 16});
+  if (nth > 1) {
+    std::atomic<int64_t> next{0};
+    auto worker = [&]() {
+      for (int64_t u; (u = next.fetch_add(1)) < nunits;) run(u);
+    };
+    std::vector<std::thread> pool;
+    try {
+      for (int t = 1; t < nth; ++t) pool.emplace_back(worker);
+    } catch (...) {  // fewer threads: the calling thread scans what is left
     }
+    worker();
+    for (auto& t : pool) t.join();
+  } else {
+    for (int64_t u = 0; u < nunits; ++u) run(u);
   }
+  bool unit = true, integer = true;
+  for (const EdgeScan& r : part) {
+    if (r.bad >= 0) return edge_error(d, kind, r.bad);
+    unit = unit && r.unit;
+    integer = integer && r.integer;
+    g.wsum_i += r.wsum_i;
+  }
+  for (double x : csum) g.wsum_f += x;
   g.n_edges = E;
   g.unit = unit;
   g.integer = integer;
   if (!build) return FEM_OK;
+  std::vector<int32_t> deg((size_t)n + 1, 0);
+  for (int64_t e = 0; e < E; ++e) {
+    deg[d->ei[e]]++;
+    deg[d->ej[e]]++;
+  }
   std::vector<int32_t>& row_ptr = g.row_ptr;
   row_ptr.assign(n + 1, 0);
   for (int32_t i = 0; i < n; ++i) row_ptr[i + 1] = row_ptr[i] + deg[i];
@@ -518,7 +604,11 @@ fem_status fem_create_problem(const fem_problem_desc* d, void* stream, fem_probl
   } else if (kind == FEM_MAXKSAT) {
     if ((st = host_sat(d, hs)) != FEM_OK) return st;
   } else {
-    if ((st = host_graph(kind, d->q, d, hg, !device_build)) != FEM_OK) return st;
+    // the device builder validates the edges itself; QUBO reads them on the host first
+    // (its per-node constants), so it validates them here as well
+    if ((st = device_build && d->kind != FEM_QUBO ? edge_list_basics(d) : host_graph(kind, d->q, d, hg, !device_build)) !=
+        FEM_OK)
+      return st;
   }
   // QUBO: the gradient's per-node constant sum_j Q_ij + d_i and the linear terms
   std::vector<float> qoff;
@@ -610,7 +700,7 @@ fem_status fem_create_problem(const fem_problem_desc* d, void* stream, fem_probl
   FEM_CUDA(cudaDeviceGetAttribute(&p->sm_count, cudaDevAttrMultiProcessorCount, p->device));
   if (d->kind == FEM_MAXCUT && d->dense_J) st = dense_upload(p.get(), d->dense_J, s);
   else if (kind == FEM_MAXKSAT) st = upload_sat(p.get(), hs, s);  // internal kind
-  else if (device_build) st = device_graph_build(p.get(), kind, d->q, d, hg.unit, hg.integer, s);
+  else if (device_build) st = device_graph_build(p.get(), kind, d->q, d, s);  // sets the weight sums
   else st = upload_graph(p.get(), hg, s);
   p->nodew_sq = nodew_sq;
   if (st == FEM_OK && !nodew.empty()) st = upload(p.get(), &p->nodew, nodew, s);

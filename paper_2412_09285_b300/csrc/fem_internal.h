@@ -128,6 +128,13 @@ struct Problem {
 
 // ---- error reporting (thread-local last error)
 fem_status fail(fem_status s, const char* fmt, ...);
+
+// Edge lists are validated in chunks of kWeightChunk consecutive edges (on the host for
+// small lists, on the device for large ones); the fp64 weight sum is the sum, in chunk
+// order, of the chunks' sums taken in edge order, so both give the same total.
+constexpr int64_t kWeightChunk = 256;
+// The error for invalid edge e (the first check it fails, in the order the builders check).
+fem_status edge_error(const fem_problem_desc* d, int32_t kind, int64_t e);
 fem_status cuda_fail(cudaError_t e, const char* what);
 #define FEM_CUDA(call)                                       \
   do {                                                       \

@@ -1,8 +1,10 @@
 // Device construction of a sparse problem's CSR (fem_create_problem for large edge
-// lists).  The host has already validated every edge (indices in range, no
-// self-loops, finite nonzero weights) and computed the weight flags and sums in one
-// linear pass; what costs time on the host - placing 2|E| directed entries and
-// sorting every row - runs here:
+// lists).  After one copy of the edge list to the device, everything that costs time
+// on the host runs here:
+//   0. validation (indices in range, no self-loops, finite nonzero weights, positive
+//      for bMinCut), the weight flags (all |w| = 1, all integer) and the weight sums,
+//      one thread per chunk of kWeightChunk edges (the fp64 chunk sums are added in
+//      chunk order on the host, as the host builder adds its own);
 //   1. degrees (atomic counts), 2. an exclusive scan to the row pointers,
 //   3. a scatter of (column << 32 | edge) keys into the rows,
 //   4. a sort of every row by column (one warp per row up to 32 entries, one block
@@ -28,6 +30,45 @@ namespace {
 constexpr unsigned kMask = 0xffffffffu;
 constexpr int kScanThreads = 256, kScanItems = 8, kScanTile = kScanThreads * kScanItems;
 constexpr int kBlockSortMax = 4096;  // longest row sorted by one block in shared memory
+
+// Step 0: chunk c = edges c * kWeightChunk ..; first_bad is the lowest invalid edge
+// (all ones when none), flags bit 0 = some |w| != 1, bit 1 = some w not an integer of
+// magnitude <= 2^24; csum[c] the chunk's weight sum in edge order; wsum_i the sum of
+// the integer weights (meaningful when flags bit 1 is clear).
+__global__ void k_check_edges(const int32_t* __restrict__ ei, const int32_t* __restrict__ ej,
+                              const double* __restrict__ w, int64_t E, int32_t n, int32_t pos_only,
+                              unsigned long long* __restrict__ first_bad, int32_t* __restrict__ flags,
+                              double* __restrict__ csum, unsigned long long* __restrict__ wsum_i) {
+  const long long nchunks = (E + kWeightChunk - 1) / kWeightChunk;
+  for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < nchunks;
+       c += (long long)gridDim.x * blockDim.x) {
+    const long long e0 = c * kWeightChunk, e1 = e0 + kWeightChunk < E ? e0 + kWeightChunk : E;
+    double sf = 0.0;
+    long long si = 0;
+    bool unit = true, integer = true;
+    long long bad = -1;
+    for (long long e = e0; e < e1; ++e) {
+      const int32_t i = ei[e], j = ej[e];
+      const double x = w ? w[e] : 1.0;
+      const double a = fabs(x);
+      if (!((uint32_t)i < (uint32_t)n && (uint32_t)j < (uint32_t)n && i != j && a <= 1.7976931348623157e308 &&
+            x != 0.0 && (!pos_only || x > 0.0))) {
+        bad = e;
+        break;
+      }
+      unit = unit && a == 1.0;
+      const bool small = a <= 16777216.0;
+      const long long xi = (long long)(small ? x : 0.0);
+      integer = integer && small && (double)xi == x;
+      sf = __dadd_rn(sf, x);
+      si += xi;
+    }
+    csum[c] = sf;
+    if (bad >= 0) atomicMin(first_bad, (unsigned long long)bad);
+    if (!unit || !integer) atomicOr(flags, (unit ? 0 : 1) | (integer ? 0 : 2));
+    if (si != 0) atomicAdd(wsum_i, (unsigned long long)si);
+  }
+}
 
 __global__ void k_degrees(const int32_t* __restrict__ ei, const int32_t* __restrict__ ej, int64_t E,
                           int32_t* __restrict__ deg) {
@@ -228,22 +269,12 @@ int grid_for(long long work, int sm_count, int threads = 256) {
 
 }  // namespace
 
-fem_status device_graph_build(Problem* p, int32_t kind, int32_t q, const fem_problem_desc* d, bool unit, bool integer,
-                              cudaStream_t s) {
+fem_status device_graph_build(Problem* p, int32_t kind, int32_t q, const fem_problem_desc* d, cudaStream_t s) {
   const int32_t n = d->n;
   const int64_t E = d->n_edges, nnz = 2 * E;
   p->n_edges = E;
   p->nnz = nnz;
-  p->unit_w = unit;
-  p->int_w = integer;
   fem_status st;
-  if ((st = dev_alloc_t(p, &p->row_ptr, (size_t)n + 1)) != FEM_OK) return st;
-  if ((st = dev_alloc_t(p, &p->col, (size_t)nnz)) != FEM_OK) return st;
-  if (!unit && (st = dev_alloc_t(p, &p->w, (size_t)nnz)) != FEM_OK) return st;
-  if (!integer && (st = dev_alloc_t(p, &p->w64, (size_t)nnz)) != FEM_OK) return st;
-  const bool need_c = kind != FEM_MAXCUT || !unit;
-  if (need_c && (st = dev_alloc_t(p, &p->cnorm, (size_t)n)) != FEM_OK) return st;
-  if (kind != FEM_MAXCUT && (st = dev_alloc_t(p, &p->cnorm2, (size_t)n)) != FEM_OK) return st;
 
   // scratch of the build, stream-ordered and released at the end
   const int ntiles = (int)((n + kScanTile - 1) / kScanTile);
@@ -276,6 +307,61 @@ fem_status device_graph_build(Problem* p, int32_t kind, int32_t q, const fem_pro
   if (st == FEM_OK) st = talloc((void**)&big, sizeof(int32_t) * (size_t)n);
   if (st == FEM_OK) st = talloc((void**)&counters, sizeof(int32_t) * 8);  // nbig, ngiant, dup[3]
   if (st == FEM_OK) st = talloc((void**)&key, sizeof(unsigned long long) * (size_t)nnz);
+  const int64_t nchunks = (E + kWeightChunk - 1) / kWeightChunk;
+  double* csum = nullptr;
+  unsigned long long* check = nullptr;  // first_bad, wsum_i, flags
+  if (st == FEM_OK) st = talloc((void**)&csum, sizeof(double) * (size_t)nchunks);
+  if (st == FEM_OK) st = talloc((void**)&check, sizeof(unsigned long long) * 3);
+  if (st != FEM_OK) {
+    release();
+    return st;
+  }
+  // 0. the edge list to the device and its validation; nothing indexes with the
+  // endpoints before it has passed
+  {
+    cudaError_t e0 = cudaMemcpyAsync(ei, d->ei, sizeof(int32_t) * (size_t)E, cudaMemcpyHostToDevice, s);
+    if (e0 == cudaSuccess) e0 = cudaMemcpyAsync(ej, d->ej, sizeof(int32_t) * (size_t)E, cudaMemcpyHostToDevice, s);
+    if (e0 == cudaSuccess && d->w)
+      e0 = cudaMemcpyAsync(w, d->w, sizeof(double) * (size_t)E, cudaMemcpyHostToDevice, s);
+    if (e0 == cudaSuccess) e0 = cudaMemsetAsync(check, 0, sizeof(unsigned long long) * 3, s);
+    if (e0 == cudaSuccess) e0 = cudaMemsetAsync(check, 0xff, sizeof(unsigned long long), s);
+    if (e0 == cudaSuccess) {
+      k_check_edges<<<grid_for(nchunks, p->sm_count), 256, 0, s>>>(ei, ej, w, E, n, kind == FEM_BMINCUT ? 1 : 0,
+                                                                    check, reinterpret_cast<int32_t*>(check + 2),
+                                                                    csum, check + 1);
+      count_launches(1);
+      e0 = cudaGetLastError();
+    }
+    unsigned long long res[3] = {0, 0, 0};
+    std::vector<double> hsum((size_t)nchunks);
+    if (e0 == cudaSuccess) e0 = cudaMemcpyAsync(res, check, sizeof(res), cudaMemcpyDeviceToHost, s);
+    if (e0 == cudaSuccess)
+      e0 = cudaMemcpyAsync(hsum.data(), csum, sizeof(double) * (size_t)nchunks, cudaMemcpyDeviceToHost, s);
+    if (e0 == cudaSuccess) e0 = cudaStreamSynchronize(s);
+    if (e0 != cudaSuccess) {
+      release();
+      return cuda_fail(e0, "device graph build: edge check");
+    }
+    if (res[0] != ~0ull) {
+      release();
+      return edge_error(d, kind, (int64_t)res[0]);
+    }
+    const int32_t flags = (int32_t)(res[2] & 0xffffffffull);
+    p->unit_w = (flags & 1) == 0;
+    p->int_w = (flags & 2) == 0;
+    p->wtot_i = (int64_t)res[1];
+    double tot = 0.0;
+    for (double x : hsum) tot += x;
+    p->wtot_f = tot;
+  }
+  const bool unit = p->unit_w, integer = p->int_w;
+  if (st == FEM_OK) st = dev_alloc_t(p, &p->row_ptr, (size_t)n + 1);
+  if (st == FEM_OK) st = dev_alloc_t(p, &p->col, (size_t)nnz);
+  if (st == FEM_OK && !unit) st = dev_alloc_t(p, &p->w, (size_t)nnz);
+  if (st == FEM_OK && !integer) st = dev_alloc_t(p, &p->w64, (size_t)nnz);
+  const bool need_c = kind != FEM_MAXCUT || !unit;
+  if (st == FEM_OK && need_c) st = dev_alloc_t(p, &p->cnorm, (size_t)n);
+  if (st == FEM_OK && kind != FEM_MAXCUT) st = dev_alloc_t(p, &p->cnorm2, (size_t)n);
   if (st != FEM_OK) {
     release();
     return st;
@@ -285,9 +371,6 @@ fem_status device_graph_build(Problem* p, int32_t kind, int32_t q, const fem_pro
   auto step = [&](cudaError_t x) {
     if (e == cudaSuccess) e = x;
   };
-  step(cudaMemcpyAsync(ei, d->ei, sizeof(int32_t) * (size_t)E, cudaMemcpyHostToDevice, s));
-  step(cudaMemcpyAsync(ej, d->ej, sizeof(int32_t) * (size_t)E, cudaMemcpyHostToDevice, s));
-  if (d->w) step(cudaMemcpyAsync(w, d->w, sizeof(double) * (size_t)E, cudaMemcpyHostToDevice, s));
   step(cudaMemsetAsync(deg, 0, sizeof(int32_t) * (size_t)n, s));
   step(cudaMemsetAsync(counters, 0, sizeof(int32_t) * 8, s));
   step(cudaMemsetAsync(p->row_ptr, 0, sizeof(int32_t), s));

@@ -98,3 +98,43 @@ def test_device_build_rejects_duplicates_and_empty_rows_work(fem):
     finally:
         fem.fem_set_device_graph_build(1 << 16)
     _same_run(fem, "maxcut", sparse, 32, ["paper"])
+
+
+@pytest.mark.parametrize("defect", ["out_of_range", "self_loop", "nan_weight", "zero_weight", "negative_bmincut"])
+def test_device_validation_names_the_first_invalid_edge(fem, defect):
+    """Large edge lists are validated on the device: two invalid edges are planted and
+    the error names the lower one, with the host builder's message."""
+    n = 40000
+    g = I.er_gnm(n, 120000, seed=21, weights="pm1")
+    ei, ej, w = g.ei.copy(), g.ej.copy(), g.w.copy()
+    kind, q = "maxcut", 2
+    if defect == "negative_bmincut":
+        kind, q = "bmincut", 4
+        w = np.abs(w)
+    for b in (99999, 70001):
+        if defect == "out_of_range":
+            ej[b] = n
+        elif defect == "self_loop":
+            ej[b] = ei[b]
+        elif defect == "nan_weight":
+            w[b] = np.nan
+        elif defect == "zero_weight":
+            w[b] = 0.0
+        else:
+            w[b] = -1.0
+    msgs = []
+    try:
+        for thr in (0, -1):   # device validation, host validation
+            fem.fem_set_device_graph_build(thr)
+            with pytest.raises(fem.FemError) as e:
+                fem.Problem(kind, graph=I.Graph(n, ei, ej, w), q=q)
+            assert e.value.status == fem.FEM_ERR_INVALID_ARG
+            msgs.append(str(e.value))
+    finally:
+        fem.fem_set_device_graph_build(1 << 16)
+    assert "edge 70001:" in msgs[0], msgs[0]
+    assert msgs[0] == msgs[1]
+    # the device is still usable: a valid problem of the same size builds and anneals
+    P = fem.Problem("maxcut", graph=g)
+    P.anneal(h_init=I.initial_fields(n, 32, seed=22), n_steps=20)
+    assert P.best()["energy_i64"].shape == (32,)

@@ -1177,52 +1177,13 @@ int dense_pad(int n) { return ((n + kTile - 1) / kTile) * kTile; }
 // Host-side construction of the dense couplings (validated by the caller):
 // fp32, bf16, e4m3 and int8 copies padded to n_pad with zeros, row sums |J|, W_tot.
 fem_status dense_upload(Problem* p, const float* J, cudaStream_t s) {
-  const int n = p->n, np = dense_pad(n);
   p->dense = true;
-  p->n_pad = np;
-  std::vector<float> j32((size_t)np * np, 0.f);
-  std::vector<uint16_t> j16((size_t)np * np, 0);
-  std::vector<uint8_t> j8((size_t)np * np, 0);
-  std::vector<int8_t> ji((size_t)np * np, 0);
-  std::vector<float> cn(np, 0.f);
-  int64_t wtot = 0;
-  bool fp8_ok = true;
-  for (int i = 0; i < n; ++i) {
-    double ra = 0;
-    for (int j = 0; j < n; ++j) {
-      const float x = J[(size_t)i * n + j];
-      const size_t o = (size_t)i * np + j;
-      j32[o] = x;
-      uint16_t b;
-      const __nv_bfloat16 bb = __float2bfloat16_rn(x);
-      std::memcpy(&b, &bb, 2);
-      j16[o] = b;
-      const __nv_fp8_e4m3 f8(x);
-      std::memcpy(&j8[o], &f8, 1);
-      if (std::fabs(x) > 16.f) fp8_ok = false;
-      ji[o] = (int8_t)x;
-      ra += std::fabs(x);
-      if (j > i) wtot += (int64_t)x;
-    }
-    cn[i] = ra > 0 ? (float)(1.0 / ra) : 0.f;
-  }
-  p->dense_wtot = wtot;
-  p->dense_fp8_ok = fp8_ok;
-  fem_status st;
-  if ((st = dev_alloc_t(p, &p->J32, j32.size())) != FEM_OK) return st;
-  if ((st = dev_alloc(p, &p->J16, j16.size() * 2)) != FEM_OK) return st;
-  if ((st = dev_alloc(p, &p->J8, j8.size())) != FEM_OK) return st;
-  if ((st = dev_alloc(p, (void**)&p->Ji8, ji.size())) != FEM_OK) return st;
-  if ((st = dev_alloc_t(p, &p->rowabs, cn.size())) != FEM_OK) return st;
-  FEM_CUDA(cudaMemcpyAsync(p->J32, j32.data(), j32.size() * 4, cudaMemcpyHostToDevice, s));
-  FEM_CUDA(cudaMemcpyAsync(p->J16, j16.data(), j16.size() * 2, cudaMemcpyHostToDevice, s));
-  FEM_CUDA(cudaMemcpyAsync(p->J8, j8.data(), j8.size(), cudaMemcpyHostToDevice, s));
-  FEM_CUDA(cudaMemcpyAsync(p->Ji8, ji.data(), ji.size(), cudaMemcpyHostToDevice, s));
-  FEM_CUDA(cudaMemcpyAsync(p->rowabs, cn.data(), cn.size() * 4, cudaMemcpyHostToDevice, s));
-  FEM_CUDA(cudaStreamSynchronize(s));  // the host staging vectors die at return
-  fem_status e = make_map(&p->tmap_a16, p->J16, np, np, 2);
+  p->n_pad = dense_pad(p->n);
+  const fem_status st = dense_build(p, J, s);  // validation and operands, on the device
+  if (st != FEM_OK) return st;
+  fem_status e = make_map(&p->tmap_a16, p->J16, p->n_pad, p->n_pad, 2);
   if (e != FEM_OK) return e;
-  return make_map(&p->tmap_a8, p->J8, np, np, 1);
+  return make_map(&p->tmap_a8, p->J8, p->n_pad, p->n_pad, 1);
 }
 
 // State for R replicas: h, m, v [R][n_pad] and two operand buffers per part.

@@ -591,16 +591,8 @@ fem_status fem_create_problem(const fem_problem_desc* d, void* stream, fem_probl
   const bool device_build = !(d->kind == FEM_MAXCUT && d->dense_J) && kind != FEM_MAXKSAT && dev_min >= 0 &&
                             d->n_edges >= dev_min && d->n_edges > 0;
   if (d->kind == FEM_MAXCUT && d->dense_J) {
-    // symmetric, zero diagonal, integers with |J_ij| <= 127 (exact in bf16 and int8)
-    const float* J = d->dense_J;
-    for (int32_t i = 0; i < d->n; ++i)
-      for (int32_t j = 0; j < d->n; ++j) {
-        const float x = J[(size_t)i * d->n + j];
-        if (!std::isfinite(x) || x != std::rint(x) || std::fabs(x) > 127.f)
-          return fail(FEM_ERR_INVALID_ARG, "dense_J[%d][%d] must be an integer with |J| <= 127", i, j);
-        if (i == j && x != 0.f) return fail(FEM_ERR_INVALID_ARG, "dense_J must have a zero diagonal");
-        if (j > i && x != J[(size_t)j * d->n + i]) return fail(FEM_ERR_INVALID_ARG, "dense_J must be symmetric");
-      }
+    // symmetric, zero diagonal, integers with |J_ij| <= 127 (exact in bf16 and int8):
+    // checked on the device after one copy (dense_build)
   } else if (kind == FEM_MAXKSAT) {
     if ((st = host_sat(d, hs)) != FEM_OK) return st;
   } else {

@@ -170,6 +170,9 @@ fem_status bmincut_states_all(Problem* p, int32_t* out, cudaStream_t s);
 // ---- dense MaxCut on the tensor cores (dense_tc.cu)
 int dense_pad(int n);
 fem_status dense_upload(Problem* p, const float* J, cudaStream_t s);
+// dense_build.cu: validates the caller's n x n couplings on the device and writes the
+// operand copies, c_i, the sum above the diagonal and the e4m3 flag into p.
+fem_status dense_build(Problem* p, const float* J, cudaStream_t s);
 fem_status dense_state(Problem* p, int R, int prec, cudaStream_t s);
 fem_status dense_set_fields(Problem* p, const float* h_nr, bool on_device, cudaStream_t s);
 fem_status dense_get(Problem* p, const float* src_rn, float* dst_nr_host, cudaStream_t s);

@@ -216,6 +216,59 @@ def test_dense_argument_errors(fem):
     assert e.value.status == fem.FEM_ERR_INVALID_ARG
 
 
+@pytest.mark.parametrize("defect,msg", [
+    ("fraction", "dense_J[3][7] must be an integer with |J| <= 127"),
+    ("too_large", "dense_J[3][7] must be an integer with |J| <= 127"),
+    ("nan", "dense_J[3][7] must be an integer with |J| <= 127"),
+    ("diagonal", "dense_J must have a zero diagonal"),
+    ("asymmetric", "dense_J must be symmetric"),
+])
+def test_dense_validation_on_the_device(fem, defect, msg):
+    """The couplings are validated on the device after one copy; the lowest offending
+    entry in row-major order is reported (a second defect is planted further on), and
+    the device stays usable."""
+    n = 300
+    g = I.sk_dense(n, seed=93)
+    J = g.dense.astype(np.float32)
+    J[200, 250] = J[250, 200] = 0.5          # the later defect
+    if defect == "fraction":
+        J[3, 7] = J[7, 3] = 1.5
+    elif defect == "too_large":
+        J[3, 7] = J[7, 3] = 128.0
+    elif defect == "nan":
+        J[3, 7] = J[7, 3] = np.nan
+    elif defect == "diagonal":
+        J[3, 3] = 1.0
+    else:
+        J[3, 7] = -J[7, 3]
+    with pytest.raises(fem.FemError) as e:
+        fem.Problem("maxcut", dense=J)
+    assert e.value.status == fem.FEM_ERR_INVALID_ARG
+    assert str(e.value).endswith(msg), str(e.value)
+    P = fem.Problem("maxcut", dense=g.dense)
+    P.anneal(h_init=I.initial_fields(n, 128, seed=2), n_steps=20)
+    cut = O.maxcut_cut_edges(g.ei, g.ej, g.w, P.states().astype(np.int8))
+    assert np.array_equal(-P.best()["energy_i64"], cut)
+
+
+def test_dense_fp8_needs_small_couplings(fem):
+    """|J_ij| <= 16 is exact in e4m3; a coupling of 17 makes the fp8 path refuse the
+    problem while bf16 runs it, with exact objectives."""
+    n = 256
+    g = I.sk_dense(n, seed=95)
+    J = g.dense.astype(np.float32)
+    J[10, 20] = J[20, 10] = 17.0
+    P = fem.Problem("maxcut", dense=J)
+    h0 = I.initial_fields(n, 128, seed=3)
+    with pytest.raises(fem.FemError) as e:
+        P.anneal(h_init=h0, n_steps=20, precision="fp8")
+    assert e.value.status == fem.FEM_ERR_UNSUPPORTED
+    P.anneal(h_init=h0, n_steps=20, precision="bf16")
+    iu, ju = np.triu_indices(n, k=1)
+    cut = O.maxcut_cut_edges(iu, ju, J[iu, ju].astype(np.float64), P.states().astype(np.int8))
+    assert np.array_equal(-P.best()["energy_i64"], cut)
+
+
 def _run(fem, g, h0, launch, n_steps, windows, **kw):
     P = fem.Problem("maxcut", dense=g.dense)
     P.set_dense_launch(launch)

@@ -409,9 +409,11 @@ int64_t fem_kernel_launches(void);
  * self-loops, weights; chunk sums of the weights added in the same order as on the
  * host) before anything indexes with it, the host builder on the host threads; either
  * reports the lowest invalid edge, or a duplicate edge, as FEM_ERR_INVALID_ARG with the
- * same message.  Process-wide; the default is 65536.  Clause lists are always built
- * on the host; dense couplings are copied once and validated and converted on the
- * device. */
+ * same message.  Process-wide; the default is 65536.  Clause lists (Max-k-SAT and
+ * p-spin) follow the same threshold on their literal count: long lists are copied once
+ * and validated, transposed (occurrences in clause order) and, for p-spin, folded with
+ * the literals' negations on the device, with the host builder's tables and messages.
+ * Dense couplings are always copied once and validated and converted on the device. */
 void fem_set_device_graph_build(int64_t min_edges);
 
 /* MaxCut energies of caller-provided sign words, without allocating.

@@ -133,6 +133,9 @@ std::vector<StepScalars> make_step_scalars(const fem_anneal_params& a, int32_t s
 // Validates the edge list on the device (setting unit_w, int_w and the weight sums of
 // p) and builds the CSR there.
 fem_status device_graph_build(Problem* p, int32_t kind, int32_t q, const fem_problem_desc* d, cudaStream_t s);
+// Validates a clause list on the device and builds its tables there (p-spin: also the
+// folded term coefficients; *terms_int tells whether they are all integers).
+fem_status device_sat_build(Problem* p, const fem_problem_desc* d, bool pspin, bool* terms_int, cudaStream_t s);
 fem_status maxcut_pack_words(Problem* p, int hbuf, int wbuf, cudaStream_t s, const float* src = nullptr);
 const float* maxcut_current_fields(const Problem* p);
 fem_status maxcut_states_all(Problem* p, int32_t* out_dev, cudaStream_t s);
@@ -363,8 +366,8 @@ struct HostSat {
   std::vector<int32_t> oth;
 };
 
-static fem_status host_sat(const fem_problem_desc* d, HostSat& g) {
-  const int32_t n = d->n;
+// The checks of a clause list that read only its header (the clause and literal counts).
+static fem_status sat_basics(const fem_problem_desc* d) {
   const int64_t M = d->n_clauses;
   if (M < 0) return fail(FEM_ERR_INVALID_ARG, "n_clauses < 0");
   if (M > 0 && (!d->clause_ptr || !d->lits)) return fail(FEM_ERR_INVALID_ARG, "clause_ptr/lits must be non-NULL");
@@ -372,6 +375,14 @@ static fem_status host_sat(const fem_problem_desc* d, HostSat& g) {
   const int64_t L = M > 0 ? d->clause_ptr[M] : 0;
   if (M > 0 && d->clause_ptr[0] != 0) return fail(FEM_ERR_INVALID_ARG, "clause_ptr[0] must be 0");
   if (L < 0 || L >= (int64_t)INT32_MAX) return fail(FEM_ERR_UNSUPPORTED, "literal count must be < 2^31");
+  return FEM_OK;
+}
+
+static fem_status host_sat(const fem_problem_desc* d, HostSat& g) {
+  const int32_t n = d->n;
+  const int64_t M = d->n_clauses;
+  if (fem_status st = sat_basics(d); st != FEM_OK) return st;
+  const int64_t L = M > 0 ? d->clause_ptr[M] : 0;
   g.cl_ptr.assign(M + 1, 0);
   g.cl_lit.assign(L, 0);
   std::vector<int32_t> cnt(n + 1, 0);
@@ -588,13 +599,18 @@ fem_status fem_create_problem(const fem_problem_desc* d, void* stream, fem_probl
   HostSat hs;
   fem_status st = FEM_OK;
   const int64_t dev_min = g_device_build_min_edges.load();
+  bool sat_device = false;
   const bool device_build = !(d->kind == FEM_MAXCUT && d->dense_J) && kind != FEM_MAXKSAT && dev_min >= 0 &&
                             d->n_edges >= dev_min && d->n_edges > 0;
   if (d->kind == FEM_MAXCUT && d->dense_J) {
     // symmetric, zero diagonal, integers with |J_ij| <= 127 (exact in bf16 and int8):
     // checked on the device after one copy (dense_build)
   } else if (kind == FEM_MAXKSAT) {
-    if ((st = host_sat(d, hs)) != FEM_OK) return st;
+    if ((st = sat_basics(d)) != FEM_OK) return st;
+    // long clause lists are validated and built on the device (the literal count is
+    // the size that decides, as the edge count does for graphs)
+    sat_device = dev_min >= 0 && d->n_clauses > 0 && d->clause_ptr[d->n_clauses] >= dev_min;
+    if (!sat_device && (st = host_sat(d, hs)) != FEM_OK) return st;
   } else {
     // the device builder validates the edges itself; QUBO reads them on the host first
     // (its per-node constants), so it validates them here as well
@@ -632,7 +648,7 @@ fem_status fem_create_problem(const fem_problem_desc* d, void* stream, fem_probl
   std::vector<int64_t> pj_i64;
   bool pspin_int = true;
   if (d->kind == FEM_PSPIN) {
-    const int64_t M = d->n_clauses;
+    const int64_t M = sat_device ? 0 : d->n_clauses;  // the device builder folds the terms
     pj_f32.resize(M);
     pj_f64.resize(M);
     pj_i64.resize(M);
@@ -691,7 +707,11 @@ fem_status fem_create_problem(const fem_problem_desc* d, void* stream, fem_probl
   FEM_CUDA(cudaGetDevice(&p->device));
   FEM_CUDA(cudaDeviceGetAttribute(&p->sm_count, cudaDevAttrMultiProcessorCount, p->device));
   if (d->kind == FEM_MAXCUT && d->dense_J) st = dense_upload(p.get(), d->dense_J, s);
-  else if (kind == FEM_MAXKSAT) st = upload_sat(p.get(), hs, s);  // internal kind
+  else if (kind == FEM_MAXKSAT && sat_device) {
+    bool terms_int = true;
+    st = device_sat_build(p.get(), d, p->pspin, &terms_int, s);
+    p->pspin_int = p->pspin_int && terms_int;
+  } else if (kind == FEM_MAXKSAT) st = upload_sat(p.get(), hs, s);  // internal kind
   else if (device_build) st = device_graph_build(p.get(), kind, d->q, d, s);  // sets the weight sums
   else st = upload_graph(p.get(), hg, s);
   p->nodew_sq = nodew_sq;

@@ -227,6 +227,109 @@ __global__ void __launch_bounds__(512) k_sort_rows_block(const int32_t* __restri
   }
 }
 
+// Clause c of a Max-k-SAT / p-spin list: the first check it fails (0 when it passes):
+// 1 pointers (not 0 <= b <= e <= L), 2 more than 8 literals, 3 a literal 0 or out of
+// [-n, n], 4 a variable repeated within the clause; *lit is the offending literal.
+__host__ __device__ inline int clause_defect(const int64_t* ptr, const int32_t* lits, long long c, long long L, int32_t n,
+                                             int32_t* lit) {
+  const long long b = ptr[c], e = ptr[c + 1];
+  if (b < 0 || e < b || e > L) return 1;
+  if (e - b > 8) return 2;
+  for (long long k = b; k < e; ++k) {
+    const int32_t x = lits[k];
+    *lit = x;
+    if (x == 0 || x > n || x < -n) return 3;
+    const int32_t v = x < 0 ? -x : x;
+    for (long long k2 = b; k2 < k; ++k2)
+      if ((lits[k2] < 0 ? -lits[k2] : lits[k2]) == v) return 4;
+  }
+  return 0;
+}
+
+// res[0] = lowest failing clause (all ones when none); widths of the others: res[1] max, res[2] min.
+__global__ void k_sat_check(const int64_t* __restrict__ ptr, const int32_t* __restrict__ lits, int64_t M, int64_t L,
+                            int32_t n, unsigned long long* __restrict__ res) {
+  for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < M; c += (long long)gridDim.x * blockDim.x) {
+    int32_t lit = 0;
+    if (clause_defect(ptr, lits, c, L, n, &lit)) {
+      atomicMin(res, (unsigned long long)c);
+    } else {
+      const unsigned long long w = (unsigned long long)(ptr[c + 1] - ptr[c]);
+      atomicMax(res + 1, w);
+      atomicMin(res + 2, w);
+    }
+  }
+}
+
+// Packed literals (var << 1 | negated), int32 clause pointers and the occurrence counts.
+__global__ void k_sat_count(const int64_t* __restrict__ ptr, const int32_t* __restrict__ lits, int64_t M,
+                            int32_t* __restrict__ cl_ptr, int32_t* __restrict__ cl_lit, int32_t* __restrict__ cnt) {
+  for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < M; c += (long long)gridDim.x * blockDim.x) {
+    const long long b = ptr[c], e = ptr[c + 1];
+    cl_ptr[c] = (int32_t)b;
+    if (c == M - 1) cl_ptr[M] = (int32_t)e;
+    for (long long k = b; k < e; ++k) {
+      const int32_t x = lits[k], v = (x < 0 ? -x : x) - 1;
+      cl_lit[k] = (v << 1) | (x < 0 ? 1 : 0);
+      atomicAdd(cnt + v, 1);
+    }
+  }
+}
+
+// Each literal (clause c, position k) becomes the key (c << 3 | k) in its variable's list.
+__global__ void k_sat_scatter(const int32_t* __restrict__ cl_ptr, const int32_t* __restrict__ cl_lit, int64_t M,
+                              int32_t* __restrict__ cursor, unsigned long long* __restrict__ key) {
+  for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < M; c += (long long)gridDim.x * blockDim.x) {
+    const int32_t b = cl_ptr[c], e = cl_ptr[c + 1];
+    for (int32_t k = b; k < e; ++k)
+      key[atomicAdd(cursor + (cl_lit[k] >> 1), 1)] = ((unsigned long long)c << 3) | (unsigned)(k - b);
+  }
+}
+
+// p-spin terms: J_v with the literals' negations folded in (fp32, fp64, and int64 when
+// an integer of magnitude <= 2^40); res[0] = lowest non-finite term, res[1] bit 0 =
+// some J_v not such an integer.
+__global__ void k_pspin_terms(const int64_t* __restrict__ ptr, const int32_t* __restrict__ lits,
+                              const double* __restrict__ tw, int64_t M, float* __restrict__ pj,
+                              double* __restrict__ pj_f, int64_t* __restrict__ pj_i, unsigned long long* __restrict__ res) {
+  for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < M; c += (long long)gridDim.x * blockDim.x) {
+    double J = tw[c];
+    if (!isfinite(J)) {
+      atomicMin(res, (unsigned long long)c);
+      continue;
+    }
+    for (long long k = ptr[c]; k < ptr[c + 1]; ++k)
+      if (lits[k] < 0) J = -J;
+    const bool integer = J == rint(J) && fabs(J) <= 1099511627776.0;
+    if (!integer) atomicOr(res + 1, 1ull);
+    pj[c] = (float)J;
+    pj_f[c] = J;
+    pj_i[c] = integer ? (int64_t)J : 0;
+  }
+}
+
+// Per occurrence: the packed (clause << 3 | position); with every clause of width 3,
+// the other two literals (the first with the occurrence's own negation in bit 31) and,
+// for p-spin, the term's J.
+__global__ void k_sat_occ(const unsigned long long* __restrict__ key, int64_t L, const int32_t* __restrict__ cl_ptr,
+                          const int32_t* __restrict__ cl_lit, int32_t* __restrict__ occ, int32_t* __restrict__ oth,
+                          const float* __restrict__ pj, float* __restrict__ pjo) {
+  for (long long o = (long long)blockIdx.x * blockDim.x + threadIdx.x; o < L; o += (long long)gridDim.x * blockDim.x) {
+    const int32_t x = (int32_t)key[o], c = x >> 3, pos = x & 7;
+    occ[o] = x;
+    if (oth) {
+      const int32_t b = cl_ptr[c];
+      int32_t other[2], k2 = 0;
+      for (int32_t k = 0; k < 3; ++k)
+        if (k != pos) other[k2++] = cl_lit[b + k];
+      const uint32_t own_neg = (uint32_t)(cl_lit[b + pos] & 1);
+      oth[2 * o] = (int32_t)((uint32_t)other[0] | (own_neg << 31));
+      oth[2 * o + 1] = other[1];
+      if (pjo) pjo[o] = pj[c];
+    }
+  }
+}
+
 // One thread per row: duplicate check, packed columns, weights, row normalisations.
 // dup[0] is set (and dup[1], dup[2] name the pair) when a row repeats a column.
 __global__ void k_finish_rows(const int32_t* __restrict__ row_ptr, const unsigned long long* __restrict__ key,
@@ -265,6 +368,38 @@ int grid_for(long long work, int sm_count, int threads = 256) {
   const long long cap = (long long)sm_count * 8;
   if (b > cap) b = cap;
   return (int)(b < 1 ? 1 : b);
+}
+
+// Sorts every segment [ptr[r], ptr[r + 1]) of key, r < nrows, into increasing order:
+// one warp per segment of up to 32 keys, one block up to kBlockSortMax, the host for
+// the rare longer ones.  big (nrows ints), giant (nrows ints) and counters[0..1] (zero)
+// are scratch.  Returns with the stream synchronised.
+cudaError_t sort_segments(const int32_t* ptr, int32_t nrows, unsigned long long* key, int32_t* big, int32_t* giant,
+                          int32_t* counters, int sm, cudaStream_t s) {
+  k_sort_rows_warp<<<grid_for((long long)nrows * 32, sm), 256, 0, s>>>(ptr, nrows, key, big, counters);
+  k_sort_rows_block<<<sm * 2, 512, 0, s>>>(ptr, key, big, counters, giant, counters + 1);
+  count_launches(2);
+  cudaError_t e = cudaGetLastError();
+  int32_t ngiant = 0;
+  auto sync_copy = [&](void* dst, const void* src, size_t bytes, cudaMemcpyKind kind) {
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dst, src, bytes, kind, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  };
+  sync_copy(&ngiant, counters + 1, sizeof(int32_t), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess || ngiant == 0) return e;
+  std::vector<int32_t> rows(ngiant);
+  sync_copy(rows.data(), giant, sizeof(int32_t) * (size_t)ngiant, cudaMemcpyDeviceToHost);
+  std::vector<unsigned long long> seg;
+  for (int32_t r : rows) {
+    int32_t be[2] = {0, 0};
+    sync_copy(be, ptr + r, sizeof(be), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) break;
+    seg.resize((size_t)(be[1] - be[0]));
+    sync_copy(seg.data(), key + be[0], seg.size() * sizeof(unsigned long long), cudaMemcpyDeviceToHost);
+    std::sort(seg.begin(), seg.end());
+    sync_copy(key + be[0], seg.data(), seg.size() * sizeof(unsigned long long), cudaMemcpyHostToDevice);
+  }
+  return e;
 }
 
 }  // namespace
@@ -382,29 +517,10 @@ fem_status device_graph_build(Problem* p, int32_t kind, int32_t q, const fem_pro
     k_scan_add<<<grid_for(n, sm), 256, 0, s>>>(p->row_ptr, n, sums);
     step(cudaMemcpyAsync(cursor, p->row_ptr, sizeof(int32_t) * (size_t)n, cudaMemcpyDeviceToDevice, s));
     k_scatter<<<grid_for(E, sm), 256, 0, s>>>(ei, ej, E, cursor, key);
-    k_sort_rows_warp<<<grid_for((long long)n * 32, sm), 256, 0, s>>>(p->row_ptr, n, key, big, counters);
-    k_sort_rows_block<<<sm * 2, 512, 0, s>>>(p->row_ptr, key, big, counters, giant, counters + 1);
-    count_launches(7);
+    count_launches(5);
     step(cudaGetLastError());
   }
-  // rows longer than the block sort handles (rare hubs) are sorted on the host
-  int32_t ngiant = 0;
-  if (e == cudaSuccess) step(cudaMemcpyAsync(&ngiant, counters + 1, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
-  if (e == cudaSuccess) step(cudaStreamSynchronize(s));
-  if (e == cudaSuccess && ngiant > 0) {
-    std::vector<int32_t> rows(ngiant);
-    step(cudaMemcpy(rows.data(), giant, sizeof(int32_t) * (size_t)ngiant, cudaMemcpyDeviceToHost));
-    std::vector<unsigned long long> seg;
-    for (int32_t r : rows) {
-      if (e != cudaSuccess) break;
-      int32_t be[2];
-      step(cudaMemcpy(be, p->row_ptr + r, sizeof(be), cudaMemcpyDeviceToHost));
-      seg.resize((size_t)(be[1] - be[0]));
-      step(cudaMemcpy(seg.data(), key + be[0], seg.size() * sizeof(unsigned long long), cudaMemcpyDeviceToHost));
-      std::sort(seg.begin(), seg.end());
-      step(cudaMemcpy(key + be[0], seg.data(), seg.size() * sizeof(unsigned long long), cudaMemcpyHostToDevice));
-    }
-  }
+  if (e == cudaSuccess) step(sort_segments(p->row_ptr, n, key, big, giant, counters, p->sm_count, s));
   int32_t dup[3] = {0, 0, 0};
   if (e == cudaSuccess) {
     k_finish_rows<<<grid_for(n, p->sm_count), 256, 0, s>>>(p->row_ptr, key, n, w, unit ? 1 : 0, integer ? 1 : 0, kind, q,
@@ -417,6 +533,161 @@ fem_status device_graph_build(Problem* p, int32_t kind, int32_t q, const fem_pro
   if (e == cudaSuccess) step(cudaStreamSynchronize(s));
   if (e != cudaSuccess) return cuda_fail(e, "device graph build");
   if (dup[0]) return fail(FEM_ERR_INVALID_ARG, "duplicate edge (%d, %d)", dup[1], dup[2]);
+  return FEM_OK;
+}
+
+}  // namespace fem
+
+namespace fem {
+
+// Max-k-SAT and p-spin clause lists on the device (fem_create_problem for long lists):
+// the clause pointers and literals are copied once, validated (k_sat_check: the lowest
+// failing clause is reported with the host builder's message), packed, counted per
+// variable, scanned into the occurrence pointers, scattered as (clause << 3 | position)
+// keys and sorted per variable, so every variable's occurrences are in clause order as
+// the host builder lists them; then the per-occurrence tables.  p-spin terms are folded
+// with their literals' negations here too.  Sets the clause fields of p (and pj, pj_f,
+// pj_i, pjo and *terms_int for p-spin).
+fem_status device_sat_build(Problem* p, const fem_problem_desc* d, bool pspin, bool* terms_int, cudaStream_t s) {
+  const int32_t n = d->n;
+  const int64_t M = d->n_clauses, L = d->clause_ptr[M];
+  const int sm = p->sm_count;
+  p->n_clauses = M;
+  p->n_occ = L;
+  const int ntiles = (int)((n + kScanTile - 1) / kScanTile);
+  int64_t* dptr = nullptr;
+  int32_t *dlits = nullptr, *cnt = nullptr, *sums = nullptr, *cursor = nullptr, *big = nullptr, *counters = nullptr;
+  double* tw = nullptr;
+  unsigned long long *key = nullptr, *res = nullptr;
+  std::vector<void*> tmp;
+  auto talloc = [&](void** ptr, size_t bytes) -> fem_status {
+    const cudaError_t e = cudaMallocAsync(ptr, bytes < 16 ? 16 : bytes, s);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      *ptr = nullptr;
+      return fail(FEM_ERR_OOM, "device clause build: %zu bytes of scratch", bytes);
+    }
+    tmp.push_back(*ptr);
+    return FEM_OK;
+  };
+  auto release = [&]() {
+    for (void* x : tmp) cudaFreeAsync(x, s);
+    tmp.clear();
+  };
+  fem_status st = FEM_OK;
+  if (st == FEM_OK) st = talloc((void**)&dptr, sizeof(int64_t) * (size_t)(M + 1));
+  if (st == FEM_OK) st = talloc((void**)&dlits, sizeof(int32_t) * (size_t)L);
+  if (st == FEM_OK) st = talloc((void**)&res, sizeof(unsigned long long) * 4);
+  if (st == FEM_OK && pspin) st = talloc((void**)&tw, sizeof(double) * (size_t)M);
+  if (st != FEM_OK) {
+    release();
+    return st;
+  }
+  // 0. copy and validate; nothing indexes with a literal before this has passed
+  cudaError_t e = cudaMemcpyAsync(dptr, d->clause_ptr, sizeof(int64_t) * (size_t)(M + 1), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(dlits, d->lits, sizeof(int32_t) * (size_t)L, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess && pspin) e = cudaMemcpyAsync(tw, d->term_weight, sizeof(double) * (size_t)M, cudaMemcpyHostToDevice, s);
+  const unsigned long long init[4] = {~0ull, 0ull, ~0ull, 0ull};  // first bad, max width, min width, unused
+  if (e == cudaSuccess) e = cudaMemcpyAsync(res, init, sizeof(init), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) {
+    k_sat_check<<<grid_for(M, sm), 256, 0, s>>>(dptr, dlits, M, L, n, res);
+    count_launches(1);
+    e = cudaGetLastError();
+  }
+  unsigned long long chk[4] = {0, 0, 0, 0};
+  if (e == cudaSuccess) e = cudaMemcpyAsync(chk, res, sizeof(chk), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) {
+    release();
+    return cuda_fail(e, "device clause build: check");
+  }
+  if (chk[0] != ~0ull) {
+    release();
+    const long long c = (long long)chk[0];
+    int32_t lit = 0;
+    const int why = clause_defect(d->clause_ptr, d->lits, c, L, n, &lit);
+    if (why == 2) return fail(FEM_ERR_UNSUPPORTED, "clause %lld has more than 8 literals", c);
+    if (why == 3) return fail(FEM_ERR_INVALID_ARG, "clause %lld: literal %d out of range", c, lit);
+    if (why == 4) return fail(FEM_ERR_INVALID_ARG, "clause %lld repeats variable %d", c, lit < 0 ? -lit : lit);
+    return fail(FEM_ERR_INVALID_ARG, "clause_ptr must be non-decreasing and end at the literal count");
+  }
+  const int32_t max_w = (int32_t)chk[1], min_w = (int32_t)chk[2];
+  p->max_width = max_w;
+  const bool three = M > 0 && min_w == 3 && max_w == 3;
+  // p-spin terms (their validation follows the clauses', as on the host)
+  if (pspin) {
+    if ((st = dev_alloc_t(p, &p->pj, (size_t)M)) != FEM_OK || (st = dev_alloc_t(p, &p->pj_f, (size_t)M)) != FEM_OK ||
+        (st = dev_alloc_t(p, &p->pj_i, (size_t)M)) != FEM_OK) {
+      release();
+      return st;
+    }
+    const unsigned long long tinit[2] = {~0ull, 0ull};
+    e = cudaMemcpyAsync(res, tinit, sizeof(tinit), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) {
+      k_pspin_terms<<<grid_for(M, sm), 256, 0, s>>>(dptr, dlits, tw, M, p->pj, p->pj_f, p->pj_i, res);
+      count_launches(1);
+      e = cudaGetLastError();
+    }
+    unsigned long long tr[2] = {0, 0};
+    if (e == cudaSuccess) e = cudaMemcpyAsync(tr, res, sizeof(tr), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) {
+      release();
+      return cuda_fail(e, "device clause build: terms");
+    }
+    if (tr[0] != ~0ull) {
+      release();
+      return fail(FEM_ERR_INVALID_ARG, "term_weight[%lld] must be finite", (long long)tr[0]);
+    }
+    *terms_int = (tr[1] & 1ull) == 0;
+  }
+  // 1. packed literals, counts, occurrence pointers
+  if ((st = dev_alloc_t(p, &p->cl_ptr, (size_t)M + 1)) != FEM_OK || (st = dev_alloc_t(p, &p->cl_lit, (size_t)L)) != FEM_OK ||
+      (st = dev_alloc_t(p, &p->occ_ptr, (size_t)n + 1)) != FEM_OK || (st = dev_alloc_t(p, &p->occ, (size_t)L)) != FEM_OK ||
+      (three && (st = dev_alloc_t(p, &p->oth, 2 * (size_t)L)) != FEM_OK) ||
+      (three && pspin && (st = dev_alloc_t(p, &p->pjo, (size_t)L)) != FEM_OK)) {
+    release();
+    return st;
+  }
+  if (st == FEM_OK) st = talloc((void**)&cnt, sizeof(int32_t) * (size_t)n);
+  if (st == FEM_OK) st = talloc((void**)&sums, sizeof(int32_t) * (size_t)ntiles);
+  if (st == FEM_OK) st = talloc((void**)&cursor, sizeof(int32_t) * (size_t)n);
+  if (st == FEM_OK) st = talloc((void**)&big, sizeof(int32_t) * (size_t)n);
+  if (st == FEM_OK) st = talloc((void**)&counters, sizeof(int32_t) * 8);
+  if (st == FEM_OK) st = talloc((void**)&key, sizeof(unsigned long long) * (size_t)L);
+  if (st != FEM_OK) {
+    release();
+    return st;
+  }
+  e = cudaMemsetAsync(cnt, 0, sizeof(int32_t) * (size_t)n, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(counters, 0, sizeof(int32_t) * 8, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(p->occ_ptr, 0, sizeof(int32_t), s);
+  if (e == cudaSuccess) {
+    k_sat_count<<<grid_for(M, sm), 256, 0, s>>>(dptr, dlits, M, p->cl_ptr, p->cl_lit, cnt);
+    k_scan_tiles<<<ntiles, kScanThreads, 0, s>>>(cnt, n, p->occ_ptr, sums);
+    k_scan_sums<<<1, kScanThreads, 0, s>>>(sums, ntiles);
+    k_scan_add<<<grid_for(n, sm), 256, 0, s>>>(p->occ_ptr, n, sums);
+    count_launches(4);
+    e = cudaGetLastError();
+  }
+  // 2. keys into the variables' lists, sorted into clause order
+  if (e == cudaSuccess) e = cudaMemcpyAsync(cursor, p->occ_ptr, sizeof(int32_t) * (size_t)n, cudaMemcpyDeviceToDevice, s);
+  if (e == cudaSuccess) {
+    k_sat_scatter<<<grid_for(M, sm), 256, 0, s>>>(p->cl_ptr, p->cl_lit, M, cursor, key);
+    count_launches(1);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = sort_segments(p->occ_ptr, n, key, big, cursor, counters, sm, s);
+  // 3. the per-occurrence tables
+  if (e == cudaSuccess && L > 0) {
+    k_sat_occ<<<grid_for(L, sm), 256, 0, s>>>(key, L, p->cl_ptr, p->cl_lit, p->occ, three ? p->oth : nullptr,
+                                               p->pj, three && pspin ? p->pjo : nullptr);
+    count_launches(1);
+    e = cudaGetLastError();
+  }
+  release();
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail(e, "device clause build");
   return FEM_OK;
 }
 

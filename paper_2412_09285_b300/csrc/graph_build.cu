@@ -15,7 +15,9 @@
 //      bMinCut: c^f = q / sum_j W_ij, c^a = q / sqrt(sum_j W_ij)).
 // The columns of a row end up in increasing order and every row sum is taken in that
 // order in fp64, exactly as in the host builder, so both give the same arrays bit
-// for bit.
+// for bit.  Long clause lists (Max-k-SAT, p-spin) go through the same machinery
+// (device_sat_build at the end of this file): validation, packed literals, counts, the
+// scan, a scatter of (clause << 3 | position) keys and the per-variable sorts.
 #include <cuda_runtime.h>
 
 #include <algorithm>

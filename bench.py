@@ -297,6 +297,7 @@ def _make_problem(fem, wl, inst, stream, dense_launch="auto"):
 # summary's traffic figure counts only while they are unchanged.
 KERNEL_SOURCES = {
     "sparse": ["maxcut_sparse.cu", "step_common.cuh", "step_scalars.h"],
+    "exact": ["maxcut_gather.cu", "step_common.cuh", "step_scalars.h"],
     "dense": ["dense_tc.cu", "step_common.cuh", "step_scalars.h"],
     "batched": ["batch.cu", "bmincut_core.cuh", "sat_core.cuh", "step_common.cuh", "step_scalars.h"],
     "bmincut": ["bmincut_sparse.cu", "bmincut_core.cuh", "step_common.cuh", "step_scalars.h"],
@@ -305,7 +306,7 @@ KERNEL_SOURCES = {
 # the committed ncu summary of each single-problem workload whose traffic is reported
 _SINGLE_PROFILES = {"bmincut": ("bmincut_step_rgg1M_q4_R16.md", "bmincut"), "sat": ("sat_step_3sat1M_R16.md", "sat"),
                     "pspin": ("pspin_step_3spin1M_R16.md", "sat"),
-                    "qubo": ("maxcut_step_exact_n1M_R32.md", "sparse", "qubo_traffic_bytes_per_launch")}
+                    "qubo": ("maxcut_step_exact_n1M_R32.md", "exact", "qubo_traffic_bytes_per_launch")}
 
 
 def source_sha256(kind):
@@ -377,7 +378,7 @@ def _roofline(wl, inst, step_ms, precision, dense_launch=None, grad_mode="paper"
             # the exact-mode MaxCut step: h, m, v, the gathered marginals m = tanh(h/2) read
             # once and written once, CSR, sign words, per-node offsets
             alg = 24 * n * R_ + 8 * n * R_ + 4 * nnz + 4 * (n + 1) + 4 * n * (R_ // 32) + 4 * n
-            kernel = "k_maxcut_step<exact, adam, unit> (QUBO offsets)"
+            kernel = "k_exact_gather<adam, unit> (QUBO offsets)"
         elif pr == "sat":
             L = inst.units
             # h, m, v, the marginals read once and written once, occurrence pointers and
@@ -407,9 +408,9 @@ def _roofline(wl, inst, step_ms, precision, dense_launch=None, grad_mode="paper"
         ach = alg / (step_ms / 1e3) / 1e9
         return {"bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                 "frac": ach / peaks["hbm_gbs"],
-                "traffic": (_traffic_from_profile("maxcut_step_exact_n1M_R32.md", "sparse")
+                "traffic": (_traffic_from_profile("maxcut_step_exact_n1M_R32.md", "exact")
                             if wl is WORKLOADS["sparse"] and opt == "adam" else None),
-                "kernel": f"k_maxcut_step<exact, {opt}, unit>", "algorithmic_bytes_per_launch": alg,
+                "kernel": f"k_exact_gather<{opt}, unit>", "algorithmic_bytes_per_launch": alg,
                 "launch_ms": step_ms, "peak_source": f"{src} hbm_gbs (copy), of {src}",
                 "frac_of_8TBs": ach / 8000.0}
     if wl["kind"] == "sparse":

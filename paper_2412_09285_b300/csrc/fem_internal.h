@@ -101,6 +101,9 @@ struct Problem {
   // exact mode, what a neighbour term gathers, ping-pong: sparse MaxCut / QUBO m = tanh(h/2)
   // ([n][R]); bMinCut and colouring q (P(s) - 1/q) ([n][R][q], allocated on first use)
   float* mag[2] = {nullptr, nullptr};
+  CUtensorMap tmap_mag[2];                       // exact-mode MaxCut: mag[b] for the gather kernel
+  const float* tmap_mag_for[2] = {nullptr, nullptr};
+  int32_t tmap_mag_R = 0;
   int32_t words_per_node = 0;
   void* mt[2] = {nullptr, nullptr};    // dense: discretised marginals for the tensor cores
   int32_t* cnt[3] = {nullptr, nullptr, nullptr};  // bMinCut group counts n_r(s), [R][q], rotating
@@ -173,6 +176,11 @@ fem_status dense_upload(Problem* p, const float* J, cudaStream_t s);
 // dense_build.cu: validates the caller's n x n couplings on the device and writes the
 // operand copies, c_i, the sum above the diagonal and the e4m3 flag into p.
 fem_status dense_build(Problem* p, const float* J, cudaStream_t s);
+// maxcut_gather.cu: one exact-mode sparse MaxCut / QUBO step with TMA gathers, reading
+// h[in], mag[in] and writing h[in ^ 1], mag[in ^ 1], words[in ^ 1].
+fem_status maxcut_exact_gather_step(Problem* p, int in, const StepScalars& s, cudaStream_t st);
+// Whether exact-mode sparse MaxCut / QUBO steps take the TMA-gather kernel (fem_set_exact_gather).
+bool exact_gather_enabled();
 fem_status dense_state(Problem* p, int R, int prec, cudaStream_t s);
 fem_status dense_set_fields(Problem* p, const float* h_nr, bool on_device, cudaStream_t s);
 fem_status dense_get(Problem* p, const float* src_rn, float* dst_nr_host, cudaStream_t s);

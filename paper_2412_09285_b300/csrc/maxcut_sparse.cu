@@ -37,12 +37,13 @@ struct MaxcutArgs {
   const float* offset;  // exact mode: per-node constant of the field (QUBO), NULL for MaxCut
 };
 
-// Exact-mode step: one warp per (node, block of 32 replicas); lane = replica.
-// Neighbour column indices are loaded 32 at a time (one coalesced load) and
+// Exact-mode step, direct gathers: one warp per (node, block of 32 replicas); lane =
+// replica.  Neighbour column indices are loaded 32 at a time (one coalesced load) and
 // broadcast by shuffles; each lane gathers its replica's m_j of every neighbour (a
-// 128-byte line per neighbour and warp).  The kernel is bound by those gathers,
-// most of which miss L2 at n = 2^20 (m is 128 MiB); grouping nodes per warp,
-// eviction hints and replica blocking were all slower.
+// 128-byte line per neighbour and warp).  Bound by those gathers, most of which miss
+// L2 at n = 2^20 (m is 128 MiB).  The default exact-mode kernel is the TMA-gather
+// tile kernel (maxcut_gather.cu), which computes the same sums in the same order with
+// the same update; this one stays as its reference (fem_set_exact_gather(0)).
 template <int OPT, bool UNIT>
 __global__ void __launch_bounds__(256) k_maxcut_step(MaxcutArgs a, StepScalars s) {
   const int lane = threadIdx.x & 31;
@@ -81,8 +82,8 @@ __global__ void __launch_bounds__(256) k_maxcut_step(MaxcutArgs a, StepScalars s
     // sum_j Q_ij m_j + (sum_j Q_ij + d_i)
     float field = a.ccoef * facc;
     if (a.offset) field += a.offset[i];
-    const float g = s.gq * (field + hi * s.inv_beta) * one_minus_m2(hi);
-    opt_update<OPT>(hi, mi, vi, g, s);
+    const float g = s.gq * (field + hi * s.inv_beta) * one_minus_m2_fast(hi);
+    opt_update_fast<OPT>(hi, mi, vi, g, s);
     a.h_out[idx] = hi;
     a.m[idx] = mi;
     if (OPT != FEM_OPT_SGD) a.v[idx] = vi;
@@ -556,6 +557,17 @@ fem_status maxcut_sparse_steps(Problem* p, const fem_anneal_params& a,
   args.v = p->v;
   args.ccoef = p->qubo ? 1.f : 2.f;
   args.offset = p->qubo ? p->qoff : nullptr;
+  if (p->grad_mode == FEM_GRAD_EXACT && exact_gather_enabled()) {
+    // the TMA-gather kernel (maxcut_gather.cu): the same arithmetic and bits
+    for (size_t k = 0; k < sc.size(); ++k) {
+      const fem_status st = maxcut_exact_gather_step(p, p->cur, sc[k], s);
+      if (st != FEM_OK) return st;
+      p->cur ^= 1;
+    }
+    count_launches((int64_t)sc.size());
+    FEM_CUDA(cudaGetLastError());
+    return FEM_OK;
+  }
   for (size_t k = 0; k < sc.size(); ++k) {
     if (p->grad_mode == FEM_GRAD_PAPER) {
       args.h_in = p->h[0];

@@ -84,6 +84,7 @@ def _load():
         "fem_anneal_batch": (S, [P, C.c_int32, C.POINTER(fem_anneal_params), P, P]),
         "fem_inject_allocation_failure": (None, [C.c_int64]),
         "fem_set_device_graph_build": (None, [C.c_int64]),
+        "fem_set_exact_gather": (None, [C.c_int32]),
         "fem_destroy": (None, [P]),
         "fem_status_string": (C.c_char_p, [S]),
         "fem_last_error": (C.c_char_p, []),
@@ -211,6 +212,12 @@ def fem_inject_step_stall(handle, row_tile):
 def fem_set_device_graph_build(min_edges):
     """Graphs with at least min_edges edges build their CSR on the device (< 0: never)."""
     _lib.fem_set_device_graph_build(int(min_edges))
+
+
+def fem_set_exact_gather(on):
+    """Exact-mode sparse MaxCut / QUBO steps on the TMA-gather kernel (True, the default)
+    or the direct-gather kernel (False); both give the same bits."""
+    _lib.fem_set_exact_gather(1 if on else 0)
 
 
 def fem_inject_allocation_failure(after):

@@ -418,9 +418,9 @@ void fem_set_device_graph_build(int64_t min_edges);
 
 /* Which kernel runs the exact-gradient steps of sparse MaxCut and QUBO: on (the
  * default) the tile kernel whose neighbour gathers are TMA gather4 copies into shared
- * memory, off the kernel that gathers each neighbour's line directly.  Both compute
- * the same sums in the same order and give the same bits.  Process-wide. */
-void fem_set_exact_gather(int32_t on);
+ * memory, off the kernel that gathers each neighbour's line directly.  Both compute the
+ * same sums in the same order and give the same bits.  Process-wide. */
+void fem_set_tma_gather(int32_t on);
 
 /* MaxCut energies of caller-provided sign words, without allocating.
  * The paper has no counterpart: this is a library service for callers that cannot

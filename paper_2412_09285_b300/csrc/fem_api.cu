@@ -533,9 +533,9 @@ static fem_status check_sticky(Problem* p, cudaStream_t s) {
   return FEM_OK;
 }
 
-// fem_set_exact_gather: exact-mode sparse MaxCut / QUBO steps on the TMA-gather kernel.
-static std::atomic<int32_t> g_exact_gather{1};
-bool exact_gather_enabled() { return g_exact_gather.load() != 0; }
+// fem_set_tma_gather: exact-mode sparse MaxCut / QUBO steps on the TMA-gather kernel.
+static std::atomic<int32_t> g_tma_gather{1};
+bool tma_gather_enabled() { return g_tma_gather.load() != 0; }
 
 }  // namespace fem
 
@@ -966,7 +966,7 @@ fem_status fem_inject_step_stall(fem_problem_t p, int32_t row_tile) {
 
 void fem_set_device_graph_build(int64_t min_edges) { g_device_build_min_edges.store(min_edges); }
 
-void fem_set_exact_gather(int32_t on) { fem::g_exact_gather.store(on ? 1 : 0); }
+void fem_set_tma_gather(int32_t on) { fem::g_tma_gather.store(on ? 1 : 0); }
 
 void fem_inject_allocation_failure(int64_t after) { g_fail_alloc_after.store(after < 0 ? -1 : after); }
 

@@ -43,7 +43,7 @@ struct MaxcutArgs {
 // 128-byte line per neighbour and warp).  Bound by those gathers, most of which miss
 // L2 at n = 2^20 (m is 128 MiB).  The default exact-mode kernel is the TMA-gather
 // tile kernel (maxcut_gather.cu), which computes the same sums in the same order with
-// the same update; this one stays as its reference (fem_set_exact_gather(0)).
+// the same update; this one stays as its reference (fem_set_tma_gather(0)).
 template <int OPT, bool UNIT>
 __global__ void __launch_bounds__(256) k_maxcut_step(MaxcutArgs a, StepScalars s) {
   const int lane = threadIdx.x & 31;
@@ -557,7 +557,7 @@ fem_status maxcut_sparse_steps(Problem* p, const fem_anneal_params& a,
   args.v = p->v;
   args.ccoef = p->qubo ? 1.f : 2.f;
   args.offset = p->qubo ? p->qoff : nullptr;
-  if (p->grad_mode == FEM_GRAD_EXACT && exact_gather_enabled()) {
+  if (p->grad_mode == FEM_GRAD_EXACT && tma_gather_enabled()) {
     // the TMA-gather kernel (maxcut_gather.cu): the same arithmetic and bits
     for (size_t k = 0; k < sc.size(); ++k) {
       const fem_status st = maxcut_exact_gather_step(p, p->cur, sc[k], s);

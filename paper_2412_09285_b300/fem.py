@@ -84,7 +84,7 @@ def _load():
         "fem_anneal_batch": (S, [P, C.c_int32, C.POINTER(fem_anneal_params), P, P]),
         "fem_inject_allocation_failure": (None, [C.c_int64]),
         "fem_set_device_graph_build": (None, [C.c_int64]),
-        "fem_set_exact_gather": (None, [C.c_int32]),
+        "fem_set_tma_gather": (None, [C.c_int32]),
         "fem_destroy": (None, [P]),
         "fem_status_string": (C.c_char_p, [S]),
         "fem_last_error": (C.c_char_p, []),
@@ -214,10 +214,10 @@ def fem_set_device_graph_build(min_edges):
     _lib.fem_set_device_graph_build(int(min_edges))
 
 
-def fem_set_exact_gather(on):
-    """Exact-mode sparse MaxCut / QUBO steps on the TMA-gather kernel (True, the default)
-    or the direct-gather kernel (False); both give the same bits."""
-    _lib.fem_set_exact_gather(1 if on else 0)
+def fem_set_tma_gather(on):
+    """Exact-mode sparse MaxCut / QUBO steps on the TMA-gather tile kernel (True, the
+    default) or the direct-gather kernel (False); both give the same bits."""
+    _lib.fem_set_tma_gather(1 if on else 0)
 
 
 def fem_inject_allocation_failure(after):

@@ -23,7 +23,7 @@ def fem():
     build.build()
     from paper_2412_09285_b300 import fem as F
     yield F
-    F.fem_set_exact_gather(True)
+    F.fem_set_tma_gather(True)
 
 
 def _with_hubs(g, spec, seed):
@@ -41,11 +41,11 @@ def _with_hubs(g, spec, seed):
 def _both(fem, make, R, n_steps=120, t_end=60, **kw):
     out = []
     for on in (True, False):
-        fem.fem_set_exact_gather(on)
+        fem.fem_set_tma_gather(on)
         P = make()
         P.anneal(h_init=I.initial_fields(P.n, R, seed=7), n_steps=n_steps, t_end=t_end, grad_mode="exact", **kw)
         out.append((P.state(), P.best()))
-    fem.fem_set_exact_gather(True)
+    fem.fem_set_tma_gather(True)
     (sa, ra), (sb, rb) = out
     for x, y, name in zip(sa, sb, "hmv"):
         assert np.array_equal(x, y), name

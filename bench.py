@@ -298,6 +298,7 @@ def _make_problem(fem, wl, inst, stream, dense_launch="auto"):
 KERNEL_SOURCES = {
     "sparse": ["maxcut_sparse.cu", "step_common.cuh", "step_scalars.h"],
     "exact": ["maxcut_gather.cu", "step_common.cuh", "step_scalars.h"],
+    "paper_tile": ["maxcut_paper_tile.cu", "step_common.cuh", "step_scalars.h"],
     "dense": ["dense_tc.cu", "step_common.cuh", "step_scalars.h"],
     "batched": ["batch.cu", "bmincut_core.cuh", "sat_core.cuh", "step_common.cuh", "step_scalars.h"],
     "bmincut": ["bmincut_sparse.cu", "bmincut_core.cuh", "step_common.cuh", "step_scalars.h"],
@@ -419,11 +420,16 @@ def _roofline(wl, inst, step_ms, precision, dense_launch=None, grad_mode="paper"
         # row_ptr, the sign words read once and written once (4 B per node per 32 replicas)
         alg = sb * n * R + 4 * nnz + 4 * (n + 1) + 8 * n * (R // 32)
         ach = alg / (step_ms / 1e3) / 1e9
+        # the staged tile kernel runs graphs of >= 4096 groups of four nodes (not with SGD)
+        groups4 = (n + 3) // 4
+        tile = opt != "sgd" and groups4 >= 4096
+        kernel = (f"k_paper_tile<{opt}, unit>" if tile
+                  else f"k_maxcut_step_paper<{opt}, unit, {4 if groups4 >= 4096 else 1}>")
         return {"bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                 "frac": ach / peaks["hbm_gbs"],
-                "traffic": (_traffic_from_profile("maxcut_step_sparse_n1M_R32.md", "sparse")
+                "traffic": (_traffic_from_profile("maxcut_step_sparse_n1M_R32.md", "paper_tile")
                             if wl is WORKLOADS["sparse"] and opt == "adam" else None),
-                "kernel": f"k_maxcut_step_paper<{opt}, unit, 4>", "algorithmic_bytes_per_launch": alg,
+                "kernel": kernel, "algorithmic_bytes_per_launch": alg,
                 "launch_ms": step_ms, "peak_source": f"{src} hbm_gbs (copy), of {src}",
                 "frac_of_8TBs": ach / 8000.0}
     n = inst.n

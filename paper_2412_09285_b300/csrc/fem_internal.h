@@ -179,7 +179,10 @@ fem_status dense_build(Problem* p, const float* J, cudaStream_t s);
 // maxcut_gather.cu: one exact-mode sparse MaxCut / QUBO step with TMA gathers, reading
 // h[in], mag[in] and writing h[in ^ 1], mag[in ^ 1], words[in ^ 1].
 fem_status maxcut_exact_gather_step(Problem* p, int in, const StepScalars& s, cudaStream_t st);
-// Whether exact-mode sparse MaxCut / QUBO steps take the TMA-gather kernel (fem_set_tma_gather).
+// maxcut_paper_tile.cu: one paper-mode sparse MaxCut step with staged operands, reading
+// words[in] and writing words[in ^ 1] (h, m, v in place).
+fem_status maxcut_paper_tile_step(Problem* p, int in, const StepScalars& s, cudaStream_t st);
+// Whether the sparse MaxCut / QUBO steps take the staged tile kernels (fem_set_tma_gather).
 bool tma_gather_enabled();
 fem_status dense_state(Problem* p, int R, int prec, cudaStream_t s);
 fem_status dense_set_fields(Problem* p, const float* h_nr, bool on_device, cudaStream_t s);

@@ -1,11 +1,13 @@
-"""The exact-gradient sparse MaxCut / QUBO step on its two kernels: the tile kernel
-whose neighbour lines arrive by TMA gather4 copies (the default) and the kernel that
-gathers each line directly.  Both sum the neighbours in CSR order with the same fp32
-update, so every field, moment and energy must agree bit for bit: unit, +-1 and real
-weights; hub rows longer than a tile's staged capacity (the direct-gather remainder);
-isolated nodes and n not a multiple of the 32-node tile; R = 32 and 64 (two replica
-blocks); QUBO offsets; Adam, RMSprop and SGD.  The oracle parity of exact mode runs in
-tests/test_maxcut_gpu.py and tests/test_qubo_gpu.py on the default kernel."""
+"""The sparse MaxCut / QUBO steps on their two kernels each: the tile kernels that stage
+their operands in shared memory (the defaults: exact mode with TMA gather4 copies of
+the neighbours' lines, paper mode with bulk copies of the state and producer-gathered
+sign words) and the kernels that load everything directly.  Both sum the neighbours in
+CSR order with the same fp32 update, so every field, moment and energy must agree bit
+for bit: unit, +-1 and real weights; hub rows longer than a tile's staged capacity
+(the direct remainder); isolated nodes and n not a multiple of the tile; R = 32 and 64
+(two replica blocks); QUBO offsets; Adam, RMSprop and SGD; both gradient modes.  The
+oracle parity of both modes runs in tests/test_maxcut_gpu.py and tests/test_qubo_gpu.py
+on the default kernels."""
 import numpy as np
 import pytest
 
@@ -38,12 +40,12 @@ def _with_hubs(g, spec, seed):
     return I.Graph(g.n, [a for a, _ in e], [b for _, b in e], [have[k] for k in e])
 
 
-def _both(fem, make, R, n_steps=120, t_end=60, **kw):
+def _both(fem, make, R, n_steps=120, t_end=60, mode="exact", **kw):
     out = []
     for on in (True, False):
         fem.fem_set_tma_gather(on)
         P = make()
-        P.anneal(h_init=I.initial_fields(P.n, R, seed=7), n_steps=n_steps, t_end=t_end, grad_mode="exact", **kw)
+        P.anneal(h_init=I.initial_fields(P.n, R, seed=7), n_steps=n_steps, t_end=t_end, grad_mode=mode, **kw)
         out.append((P.state(), P.best()))
     fem.fem_set_tma_gather(True)
     (sa, ra), (sb, rb) = out
@@ -53,24 +55,29 @@ def _both(fem, make, R, n_steps=120, t_end=60, **kw):
     assert ra["best_replica"] == rb["best_replica"]
 
 
+@pytest.mark.parametrize("mode", ["exact", "paper"])
 @pytest.mark.parametrize("weights", ["unit", "pm1", "real"])
 @pytest.mark.parametrize("R", [32, 64])
-def test_gather_kernel_equals_direct_kernel(fem, weights, R):
-    g = I.er_gnm(20011, 60000, seed=3, weights=weights)   # n not a multiple of 32
-    _both(fem, lambda: fem.Problem("maxcut", graph=g), R)
+def test_tile_kernel_equals_direct_kernel(fem, weights, R, mode):
+    g = I.er_gnm(20011, 60000, seed=3, weights=weights)   # n not a multiple of the tile
+    _both(fem, lambda: fem.Problem("maxcut", graph=g), R, mode=mode)
 
 
-def test_hub_rows_and_isolated_nodes(fem):
+@pytest.mark.parametrize("mode", ["exact", "paper"])
+@pytest.mark.parametrize("weights", ["pm1", "real"])
+def test_hub_rows_and_isolated_nodes(fem, mode, weights):
     g = _with_hubs(I.er_gnm(20000, 30000, seed=4, weights="pm1"), [(3, 300), (1, 6000)], seed=5)
-    sparse = I.Graph(1 << 16, g.ei, g.ej, g.w)   # many isolated nodes
-    _both(fem, lambda: fem.Problem("maxcut", graph=sparse), 32)
+    w = g.w if weights == "pm1" else np.random.Generator(np.random.PCG64(55)).uniform(0.5, 2.0, g.n_edges)
+    sparse = I.Graph(1 << 16, g.ei, g.ej, w)   # many isolated nodes
+    _both(fem, lambda: fem.Problem("maxcut", graph=sparse), 32, mode=mode)
 
 
+@pytest.mark.parametrize("mode", ["exact", "paper"])
 @pytest.mark.parametrize("opt,kw", [("rmsprop", dict(lr=0.02, alpha=0.9, momentum=0.5)),
                                     ("sgd", dict(lr=0.5, momentum=0.6, dampening=0.1))])
-def test_other_optimizers(fem, opt, kw):
+def test_other_optimizers(fem, opt, kw, mode):
     g = I.er_gnm(9000, 27000, seed=6, weights="pm1")
-    _both(fem, lambda: fem.Problem("maxcut", graph=g), 32, optimizer=opt, **kw)
+    _both(fem, lambda: fem.Problem("maxcut", graph=g), 32, mode=mode, optimizer=opt, **kw)
 
 
 def test_qubo_offsets(fem):
@@ -79,6 +86,7 @@ def test_qubo_offsets(fem):
     _both(fem, lambda: fem.Problem("qubo", graph=g, linear=d), 32)
 
 
-def test_full_size_one_window(fem):
+@pytest.mark.parametrize("mode", ["exact", "paper"])
+def test_full_size_one_window(fem, mode):
     g = I.er_gnm(1 << 20, 3 << 20, seed=2024, weights="pm1")
-    _both(fem, lambda: fem.Problem("maxcut", graph=g), 32, n_steps=2000, t_end=5)
+    _both(fem, lambda: fem.Problem("maxcut", graph=g), 32, n_steps=2000, t_end=5, mode=mode)

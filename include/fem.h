@@ -416,10 +416,12 @@ int64_t fem_kernel_launches(void);
  * Dense couplings are always copied once and validated and converted on the device. */
 void fem_set_device_graph_build(int64_t min_edges);
 
-/* Which kernel runs the exact-gradient steps of sparse MaxCut and QUBO: on (the
- * default) the tile kernel whose neighbour gathers are TMA gather4 copies into shared
- * memory, off the kernel that gathers each neighbour's line directly.  Both compute the
- * same sums in the same order and give the same bits.  Process-wide. */
+/* Which kernels run the sparse MaxCut and QUBO steps: on (the default) the tile kernels
+ * that stage their operands in shared memory ahead of use - exact mode with TMA gather4
+ * copies of the neighbours' lines, paper mode (Adam and RMSprop, graphs of at least
+ * 4096 groups of four nodes) with bulk copies of the state and sign words gathered by a
+ * producer warp - off the kernels that load everything directly.  Both compute the same
+ * sums in the same order and give the same bits.  Process-wide. */
 void fem_set_tma_gather(int32_t on);
 
 /* MaxCut energies of caller-provided sign words, without allocating.

@@ -533,7 +533,7 @@ static fem_status check_sticky(Problem* p, cudaStream_t s) {
   return FEM_OK;
 }
 
-// fem_set_tma_gather: exact-mode sparse MaxCut / QUBO steps on the TMA-gather kernel.
+// fem_set_tma_gather: sparse MaxCut / QUBO steps on the staged tile kernels.
 static std::atomic<int32_t> g_tma_gather{1};
 bool tma_gather_enabled() { return g_tma_gather.load() != 0; }
 

@@ -215,8 +215,9 @@ def fem_set_device_graph_build(min_edges):
 
 
 def fem_set_tma_gather(on):
-    """Exact-mode sparse MaxCut / QUBO steps on the TMA-gather tile kernel (True, the
-    default) or the direct-gather kernel (False); both give the same bits."""
+    """Sparse MaxCut / QUBO steps on the staged tile kernels (True, the default: exact mode
+    with TMA gather4 copies, paper mode with bulk-copied state) or the direct kernels
+    (False); both give the same bits."""
     _lib.fem_set_tma_gather(1 if on else 0)
 
 

@@ -311,9 +311,12 @@ _SINGLE_PROFILES = {"bmincut": ("bmincut_step_rgg1M_q4_R16.md", "bmincut"), "sat
 
 
 def source_sha256(kind):
-    """sha256 over the concatenated sources of one kernel family (see KERNEL_SOURCES)."""
+    """sha256 over the code-generation flags and the concatenated sources of one kernel
+    family (see KERNEL_SOURCES)."""
+    from paper_2412_09285_b300 import build as B
     csrc = os.path.join(ROOT, "paper_2412_09285_b300", "csrc")
     h = hashlib.sha256()
+    h.update(" ".join(B.ARCH + B.CODEGEN).encode())
     for f in KERNEL_SOURCES[kind]:
         with open(os.path.join(csrc, f), "rb") as fh:
             h.update(fh.read())

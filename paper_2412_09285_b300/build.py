@@ -19,8 +19,15 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libfem.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall",
-         "--expt-relaxed-constexpr", "-I", INCLUDE, "-I", CSRC]
+# Code generation.  -ftz=true flushes single-precision denormals to zero in every
+# kernel: the approximate exponential, reciprocal and square root of the step kernels
+# then run without their denormal handling (fewer instructions in kernels bound by
+# instruction issue), while divisions and square roots written as such stay
+# IEEE-rounded (prec-div, prec-sqrt).  fp64 arithmetic is not affected.
+CODEGEN = ["-O3", "-std=c++17", "-lineinfo", "-ftz=true"]
+FLAGS = CODEGEN + ["-Xcompiler", "-fPIC", "-Xcompiler", "-Wall", "--expt-relaxed-constexpr",
+                   "-I", INCLUDE, "-I", CSRC]
+STAMP = os.path.join(BUILD, "flags.txt")
 
 
 def _nvcc():
@@ -36,8 +43,8 @@ def _headers():
     return hs
 
 
-def _stale(obj, src, headers):
-    if not os.path.exists(obj):
+def _stale(obj, src, headers, flags_changed=False):
+    if flags_changed or not os.path.exists(obj):
         return True
     t = os.path.getmtime(obj)
     return any(os.path.getmtime(x) > t for x in [src] + headers)
@@ -49,12 +56,19 @@ def build(verbose: bool = False, extra_flags=None) -> str:
     srcs = sorted(os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith(".cu"))
     headers = _headers()
     flags = FLAGS + list(extra_flags or [])
+    # objects compiled with other code-generation flags are rebuilt
+    stamp = " ".join(ARCH + CODEGEN + list(extra_flags or []))
+    try:
+        with open(STAMP) as fh:
+            flags_changed = fh.read().strip() != stamp
+    except OSError:
+        flags_changed = True
     jobs = []
     objs = []
     for s in srcs:
         o = os.path.join(BUILD, os.path.basename(s)[:-3] + ".o")
         objs.append(o)
-        if _stale(o, s, headers):
+        if _stale(o, s, headers, flags_changed):
             jobs.append([nvcc] + ARCH + flags + ["-c", s, "-o", o])
 
     def run(cmd):
@@ -69,6 +83,9 @@ def build(verbose: bool = False, extra_flags=None) -> str:
         for done in ex.map(run, jobs):
             if verbose:
                 print("compiled", os.path.basename(done), file=sys.stderr)
+    if flags_changed:
+        with open(STAMP, "w") as fh:
+            fh.write(stamp + "\n")
     if jobs or not os.path.exists(LIB) or any(os.path.getmtime(o) > os.path.getmtime(LIB) for o in objs):
         cmd = [nvcc] + ARCH + ["-shared", "-cudart", "static", "-o", LIB] + objs
         r = subprocess.run(cmd, capture_output=True, text=True)

@@ -26,10 +26,15 @@
 namespace fem {
 namespace {
 
+// Resident blocks per SM the registers are budgeted for: five for paper mode with
+// q <= 4 (measured faster than four), three for q >= 7, else four (more would spill).
+template <int Q, int MODE>
+constexpr int bmincut_blocks() { return Q >= 7 ? 3 : ((Q <= 4 && MODE == FEM_GRAD_PAPER) ? 5 : 4); }
+
 // One thread per (node, replica); a warp covers 32 consecutive (node, replica)
 // pairs, so R % RPW == 0 keeps every packed word inside one group of lanes.
 template <int Q, int MODE>
-__global__ void __launch_bounds__(256, Q >= 7 ? 3 : 4) k_bmincut_step(BmcArgs a, StepScalars s) {
+__global__ void __launch_bounds__(256, bmincut_blocks<Q, MODE>()) k_bmincut_step(BmcArgs a, StepScalars s) {
   extern __shared__ unsigned long long smem_u64[];
   const int RQ = a.R * Q;
   unsigned long long* sps = smem_u64;                                // [R*Q] exact mode

@@ -98,8 +98,13 @@ __device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t b
                : "memory");
 }
 
+// Resident blocks per SM the registers are budgeted for: seven with Adam (measured faster
+// than six), six with RMSprop and SGD (seven spill there), five with weights.
 template <int OPT, bool UNIT>
-__global__ void __launch_bounds__(kThreads, UNIT ? 6 : 5) k_paper_tile(PArgs a, StepScalars s) {
+constexpr int tile_blocks() { return !UNIT ? 5 : (OPT == FEM_OPT_ADAM ? 7 : 6); }
+
+template <int OPT, bool UNIT>
+__global__ void __launch_bounds__(kThreads, tile_blocks<OPT, UNIT>()) k_paper_tile(PArgs a, StepScalars s) {
   __shared__ __align__(128) Stage st[kStages];
   __shared__ __align__(8) uint64_t full[kStages], empty[kStages];
   __shared__ int32_t abort_flag;

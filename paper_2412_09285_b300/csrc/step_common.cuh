@@ -51,10 +51,11 @@ __device__ __forceinline__ void opt_update(float& h, float& m, float& v, float g
   }
 }
 
-// Square root by the hardware approximation (sqrt.approx.f32, a few ulp).
+// Square root by the hardware approximation (a few ulp), denormal input and result
+// flushed to zero like the rest of the single-precision arithmetic (-ftz=true).
 __device__ __forceinline__ float sqrt_approx(float x) {
   float y;
-  asm("sqrt.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
+  asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
   return y;
 }
 

@@ -19,12 +19,9 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libfem.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-# Code generation.  -ftz=true flushes single-precision denormals to zero in every
-# kernel: the approximate exponential, reciprocal and square root of the step kernels
-# then run without their denormal handling (fewer instructions in kernels bound by
-# instruction issue), while divisions and square roots written as such stay
-# IEEE-rounded (prec-div, prec-sqrt).  fp64 arithmetic is not affected.
-CODEGEN = ["-O3", "-std=c++17", "-lineinfo", "-ftz=true"]
+# Code generation (single-precision denormals are kept: the step kernels flush them only
+# in their approximate instructions, written with the .ftz forms in step_common.cuh).
+CODEGEN = ["-O3", "-std=c++17", "-lineinfo"]
 FLAGS = CODEGEN + ["-Xcompiler", "-fPIC", "-Xcompiler", "-Wall", "--expt-relaxed-constexpr",
                    "-I", INCLUDE, "-I", CSRC]
 STAMP = os.path.join(BUILD, "flags.txt")

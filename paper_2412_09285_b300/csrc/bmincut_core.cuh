@@ -52,10 +52,10 @@ __device__ __forceinline__ void softmax_q(const float (&h)[Q], float (&P)[Q], fl
   float ex[Q], Z = 0.f;
 #pragma unroll
   for (int s = 0; s < Q; ++s) {
-    ex[s] = __expf(h[s] - mx);
+    ex[s] = exp_approx(h[s] - mx);
     Z += ex[s];
   }
-  const float invZ = __fdividef(1.f, Z), lz = __logf(Z);
+  const float invZ = div_approx(1.f, Z), lz = log_approx(Z);
 #pragma unroll
   for (int s = 0; s < Q; ++s) {
     P[s] = ex[s] * invZ;
@@ -79,7 +79,7 @@ __device__ __forceinline__ void centred_q(const float (&h)[Q], float (&d)[Q]) {
     u[q] = expm1f(h[q] - mx);
     su += u[q];
   }
-  const float invZ = __fdividef(1.f, (float)Q + su);  // Z in [1, q]
+  const float invZ = div_approx(1.f, (float)Q + su);  // Z in [1, q]
 #pragma unroll
   for (int q = 0; q < Q; ++q) d[q] = fmaf((float)Q, u[q], -su) * invZ;
 }

@@ -304,7 +304,7 @@ __global__ void __launch_bounds__(kThreads, tile_blocks<OPT, UNIT>()) k_paper_ti
             }
           }
           const int deg = rb[k + 1] - rb[k];
-          const float field = UNIT ? (deg > 0 ? __fdividef((float)(deg - 2 * nneg_u[k]), (float)deg) : 0.f)
+          const float field = UNIT ? (deg > 0 ? div_approx((float)(deg - 2 * nneg_u[k]), (float)deg) : 0.f)
                                    : (S.cn[kNpw * warp + k] * facc);
           float hk = h[k], mk = m[k], vk = v[k];
           const float gk = s.gq * (field + hk * s.inv_beta) * one_minus_m2_fast(hk);

@@ -200,7 +200,7 @@ __global__ void __launch_bounds__(256, 5) k_maxcut_step_paper(MaxcutArgs a, Step
         }
       }
       const int deg = rb[k + 1] - rb[k];
-      const float field = UNIT ? (deg > 0 ? __fdividef((float)(deg - 2 * nneg), (float)deg) : 0.f)
+      const float field = UNIT ? (deg > 0 ? div_approx((float)(deg - 2 * nneg), (float)deg) : 0.f)
                                : (a.cnorm[min(i0 + k, a.n - 1)] * facc);
       float hk = h[k], mk = m[k], vk = v[k];
       const float gk = s.gq * (field + hk * s.inv_beta) * one_minus_m2_fast(hk);

@@ -25,7 +25,7 @@ struct SatArgs {
 };
 
 // sigmoid with the fast exponential and reciprocal (relative error ~1e-6)
-__device__ __forceinline__ float sigmoidf_fast(float x) { return __fdividef(1.f, 1.f + __expf(-x)); }
+__device__ __forceinline__ float sigmoidf_fast(float x) { return div_approx(1.f, 1.f + exp_approx(-x)); }
 
 // The update of element e = i*R + r (variable i, replica r) of one step.
 // p-spin (a.jw != NULL, SM multi-variable interactions): the marginal buffers hold

@@ -51,17 +51,45 @@ __device__ __forceinline__ void opt_update(float& h, float& m, float& v, float g
   }
 }
 
-// Square root by the hardware approximation (a few ulp), denormal input and result
-// flushed to zero like the rest of the single-precision arithmetic (-ftz=true).
+// The approximate operations of the step kernels.  Each takes one hardware instruction
+// in its .ftz form (denormal input and result flushed to zero; the plain forms wrap the
+// instruction in denormal handling, which costs kernels bound by instruction issue), and
+// never on a value whose denormals matter: a quotient multiplies its numerator, which
+// keeps IEEE denormals, by the reciprocal of a normal divisor, so a denormal gradient
+// still moves a denormal field, and its sign, as in exact arithmetic.  The products are
+// __fmul_rn, which the compiler never contracts into a neighbouring add, so kernels
+// that share these sequences round alike.
+// Square root (PTX sqrt.approx, a few ulp); a denormal argument gives 0 (callers add
+// eps to it).
 __device__ __forceinline__ float sqrt_approx(float x) {
   float y;
   asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
   return y;
 }
+// a / b for |b| in [2^-126, 2^126] (PTX rcp.approx, 1 ulp, times a: 2 ulp); above that
+// range it gives 0, where |a / b| is below 2^-126 for every caller here anyway.
+__device__ __forceinline__ float div_approx(float a, float b) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(b));
+  return __fmul_rn(a, r);
+}
+// e^x by the identity e^x = 2^(x log2 e) on the approximate base-2 exponential (PTX
+// ex2.approx): relative error about 2^-22 + |x| 2^-24, the second term from rounding
+// the product; 0 for x below about -87.3 (results under 2^-126).
+__device__ __forceinline__ float exp_approx(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(__fmul_rn(x, 1.4426950408889634f)));
+  return y;
+}
+// ln x = log2(x) ln 2 on the approximate base-2 logarithm (PTX lg2.approx), x normal.
+__device__ __forceinline__ float log_approx(float x) {
+  float y;
+  asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return __fmul_rn(y, 0.6931471805599453f);
+}
 
-// The same updates with the divisions done by the fast reciprocal (__fdividef,
-// 2 ulp) and the approximate square root; the divisors here are >= eps and far
-// below 2^126.
+// The same updates with approximate divisions and square roots (div_approx,
+// sqrt_approx); the divisors here are >= eps and far below 2^126.
 // opt_update_fast_core is the update of a gradient that already includes wd*h
 // (callers that must not branch per element add it with an fmaf, which leaves g
 // unchanged when wd == 0).
@@ -71,10 +99,10 @@ __device__ __forceinline__ void opt_update_fast_core(float& h, float& m, float& 
   if (OPT == FEM_OPT_ADAM) {
     m = fmaf(s.b1, m, s.omb1 * g);
     v = fmaf(s.b2, v, s.omb2 * g * g);
-    h = fmaf(-s.lr, __fdividef(m, fmaf(sqrt_approx(v), s.inv_sqrt_bc2, s.eps)), h);
+    h = fmaf(-s.lr, div_approx(m, fmaf(sqrt_approx(v), s.inv_sqrt_bc2, s.eps)), h);
   } else if (OPT == FEM_OPT_RMSPROP) {
     v = fmaf(s.b1, v, s.omb1 * g * g);
-    const float q = __fdividef(g, sqrt_approx(v) + s.eps);
+    const float q = div_approx(g, sqrt_approx(v) + s.eps);
     if (s.momentum > 0.f) {
       m = fmaf(s.momentum, m, q);
       h = fmaf(-s.lr, m, h);
@@ -136,9 +164,9 @@ __device__ __forceinline__ void split_element(long long e, int R, int& i, int& r
 
 // 1 - tanh(h/2)^2 with the fast exponential (relative error ~1e-6).
 __device__ __forceinline__ float one_minus_m2_fast(float h) {
-  const float e = __expf(-fabsf(h));
+  const float e = exp_approx(-fabsf(h));
   const float d = 1.f + e;
-  return __fdividef(4.f * e, d * d);
+  return div_approx(4.f * e, d * d);
 }
 
 // The same update with the optimizer chosen at run time (a warp-uniform branch).

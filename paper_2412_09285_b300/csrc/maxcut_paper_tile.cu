@@ -52,7 +52,8 @@ struct alignas(128) Stage {
   float h[kNodes * 32], m[kNodes * 32], v[kNodes * 32];
   uint32_t adj[kCap];              // entry k's neighbour sign word (XOR the weight sign for unit weights)
   float w[kCap];
-  float cn[kNodes];
+  float cn[kNodes];                // weights: c_i; unit weights: 1/deg_i (0 for deg_i = 0)
+  uint32_t mask[kNodes];           // unit weights: node's entries within its group's first 32
   int32_t rptr[kNodes + 1];        // the tile's row pointers relative to base
   int32_t base;
 };
@@ -103,14 +104,17 @@ __device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t b
 template <int OPT, bool UNIT>
 constexpr int tile_blocks() { return !UNIT ? 5 : (OPT == FEM_OPT_ADAM ? 7 : 6); }
 
-template <int OPT, bool UNIT>
+// R32: the replica count is 32 (one sign word per node), a compile-time constant, so the
+// state rows' offsets are immediates.
+template <int OPT, bool UNIT, bool R32>
 __global__ void __launch_bounds__(kThreads, tile_blocks<OPT, UNIT>()) k_paper_tile(PArgs a, StepScalars s) {
+  const int R = R32 ? 32 : a.R, wpn = R32 ? 1 : a.wpn;
   __shared__ __align__(128) Stage st[kStages];
   __shared__ __align__(8) uint64_t full[kStages], empty[kStages];
   __shared__ int32_t abort_flag;
   volatile int32_t* abort_v = &abort_flag;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const long long tiles = (long long)((a.n + kNodes - 1) / kNodes) * a.wpn;
+  const long long tiles = (long long)((a.n + kNodes - 1) / kNodes) * wpn;
   if (threadIdx.x == 0) {
     for (int b = 0; b < kStages; ++b) {
       mbar_init(&full[b], 1);
@@ -121,8 +125,8 @@ __global__ void __launch_bounds__(kThreads, tile_blocks<OPT, UNIT>()) k_paper_ti
   }
   __syncthreads();
   auto tile_pos = [&](long long t, int& i0, int& wb) {
-    const long long nb = a.wpn == 1 ? t : t / a.wpn;
-    wb = a.wpn == 1 ? 0 : (int)(t - nb * a.wpn);
+    const long long nb = wpn == 1 ? t : t / wpn;
+    wb = wpn == 1 ? 0 : (int)(t - nb * wpn);
     i0 = (int)nb * kNodes;
   };
 
@@ -153,7 +157,7 @@ __global__ void __launch_bounds__(kThreads, tile_blocks<OPT, UNIT>()) k_paper_ti
       for (int q = 0; q < kQ; ++q) {
         const int k = lane + 32 * q;
         if (k < ecap) {
-          const uint32_t wd = __ldg(a.words_in + (size_t)(c[q] & 0x7fffffffu) * a.wpn + wb);
+          const uint32_t wd = __ldg(a.words_in + (size_t)(c[q] & 0x7fffffffu) * wpn + wb);
           adj[q] = UNIT ? wd ^ (0u - (c[q] >> 31)) : wd;
           if (!UNIT) w[q] = __ldg(a.w + base + k);
         }
@@ -191,6 +195,19 @@ __global__ void __launch_bounds__(kThreads, tile_blocks<OPT, UNIT>()) k_paper_ti
       if (lane <= kNodes) S.rptr[lane] = r0 - base;
       if (lane == 0) S.base = base;
       if (!UNIT && lane < kNodes) S.cn[lane] = cn0;
+      if (UNIT) {
+        // per node of the tile (lane = node): 1/deg with the reciprocal of the direct
+        // kernel's quotient, and the node's entry mask within its group's first 32 entries
+        const int rnext = __shfl_down_sync(kFullMask, r0, 1);
+        const int gfirst = __shfl_sync(kFullMask, r0, lane & ~(kNpw - 1) & 31);
+        const int glast = __shfl_sync(kFullMask, r0, ((lane & ~(kNpw - 1)) + kNpw) & 31);
+        if (lane < kNodes) {
+          const int len = rnext - r0, off = r0 - gfirst;
+          S.cn[lane] = len > 0 ? rcp_approx((float)len) : 0.f;
+          S.mask[lane] = (glast - gfirst > 32 || len == 0) ? 0u
+                         : (len >= 32 ? 0xffffffffu : ((1u << len) - 1u) << off);
+        }
+      }
 #pragma unroll
       for (int q = 0; q < kQ; ++q) {
         const int k = lane + 32 * q;
@@ -202,15 +219,15 @@ __global__ void __launch_bounds__(kThreads, tile_blocks<OPT, UNIT>()) k_paper_ti
       __syncwarp();
       const uint32_t rows_b = (uint32_t)nn * 128u;
       if (lane == 0) mbar_expect_tx(&full[b], rows_b * (OPT == FEM_OPT_SGD ? 2u : 3u));
-      if (a.wpn == 1) {
+      if (wpn == 1) {
         if (lane == 0) {
-          const size_t off = (size_t)i0 * a.R;
+          const size_t off = (size_t)i0 * R;
           bulk_load(S.h, a.h + off, rows_b, &full[b]);
           bulk_load(S.m, a.m + off, rows_b, &full[b]);
           if (OPT != FEM_OPT_SGD) bulk_load(S.v, a.v + off, rows_b, &full[b]);
         }
       } else if (lane < nn) {
-        const size_t off = (size_t)(i0 + lane) * a.R + (size_t)wb * 32;
+        const size_t off = (size_t)(i0 + lane) * R + (size_t)wb * 32;
         bulk_load(S.h + 32 * lane, a.h + off, 128u, &full[b]);
         bulk_load(S.m + 32 * lane, a.m + off, 128u, &full[b]);
         if (OPT != FEM_OPT_SGD) bulk_load(S.v + 32 * lane, a.v + off, 128u, &full[b]);
@@ -250,7 +267,7 @@ __global__ void __launch_bounds__(kThreads, tile_blocks<OPT, UNIT>()) k_paper_ti
         auto adj_at = [&](int e) -> uint32_t {
           if (e < kCap) return S.adj[e];
           const uint32_t c = __ldg(a.col + gbase + e);
-          const uint32_t wd = __ldg(a.words_in + (size_t)(c & 0x7fffffffu) * a.wpn + wb);
+          const uint32_t wd = __ldg(a.words_in + (size_t)(c & 0x7fffffffu) * wpn + wb);
           return UNIT ? wd ^ (0u - (c >> 31)) : wd;
         };
         auto w_at = [&](int e) -> float { return e < kCap ? S.w[e] : __ldg(a.w + gbase + e); };
@@ -274,10 +291,7 @@ __global__ void __launch_bounds__(kThreads, tile_blocks<OPT, UNIT>()) k_paper_ti
           const uint32_t adj = rb[0] + lane < bN ? adj_at(rb[0] + lane) : 0u;
           const uint32_t tr = warp_transpose32(adj, lane);
 #pragma unroll
-          for (int k = 0; k < kNpw; ++k) {
-            const int len = rb[k + 1] - rb[k];
-            nneg_u[k] = __popc(tr & (len == 0 ? 0u : (len >= 32 ? 0xffffffffu : ((1u << len) - 1u)) << (rb[k] - rb[0])));
-          }
+          for (int k = 0; k < kNpw; ++k) nneg_u[k] = __popc(tr & S.mask[kNpw * warp + k]);
         } else if (UNIT) {
           for (int c0 = rb[0]; c0 < bN; c0 += 32) {
             const uint32_t cur = c0 + lane < bN ? adj_at(c0 + lane) : 0u;
@@ -304,14 +318,16 @@ __global__ void __launch_bounds__(kThreads, tile_blocks<OPT, UNIT>()) k_paper_ti
             }
           }
           const int deg = rb[k + 1] - rb[k];
-          const float field = UNIT ? (deg > 0 ? div_approx((float)(deg - 2 * nneg_u[k]), (float)deg) : 0.f)
+          // unit weights: div_approx((float)(deg - 2 nneg), (float)deg) of the direct kernel,
+          // with the producer's reciprocal (0 for deg = 0, where the numerator is 0 too)
+          const float field = UNIT ? __fmul_rn((float)(deg - 2 * nneg_u[k]), S.cn[kNpw * warp + k])
                                    : (S.cn[kNpw * warp + k] * facc);
           float hk = h[k], mk = m[k], vk = v[k];
           const float gk = s.gq * (field + hk * s.inv_beta) * one_minus_m2_fast(hk);
           opt_update_fast<OPT>(hk, mk, vk, gk, s);
           ball[k] = __ballot_sync(kFullMask, hk < 0.f);
           if (i0 + k < a.n) {
-            const size_t idx = (size_t)(i0 + k) * a.R + (size_t)wb * 32 + lane;
+            const size_t idx = (size_t)(i0 + k) * R + (size_t)wb * 32 + lane;
             a.h[idx] = hk;
             a.m[idx] = mk;
             if (OPT != FEM_OPT_SGD) a.v[idx] = vk;
@@ -320,7 +336,7 @@ __global__ void __launch_bounds__(kThreads, tile_blocks<OPT, UNIT>()) k_paper_ti
         uint32_t mine = ball[0];
 #pragma unroll
         for (int k = 1; k < kNpw; ++k) mine = lane == k ? ball[k] : mine;
-        if (lane < kNpw && i0 + lane < a.n) a.words_out[(size_t)(i0 + lane) * a.wpn + wb] = mine;
+        if (lane < kNpw && i0 + lane < a.n) a.words_out[(size_t)(i0 + lane) * wpn + wb] = mine;
       }
       __syncwarp();
       if (lane == 0) mbar_arrive(&empty[b]);
@@ -334,9 +350,9 @@ __global__ void __launch_bounds__(kThreads, tile_blocks<OPT, UNIT>()) k_paper_ti
   }
 }
 
-template <int OPT, bool UNIT>
+template <int OPT, bool UNIT, bool R32>
 fem_status launch(const PArgs& a, const StepScalars& s, int sm_count, cudaStream_t st) {
-  constexpr auto k = k_paper_tile<OPT, UNIT>;
+  constexpr auto k = k_paper_tile<OPT, UNIT, R32>;
   static int per_sm = 0;
   if (per_sm == 0) {
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kThreads, 0) != cudaSuccess || per_sm < 1) {
@@ -372,13 +388,23 @@ fem_status maxcut_paper_tile_step(Problem* p, int in, const StepScalars& s, cuda
   a.words_out = p->words[in ^ 1];
   a.err = p->err;
   const bool unit = p->unit_w;
+  if (p->R == 32) {
+    switch (p->optimizer) {
+      case FEM_OPT_ADAM: return unit ? launch<FEM_OPT_ADAM, true, true>(a, s, p->sm_count, st)
+                                     : launch<FEM_OPT_ADAM, false, true>(a, s, p->sm_count, st);
+      case FEM_OPT_RMSPROP: return unit ? launch<FEM_OPT_RMSPROP, true, true>(a, s, p->sm_count, st)
+                                        : launch<FEM_OPT_RMSPROP, false, true>(a, s, p->sm_count, st);
+      default: return unit ? launch<FEM_OPT_SGD, true, true>(a, s, p->sm_count, st)
+                           : launch<FEM_OPT_SGD, false, true>(a, s, p->sm_count, st);
+    }
+  }
   switch (p->optimizer) {
-    case FEM_OPT_ADAM: return unit ? launch<FEM_OPT_ADAM, true>(a, s, p->sm_count, st)
-                                   : launch<FEM_OPT_ADAM, false>(a, s, p->sm_count, st);
-    case FEM_OPT_RMSPROP: return unit ? launch<FEM_OPT_RMSPROP, true>(a, s, p->sm_count, st)
-                                      : launch<FEM_OPT_RMSPROP, false>(a, s, p->sm_count, st);
-    default: return unit ? launch<FEM_OPT_SGD, true>(a, s, p->sm_count, st)
-                         : launch<FEM_OPT_SGD, false>(a, s, p->sm_count, st);
+    case FEM_OPT_ADAM: return unit ? launch<FEM_OPT_ADAM, true, false>(a, s, p->sm_count, st)
+                                   : launch<FEM_OPT_ADAM, false, false>(a, s, p->sm_count, st);
+    case FEM_OPT_RMSPROP: return unit ? launch<FEM_OPT_RMSPROP, true, false>(a, s, p->sm_count, st)
+                                      : launch<FEM_OPT_RMSPROP, false, false>(a, s, p->sm_count, st);
+    default: return unit ? launch<FEM_OPT_SGD, true, false>(a, s, p->sm_count, st)
+                         : launch<FEM_OPT_SGD, false, false>(a, s, p->sm_count, st);
   }
 }
 

@@ -66,13 +66,15 @@ __device__ __forceinline__ float sqrt_approx(float x) {
   asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
   return y;
 }
-// a / b for |b| in [2^-126, 2^126] (PTX rcp.approx, 1 ulp, times a: 2 ulp); above that
-// range it gives 0, where |a / b| is below 2^-126 for every caller here anyway.
-__device__ __forceinline__ float div_approx(float a, float b) {
+// 1 / b (PTX rcp.approx, 1 ulp) for |b| in [2^-126, 2^126]; 0 above that range.
+__device__ __forceinline__ float rcp_approx(float b) {
   float r;
   asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(b));
-  return __fmul_rn(a, r);
+  return r;
 }
+// a / b as a times rcp_approx(b) (2 ulp); above the range it gives 0, where |a / b| is below
+// 2^-126 for every caller here anyway.
+__device__ __forceinline__ float div_approx(float a, float b) { return __fmul_rn(a, rcp_approx(b)); }
 // e^x by the identity e^x = 2^(x log2 e) on the approximate base-2 exponential (PTX
 // ex2.approx): relative error about 2^-22 + |x| 2^-24, the second term from rounding
 // the product; 0 for x below about -87.3 (results under 2^-126).

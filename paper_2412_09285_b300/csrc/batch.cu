@@ -65,7 +65,7 @@ namespace {
 // The element code reads its arguments from a block-shared copy, written by thread 0
 // per item: values the compiler would otherwise hold in registers for the whole item
 // (and spill) are re-read from shared memory where they are used.
-template <int Q, int MODE>
+template <int Q, int MODE, int RC = 0>
 __device__ void run_bmincut_item(const BatchMember& b, const BatchItem& it, const StepScalars& s, int t,
                                  int32_t* scnt, unsigned long long* sps, BmcArgs& a) {
   if (threadIdx.x == 0) {
@@ -98,7 +98,7 @@ __device__ void run_bmincut_item(const BatchMember& b, const BatchItem& it, cons
     a.ps_zero = b.psum[(t + 2) % 3];
   }
   __syncthreads();
-  const int RQ = a.R * Q;
+  const int RQ = (RC ? RC : a.R) * Q;
   for (int x = threadIdx.x; x < RQ; x += blockDim.x) {
     scnt[x] = 0;
     if (MODE == FEM_GRAD_EXACT) sps[x] = 0ull;
@@ -111,7 +111,7 @@ __device__ void run_bmincut_item(const BatchMember& b, const BatchItem& it, cons
   const int lane = threadIdx.x & 31;
   for (long long base = it.e0 + (threadIdx.x & ~31); base < it.e1; base += blockDim.x) {
     const long long e = base + lane;
-    bmincut_element<Q, MODE>(a, s, e, e < it.e1, lane, scnt, sps);
+    bmincut_element<Q, MODE, RC>(a, s, e, e < it.e1, lane, scnt, sps);
   }
   __syncthreads();
   for (int x = threadIdx.x; x < RQ; x += blockDim.x) {
@@ -121,6 +121,7 @@ __device__ void run_bmincut_item(const BatchMember& b, const BatchItem& it, cons
   __syncthreads();
 }
 
+template <int RC = 0>
 __device__ void run_sat_item(const BatchMember& b, const BatchItem& it, const StepScalars& s, int t, SatArgs& a) {
   if (threadIdx.x == 0) {
     a = SatArgs{};
@@ -146,7 +147,7 @@ __device__ void run_sat_item(const BatchMember& b, const BatchItem& it, const St
   // p-spin members take the per-element path, which gives the same bits, since the
   // four-replica p-spin code would spill in this kernel
   if (sat_k3_shape(a) && !a.jw) {
-    for (long long e = it.e0 + threadIdx.x * 4; e < it.e1; e += blockDim.x * 4) sat_element_k3<2, false>(a, s, e);
+    for (long long e = it.e0 + threadIdx.x * 4; e < it.e1; e += blockDim.x * 4) sat_element_k3<2, false, RC>(a, s, e);
   } else {
     for (long long e = it.e0 + threadIdx.x; e < it.e1; e += blockDim.x) sat_element(a, s, e);
   }
@@ -154,8 +155,9 @@ __device__ void run_sat_item(const BatchMember& b, const BatchItem& it, const St
 }
 
 // The q-state members' step: blocks walk their items (the first n_items of the list).
-// Q and MODE are shared by all of them; s carries the q-state gradient scale (gamma).
-template <int Q, int MODE>
+// Q and MODE are shared by all of them; s carries the q-state gradient scale (gamma).  RC: the
+// members' replica count as a compile-time constant (0: run time).
+template <int Q, int MODE, int RC = 0>
 __global__ void __launch_bounds__(256, Q >= 7 ? 3 : 4) k_batch_bmincut(const BatchMember* __restrict__ members,
                                                        const BatchItem* __restrict__ items, int32_t n_items,
                                                        int32_t max_rq, StepScalars s, int32_t t) {
@@ -165,34 +167,36 @@ __global__ void __launch_bounds__(256, Q >= 7 ? 3 : 4) k_batch_bmincut(const Bat
   __shared__ BmcArgs args;
   for (int k = blockIdx.x; k < n_items; k += gridDim.x) {
     const BatchItem it = items[k];
-    run_bmincut_item<Q, MODE>(members[it.member], it, s, t, scnt, sps, args);
+    run_bmincut_item<Q, MODE, RC>(members[it.member], it, s, t, scnt, sps, args);
   }
 }
 
 // The clause-shaped members' step (Max-k-SAT and p-spin); s carries the single-field
-// gradient scale (gamma/4).
+// gradient scale (gamma/4).  RC: the members' replica count at compile time (0: run time).
+template <int RC = 0>
 __global__ void __launch_bounds__(256, 4) k_batch_sat(const BatchMember* __restrict__ members,
                                                    const BatchItem* __restrict__ items, int32_t n_items,
                                                    StepScalars s, int32_t t) {
   __shared__ SatArgs args;
   for (int k = blockIdx.x; k < n_items; k += gridDim.x) {
     const BatchItem it = items[k];
-    run_sat_item(members[it.member], it, s, t, args);
+    run_sat_item<RC>(members[it.member], it, s, t, args);
   }
 }
 
 using BatchKernel = void (*)(const BatchMember*, const BatchItem*, int32_t, int32_t, StepScalars, int32_t);
 
+// r16: every member has R = 16 (one or two packed words per node from q = 3 on)
 template <int MODE>
-BatchKernel pick_q(int q) {
+BatchKernel pick_q(int q, bool r16) {
   switch (q) {
     case 2: return k_batch_bmincut<2, MODE>;
-    case 3: return k_batch_bmincut<3, MODE>;
-    case 4: return k_batch_bmincut<4, MODE>;
-    case 5: return k_batch_bmincut<5, MODE>;
-    case 6: return k_batch_bmincut<6, MODE>;
-    case 7: return k_batch_bmincut<7, MODE>;
-    default: return k_batch_bmincut<8, MODE>;
+    case 3: return r16 ? k_batch_bmincut<3, MODE, 16> : k_batch_bmincut<3, MODE>;
+    case 4: return r16 ? k_batch_bmincut<4, MODE, 16> : k_batch_bmincut<4, MODE>;
+    case 5: return r16 ? k_batch_bmincut<5, MODE, 16> : k_batch_bmincut<5, MODE>;
+    case 6: return r16 ? k_batch_bmincut<6, MODE, 16> : k_batch_bmincut<6, MODE>;
+    case 7: return r16 ? k_batch_bmincut<7, MODE, 16> : k_batch_bmincut<7, MODE>;
+    default: return r16 ? k_batch_bmincut<8, MODE, 16> : k_batch_bmincut<8, MODE>;
   }
 }
 
@@ -366,8 +370,8 @@ static int batch_launch(Batch* b, BatchKernel k, const StepScalars& sq, const St
     ++n;
   }
   if (b->n_sat > 0) {
-    k_batch_sat<<<batch_grid(b, k_batch_sat, 0, b->n_sat), 256, 0, s>>>(b->d_members, b->d_items + b->n_bmc,
-                                                                         b->n_sat, s1, t);
+    const auto ks = b->R == 16 ? k_batch_sat<16> : k_batch_sat<0>;
+    ks<<<batch_grid(b, ks, 0, b->n_sat), 256, 0, s>>>(b->d_members, b->d_items + b->n_bmc, b->n_sat, s1, t);
     ++n;
   }
   return n;
@@ -443,7 +447,8 @@ fem_status fem_batch_anneal(fem_batch_t b, const fem_anneal_params* a, const flo
     fem_status st = batch_prepare(b, s);
     if (st != FEM_OK) return st;
   }
-  const BatchKernel k = b->mode == FEM_GRAD_EXACT ? pick_q<FEM_GRAD_EXACT>(b->q) : pick_q<FEM_GRAD_PAPER>(b->q);
+  const BatchKernel k = b->mode == FEM_GRAD_EXACT ? pick_q<FEM_GRAD_EXACT>(b->q, R == 16)
+                                                 : pick_q<FEM_GRAD_PAPER>(b->q, R == 16);
   if (batch_smem(b) > 48 * 1024)
     FEM_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)batch_smem(b)));
   const std::vector<StepScalars> sc = make_step_scalars(*a, 0);      // q-state scale

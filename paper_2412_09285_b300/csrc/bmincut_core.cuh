@@ -138,20 +138,23 @@ __device__ __forceinline__ void store_q(float* p, const float (&x)[Q]) {
 // neighbour contraction, centred gradient, optimizer, argmax word and the block's
 // shared-memory counts (scnt / sps, [R][Q]).  All 32 lanes of the warp must call it
 // together (word packing shuffles); lanes with act == false contribute nothing.
-template <int Q, int MODE>
+// RC: the replica count as a compile-time constant (0: a.R at run time), for
+// immediate offsets and shifts instead of run-time multiplies and divisions.
+template <int Q, int MODE, int RC = 0>
 __device__ __forceinline__ void bmincut_element(const BmcArgs& a, const StepScalars& s, long long e,
                                                 bool act, int lane, int32_t* scnt,
                                                 unsigned long long* sps) {
   constexpr int B = QBits<Q>::B, RPW = QBits<Q>::RPW;
+  const int R = RC ? RC : a.R, wpn = RC ? RC * B / 32 : a.wpn;
   constexpr uint32_t SM = QBits<Q>::MASK;
   {
     int i = 0, r = 0;
-    if (act) split_element(e, a.R, i, r);
+    if (act) split_element(e, R, i, r);
     const int wsel = r / RPW, sh = (r % RPW) * B;
     float h[Q], mm[Q], vv[Q];
 #pragma unroll
     for (int q = 0; q < Q; ++q) h[q] = mm[q] = vv[q] = 0.f;
-    const size_t idx = ((size_t)i * a.R + r) * Q;
+    const size_t idx = ((size_t)i * R + r) * Q;
     float acc[Q];
 #pragma unroll
     for (int q = 0; q < Q; ++q) acc[q] = 0.f;
@@ -162,10 +165,10 @@ __device__ __forceinline__ void bmincut_element(const BmcArgs& a, const StepScal
     // R = 32, q = 3, 4 with R = 16): the lanes of a node load up to R neighbours'
     // words at once, a warp bit-transpose turns them into bit planes, and popcounts
     // give the per-state counts (warp-uniform condition; every lane takes part).
-    const bool planes = MODE == FEM_GRAD_PAPER && B <= 2 && !a.w && a.R * B == 32;
+    const bool planes = MODE == FEM_GRAD_PAPER && B <= 2 && !a.w && R * B == 32;
     // q = 5..8 (4 bits per replica) with R = 16: two packed words per node, one bit-plane
     // pass per word
-    const bool planes4 = MODE == FEM_GRAD_PAPER && B == 4 && !a.w && a.R == 16;
+    const bool planes4 = MODE == FEM_GRAD_PAPER && B == 4 && !a.w && R == 16;
     if (act) {
       load_q<Q>(a.h_in + idx, h);
       load_q<Q>(a.m + idx, mm);
@@ -174,13 +177,13 @@ __device__ __forceinline__ void bmincut_element(const BmcArgs& a, const StepScal
       end = a.row_ptr[i + 1];
       if (a.nodew) Vi = a.nodew[i];
       if (MODE == FEM_GRAD_PAPER) {
-        own = (int)((a.words_in[(size_t)i * a.wpn + wsel] >> sh) & SM);
+        own = (int)((a.words_in[(size_t)i * wpn + wsel] >> sh) & SM);
         cf = a.cf[i];
         ca = a.ca[i];
       }
     }
     if (MODE == FEM_GRAD_PAPER && planes) {
-      const int G = a.R;  // lanes per node: 16 or 32
+      const int G = R;  // lanes per node: 16 or 32
       const int deg = end - beg, sub = lane & (G - 1);
       int maxdeg = deg;
       if (G == 16) maxdeg = max(maxdeg, __shfl_xor_sync(kFullMask, maxdeg, 16));
@@ -247,7 +250,7 @@ __device__ __forceinline__ void bmincut_element(const BmcArgs& a, const StepScal
           unsigned long long pk = 0ull;
           for (int k = beg; k < end; ++k) {
             const uint32_t j = a.col[k] & 0x7fffffffu;
-            const uint32_t sj = (a.words_in[(size_t)j * a.wpn + wsel] >> sh) & SM;
+            const uint32_t sj = (a.words_in[(size_t)j * wpn + wsel] >> sh) & SM;
             pk += 1ull << (F * sj);
           }
 #pragma unroll
@@ -256,7 +259,7 @@ __device__ __forceinline__ void bmincut_element(const BmcArgs& a, const StepScal
           for (int k = beg; k < end; ++k) {
             const uint32_t j = a.col[k] & 0x7fffffffu;
             const float wk = a.w ? a.w[k] : 1.f;
-            const int sj = (int)((a.words_in[(size_t)j * a.wpn + wsel] >> sh) & SM);
+            const int sj = (int)((a.words_in[(size_t)j * wpn + wsel] >> sh) & SM);
 #pragma unroll
             for (int q = 0; q < Q; ++q) acc[q] += (sj == q) ? wk : 0.f;
           }
@@ -282,7 +285,7 @@ __device__ __forceinline__ void bmincut_element(const BmcArgs& a, const StepScal
 #pragma unroll
           for (int u = 0; u < G; ++u) {
             if (k0 + u < end) {
-              load_q<Q>(a.d_in + ((size_t)jj[u] * a.R + r) * Q, dj[u]);
+              load_q<Q>(a.d_in + ((size_t)jj[u] * R + r) * Q, dj[u]);
             } else {
 #pragma unroll
               for (int q = 0; q < Q; ++q) dj[u][q] = 0.f;
@@ -369,7 +372,7 @@ __device__ __forceinline__ void bmincut_element(const BmcArgs& a, const StepScal
     uint32_t word = act ? ((uint32_t)sn << sh) : 0u;
 #pragma unroll
     for (int off = 1; off < RPW; off <<= 1) word |= __shfl_xor_sync(kFullMask, word, off);
-    if (act && (r % RPW) == 0) a.words_out[(size_t)i * a.wpn + wsel] = word;
+    if (act && (r % RPW) == 0) a.words_out[(size_t)i * wpn + wsel] = word;
   }
 }
 

@@ -33,10 +33,12 @@ constexpr int bmincut_blocks() { return Q >= 7 ? 3 : ((Q <= 4 && MODE == FEM_GRA
 
 // One thread per (node, replica); a warp covers 32 consecutive (node, replica)
 // pairs, so R % RPW == 0 keeps every packed word inside one group of lanes.
-template <int Q, int MODE>
+// RC: the replica count as a compile-time constant (0: run time).
+template <int Q, int MODE, int RC = 0>
 __global__ void __launch_bounds__(256, bmincut_blocks<Q, MODE>()) k_bmincut_step(BmcArgs a, StepScalars s) {
   extern __shared__ unsigned long long smem_u64[];
-  const int RQ = a.R * Q;
+  const int R = RC ? RC : a.R;
+  const int RQ = R * Q;
   unsigned long long* sps = smem_u64;                                // [R*Q] exact mode
   int32_t* scnt = reinterpret_cast<int32_t*>(smem_u64 + (MODE == FEM_GRAD_EXACT ? RQ : 0));
   for (int x = threadIdx.x; x < RQ; x += blockDim.x) {
@@ -51,12 +53,12 @@ __global__ void __launch_bounds__(256, bmincut_blocks<Q, MODE>()) k_bmincut_step
   }
   __syncthreads();
   const int lane = threadIdx.x & 31;
-  const long long total = (long long)a.n * a.R;
+  const long long total = (long long)a.n * R;
   const long long stride = (long long)gridDim.x * blockDim.x;
   for (long long base = (long long)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < total;
        base += stride) {
     const long long e = base + lane;
-    bmincut_element<Q, MODE>(a, s, e, e < total, lane, scnt, sps);
+    bmincut_element<Q, MODE, RC>(a, s, e, e < total, lane, scnt, sps);
   }
   __syncthreads();
   for (int x = threadIdx.x; x < RQ; x += blockDim.x) {
@@ -269,7 +271,11 @@ fem_status steps_q(Problem* p, const std::vector<StepScalars>& sc, int t_begin, 
   const bool exact = p->grad_mode == FEM_GRAD_EXACT;
   if (exact && (!p->mag[0] || !p->mag[1])) return fail(FEM_ERR_STATE, "exact-mode buffers are not allocated");
   const size_t smem = (size_t)p->R * Q * (exact ? 12 : 4);
-  auto kern = exact ? k_bmincut_step<Q, FEM_GRAD_EXACT> : k_bmincut_step<Q, FEM_GRAD_PAPER>;
+  // R = 16 (with its one or two packed words per node) runs an instantiation with the
+  // replica count fixed at compile time
+  const bool r16 = p->R == 16 && p->words_per_node == 16 * QBits<Q>::B / 32;
+  auto kern = exact ? (r16 ? k_bmincut_step<Q, FEM_GRAD_EXACT, 16> : k_bmincut_step<Q, FEM_GRAD_EXACT>)
+                    : (r16 ? k_bmincut_step<Q, FEM_GRAD_PAPER, 16> : k_bmincut_step<Q, FEM_GRAD_PAPER>);
   if (smem > 48 * 1024) FEM_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   const int grid = resident_grid(kern, p->sm_count, (long long)p->n * p->R, smem);
   for (size_t k = 0; k < sc.size(); ++k) {

@@ -119,16 +119,19 @@ __device__ __forceinline__ void gather4(void* dst, const CUtensorMap* tm, int x,
       : "memory");
 }
 
-template <int OPT, bool UNIT>
+// R32: the replica count is 32 (one block of replicas per node), a compile-time constant, so
+// the state rows' offsets are immediates.
+template <int OPT, bool UNIT, bool R32>
 __global__ void __launch_bounds__(kThreads, 4) k_exact_gather(const __grid_constant__ CUtensorMap tm_mag, GatherArgs a,
                                                               StepScalars s) {
+  const int R = R32 ? 32 : a.R, wpn = R32 ? 1 : a.wpn;
   extern __shared__ uint8_t smem_raw[];
   Stage* st = reinterpret_cast<Stage*>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   __shared__ __align__(8) uint64_t full[kStages], empty[kStages];
   __shared__ int32_t abort_flag;
   volatile int32_t* abort_v = &abort_flag;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const long long tiles = (long long)((a.n + kNodes - 1) / kNodes) * a.wpn;
+  const long long tiles = (long long)((a.n + kNodes - 1) / kNodes) * wpn;
   if (threadIdx.x == 0) {
     for (int b = 0; b < kStages; ++b) {
       mbar_init(&full[b], 1);
@@ -144,7 +147,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_exact_gather(const __grid_const
     // ---- producer.  The row pointers run two tiles ahead and the CSR entries one tile
     // ahead in registers, so a tile's stage is filled without waiting on memory.
     constexpr int kQ = kCap / 32;  // entries per lane and tile
-    auto first_node = [&](long long t) { return (int)(a.wpn == 1 ? t : t / a.wpn) * kNodes; };
+    auto first_node = [&](long long t) { return (int)(wpn == 1 ? t : t / wpn) * kNodes; };
     auto load_rp = [&](long long t, int& rp, int& rl) {
       if (t < tiles) {
         const int i0 = first_node(t);
@@ -184,8 +187,8 @@ __global__ void __launch_bounds__(kThreads, 4) k_exact_gather(const __grid_const
         break;
       }
       Stage& S = st[b];
-      const long long nb = a.wpn == 1 ? t1 : t1 / a.wpn;
-      const int wb = a.wpn == 1 ? 0 : (int)(t1 - nb * a.wpn);
+      const long long nb = wpn == 1 ? t1 : t1 / wpn;
+      const int wb = wpn == 1 ? 0 : (int)(t1 - nb * wpn);
       const int i0 = (int)nb * kNodes, nn = min(kNodes, a.n - i0);
       const int base = __shfl_sync(kFullMask, rp1, 0);
       if (lane < kNodes) {
@@ -219,15 +222,15 @@ __global__ void __launch_bounds__(kThreads, 4) k_exact_gather(const __grid_const
         const int y3 = k + 3 < ecap ? (int)(S.col[k + 3] & 0x7fffffffu) : y0;
         gather4(S.rows + 32 * k, &tm_mag, wb * 32, y0, y1, y2, y3, &full[b]);
       }
-      if (a.wpn == 1) {
+      if (wpn == 1) {
         if (lane == 0) {
-          const size_t off = (size_t)i0 * a.R;
+          const size_t off = (size_t)i0 * R;
           bulk_load(S.h, a.h_in + off, rows_b, &full[b]);
           bulk_load(S.m, a.m + off, rows_b, &full[b]);
           if (OPT != FEM_OPT_SGD) bulk_load(S.v, a.v + off, rows_b, &full[b]);
         }
       } else if (lane < nn) {
-        const size_t off = (size_t)(i0 + lane) * a.R + (size_t)wb * 32;
+        const size_t off = (size_t)(i0 + lane) * R + (size_t)wb * 32;
         bulk_load(S.h + 32 * lane, a.h_in + off, 128u, &full[b]);
         bulk_load(S.m + 32 * lane, a.m + off, 128u, &full[b]);
         if (OPT != FEM_OPT_SGD) bulk_load(S.v + 32 * lane, a.v + off, 128u, &full[b]);
@@ -261,8 +264,8 @@ __global__ void __launch_bounds__(kThreads, 4) k_exact_gather(const __grid_const
         break;
       }
       const Stage& S = st[b];
-      const long long nb = a.wpn == 1 ? t : t / a.wpn;
-      const int wb = a.wpn == 1 ? 0 : (int)(t - nb * a.wpn);
+      const long long nb = wpn == 1 ? t : t / wpn;
+      const int wb = wpn == 1 ? 0 : (int)(t - nb * wpn);
       const int i0 = (int)nb * kNodes, nn = min(kNodes, a.n - i0);
       for (int j = warp; j < nn; j += kConsumers) {
         const int i = i0 + j;
@@ -276,7 +279,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_exact_gather(const __grid_const
         }
         for (int k = max(beg, kCap); k < end; ++k) {  // beyond the staged rows: direct gathers
           const uint32_t c = __ldg(a.col + S.base + k);
-          const float mj = a.mag_in[(size_t)(c & 0x7fffffffu) * a.R + (size_t)wb * 32 + lane];
+          const float mj = a.mag_in[(size_t)(c & 0x7fffffffu) * R + (size_t)wb * 32 + lane];
           if (UNIT) facc += (c >> 31) ? -mj : mj;
           else facc = fmaf(__ldg(a.w + S.base + k), mj, facc);
         }
@@ -286,13 +289,13 @@ __global__ void __launch_bounds__(kThreads, 4) k_exact_gather(const __grid_const
         if (a.offset) field += S.off[j];
         const float g = s.gq * (field + hi * s.inv_beta) * one_minus_m2_fast(hi);
         opt_update_fast<OPT>(hi, mi, vi, g, s);
-        const size_t idx = (size_t)i * a.R + (size_t)wb * 32 + lane;
+        const size_t idx = (size_t)i * R + (size_t)wb * 32 + lane;
         a.h_out[idx] = hi;
         a.m[idx] = mi;
         if (OPT != FEM_OPT_SGD) a.v[idx] = vi;
         a.mag_out[idx] = tanhf(0.5f * hi);
         const uint32_t ball = __ballot_sync(kFullMask, hi < 0.f);
-        if (lane == 0) a.words_out[(size_t)i * a.wpn + wb] = ball;
+        if (lane == 0) a.words_out[(size_t)i * wpn + wb] = ball;
       }
       __syncwarp();
       if (lane == 0) mbar_arrive(&empty[b]);
@@ -335,9 +338,9 @@ fem_status mag_map(CUtensorMap* m, const float* base, int32_t n, int32_t R) {
   return FEM_OK;
 }
 
-template <int OPT, bool UNIT>
+template <int OPT, bool UNIT, bool R32>
 fem_status launch(const CUtensorMap& tm, const GatherArgs& a, const StepScalars& s, int sm_count, cudaStream_t st) {
-  constexpr auto k = k_exact_gather<OPT, UNIT>;
+  constexpr auto k = k_exact_gather<OPT, UNIT, R32>;
   static int grid_per_sm = 0;
   const size_t smem = kStages * sizeof(Stage) + 1024;
   if (grid_per_sm == 0) {
@@ -390,13 +393,24 @@ fem_status maxcut_exact_gather_step(Problem* p, int in, const StepScalars& s, cu
   const CUtensorMap& tm = p->tmap_mag[in];
   fem_status r;
   const bool unit = p->unit_w;
+  if (p->R == 32) {
+    switch (p->optimizer) {
+      case FEM_OPT_ADAM: r = unit ? launch<FEM_OPT_ADAM, true, true>(tm, a, s, p->sm_count, st)
+                                  : launch<FEM_OPT_ADAM, false, true>(tm, a, s, p->sm_count, st); break;
+      case FEM_OPT_RMSPROP: r = unit ? launch<FEM_OPT_RMSPROP, true, true>(tm, a, s, p->sm_count, st)
+                                     : launch<FEM_OPT_RMSPROP, false, true>(tm, a, s, p->sm_count, st); break;
+      default: r = unit ? launch<FEM_OPT_SGD, true, true>(tm, a, s, p->sm_count, st)
+                        : launch<FEM_OPT_SGD, false, true>(tm, a, s, p->sm_count, st); break;
+    }
+    return r;
+  }
   switch (p->optimizer) {
-    case FEM_OPT_ADAM: r = unit ? launch<FEM_OPT_ADAM, true>(tm, a, s, p->sm_count, st)
-                                : launch<FEM_OPT_ADAM, false>(tm, a, s, p->sm_count, st); break;
-    case FEM_OPT_RMSPROP: r = unit ? launch<FEM_OPT_RMSPROP, true>(tm, a, s, p->sm_count, st)
-                                   : launch<FEM_OPT_RMSPROP, false>(tm, a, s, p->sm_count, st); break;
-    default: r = unit ? launch<FEM_OPT_SGD, true>(tm, a, s, p->sm_count, st)
-                      : launch<FEM_OPT_SGD, false>(tm, a, s, p->sm_count, st); break;
+    case FEM_OPT_ADAM: r = unit ? launch<FEM_OPT_ADAM, true, false>(tm, a, s, p->sm_count, st)
+                                : launch<FEM_OPT_ADAM, false, false>(tm, a, s, p->sm_count, st); break;
+    case FEM_OPT_RMSPROP: r = unit ? launch<FEM_OPT_RMSPROP, true, false>(tm, a, s, p->sm_count, st)
+                                   : launch<FEM_OPT_RMSPROP, false, false>(tm, a, s, p->sm_count, st); break;
+    default: r = unit ? launch<FEM_OPT_SGD, true, false>(tm, a, s, p->sm_count, st)
+                      : launch<FEM_OPT_SGD, false, false>(tm, a, s, p->sm_count, st); break;
   }
   return r;
 }

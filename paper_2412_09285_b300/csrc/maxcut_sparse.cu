@@ -101,29 +101,31 @@ __global__ void __launch_bounds__(256) k_maxcut_step(MaxcutArgs a, StepScalars s
 // group ahead.  Each gathered word is pre-XORed with the weight sign (unit
 // weights), so one shuffle and one bit test per edge give the neighbour term:
 //   sum_j W_ij sgn(m_j) = deg_i - 2 * #{j : W_ij sgn(m_j) = -1}.
-template <int OPT, bool UNIT, int NPW>
+// R32: the replica count is 32 (one sign word per node), a compile-time constant.
+template <int OPT, bool UNIT, int NPW, bool R32 = false>
 __global__ void __launch_bounds__(256, 5) k_maxcut_step_paper(MaxcutArgs a, StepScalars s) {
+  const int R = R32 ? 32 : a.R, wpn = R32 ? 1 : a.wpn;
   const int lane = threadIdx.x & 31;
   const int ngroups = (a.n + NPW - 1) / NPW;
-  const long long total = (long long)ngroups * a.wpn;
+  const long long total = (long long)ngroups * wpn;
   const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
   long long g = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   auto row_ptrs = [&](long long gg) -> int {
     if (gg >= total) return 0;
-    const int ng = a.wpn == 1 ? (int)gg : (int)(gg / a.wpn);
+    const int ng = wpn == 1 ? (int)gg : (int)(gg / wpn);
     return lane <= NPW ? __ldg(a.row_ptr + min(ng * NPW + lane, a.n)) : 0;
   };
   int rp = row_ptrs(g);
   for (; g < total; g += nwarps) {
-    const int ng = a.wpn == 1 ? (int)g : (int)(g / a.wpn);
-    const int wb = a.wpn == 1 ? 0 : (int)(g - (long long)ng * a.wpn);
+    const int ng = wpn == 1 ? (int)g : (int)(g / wpn);
+    const int wb = wpn == 1 ? 0 : (int)(g - (long long)ng * wpn);
     const int i0 = ng * NPW;
     float h[NPW], m[NPW], v[NPW];
 #pragma unroll
     for (int k = 0; k < NPW; ++k) {
       h[k] = 0.f; m[k] = 0.f; v[k] = 0.f;
       if (i0 + k < a.n) {
-        const size_t idx = (size_t)(i0 + k) * a.R + (size_t)wb * 32 + lane;
+        const size_t idx = (size_t)(i0 + k) * R + (size_t)wb * 32 + lane;
         h[k] = a.h_in[idx];
         m[k] = a.m[idx];
         if (OPT != FEM_OPT_SGD) v[k] = a.v[idx];
@@ -143,7 +145,7 @@ __global__ void __launch_bounds__(256, 5) k_maxcut_step_paper(MaxcutArgs a, Step
       wv = 0.f;
       if (e < bN) {
         const uint32_t c = __ldg(a.col + e);
-        const uint32_t wd = __ldg(a.words_in + (size_t)(c & 0x7fffffffu) * a.wpn + wb);
+        const uint32_t wd = __ldg(a.words_in + (size_t)(c & 0x7fffffffu) * wpn + wb);
         if (UNIT) {
           adj = wd ^ (0u - (c >> 31));
         } else {
@@ -207,7 +209,7 @@ __global__ void __launch_bounds__(256, 5) k_maxcut_step_paper(MaxcutArgs a, Step
       opt_update_fast<OPT>(hk, mk, vk, gk, s);
       ball[k] = __ballot_sync(kFullMask, hk < 0.f);
       if (i0 + k < a.n) {
-        const size_t idx = (size_t)(i0 + k) * a.R + (size_t)wb * 32 + lane;
+        const size_t idx = (size_t)(i0 + k) * R + (size_t)wb * 32 + lane;
         a.h_out[idx] = hk;
         a.m[idx] = mk;
         if (OPT != FEM_OPT_SGD) a.v[idx] = vk;
@@ -216,7 +218,7 @@ __global__ void __launch_bounds__(256, 5) k_maxcut_step_paper(MaxcutArgs a, Step
     uint32_t mine = ball[0];
 #pragma unroll
     for (int k = 1; k < NPW; ++k) mine = lane == k ? ball[k] : mine;
-    if (lane < NPW && i0 + lane < a.n) a.words_out[(size_t)(i0 + lane) * a.wpn + wb] = mine;
+    if (lane < NPW && i0 + lane < a.n) a.words_out[(size_t)(i0 + lane) * wpn + wb] = mine;
   }
 }
 
@@ -496,6 +498,9 @@ void launch_step(const MaxcutArgs& a, const StepScalars& s, int sm_count, long l
     if (warps < kSmallGraphWarps) {
       constexpr auto k = k_maxcut_step_paper<OPT, UNIT, 1>;
       k<<<resident_grid<k>(sm_count, per_node), 256, 0, st>>>(a, s);
+    } else if (a.R == 32) {
+      constexpr auto k = k_maxcut_step_paper<OPT, UNIT, kNodesPerWarp, true>;
+      k<<<resident_grid<k>(sm_count, warps), 256, 0, st>>>(a, s);
     } else {
       constexpr auto k = k_maxcut_step_paper<OPT, UNIT, kNodesPerWarp>;
       k<<<resident_grid<k>(sm_count, warps), 256, 0, st>>>(a, s);

@@ -26,13 +26,14 @@ namespace {
 // compiled with only the registers it needs.  The four-replica paths wait on their
 // marginal gathers, so they are built for more resident blocks (5 and 4 per SM),
 // taking one and two occurrences at a time, which fits their registers without spills.
-template <int PATH>
+// RC: the replica count as a compile-time constant for the four-replica paths (0: run time).
+template <int PATH, int RC = 0>
 __global__ void __launch_bounds__(256, PATH == 1 ? 5 : (PATH == 2 ? 4 : 1)) k_sat_step(SatArgs a, StepScalars s) {
-  const long long total = (long long)a.n * a.R;
+  const long long total = (long long)a.n * (RC ? RC : a.R);
   if (PATH > 0) {
     for (long long e = ((long long)blockIdx.x * blockDim.x + threadIdx.x) * 4; e < total;
          e += (long long)gridDim.x * blockDim.x * 4)
-      sat_element_k3<PATH == 1 ? 1 : 2, PATH == 2>(a, s, e);
+      sat_element_k3<PATH == 1 ? 1 : 2, PATH == 2, RC>(a, s, e);
     return;
   }
   for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
@@ -191,9 +192,12 @@ fem_status sat_marginals(Problem* p, int t, cudaStream_t st) {
 }
 
 fem_status sat_steps(Problem* p, const std::vector<StepScalars>& sc, int t_begin, cudaStream_t st) {
-  static const SatStep kernels[3] = {k_sat_step<0>, k_sat_step<1>, k_sat_step<2>};
-  static int per_sm[3] = {0, 0, 0};
-  const int path = (p->oth && p->R % 4 == 0) ? (!p->pspin ? 1 : (p->pjo ? 2 : 0)) : 0;
+  // path 3: path 2 (3-spin terms) with R = 16 fixed at compile time.  The same form of
+  // path 1 (Max-3-SAT) spilled at its five resident blocks per SM and was slower.
+  static const SatStep kernels[4] = {k_sat_step<0>, k_sat_step<1>, k_sat_step<2>, k_sat_step<2, 16>};
+  static int per_sm[4] = {0, 0, 0, 0};
+  int path = (p->oth && p->R % 4 == 0) ? (!p->pspin ? 1 : (p->pjo ? 2 : 0)) : 0;
+  if (path == 2 && p->R == 16) path = 3;
   if (per_sm[path] == 0) {
     int b = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kernels[path], 256, 0) != cudaSuccess || b < 1) b = 1;

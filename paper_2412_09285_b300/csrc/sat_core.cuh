@@ -105,10 +105,12 @@ __device__ __forceinline__ float sat_factor(int lit, float p) {
   return fmaf((lit & 1) ? 1.f : -1.f, p, (lit & 1) ? 0.f : 1.f);  // negated literal: P, else 1 - P
 }
 
-template <int U, bool PSPIN>
+// RC: the replica count as a compile-time constant (0: a.R at run time).
+template <int U, bool PSPIN, int RC = 0>
 __device__ __forceinline__ void sat_element_k3(const SatArgs& a, const StepScalars& s, long long e) {
+  const int R = RC ? RC : a.R;
   int i, r;
-  split_element(e, a.R, i, r);
+  split_element(e, R, i, r);
   const bool sgd = a.opt == FEM_OPT_SGD;
   float4 h = ld_state<PSPIN>(a.h + e), m = ld_state<PSPIN>(a.m + e);
   float4 v = sgd ? make_float4(0.f, 0.f, 0.f, 0.f) : ld_state<PSPIN>(a.v + e);
@@ -127,8 +129,8 @@ __device__ __forceinline__ void sat_element_k3(const SatArgs& a, const StepScala
 #pragma unroll
     for (int u = 0; u < U; ++u) {
       if (o + u < oe) {
-        pa[u] = ld_f4(P + (size_t)(((uint32_t)ot[u].x & 0x7fffffffu) >> 1) * a.R);
-        pb[u] = ld_f4(P + (size_t)((uint32_t)ot[u].y >> 1) * a.R);
+        pa[u] = ld_f4(P + (size_t)(((uint32_t)ot[u].x & 0x7fffffffu) >> 1) * R);
+        pb[u] = ld_f4(P + (size_t)((uint32_t)ot[u].y >> 1) * R);
       }
     }
 #pragma unroll

@@ -495,7 +495,10 @@ void launch_step(const MaxcutArgs& a, const StepScalars& s, int sm_count, long l
                  cudaStream_t st) {
   const long long per_node = (long long)a.n * a.wpn;
   if (MODE == FEM_GRAD_PAPER) {
-    if (warps < kSmallGraphWarps) {
+    if (warps < kSmallGraphWarps && a.R == 32) {
+      constexpr auto k = k_maxcut_step_paper<OPT, UNIT, 1, true>;
+      k<<<resident_grid<k>(sm_count, per_node), 256, 0, st>>>(a, s);
+    } else if (warps < kSmallGraphWarps) {
       constexpr auto k = k_maxcut_step_paper<OPT, UNIT, 1>;
       k<<<resident_grid<k>(sm_count, per_node), 256, 0, st>>>(a, s);
     } else if (a.R == 32) {

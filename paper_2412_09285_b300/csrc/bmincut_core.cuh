@@ -241,7 +241,9 @@ __device__ __forceinline__ void bmincut_element(const BmcArgs& a, const StepScal
       }
 #pragma unroll
       for (int q = 0; q < Q; ++q) acc[q] = (float)c8[q];
-    } else if (act) {
+    } else if (MODE == FEM_GRAD_EXACT || act) {
+      // in exact mode every lane takes this branch (its sums shuffle within the warp); an
+      // inactive lane has beg == end, so its loops add nothing
       if (MODE == FEM_GRAD_PAPER) {
         if (!a.w && end - beg < (Q <= 4 ? 65536 : 256)) {
           // unit weights: integer counts packed 16 (q <= 4) or 8 bits wide in one word,
@@ -268,34 +270,83 @@ __device__ __forceinline__ void bmincut_element(const BmcArgs& a, const StepScal
         // accumulate sum_j W_ij (P_j(s) - 1/q): the constant drops out of every
         // difference below.  Each neighbour's q (P_j(s) - 1/q) (centred_q) was written
         // by the step that produced h_j, once per node rather than once per edge.
-        // G neighbours at a time: their column loads, then their gathers, then the sums
-        // in neighbour order (the same arithmetic as one at a time), so a thread waits
-        // for two memory round trips per G neighbours instead of two per neighbour
+        // G neighbours at a time: their gathers, then the sums in neighbour order (the
+        // same arithmetic as one at a time).  When a node's replicas fill aligned groups
+        // of lanes (R = 16: half a warp; R a multiple of 32: whole warps), its lanes load
+        // the node's column indices (and weights) with one coalesced load per group of
+        // entries and pass them on by shuffles, so a thread waits for one memory round
+        // trip per G neighbours; otherwise each thread loads them itself (two).
         constexpr int G = Q <= 4 ? 4 : 2;
-        for (int k0 = beg; k0 < end; k0 += G) {
-          uint32_t jj[G];
-          float wkk[G];
+        if (R == 16 || R % 32 == 0) {
+          const int L = R == 16 ? 16 : 32;  // lanes per node
+          const int sub = lane & (L - 1), gbase = lane & ~(L - 1);
+          const int deg = end - beg;
+          // the loops run to the larger degree of the warp's nodes, so that every lane
+          // takes part in the shuffles (the lanes of one node share deg)
+          const int maxdeg = L == 16 ? max(deg, __shfl_xor_sync(kFullMask, deg, 16)) : deg;
+          for (int c0 = 0; c0 < maxdeg; c0 += L) {
+            const int kk = c0 + sub;
+            const bool have = kk < deg;
+            const uint32_t myc = have ? (a.col[beg + kk] & 0x7fffffffu) : 0u;
+            const float myw = have && a.w ? a.w[beg + kk] : 1.f;
+            const int cnt = min(maxdeg - c0, L);
+            for (int k0 = 0; k0 < cnt; k0 += G) {
+              uint32_t jj[G];
+              float wkk[G];
+              bool okk[G];
 #pragma unroll
-          for (int u = 0; u < G; ++u) {
-            const bool ok = k0 + u < end;
-            jj[u] = ok ? (a.col[k0 + u] & 0x7fffffffu) : 0u;
-            wkk[u] = ok && a.w ? a.w[k0 + u] : 1.f;
-          }
-          float dj[G][Q];
+              for (int u = 0; u < G; ++u) {
+                const int e = k0 + u;
+                okk[u] = e < L && c0 + e < deg;
+                const int src = gbase + (e < L ? e : L - 1);
+                jj[u] = __shfl_sync(kFullMask, myc, src);
+                wkk[u] = __shfl_sync(kFullMask, myw, src);
+              }
+              float dj[G][Q];
 #pragma unroll
-          for (int u = 0; u < G; ++u) {
-            if (k0 + u < end) {
-              load_q<Q>(a.d_in + ((size_t)jj[u] * R + r) * Q, dj[u]);
-            } else {
+              for (int u = 0; u < G; ++u) {
+                if (okk[u]) {
+                  load_q<Q>(a.d_in + ((size_t)jj[u] * R + r) * Q, dj[u]);
+                } else {
 #pragma unroll
-              for (int q = 0; q < Q; ++q) dj[u][q] = 0.f;
+                  for (int q = 0; q < Q; ++q) dj[u][q] = 0.f;
+                }
+              }
+#pragma unroll
+              for (int u = 0; u < G; ++u) {
+                if (okk[u]) {
+#pragma unroll
+                  for (int q = 0; q < Q; ++q) acc[q] = fmaf(wkk[u], dj[u][q] * (1.f / Q), acc[q]);
+                }
+              }
             }
           }
+        } else {
+          for (int k0 = beg; k0 < end; k0 += G) {
+            uint32_t jj[G];
+            float wkk[G];
 #pragma unroll
-          for (int u = 0; u < G; ++u) {
-            if (k0 + u < end) {
+            for (int u = 0; u < G; ++u) {
+              const bool ok = k0 + u < end;
+              jj[u] = ok ? (a.col[k0 + u] & 0x7fffffffu) : 0u;
+              wkk[u] = ok && a.w ? a.w[k0 + u] : 1.f;
+            }
+            float dj[G][Q];
 #pragma unroll
-              for (int q = 0; q < Q; ++q) acc[q] = fmaf(wkk[u], dj[u][q] * (1.f / Q), acc[q]);
+            for (int u = 0; u < G; ++u) {
+              if (k0 + u < end) {
+                load_q<Q>(a.d_in + ((size_t)jj[u] * R + r) * Q, dj[u]);
+              } else {
+#pragma unroll
+                for (int q = 0; q < Q; ++q) dj[u][q] = 0.f;
+              }
+            }
+#pragma unroll
+            for (int u = 0; u < G; ++u) {
+              if (k0 + u < end) {
+#pragma unroll
+                for (int q = 0; q < Q; ++q) acc[q] = fmaf(wkk[u], dj[u][q] * (1.f / Q), acc[q]);
+              }
             }
           }
         }

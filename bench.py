@@ -423,9 +423,9 @@ def _roofline(wl, inst, step_ms, precision, dense_launch=None, grad_mode="paper"
         # row_ptr, the sign words read once and written once (4 B per node per 32 replicas)
         alg = sb * n * R + 4 * nnz + 4 * (n + 1) + 8 * n * (R // 32)
         ach = alg / (step_ms / 1e3) / 1e9
-        # the staged tile kernel runs graphs of >= 4096 groups of four nodes (not with SGD)
+        # the staged tile kernel runs graphs of >= 4096 groups of four nodes
         groups4 = (n + 3) // 4
-        tile = opt != "sgd" and groups4 >= 4096
+        tile = groups4 >= 4096
         kernel = (f"k_paper_tile<{opt}, unit>" if tile
                   else f"k_maxcut_step_paper<{opt}, unit, {4 if groups4 >= 4096 else 1}>")
         return {"bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",

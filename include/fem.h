@@ -418,7 +418,7 @@ void fem_set_device_graph_build(int64_t min_edges);
 
 /* Which kernels run the sparse MaxCut and QUBO steps: on (the default) the tile kernels
  * that stage their operands in shared memory ahead of use - exact mode with TMA gather4
- * copies of the neighbours' lines, paper mode (Adam and RMSprop, graphs of at least
+ * copies of the neighbours' lines, paper mode (unit or +-1 weights, graphs of at least
  * 4096 groups of four nodes) with bulk copies of the state and sign words gathered by a
  * producer warp - off the kernels that load everything directly.  Both compute the same
  * sums in the same order and give the same bits.  Process-wide. */

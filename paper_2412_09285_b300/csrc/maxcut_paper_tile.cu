@@ -99,15 +99,16 @@ __device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t b
                : "memory");
 }
 
-// Resident blocks per SM the registers are budgeted for: seven with Adam (measured faster
-// than six), six with RMSprop and SGD (seven spill there), five with weights.
-template <int OPT, bool UNIT>
-constexpr int tile_blocks() { return !UNIT ? 5 : (OPT == FEM_OPT_ADAM ? 7 : 6); }
+// Resident blocks per SM the registers are budgeted for: seven with unit weights (measured
+// faster than six and eight), six for SGD in the run-time replica form (seven spill there),
+// five with weights.
+template <int OPT, bool UNIT, bool R32>
+constexpr int tile_blocks() { return !UNIT ? 5 : (OPT == FEM_OPT_SGD && !R32 ? 6 : 7); }
 
 // R32: the replica count is 32 (one sign word per node), a compile-time constant, so the
 // state rows' offsets are immediates.
 template <int OPT, bool UNIT, bool R32>
-__global__ void __launch_bounds__(kThreads, tile_blocks<OPT, UNIT>()) k_paper_tile(PArgs a, StepScalars s) {
+__global__ void __launch_bounds__(kThreads, tile_blocks<OPT, UNIT, R32>()) k_paper_tile(PArgs a, StepScalars s) {
   const int R = R32 ? 32 : a.R, wpn = R32 ? 1 : a.wpn;
   __shared__ __align__(128) Stage st[kStages];
   __shared__ __align__(8) uint64_t full[kStages], empty[kStages];

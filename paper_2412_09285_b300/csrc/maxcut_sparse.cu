@@ -565,10 +565,8 @@ fem_status maxcut_sparse_steps(Problem* p, const fem_anneal_params& a,
   args.v = p->v;
   args.ccoef = p->qubo ? 1.f : 2.f;
   args.offset = p->qubo ? p->qoff : nullptr;
-  if (p->grad_mode == FEM_GRAD_PAPER && tma_gather_enabled() && groups >= kSmallGraphWarps &&
-      p->optimizer != FEM_OPT_SGD) {
-    // the staged tile kernel (maxcut_paper_tile.cu): the same arithmetic and bits.  With
-    // SGD (two state lines per node instead of three) the direct kernel is faster.
+  if (p->grad_mode == FEM_GRAD_PAPER && tma_gather_enabled() && groups >= kSmallGraphWarps) {
+    // the staged tile kernel (maxcut_paper_tile.cu): the same arithmetic and bits
     for (size_t k = 0; k < sc.size(); ++k) {
       const fem_status st = maxcut_paper_tile_step(p, p->cur, sc[k], s);
       if (st != FEM_OK) return st;

@@ -156,11 +156,13 @@ __device__ void run_sat_item(const BatchMember& b, const BatchItem& it, const St
 
 // The q-state members' step: blocks walk their items (the first n_items of the list).
 // Q and MODE are shared by all of them; s carries the q-state gradient scale (gamma).  RC: the
-// members' replica count as a compile-time constant (0: run time).
+// members' replica count as a compile-time constant (0: run time).  Resident blocks per SM:
+// five for paper mode with q <= 4 at R = 16 (measured faster than four), three for q >= 7,
+// else four.
 template <int Q, int MODE, int RC = 0>
-__global__ void __launch_bounds__(256, Q >= 7 ? 3 : 4) k_batch_bmincut(const BatchMember* __restrict__ members,
-                                                       const BatchItem* __restrict__ items, int32_t n_items,
-                                                       int32_t max_rq, StepScalars s, int32_t t) {
+__global__ void __launch_bounds__(256, Q >= 7 ? 3 : ((Q <= 4 && MODE == FEM_GRAD_PAPER && RC == 16) ? 5 : 4))
+    k_batch_bmincut(const BatchMember* __restrict__ members, const BatchItem* __restrict__ items, int32_t n_items,
+                    int32_t max_rq, StepScalars s, int32_t t) {
   extern __shared__ unsigned long long smem_b[];
   unsigned long long* sps = smem_b;
   int32_t* scnt = reinterpret_cast<int32_t*>(smem_b + (MODE == FEM_GRAD_EXACT ? max_rq : 0));

@@ -24,11 +24,12 @@ namespace {
 // PATH: 0 the per-element update (any clause widths, any R); 1 Max-3-SAT and 2 3-spin
 // terms with four replicas per thread (R % 4 == 0).  One kernel per path, so each is
 // compiled with only the registers it needs.  The four-replica paths wait on their
-// marginal gathers, so they are built for more resident blocks (5 and 4 per SM),
-// taking one and two occurrences at a time, which fits their registers without spills.
+// marginal gathers, so they are built for more resident blocks (5 and 4 per SM; 5 for
+// 3-spin terms in the R = 16 form, whose registers allow it), taking one and two
+// occurrences at a time, which fits their registers without spills.
 // RC: the replica count as a compile-time constant for the four-replica paths (0: run time).
 template <int PATH, int RC = 0>
-__global__ void __launch_bounds__(256, PATH == 1 ? 5 : (PATH == 2 ? 4 : 1)) k_sat_step(SatArgs a, StepScalars s) {
+__global__ void __launch_bounds__(256, PATH == 1 ? 5 : (PATH == 2 ? (RC ? 5 : 4) : 1)) k_sat_step(SatArgs a, StepScalars s) {
   const long long total = (long long)a.n * (RC ? RC : a.R);
   if (PATH > 0) {
     for (long long e = ((long long)blockIdx.x * blockDim.x + threadIdx.x) * 4; e < total;

@@ -26,16 +26,17 @@
 namespace fem {
 namespace {
 
-// Resident blocks per SM the registers are budgeted for: five for paper mode with
-// q <= 4 (measured faster than four), three for q >= 7, else four (more would spill).
-template <int Q, int MODE>
-constexpr int bmincut_blocks() { return Q >= 7 ? 3 : ((Q <= 4 && MODE == FEM_GRAD_PAPER) ? 5 : 4); }
+// Resident blocks per SM the registers are budgeted for: paper mode with q <= 4 six in the
+// R = 16 form and five otherwise (each measured faster than one block fewer), three for
+// q >= 7, else four (more would spill).
+template <int Q, int MODE, int RC>
+constexpr int bmincut_blocks() { return Q >= 7 ? 3 : ((Q <= 4 && MODE == FEM_GRAD_PAPER) ? (RC == 16 ? 6 : 5) : 4); }
 
 // One thread per (node, replica); a warp covers 32 consecutive (node, replica)
 // pairs, so R % RPW == 0 keeps every packed word inside one group of lanes.
 // RC: the replica count as a compile-time constant (0: run time).
 template <int Q, int MODE, int RC = 0>
-__global__ void __launch_bounds__(256, bmincut_blocks<Q, MODE>()) k_bmincut_step(BmcArgs a, StepScalars s) {
+__global__ void __launch_bounds__(256, bmincut_blocks<Q, MODE, RC>()) k_bmincut_step(BmcArgs a, StepScalars s) {
   extern __shared__ unsigned long long smem_u64[];
   const int R = RC ? RC : a.R;
   const int RQ = R * Q;

@@ -272,6 +272,8 @@ __global__ void __launch_bounds__(kThreads, 4) k_exact_gather(const __grid_const
         const int beg = S.rptr[j], end = S.rptr[j + 1];
         float facc = 0.f;
         const int e1 = min(end, kCap);
+        // unrolled (the sums stay in entry order): less loop overhead per staged row
+#pragma unroll 4
         for (int k = beg; k < e1; ++k) {
           const float mj = S.rows[32 * k + lane];
           if (UNIT) facc += (S.col[k] >> 31) ? -mj : mj;

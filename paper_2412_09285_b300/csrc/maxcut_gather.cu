@@ -120,8 +120,9 @@ __device__ __forceinline__ void gather4(void* dst, const CUtensorMap* tm, int x,
 }
 
 // R32: the replica count is 32 (one block of replicas per node), a compile-time constant, so
-// the state rows' offsets are immediates.
-template <int OPT, bool UNIT, bool R32>
+// the state rows' offsets are immediates.  OFF: QUBO's per-node constants of the field are
+// staged and added (MaxCut instantiations carry neither the loads nor the registers).
+template <int OPT, bool UNIT, bool R32, bool OFF>
 __global__ void __launch_bounds__(kThreads, 4) k_exact_gather(const __grid_constant__ CUtensorMap tm_mag, GatherArgs a,
                                                               StepScalars s) {
   const int R = R32 ? 32 : a.R, wpn = R32 ? 1 : a.wpn;
@@ -157,7 +158,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_exact_gather(const __grid_const
     };
     auto load_cols = [&](long long t, int rp, int rl, uint32_t (&c)[kQ], float (&w)[kQ], float& of) {
       if (t >= tiles) return;
-      if (a.offset) of = __ldg(a.offset + min(first_node(t) + lane, a.n - 1));
+      if (OFF) of = __ldg(a.offset + min(first_node(t) + lane, a.n - 1));
       const int base = __shfl_sync(kFullMask, rp, 0), ecap = min(rl - base, kCap);
 #pragma unroll
       for (int q = 0; q < kQ; ++q) {
@@ -193,7 +194,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_exact_gather(const __grid_const
       const int base = __shfl_sync(kFullMask, rp1, 0);
       if (lane < kNodes) {
         S.rptr[lane] = rp1 - base;
-        S.off[lane] = of1;
+        if (OFF) S.off[lane] = of1;
       }
       if (lane == 0) {
         S.rptr[kNodes] = rl1 - base;
@@ -288,8 +289,10 @@ __global__ void __launch_bounds__(kThreads, 4) k_exact_gather(const __grid_const
         float hi = S.h[32 * j + lane], mi = S.m[32 * j + lane];
         float vi = OPT == FEM_OPT_SGD ? 0.f : S.v[32 * j + lane];
         float field = a.ccoef * facc;
-        if (a.offset) field += S.off[j];
-        const float g = s.gq * (field + hi * s.inv_beta) * one_minus_m2_fast(hi);
+        if (OFF) field += S.off[j];
+        // field + h/beta as one explicit fma, so that the direct and the tile kernel round it
+        // alike however the compiler contracts the code around it
+        const float g = s.gq * fmaf(hi, s.inv_beta, field) * one_minus_m2_fast(hi);
         opt_update_fast<OPT>(hi, mi, vi, g, s);
         const size_t idx = (size_t)i * R + (size_t)wb * 32 + lane;
         a.h_out[idx] = hi;
@@ -340,9 +343,9 @@ fem_status mag_map(CUtensorMap* m, const float* base, int32_t n, int32_t R) {
   return FEM_OK;
 }
 
-template <int OPT, bool UNIT, bool R32>
+template <int OPT, bool UNIT, bool R32, bool OFF>
 fem_status launch(const CUtensorMap& tm, const GatherArgs& a, const StepScalars& s, int sm_count, cudaStream_t st) {
-  constexpr auto k = k_exact_gather<OPT, UNIT, R32>;
+  constexpr auto k = k_exact_gather<OPT, UNIT, R32, OFF>;
   static int grid_per_sm = 0;
   const size_t smem = kStages * sizeof(Stage) + 1024;
   if (grid_per_sm == 0) {
@@ -360,6 +363,20 @@ fem_status launch(const CUtensorMap& tm, const GatherArgs& a, const StepScalars&
   if (grid > tiles) grid = tiles;
   k<<<(int)(grid < 1 ? 1 : grid), kThreads, smem, st>>>(tm, a, s);
   return FEM_OK;
+}
+
+template <bool R32, bool OFF>
+fem_status dispatch(const Problem* p, const CUtensorMap& tm, const GatherArgs& a, const StepScalars& s,
+                    cudaStream_t st) {
+  const bool unit = p->unit_w;
+  switch (p->optimizer) {
+    case FEM_OPT_ADAM: return unit ? launch<FEM_OPT_ADAM, true, R32, OFF>(tm, a, s, p->sm_count, st)
+                                   : launch<FEM_OPT_ADAM, false, R32, OFF>(tm, a, s, p->sm_count, st);
+    case FEM_OPT_RMSPROP: return unit ? launch<FEM_OPT_RMSPROP, true, R32, OFF>(tm, a, s, p->sm_count, st)
+                                      : launch<FEM_OPT_RMSPROP, false, R32, OFF>(tm, a, s, p->sm_count, st);
+    default: return unit ? launch<FEM_OPT_SGD, true, R32, OFF>(tm, a, s, p->sm_count, st)
+                         : launch<FEM_OPT_SGD, false, R32, OFF>(tm, a, s, p->sm_count, st);
+  }
 }
 
 }  // namespace
@@ -393,30 +410,11 @@ fem_status maxcut_exact_gather_step(Problem* p, int in, const StepScalars& s, cu
   a.offset = p->qubo ? p->qoff : nullptr;
   a.err = p->err;
   const CUtensorMap& tm = p->tmap_mag[in];
-  fem_status r;
-  const bool unit = p->unit_w;
-  // R = 32 runs the compile-time form, except for QUBO problems (their per-node offsets),
-  // which measured faster in the run-time form (0.3065 against 0.3172 ms at n = 2^20)
-  if (p->R == 32 && !p->qubo) {
-    switch (p->optimizer) {
-      case FEM_OPT_ADAM: r = unit ? launch<FEM_OPT_ADAM, true, true>(tm, a, s, p->sm_count, st)
-                                  : launch<FEM_OPT_ADAM, false, true>(tm, a, s, p->sm_count, st); break;
-      case FEM_OPT_RMSPROP: r = unit ? launch<FEM_OPT_RMSPROP, true, true>(tm, a, s, p->sm_count, st)
-                                     : launch<FEM_OPT_RMSPROP, false, true>(tm, a, s, p->sm_count, st); break;
-      default: r = unit ? launch<FEM_OPT_SGD, true, true>(tm, a, s, p->sm_count, st)
-                        : launch<FEM_OPT_SGD, false, true>(tm, a, s, p->sm_count, st); break;
-    }
-    return r;
-  }
-  switch (p->optimizer) {
-    case FEM_OPT_ADAM: r = unit ? launch<FEM_OPT_ADAM, true, false>(tm, a, s, p->sm_count, st)
-                                : launch<FEM_OPT_ADAM, false, false>(tm, a, s, p->sm_count, st); break;
-    case FEM_OPT_RMSPROP: r = unit ? launch<FEM_OPT_RMSPROP, true, false>(tm, a, s, p->sm_count, st)
-                                   : launch<FEM_OPT_RMSPROP, false, false>(tm, a, s, p->sm_count, st); break;
-    default: r = unit ? launch<FEM_OPT_SGD, true, false>(tm, a, s, p->sm_count, st)
-                      : launch<FEM_OPT_SGD, false, false>(tm, a, s, p->sm_count, st); break;
-  }
-  return r;
+  // R = 32 runs the compile-time replica form, except for QUBO problems (per-node offsets),
+  // which measured faster in the run-time form (n = 2^20: 0.3133 ms in the R = 32 form
+  // with its offsets at compile time, 0.2983 ms in the run-time form)
+  if (p->qubo) return dispatch<false, true>(p, tm, a, s, st);
+  return p->R == 32 ? dispatch<true, false>(p, tm, a, s, st) : dispatch<false, false>(p, tm, a, s, st);
 }
 
 }  // namespace fem

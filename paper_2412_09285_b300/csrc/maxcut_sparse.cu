@@ -82,7 +82,9 @@ __global__ void __launch_bounds__(256) k_maxcut_step(MaxcutArgs a, StepScalars s
     // sum_j Q_ij m_j + (sum_j Q_ij + d_i)
     float field = a.ccoef * facc;
     if (a.offset) field += a.offset[i];
-    const float g = s.gq * (field + hi * s.inv_beta) * one_minus_m2_fast(hi);
+    // field + h/beta as one explicit fma, so that the direct and the tile kernel round it
+    // alike however the compiler contracts the code around it
+    const float g = s.gq * fmaf(hi, s.inv_beta, field) * one_minus_m2_fast(hi);
     opt_update_fast<OPT>(hi, mi, vi, g, s);
     a.h_out[idx] = hi;
     a.m[idx] = mi;

@@ -34,9 +34,12 @@ constexpr int bmincut_blocks() { return Q >= 7 ? 3 : ((Q <= 4 && MODE == FEM_GRA
 
 // One thread per (node, replica); a warp covers 32 consecutive (node, replica)
 // pairs, so R % RPW == 0 keeps every packed word inside one group of lanes.
-// RC: the replica count as a compile-time constant (0: run time).
-template <int Q, int MODE, int RC = 0>
-__global__ void __launch_bounds__(256, bmincut_blocks<Q, MODE, RC>()) k_bmincut_step(BmcArgs a, StepScalars s) {
+// RC: the replica count as a compile-time constant (0: run time).  OPTC: the optimizer as a
+// compile-time constant (-1: run time); the element code then holds one update, not three.
+template <int Q, int MODE, int RC = 0, int OPTC = -1>
+__global__ void __launch_bounds__(256, bmincut_blocks<Q, MODE, RC>()) k_bmincut_step(BmcArgs args, StepScalars s) {
+  BmcArgs a = args;
+  if (OPTC >= 0) a.opt = OPTC;
   extern __shared__ unsigned long long smem_u64[];
   const int R = RC ? RC : a.R;
   const int RQ = R * Q;
@@ -275,8 +278,12 @@ fem_status steps_q(Problem* p, const std::vector<StepScalars>& sc, int t_begin, 
   // R = 16 (with its one or two packed words per node) runs an instantiation with the
   // replica count fixed at compile time
   const bool r16 = p->R == 16 && p->words_per_node == 16 * QBits<Q>::B / 32;
-  auto kern = exact ? (r16 ? k_bmincut_step<Q, FEM_GRAD_EXACT, 16> : k_bmincut_step<Q, FEM_GRAD_EXACT>)
-                    : (r16 ? k_bmincut_step<Q, FEM_GRAD_PAPER, 16> : k_bmincut_step<Q, FEM_GRAD_PAPER>);
+  // ... and, with Adam (the default), the optimizer too
+  const bool adam = p->optimizer == FEM_OPT_ADAM;
+  auto kern = exact ? (r16 ? (adam ? k_bmincut_step<Q, FEM_GRAD_EXACT, 16, FEM_OPT_ADAM> : k_bmincut_step<Q, FEM_GRAD_EXACT, 16>)
+                           : k_bmincut_step<Q, FEM_GRAD_EXACT>)
+                    : (r16 ? (adam ? k_bmincut_step<Q, FEM_GRAD_PAPER, 16, FEM_OPT_ADAM> : k_bmincut_step<Q, FEM_GRAD_PAPER, 16>)
+                           : k_bmincut_step<Q, FEM_GRAD_PAPER>);
   if (smem > 48 * 1024) FEM_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   const int grid = resident_grid(kern, p->sm_count, (long long)p->n * p->R, smem);
   for (size_t k = 0; k < sc.size(); ++k) {
